@@ -1,0 +1,230 @@
+/*
+ * fw.h -- C ABI of the GB300 first-match packet classifier.
+ *
+ * The operation (Sec. I and Sec. IV of "Parallel Firewalls on General-Purpose
+ * Graphics Processing Units"): every packet is compared with an ordered rule
+ * list; the first rule that matches decides its action, and a packet that no
+ * rule matches is dropped (iptables first-match with default deny, Sec. I).
+ * A rule is a 5-tuple -- source and destination address, source and
+ * destination port, protocol -- plus an action, and a field that a rule does
+ * not specify matches every value (Sec. IV). Two decompositions are offered
+ * (Sec. IV.A data-parallel: packets split across workers, each holding the
+ * whole rule list; Sec. IV.B/C function-parallel and hybrid: the rule list
+ * split across workers, combined per packet by taking the smallest matching
+ * rule index).
+ *
+ * Conventions for every entry point:
+ *  - Integers are host byte order. Addresses are uint32, ports uint16,
+ *    protocol uint8.
+ *  - Device pointers are plain CUDA device (or managed) addresses on the
+ *    current device; host pointers are ordinary host memory (pinned memory
+ *    is faster where noted). No entry point takes ownership of a caller
+ *    buffer.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). Device-pointer calls are asynchronous with respect to the host:
+ *    they enqueue work on `stream` and return; buffers must stay valid until
+ *    that work completes.
+ *  - Every call that can fail returns an int status: FW_OK (0) or a negative
+ *    FW_E* code; nothing is thrown across the ABI. Argument errors are
+ *    detected on the host before any work is enqueued.
+ *  - There is no CPU fallback: all classification runs in CUDA kernels.
+ */
+#ifndef FW_H_
+#define FW_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define FW_OK        0
+#define FW_EINVAL   (-1)  /* bad argument: null pointer, negative size, prefix > 32, lo > hi, bad action/mode */
+#define FW_ENOMEM   (-2)  /* device or pinned host allocation failed */
+#define FW_ECUDA    (-3)  /* a CUDA runtime call or kernel launch failed */
+#define FW_EALIGN   (-4)  /* a buffer is not aligned as the call requires */
+#define FW_ETIMEOUT (-5)  /* a bounded device-side wait gave up (see fw_ruleset_check) */
+#define FW_EBUSY    (-6)  /* the object cannot take more work now (serving admission) */
+#define FW_ERANGE   (-7)  /* a size exceeds a fixed limit of the call */
+
+/* ------------------------------------------------------------------ actions */
+#define FW_DROP   0
+#define FW_ACCEPT 1
+
+/*
+ * One rule as the caller supplies it (24 bytes, Sec. IV 5-tuple + action).
+ *  src_addr/dst_addr + src_prefix/dst_prefix: the rule matches addresses whose
+ *      top `prefix` bits equal those of the rule's address; prefix 0 matches
+ *      every address; bits below the prefix are ignored. prefix must be <= 32.
+ *  sport_lo..sport_hi, dport_lo..dport_hi: inclusive port ranges; lo <= hi;
+ *      [0, 65535] is the wildcard, [p, p] an exact port.
+ *  proto, proto_any: proto_any != 0 matches every protocol, otherwise only
+ *      `proto` (protocol 0 is an ordinary value).
+ *  action: FW_DROP or FW_ACCEPT.
+ */
+typedef struct fw_rule {
+    uint32_t src_addr;
+    uint32_t dst_addr;
+    uint16_t sport_lo, sport_hi;
+    uint16_t dport_lo, dport_hi;
+    uint8_t  src_prefix, dst_prefix;
+    uint8_t  proto, proto_any;
+    uint8_t  action;
+    uint8_t  reserved[3];          /* must be zero */
+} fw_rule;
+
+/*
+ * A batch of n packet headers, structure of arrays, one element per packet.
+ * For the fastest path src/dst should be 16-byte aligned, sport/dport 8-byte
+ * and proto 4-byte aligned; other alignments are accepted and take a scalar
+ * load path.
+ */
+typedef struct fw_headers {
+    const uint32_t *src;
+    const uint32_t *dst;
+    const uint16_t *sport;
+    const uint16_t *dport;
+    const uint8_t  *proto;
+} fw_headers;
+
+/* Decomposition selector for fw_classify_ex. */
+#define FW_MODE_AUTO             0  /* library picks (packet split unless configured otherwise) */
+#define FW_MODE_PACKET_SPLIT     1  /* Sec. IV.A: one thread per packet walks the whole list */
+#define FW_MODE_RULE_SPLIT_WARP  2  /* Sec. IV.B/C at warp scale: lanes split 32-rule chunks, ballot picks the first */
+#define FW_MODE_RULE_SPLIT_BLOCK 3  /* Sec. IV.C hybrid: a block per packet group, its warps split the rules, block min */
+#define FW_MODE_RULE_SPLIT_GRID  4  /* Sec. IV.B: rule slices across blocks, global atomic-min combine */
+
+/* Encodings of the field tests (fw_config.predicate); both give identical results. */
+#define FW_PRED_CLAMP 1  /* port ranges as a 16x2 clamp, proto under a mask */
+#define FW_PRED_CMP   2  /* port ranges as unsigned subtract-and-compare */
+
+/*
+ * Launch configuration. Zero in any field means "library default".
+ *  mode:              one of FW_MODE_*.
+ *  block_threads:     threads per block (multiple of 32, <= 1024).
+ *  blocks_per_sm:     resident blocks per SM for persistent launches.
+ *  smem_rules:        rules kept resident in shared memory (packet split).
+ *  packets_per_group: packets handled together by one warp/block (rule split).
+ *  rule_slices:       number of rule slices across the grid (RULE_SPLIT_GRID).
+ *  compact:           packet split only: 1 = re-pack unresolved packets between
+ *                     rule segments, 2 = do not (plain lockstep scan).
+ *  predicate:         0 default, FW_PRED_CLAMP or FW_PRED_CMP.
+ */
+typedef struct fw_config {
+    int32_t mode;
+    int32_t block_threads;
+    int32_t blocks_per_sm;
+    int32_t smem_rules;
+    int32_t packets_per_group;
+    int32_t rule_slices;
+    int32_t compact;
+    int32_t predicate;
+    int32_t reserved[8];           /* must be zero */
+} fw_config;
+
+typedef struct fw_ruleset fw_ruleset;
+
+/* ------------------------------------------------------------ rule sets */
+/*
+ * Validate, canonicalise (mask addresses, encode wildcards) and copy `n`
+ * rules (host array, list order = priority) to device memory on the current
+ * device. n may be 0 (every packet is then unmatched). The caller keeps
+ * ownership of `rules` and may free it on return. On success *out receives
+ * a handle owned by the caller until fw_ruleset_destroy.
+ * Errors: FW_EINVAL (null out, n < 0, rules == NULL with n > 0, prefix > 32,
+ * lo > hi, action not DROP/ACCEPT, reserved bytes non-zero, n > 2^31-2),
+ * FW_ENOMEM, FW_ECUDA. Synchronous.
+ */
+int fw_ruleset_create_ex(const fw_rule *rules, int64_t n, fw_ruleset **out);
+
+/* Short form: returns the handle, or NULL with the status in fw_last_status(). */
+fw_ruleset *fw_ruleset_create(const fw_rule *rules, int64_t n);
+
+/*
+ * Free a rule set. No work that uses `rs` may still be in flight (synchronise
+ * its streams first). NULL is ignored.
+ */
+void fw_ruleset_destroy(fw_ruleset *rs);
+
+/* Number of rules, and the index of the first rule that matches every packet (-1 if none). */
+int64_t fw_ruleset_size(const fw_ruleset *rs);
+int64_t fw_ruleset_first_catch_all(const fw_ruleset *rs);
+
+/*
+ * Synchronise the device and report whether any kernel that used `rs` gave
+ * up on a bounded wait since the last check (FW_ETIMEOUT; the flag is then
+ * cleared) or a CUDA error is pending (FW_ECUDA).
+ */
+int fw_ruleset_check(fw_ruleset *rs);
+
+/* ------------------------------------------------------------ classify */
+/*
+ * Classify n packets (device SoA `hdrs`) against `rs`:
+ *   out_rule_idx[i] = smallest k whose rule matches packet i, or -1;
+ *   out_action[i]   = action of that rule, or FW_DROP when out_rule_idx[i] = -1.
+ * out_rule_idx (int32[n]) and out_action (uint8[n]) are caller-owned device
+ * buffers. n = 0 is a no-op. Asynchronous on `stream`; no allocation.
+ * Errors: FW_EINVAL (null handle/pointer with n > 0, n < 0, n > 2^31-1), FW_ECUDA.
+ */
+int fw_classify(const fw_ruleset *rs, const fw_headers *hdrs, int64_t n,
+                int32_t *out_rule_idx, uint8_t *out_action, void *stream);
+
+/*
+ * As fw_classify with an explicit decomposition / launch configuration
+ * (cfg may be NULL for defaults). FW_MODE_RULE_SPLIT_GRID takes a stream-
+ * ordered scratch allocation of one int32 per packet for the partial minima.
+ */
+int fw_classify_ex(const fw_ruleset *rs, const fw_headers *hdrs, int64_t n,
+                   int32_t *out_rule_idx, uint8_t *out_action, void *stream,
+                   const fw_config *cfg);
+
+/* ------------------------------------------------------------ host buffers */
+/*
+ * Host-ingress path: classify packets whose headers live in HOST memory and
+ * return verdicts to host memory. It stands in for the paper's loop of
+ * accumulating a batch, copying it to the device, launching and copying the
+ * verdict array back (Sec. IV.A/IV.C; Fig. 1 queue and reinject), without a
+ * kernel module.
+ *
+ * A pipeline owns its streams and per-stream device staging buffers of
+ * `chunk_packets` packets (0 = 4,194,304). Strategies:
+ *   FW_HOST_COPY:     chunks are copied H2D, classified and copied D2H on
+ *                     `n_streams` streams (1..8, 0 = 3) so copies of one chunk
+ *                     overlap the scan of another. Pinned host buffers are
+ *                     needed for the overlap; pageable ones work but serialise.
+ *   FW_HOST_ZEROCOPY: the kernels read the headers from, and write verdicts
+ *                     to, pinned host memory directly (mapped pages over the
+ *                     host link); every buffer must be pinned (page-locked by
+ *                     cudaHostAlloc / cudaHostRegister), else FW_EINVAL.
+ * fw_classify_host is synchronous: on return the verdicts are in host memory.
+ */
+#define FW_HOST_COPY     1
+#define FW_HOST_ZEROCOPY 2
+
+typedef struct fw_host_pipeline fw_host_pipeline;
+
+int fw_host_pipeline_create(int64_t chunk_packets, int n_streams, fw_host_pipeline **out);
+void fw_host_pipeline_destroy(fw_host_pipeline *pl);
+
+/*
+ * Classify n packets given in host SoA arrays `host_hdrs`; verdicts go to the
+ * host arrays out_rule_idx (int32[n]) and out_action (uint8[n]). `strategy`
+ * is FW_HOST_COPY or FW_HOST_ZEROCOPY; cfg as for fw_classify_ex (may be NULL).
+ * Errors: FW_EINVAL (null arguments, n < 0, unpinned buffer with
+ * FW_HOST_ZEROCOPY), FW_ECUDA.
+ */
+int fw_classify_host(fw_host_pipeline *pl, const fw_ruleset *rs, const fw_headers *host_hdrs, int64_t n,
+                     int32_t *out_rule_idx, uint8_t *out_action, int strategy, const fw_config *cfg);
+
+/* ------------------------------------------------------------ misc */
+int fw_last_status(void);                 /* status of the last failed short-form call on this thread */
+const char *fw_status_string(int status); /* static string, never NULL */
+int fw_abi_version(void);                 /* increments on incompatible ABI changes */
+int fw_rule_size(void);                   /* sizeof(fw_rule) == 24 */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FW_H_ */

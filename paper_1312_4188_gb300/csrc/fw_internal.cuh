@@ -1,0 +1,144 @@
+// Internal definitions shared by the CUDA translation units of the library.
+//
+// Canonical device form of a rule (built once by fw_ruleset_create_ex):
+//   match(p, r) = ((p.src ^ saddr) & smask) == 0         src prefix    (Sec. IV)
+//               & ((p.dst ^ daddr) & dmask) == 0         dst prefix
+//               & sport in [slo, shi] & dport in [dlo, dhi]   port ranges
+//               & ((p.proto ^ pval) & pmask) == 0        proto, pmask 0 = any
+// with saddr/daddr pre-masked and smask = 0 for prefix 0. Two equivalent
+// encodings of the port test are kept:
+//   clamp form:   ports = sport<<16 | dport, LO = slo<<16 | dlo, HI = shi<<16 | dhi;
+//                 both ranges hold iff min16x2(max16x2(ports, LO), HI) == ports
+//                 (per 16-bit lane, clamping a value into [lo, hi] leaves it
+//                 unchanged exactly when it lies in the range);
+//   compare form: (sport - slo) <= (shi - slo) as unsigned 32-bit, likewise dport
+//                 (a port below slo wraps to a value above 2^32 - 65536).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fw.h"
+
+namespace fwk {
+
+constexpr int kChunkRules = 256;          // rules per TMA chunk / padding granule
+constexpr uint32_t kStatusTimeout = 1u;   // a bounded wait gave up
+constexpr uint32_t kStatusBadArgs = 2u;   // device-side sanity check failed
+
+// Clamp-form record: 32 bytes = two uint4 (a: addresses, b: ports + proto).
+struct RecClamp {
+    uint4 a;  // saddr, smask, daddr, dmask
+    uint4 b;  // LO, HI, pval, pmask
+};
+
+// Compare-form record: 48 bytes = three uint4.
+struct RecCmp {
+    uint4 a;  // saddr, smask, daddr, dmask
+    uint4 b;  // slo, swidth, dlo, dwidth
+    uint4 c;  // pval, pmask, 0, 0
+};
+
+// A record that no packet matches (used to pad the device arrays): its
+// protocol value 0x100 differs from every 8-bit protocol under a full mask.
+constexpr uint32_t kNeverProto = 0x100u;
+
+struct Pkt {
+    uint32_t src, dst, ports, proto;  // ports = sport << 16 | dport
+};
+
+__device__ __forceinline__ uint32_t ports_of(uint32_t sport, uint32_t dport) { return (sport << 16) | dport; }
+
+// Non-zero exactly when the packet is outside the rule (clamp form).
+__device__ __forceinline__ uint32_t mismatch_clamp(const Pkt &p, const uint4 &a, const uint4 &b) {
+    uint32_t c = __vminu2(__vmaxu2(p.ports, b.x), b.y);
+    return ((p.src ^ a.x) & a.y) | ((p.dst ^ a.z) & a.w) | (c ^ p.ports) | ((p.proto ^ b.z) & b.w);
+}
+
+// True exactly when the packet is inside the rule (compare form).
+__device__ __forceinline__ bool match_cmp(const Pkt &p, const uint4 &a, const uint4 &b, const uint4 &c) {
+    uint32_t mm = ((p.src ^ a.x) & a.y) | ((p.dst ^ a.z) & a.w) | ((p.proto ^ c.x) & c.y);
+    uint32_t sp = p.ports >> 16, dp = p.ports & 0xFFFFu;
+    return (mm == 0u) & ((sp - b.x) <= b.y) & ((dp - b.z) <= b.w);
+}
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// 1-D bulk copy global -> shared (TMA engine), completion signalled on `bar`.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of `bar` to complete, giving up after ~limit_ns.
+// Returns false (and sets kStatusTimeout in *status) on give-up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, unsigned *status,
+                                                  uint64_t limit_ns = 200000000ull) {
+    if (mbar_try_wait(bar, parity)) return true;
+    uint64_t t0 = global_ns();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 63u && global_ns() - t0 > limit_ns) {
+            atomicOr(status, kStatusTimeout);
+            return false;
+        }
+    }
+}
+
+}  // namespace fwk
+
+// Host-side view of a rule set (opaque to callers).
+struct fw_ruleset {
+    int64_t n;                // rules supplied
+    int64_t n_eff;            // rules a scan can reach (first catch-all + 1, else n)
+    int64_t n_pad;            // device array length: n_eff rounded up to kChunkRules (>= kChunkRules)
+    int64_t first_catch_all;  // -1 if none
+    int device;
+    fwk::RecClamp *d_clamp;   // n_pad records
+    fwk::RecCmp *d_cmp;       // n_pad records
+    uint8_t *d_action;        // n_pad actions
+    unsigned *d_status;       // device error flags (kStatus*)
+};
+
+namespace fwk {
+int set_status(int s);  // records s as this thread's last status; returns s
+int cuda_status(cudaError_t e);
+}  // namespace fwk

@@ -1,0 +1,167 @@
+// Rule-set construction: validation, canonicalisation and upload.
+//
+// The rule model is the paper's 5-tuple with wildcard fields (Sec. IV): an
+// address is matched under a prefix mask, ports under inclusive ranges, the
+// protocol exactly or not at all. Canonicalisation turns each rule into the
+// two device record forms described in fw_internal.cuh and records the first
+// catch-all rule (all five fields wildcards): under first match (Sec. I) no
+// packet is ever decided by a rule after it, so scans stop there.
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "fw_internal.cuh"
+
+namespace fwk {
+
+static thread_local int g_last_status = FW_OK;
+
+int set_status(int s) {
+    if (s != FW_OK) g_last_status = s;
+    return s;
+}
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return FW_OK;
+    if (e == cudaErrorMemoryAllocation) return FW_ENOMEM;
+    return FW_ECUDA;
+}
+
+static uint32_t prefix_mask(unsigned prefix) {
+    return prefix == 0 ? 0u : (0xFFFFFFFFu << (32u - prefix));
+}
+
+static bool is_catch_all(const fw_rule &r) {
+    return r.src_prefix == 0 && r.dst_prefix == 0 && r.sport_lo == 0 && r.sport_hi == 0xFFFF && r.dport_lo == 0 &&
+           r.dport_hi == 0xFFFF && r.proto_any != 0;
+}
+
+static int validate(const fw_rule &r) {
+    if (r.src_prefix > 32 || r.dst_prefix > 32) return FW_EINVAL;
+    if (r.sport_lo > r.sport_hi || r.dport_lo > r.dport_hi) return FW_EINVAL;
+    if (r.action != FW_DROP && r.action != FW_ACCEPT) return FW_EINVAL;
+    if (r.reserved[0] | r.reserved[1] | r.reserved[2]) return FW_EINVAL;
+    return FW_OK;
+}
+
+static void canon(const fw_rule &r, RecClamp *c, RecCmp *m) {
+    uint32_t sm = prefix_mask(r.src_prefix), dm = prefix_mask(r.dst_prefix);
+    uint32_t pm = r.proto_any ? 0u : 0xFFu;
+    uint32_t pv = r.proto_any ? 0u : r.proto;
+    c->a = make_uint4(r.src_addr & sm, sm, r.dst_addr & dm, dm);
+    c->b = make_uint4((uint32_t(r.sport_lo) << 16) | r.dport_lo, (uint32_t(r.sport_hi) << 16) | r.dport_hi, pv, pm);
+    m->a = c->a;
+    m->b = make_uint4(r.sport_lo, uint32_t(r.sport_hi) - r.sport_lo, r.dport_lo, uint32_t(r.dport_hi) - r.dport_lo);
+    m->c = make_uint4(pv, pm, 0u, 0u);
+}
+
+static void never_match(RecClamp *c, RecCmp *m) {
+    c->a = make_uint4(0, 0, 0, 0);
+    c->b = make_uint4(0, 0xFFFFFFFFu, kNeverProto, 0xFFFFFFFFu);
+    m->a = c->a;
+    m->b = make_uint4(0, 0xFFFFFFFFu, 0, 0xFFFFFFFFu);
+    m->c = make_uint4(kNeverProto, 0xFFFFFFFFu, 0, 0);
+}
+
+}  // namespace fwk
+
+using namespace fwk;
+
+extern "C" int fw_ruleset_create_ex(const fw_rule *rules, int64_t n, fw_ruleset **out) {
+    if (out == nullptr) return set_status(FW_EINVAL);
+    *out = nullptr;
+    if (n < 0 || (n > 0 && rules == nullptr) || n > (int64_t(1) << 30)) return set_status(FW_EINVAL);
+    int64_t first_ca = -1;
+    for (int64_t k = 0; k < n; ++k) {
+        int s = validate(rules[k]);
+        if (s != FW_OK) return set_status(s);
+        if (first_ca < 0 && is_catch_all(rules[k])) first_ca = k;
+    }
+    fw_ruleset *rs = new (std::nothrow) fw_ruleset();
+    if (rs == nullptr) return set_status(FW_ENOMEM);
+    rs->n = n;
+    rs->first_catch_all = first_ca;
+    rs->n_eff = first_ca >= 0 ? first_ca + 1 : n;
+    rs->n_pad = ((rs->n_eff + kChunkRules - 1) / kChunkRules) * kChunkRules;
+    if (rs->n_pad == 0) rs->n_pad = kChunkRules;
+    cudaGetDevice(&rs->device);
+
+    std::vector<RecClamp> hc(rs->n_pad);
+    std::vector<RecCmp> hm(rs->n_pad);
+    std::vector<uint8_t> ha(rs->n_pad, FW_DROP);
+    for (int64_t k = 0; k < rs->n_pad; ++k) {
+        if (k < rs->n_eff) {
+            canon(rules[k], &hc[k], &hm[k]);
+            ha[k] = rules[k].action;
+        } else {
+            never_match(&hc[k], &hm[k]);
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&rs->d_clamp, rs->n_pad * sizeof(RecClamp));
+    if (e == cudaSuccess) e = cudaMalloc(&rs->d_cmp, rs->n_pad * sizeof(RecCmp));
+    if (e == cudaSuccess) e = cudaMalloc(&rs->d_action, rs->n_pad);
+    if (e == cudaSuccess) e = cudaMalloc(&rs->d_status, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemcpy(rs->d_clamp, hc.data(), rs->n_pad * sizeof(RecClamp), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(rs->d_cmp, hm.data(), rs->n_pad * sizeof(RecCmp), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(rs->d_action, ha.data(), rs->n_pad, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(rs->d_status, 0, sizeof(unsigned));
+    if (e != cudaSuccess) {
+        fw_ruleset_destroy(rs);
+        cudaGetLastError();
+        return set_status(cuda_status(e));
+    }
+    *out = rs;
+    return FW_OK;
+}
+
+extern "C" fw_ruleset *fw_ruleset_create(const fw_rule *rules, int64_t n) {
+    fw_ruleset *rs = nullptr;
+    fw_ruleset_create_ex(rules, n, &rs);
+    return rs;
+}
+
+extern "C" void fw_ruleset_destroy(fw_ruleset *rs) {
+    if (rs == nullptr) return;
+    if (rs->d_clamp) cudaFree(rs->d_clamp);
+    if (rs->d_cmp) cudaFree(rs->d_cmp);
+    if (rs->d_action) cudaFree(rs->d_action);
+    if (rs->d_status) cudaFree(rs->d_status);
+    delete rs;
+}
+
+extern "C" int64_t fw_ruleset_size(const fw_ruleset *rs) { return rs ? rs->n : -1; }
+extern "C" int64_t fw_ruleset_first_catch_all(const fw_ruleset *rs) { return rs ? rs->first_catch_all : -1; }
+
+extern "C" int fw_ruleset_check(fw_ruleset *rs) {
+    if (rs == nullptr) return set_status(FW_EINVAL);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return set_status(cuda_status(e));
+    unsigned st = 0;
+    e = cudaMemcpy(&st, rs->d_status, sizeof(st), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return set_status(cuda_status(e));
+    if (st != 0) {
+        cudaMemset(rs->d_status, 0, sizeof(unsigned));
+        return set_status((st & kStatusTimeout) ? FW_ETIMEOUT : FW_ECUDA);
+    }
+    return FW_OK;
+}
+
+extern "C" int fw_last_status(void) { return g_last_status; }
+
+extern "C" const char *fw_status_string(int s) {
+    switch (s) {
+        case FW_OK: return "ok";
+        case FW_EINVAL: return "invalid argument";
+        case FW_ENOMEM: return "out of memory";
+        case FW_ECUDA: return "CUDA error";
+        case FW_EALIGN: return "misaligned buffer";
+        case FW_ETIMEOUT: return "bounded device wait timed out";
+        case FW_EBUSY: return "busy: no capacity for more work";
+        case FW_ERANGE: return "size exceeds the call's fixed limit";
+        default: return "unknown status";
+    }
+}
+
+extern "C" int fw_abi_version(void) { return 1; }
+extern "C" int fw_rule_size(void) { return (int)sizeof(fw_rule); }

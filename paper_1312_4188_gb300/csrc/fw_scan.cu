@@ -1,0 +1,474 @@
+// First-match scan kernels and the fw_classify / fw_classify_ex entry points.
+//
+// Packet split (Sec. IV.A, data-parallel): every worker holds the whole rule
+// list and each packet is compared with it by one thread, in list order,
+// stopping at the first match. Here a persistent block keeps a prefix of the
+// canonical rule records resident in shared memory, brought in by 1-D TMA bulk
+// copies in 256-rule chunks, each with its own mbarrier; a warp waits for a
+// chunk only when one of its packets first reaches it. All lanes of a warp
+// read the same rule at the same time (a broadcast shared-memory load), so one
+// load feeds 32 packet checks. Rules past the resident prefix are read from
+// global memory (L1/L2 cached) the same way.
+//
+// Rule split (Sec. IV.B function-parallel, Sec. IV.C hybrid): the rule list is
+// divided among workers and the per-packet combine is the minimum matching
+// index (first match, Sec. I). Lane l of a warp tests rule 32c + l of chunk c;
+// __ballot_sync + __ffs gives the chunk's first match, i.e. the warp-level
+// minimum. A block-level minimum (shared-memory atomicMin) combines the warps
+// of a block that split one packet group's chunks; a grid-level minimum
+// (global atomicMin into stream-ordered scratch, then a finalize pass)
+// combines blocks that own different rule slices.
+#include <algorithm>
+#include <climits>
+#include <cstring>
+
+#include "fw_internal.cuh"
+
+namespace fwk {
+
+struct HdrPtrs {
+    const uint32_t *src;
+    const uint32_t *dst;
+    const uint16_t *sport;
+    const uint16_t *dport;
+    const uint8_t *proto;
+};
+
+struct ScanParams {
+    const RecClamp *clamp;
+    const RecCmp *cmp;
+    const uint8_t *action;
+    int n_scan;   // rules scanned: n_eff rounded up to a multiple of 4 (padding never matches)
+    int n_smem;   // rules resident in shared memory (multiple of kChunkRules, <= n_pad)
+    HdrPtrs h;
+    int64_t n;
+    int32_t *out_idx;
+    uint8_t *out_act;
+    unsigned *status;
+};
+
+// ------------------------------------------------------------ packet loads
+template <bool VEC>
+__device__ __forceinline__ void load_quad(const HdrPtrs &h, int64_t n, int64_t q, Pkt pk[4], int &cnt) {
+    const int64_t base = q * 4;
+    if (VEC && base + 3 < n) {
+        uint4 s = __ldcs(reinterpret_cast<const uint4 *>(h.src) + q);
+        uint4 d = __ldcs(reinterpret_cast<const uint4 *>(h.dst) + q);
+        uint2 sp = __ldcs(reinterpret_cast<const uint2 *>(h.sport) + q);
+        uint2 dp = __ldcs(reinterpret_cast<const uint2 *>(h.dport) + q);
+        uint32_t pr = __ldcs(reinterpret_cast<const unsigned int *>(h.proto) + q);
+        pk[0] = {s.x, d.x, (sp.x << 16) | (dp.x & 0xFFFFu), pr & 0xFFu};
+        pk[1] = {s.y, d.y, (sp.x & 0xFFFF0000u) | (dp.x >> 16), (pr >> 8) & 0xFFu};
+        pk[2] = {s.z, d.z, (sp.y << 16) | (dp.y & 0xFFFFu), (pr >> 16) & 0xFFu};
+        pk[3] = {s.w, d.w, (sp.y & 0xFFFF0000u) | (dp.y >> 16), pr >> 24};
+        cnt = 4;
+    } else {
+        cnt = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int64_t i = base + j;
+            if (i < n) {
+                pk[j] = {h.src[i], h.dst[i], ports_of(h.sport[i], h.dport[i]), h.proto[i]};
+                cnt = j + 1;
+            } else {
+                pk[j] = {0, 0, 0, 0};
+            }
+        }
+    }
+}
+
+template <bool VEC>
+__device__ __forceinline__ void store_quad(const ScanParams &p, int64_t q, const int idx[4], int cnt) {
+    const int64_t base = q * 4;
+    uint32_t a[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a[j] = idx[j] >= 0 ? __ldg(p.action + idx[j]) : (uint32_t)FW_DROP;
+    if (VEC && cnt == 4) {
+        __stcs(reinterpret_cast<int4 *>(p.out_idx) + q, make_int4(idx[0], idx[1], idx[2], idx[3]));
+        __stcs(reinterpret_cast<unsigned int *>(p.out_act) + q, a[0] | (a[1] << 8) | (a[2] << 16) | (a[3] << 24));
+    } else {
+        for (int j = 0; j < cnt; ++j) {
+            p.out_idx[base + j] = idx[j];
+            p.out_act[base + j] = (uint8_t)a[j];
+        }
+    }
+}
+
+// ------------------------------------------------------------ rule scans
+// First index in [0, n_scan) whose rule matches, or -1. Rules below n_smem come
+// from shared memory (chunk c usable once bars[c] completed), the rest from
+// global memory. Returns -2 if a chunk wait timed out.
+__device__ __forceinline__ int scan_clamp(const Pkt &pk, const RecClamp *__restrict__ sm, int n_smem,
+                                          const RecClamp *__restrict__ gm, int n_scan, uint64_t *bars,
+                                          unsigned *status) {
+    int k = 0;
+    const int lim = min(n_scan, n_smem);
+    while (k < lim) {
+        if (!mbar_wait_bounded(&bars[k / kChunkRules], 0, status)) return -2;
+        const int kend = min(lim, k + kChunkRules);
+        for (; k < kend; k += 4) {
+            const uint4 a0 = sm[k].a, b0 = sm[k].b, a1 = sm[k + 1].a, b1 = sm[k + 1].b;
+            const uint4 a2 = sm[k + 2].a, b2 = sm[k + 2].b, a3 = sm[k + 3].a, b3 = sm[k + 3].b;
+            const uint32_t m0 = mismatch_clamp(pk, a0, b0), m1 = mismatch_clamp(pk, a1, b1);
+            const uint32_t m2 = mismatch_clamp(pk, a2, b2), m3 = mismatch_clamp(pk, a3, b3);
+            if ((m0 == 0u) | (m1 == 0u) | (m2 == 0u) | (m3 == 0u))
+                return k + (m0 == 0u ? 0 : m1 == 0u ? 1 : m2 == 0u ? 2 : 3);
+        }
+    }
+    for (; k < n_scan; k += 4) {
+        const uint4 a0 = __ldg(&gm[k].a), b0 = __ldg(&gm[k].b), a1 = __ldg(&gm[k + 1].a), b1 = __ldg(&gm[k + 1].b);
+        const uint4 a2 = __ldg(&gm[k + 2].a), b2 = __ldg(&gm[k + 2].b), a3 = __ldg(&gm[k + 3].a),
+                    b3 = __ldg(&gm[k + 3].b);
+        const uint32_t m0 = mismatch_clamp(pk, a0, b0), m1 = mismatch_clamp(pk, a1, b1);
+        const uint32_t m2 = mismatch_clamp(pk, a2, b2), m3 = mismatch_clamp(pk, a3, b3);
+        if ((m0 == 0u) | (m1 == 0u) | (m2 == 0u) | (m3 == 0u))
+            return k + (m0 == 0u ? 0 : m1 == 0u ? 1 : m2 == 0u ? 2 : 3);
+    }
+    return -1;
+}
+
+__device__ __forceinline__ int scan_cmp(const Pkt &pk, const RecCmp *__restrict__ sm, int n_smem,
+                                        const RecCmp *__restrict__ gm, int n_scan, uint64_t *bars,
+                                        unsigned *status) {
+    int k = 0;
+    const int lim = min(n_scan, n_smem);
+    while (k < lim) {
+        if (!mbar_wait_bounded(&bars[k / kChunkRules], 0, status)) return -2;
+        const int kend = min(lim, k + kChunkRules);
+        for (; k < kend; k += 4) {
+            const bool m0 = match_cmp(pk, sm[k].a, sm[k].b, sm[k].c);
+            const bool m1 = match_cmp(pk, sm[k + 1].a, sm[k + 1].b, sm[k + 1].c);
+            const bool m2 = match_cmp(pk, sm[k + 2].a, sm[k + 2].b, sm[k + 2].c);
+            const bool m3 = match_cmp(pk, sm[k + 3].a, sm[k + 3].b, sm[k + 3].c);
+            if (m0 | m1 | m2 | m3) return k + (m0 ? 0 : m1 ? 1 : m2 ? 2 : 3);
+        }
+    }
+    for (; k < n_scan; k += 4) {
+        const bool m0 = match_cmp(pk, __ldg(&gm[k].a), __ldg(&gm[k].b), __ldg(&gm[k].c));
+        const bool m1 = match_cmp(pk, __ldg(&gm[k + 1].a), __ldg(&gm[k + 1].b), __ldg(&gm[k + 1].c));
+        const bool m2 = match_cmp(pk, __ldg(&gm[k + 2].a), __ldg(&gm[k + 2].b), __ldg(&gm[k + 2].c));
+        const bool m3 = match_cmp(pk, __ldg(&gm[k + 3].a), __ldg(&gm[k + 3].b), __ldg(&gm[k + 3].c));
+        if (m0 | m1 | m2 | m3) return k + (m0 ? 0 : m1 ? 1 : m2 ? 2 : 3);
+    }
+    return -1;
+}
+
+// ------------------------------------------------------------ packet split kernel
+// Persistent grid; each thread takes packet quads (4 consecutive packets) in a
+// grid-stride loop and scans them one after another.
+template <int PRED, bool VEC>
+__global__ void __launch_bounds__(1024) k_packet_split(ScanParams p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int rec_bytes = PRED == FW_PRED_CLAMP ? (int)sizeof(RecClamp) : (int)sizeof(RecCmp);
+    const int n_chunks = p.n_smem / kChunkRules;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)p.n_smem * rec_bytes);
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < n_chunks; ++c) mbar_init(&bars[c], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned char *src = PRED == FW_PRED_CLAMP ? reinterpret_cast<const unsigned char *>(p.clamp)
+                                                        : reinterpret_cast<const unsigned char *>(p.cmp);
+        const uint32_t bytes = kChunkRules * rec_bytes;
+        for (int c = 0; c < n_chunks; ++c) {
+            mbar_arrive_expect_tx(&bars[c], bytes);
+            bulk_load(smem + (size_t)c * bytes, src + (size_t)c * bytes, bytes, &bars[c]);
+        }
+    }
+    const int64_t nq = (p.n + 3) / 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += stride) {
+        Pkt pk[4];
+        int cnt;
+        load_quad<VEC>(p.h, p.n, q, pk, cnt);
+        int idx[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int r;
+            if (PRED == FW_PRED_CLAMP)
+                r = scan_clamp(pk[j], reinterpret_cast<const RecClamp *>(smem), p.n_smem, p.clamp, p.n_scan, bars,
+                               p.status);
+            else
+                r = scan_cmp(pk[j], reinterpret_cast<const RecCmp *>(smem), p.n_smem, p.cmp, p.n_scan, bars,
+                             p.status);
+            idx[j] = r < 0 ? -1 : r;
+        }
+        store_quad<VEC>(p, q, idx, cnt);
+    }
+    // Do not leave while a bulk copy into this block's shared memory may be in flight.
+    if (threadIdx.x == 0)
+        for (int c = 0; c < n_chunks; ++c) mbar_wait_bounded(&bars[c], 0, p.status);
+}
+
+// ------------------------------------------------------------ rule split kernel
+struct SplitParams {
+    const RecClamp *clamp;
+    const uint8_t *action;
+    int n_scan;        // rules scanned (multiple of 4; padded records never match)
+    int slice_rules;   // rules per slice along gridDim.y (multiple of 32)
+    int group;         // packets per group (multiple of 32)
+    HdrPtrs h;
+    int64_t n;
+    int32_t *out_idx;
+    uint8_t *out_act;
+    int32_t *partial;  // grid mode: per-packet minimum across slices (pre-set to kNoMatch)
+};
+
+constexpr int kNoMatch = 0x7F7F7F7F;  // byte-fill sentinel, larger than any rule index
+
+// BLOCK = true: all warps of the block share one packet group and split its
+// chunks round-robin. BLOCK = false: each warp owns a packet group alone.
+template <bool BLOCK>
+__global__ void __launch_bounds__(512) k_rule_split(SplitParams p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const int G = p.group;
+    const int groups_per_block = BLOCK ? 1 : nwarps;
+    const int my_group = BLOCK ? 0 : warp;
+    const int gw = BLOCK ? nwarps : 1;          // warps sharing a group
+    const int w_in_group = BLOCK ? warp : 0;
+    const int gt = BLOCK ? threadIdx.x : lane;  // thread index within the group
+    const int gthreads = gw * 32;
+    Pkt *stage = reinterpret_cast<Pkt *>(smem) + (size_t)my_group * G;
+    int *best = reinterpret_cast<int *>(smem + (size_t)groups_per_block * G * sizeof(Pkt)) + (size_t)my_group * G;
+
+    const int r0 = blockIdx.y * p.slice_rules;
+    const int r1 = min(p.n_scan, r0 + p.slice_rules);
+    const int64_t n_groups = (p.n + G - 1) / G;
+    for (int64_t g = (int64_t)blockIdx.x * groups_per_block + my_group; g < n_groups;
+         g += (int64_t)gridDim.x * groups_per_block) {
+        const int64_t base = g * G;
+        for (int t = gt; t < G; t += gthreads) {
+            const int64_t i = base + t;
+            if (i < p.n) {
+                stage[t] = {p.h.src[i], p.h.dst[i], ports_of(p.h.sport[i], p.h.dport[i]), p.h.proto[i]};
+                best[t] = INT_MAX;
+            } else {
+                stage[t] = {0, 0, 0, 0};
+                best[t] = -1;  // no packet: never pending
+            }
+        }
+        if (BLOCK) __syncthreads(); else __syncwarp();
+        for (int c0 = r0 + w_in_group * 32; c0 < r1; c0 += gw * 32) {
+            const int k = c0 + lane;
+            uint4 a = make_uint4(0, 0, 0, 0), b = make_uint4(0, 0xFFFFFFFFu, kNeverProto, 0xFFFFFFFFu);
+            if (k < r1) {
+                a = __ldg(&p.clamp[k].a);
+                b = __ldg(&p.clamp[k].b);
+            }
+            // Packets already decided by an earlier (or this) chunk are skipped. The
+            // pending set is taken by ballot so that the loop stays warp-uniform;
+            // a stale read only costs a redundant check (atomicMin keeps the minimum).
+            bool pending = false;
+            for (int t0 = 0; t0 < G; t0 += 32) {
+                unsigned pend = __ballot_sync(0xFFFFFFFFu, *reinterpret_cast<volatile int *>(&best[t0 + lane]) > c0);
+                pending |= pend != 0u;
+                while (pend != 0u) {
+                    const int t = t0 + __ffs(pend) - 1;
+                    pend &= pend - 1u;
+                    const Pkt pk = stage[t];
+                    const unsigned bal = __ballot_sync(0xFFFFFFFFu, mismatch_clamp(pk, a, b) == 0u);
+                    if (bal != 0u && lane == 0) atomicMin(&best[t], c0 + __ffs(bal) - 1);
+                }
+            }
+            if (!pending) break;
+        }
+        if (BLOCK) __syncthreads(); else __syncwarp();
+        for (int t = gt; t < G; t += gthreads) {
+            const int64_t i = base + t;
+            if (i >= p.n) break;
+            const int bt = best[t];
+            if (p.partial != nullptr) {
+                if (bt != INT_MAX) atomicMin(&p.partial[i], bt);
+            } else {
+                const int r = bt == INT_MAX ? -1 : bt;
+                p.out_idx[i] = r;
+                p.out_act[i] = r >= 0 ? __ldg(p.action + r) : (uint8_t)FW_DROP;
+            }
+        }
+        if (BLOCK) __syncthreads(); else __syncwarp();
+    }
+}
+
+__global__ void k_rule_split_finalize(const int32_t *__restrict__ partial, const uint8_t *__restrict__ action,
+                                      int64_t n, int32_t *__restrict__ out_idx, uint8_t *__restrict__ out_act) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int v = partial[i];
+        const int r = v == kNoMatch ? -1 : v;
+        out_idx[i] = r;
+        out_act[i] = r >= 0 ? __ldg(action + r) : (uint8_t)FW_DROP;
+    }
+}
+
+// ------------------------------------------------------------ host side
+static int sm_count(int dev) {
+    static int cached[64] = {0};
+    if (dev < 0 || dev >= 64) return 148;
+    if (cached[dev] == 0) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = v > 0 ? v : 148;
+    }
+    return cached[dev];
+}
+
+static bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+template <class K>
+static cudaError_t ensure_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *out_idx, uint8_t *out_act,
+                        cudaStream_t st, const fw_config &cfg) {
+    ScanParams p;
+    p.clamp = rs->d_clamp;
+    p.cmp = rs->d_cmp;
+    p.action = rs->d_action;
+    p.n_scan = (int)((rs->n_eff + 3) / 4 * 4);
+    const int pred = cfg.predicate == 0 ? FW_PRED_CLAMP : cfg.predicate;
+    const int rec_bytes = pred == FW_PRED_CLAMP ? (int)sizeof(RecClamp) : (int)sizeof(RecCmp);
+    int want = cfg.smem_rules > 0 ? cfg.smem_rules : (cfg.smem_rules < 0 ? 0 : 3072);
+    want = (want / kChunkRules) * kChunkRules;
+    const int need = (int)((p.n_scan + kChunkRules - 1) / kChunkRules * kChunkRules);
+    p.n_smem = std::min(want, need);
+    p.h = h;
+    p.n = n;
+    p.out_idx = out_idx;
+    p.out_act = out_act;
+    p.status = rs->d_status;
+    const int threads = cfg.block_threads > 0 ? cfg.block_threads : 512;
+    const int per_sm = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : 2;
+    if (threads % 32 != 0 || threads > 1024) return FW_EINVAL;
+    const size_t smem = (size_t)p.n_smem * rec_bytes + (size_t)(p.n_smem / kChunkRules) * 8;
+    if (smem > 227 * 1024) return FW_EINVAL;
+    const bool vec = aligned(h.src, 16) && aligned(h.dst, 16) && aligned(h.sport, 8) && aligned(h.dport, 8) &&
+                     aligned(h.proto, 4) && aligned(out_idx, 16) && aligned(out_act, 4);
+    const int64_t nq = (n + 3) / 4;
+    int64_t blocks = (int64_t)sm_count(rs->device) * per_sm;
+    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (nq + threads - 1) / threads));
+    cudaError_t e;
+#define FW_LAUNCH_PS(PR, V)                                                                    \
+    do {                                                                                       \
+        e = ensure_smem(k_packet_split<PR, V>, smem);                                          \
+        if (e == cudaSuccess) k_packet_split<PR, V><<<(unsigned)blocks, threads, smem, st>>>(p); \
+    } while (0)
+    if (pred == FW_PRED_CLAMP) {
+        if (vec) FW_LAUNCH_PS(FW_PRED_CLAMP, true); else FW_LAUNCH_PS(FW_PRED_CLAMP, false);
+    } else if (pred == FW_PRED_CMP) {
+        if (vec) FW_LAUNCH_PS(FW_PRED_CMP, true); else FW_LAUNCH_PS(FW_PRED_CMP, false);
+    } else {
+        return FW_EINVAL;
+    }
+#undef FW_LAUNCH_PS
+    if (e != cudaSuccess) return cuda_status(e);
+    return cuda_status(cudaGetLastError());
+}
+
+int launch_rule_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *out_idx, uint8_t *out_act,
+                      cudaStream_t st, const fw_config &cfg) {
+    SplitParams p;
+    p.clamp = rs->d_clamp;
+    p.action = rs->d_action;
+    p.n_scan = (int)((rs->n_eff + 3) / 4 * 4);
+    p.h = h;
+    p.n = n;
+    p.out_idx = out_idx;
+    p.out_act = out_act;
+    p.partial = nullptr;
+    const bool block_mode = cfg.mode == FW_MODE_RULE_SPLIT_BLOCK;
+    const bool grid_mode = cfg.mode == FW_MODE_RULE_SPLIT_GRID;
+    const int threads = cfg.block_threads > 0 ? cfg.block_threads : 256;
+    if (threads % 32 != 0 || threads > 512) return FW_EINVAL;
+    int G = cfg.packets_per_group > 0 ? cfg.packets_per_group : (block_mode ? 256 : 64);
+    if (G % 32 != 0 || G > 4096) return FW_EINVAL;
+    p.group = G;
+    const int nwarps = threads / 32;
+    const int groups_per_block = block_mode ? 1 : nwarps;
+    const size_t smem = (size_t)groups_per_block * G * (sizeof(Pkt) + sizeof(int));
+    if (smem > 227 * 1024) return FW_EINVAL;
+    int slices = 1;
+    if (grid_mode) {
+        slices = cfg.rule_slices > 0 ? cfg.rule_slices : 8;
+        slices = std::max(1, std::min(std::min(slices, 65535), (p.n_scan + 31) / 32));
+    }
+    p.slice_rules = ((p.n_scan + slices - 1) / slices + 31) / 32 * 32;
+    if (p.slice_rules == 0) p.slice_rules = 32;
+    slices = (p.n_scan + p.slice_rules - 1) / p.slice_rules;
+    if (slices < 1) slices = 1;
+    const int per_sm = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : 4;
+    const int64_t n_groups = (n + G - 1) / G;
+    int64_t bx = std::max<int64_t>(1, (int64_t)sm_count(rs->device) * per_sm / (grid_mode ? slices : 1));
+    bx = std::min<int64_t>(bx, (n_groups + groups_per_block - 1) / groups_per_block);
+    bx = std::max<int64_t>(bx, 1);
+    cudaError_t e = cudaSuccess;
+    if (grid_mode) {
+        e = cudaMallocAsync(reinterpret_cast<void **>(&p.partial), (size_t)n * sizeof(int32_t), st);
+        if (e != cudaSuccess) return cuda_status(e);
+        e = cudaMemsetAsync(p.partial, 0x7F, (size_t)n * sizeof(int32_t), st);
+    }
+    dim3 grid((unsigned)bx, (unsigned)slices);
+    if (e == cudaSuccess) {
+        if (block_mode) {
+            e = ensure_smem(k_rule_split<true>, smem);
+            if (e == cudaSuccess) k_rule_split<true><<<grid, threads, smem, st>>>(p);
+        } else {
+            e = ensure_smem(k_rule_split<false>, smem);
+            if (e == cudaSuccess) k_rule_split<false><<<grid, threads, smem, st>>>(p);
+        }
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (grid_mode) {
+        if (e == cudaSuccess) {
+            const int fb = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count(rs->device) * 8);
+            k_rule_split_finalize<<<std::max(fb, 1), 256, 0, st>>>(p.partial, p.action, n, out_idx, out_act);
+            e = cudaGetLastError();
+        }
+        cudaFreeAsync(p.partial, st);
+    }
+    return cuda_status(e);
+}
+
+}  // namespace fwk
+
+using namespace fwk;
+
+static int classify_impl(const fw_ruleset *rs, const fw_headers *hdrs, int64_t n, int32_t *out_idx,
+                         uint8_t *out_act, void *stream, const fw_config *cfg_in) {
+    if (rs == nullptr || n < 0 || n > INT_MAX) return FW_EINVAL;
+    if (n == 0) return FW_OK;
+    if (hdrs == nullptr || hdrs->src == nullptr || hdrs->dst == nullptr || hdrs->sport == nullptr ||
+        hdrs->dport == nullptr || hdrs->proto == nullptr || out_idx == nullptr || out_act == nullptr)
+        return FW_EINVAL;
+    fw_config cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    if (cfg_in != nullptr) cfg = *cfg_in;
+    for (int i = 0; i < 8; ++i)
+        if (cfg.reserved[i] != 0) return FW_EINVAL;
+    HdrPtrs h{hdrs->src, hdrs->dst, hdrs->sport, hdrs->dport, hdrs->proto};
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    switch (cfg.mode) {
+        case FW_MODE_AUTO:
+        case FW_MODE_PACKET_SPLIT:
+            return launch_packet_split(rs, h, n, out_idx, out_act, st, cfg);
+        case FW_MODE_RULE_SPLIT_WARP:
+        case FW_MODE_RULE_SPLIT_BLOCK:
+        case FW_MODE_RULE_SPLIT_GRID:
+            return launch_rule_split(rs, h, n, out_idx, out_act, st, cfg);
+        default:
+            return FW_EINVAL;
+    }
+}
+
+extern "C" int fw_classify(const fw_ruleset *rs, const fw_headers *hdrs, int64_t n, int32_t *out_rule_idx,
+                           uint8_t *out_action, void *stream) {
+    return set_status(classify_impl(rs, hdrs, n, out_rule_idx, out_action, stream, nullptr));
+}
+
+extern "C" int fw_classify_ex(const fw_ruleset *rs, const fw_headers *hdrs, int64_t n, int32_t *out_rule_idx,
+                              uint8_t *out_action, void *stream, const fw_config *cfg) {
+    return set_status(classify_impl(rs, hdrs, n, out_rule_idx, out_action, stream, cfg));
+}

@@ -1,0 +1,263 @@
+"""Thin Python binding of the C ABI in ``include/fw.h`` (ctypes).
+
+Argument marshalling only: every step of classification runs in the CUDA
+library ``libfw.so``. PyTorch supplies device memory and streams. If the
+library is missing the calls raise; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from .workload import HEADER_FIELDS, RULE_DTYPE
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfw.so")
+
+FW_OK = 0
+FW_EINVAL = -1
+FW_ENOMEM = -2
+FW_ECUDA = -3
+FW_EALIGN = -4
+FW_ETIMEOUT = -5
+FW_EBUSY = -6
+FW_ERANGE = -7
+
+FW_DROP = 0
+FW_ACCEPT = 1
+
+FW_MODE_AUTO = 0
+FW_MODE_PACKET_SPLIT = 1
+FW_MODE_RULE_SPLIT_WARP = 2
+FW_MODE_RULE_SPLIT_BLOCK = 3
+FW_MODE_RULE_SPLIT_GRID = 4
+MODES = {
+    "auto": FW_MODE_AUTO,
+    "packet_split": FW_MODE_PACKET_SPLIT,
+    "rule_split_warp": FW_MODE_RULE_SPLIT_WARP,
+    "rule_split_block": FW_MODE_RULE_SPLIT_BLOCK,
+    "rule_split_grid": FW_MODE_RULE_SPLIT_GRID,
+}
+FW_PRED_CLAMP = 1
+FW_PRED_CMP = 2
+FW_HOST_COPY = 1
+FW_HOST_ZEROCOPY = 2
+
+
+class FwError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})" if what else status_string(status))
+
+
+class fw_headers(ctypes.Structure):
+    _fields_ = [("src", ctypes.c_void_p), ("dst", ctypes.c_void_p), ("sport", ctypes.c_void_p),
+                ("dport", ctypes.c_void_p), ("proto", ctypes.c_void_p)]
+
+
+class fw_config(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("smem_rules", ctypes.c_int32), ("packets_per_group", ctypes.c_int32),
+                ("rule_slices", ctypes.c_int32), ("compact", ctypes.c_int32), ("predicate", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 8)]
+
+
+def make_config(mode=FW_MODE_AUTO, **kw) -> fw_config:
+    if isinstance(mode, str):
+        mode = MODES[mode]
+    c = fw_config()
+    c.mode = mode
+    for k, v in kw.items():
+        setattr(c, k, int(v))
+    return c
+
+
+_lock = threading.Lock()
+_lib = None
+
+P = ctypes.c_void_p
+I64 = ctypes.c_int64
+
+SIGNATURES = {
+    "fw_ruleset_create_ex": (ctypes.c_int, [P, I64, ctypes.POINTER(P)]),
+    "fw_ruleset_create": (P, [P, I64]),
+    "fw_ruleset_destroy": (None, [P]),
+    "fw_ruleset_size": (I64, [P]),
+    "fw_ruleset_first_catch_all": (I64, [P]),
+    "fw_ruleset_check": (ctypes.c_int, [P]),
+    "fw_classify": (ctypes.c_int, [P, ctypes.POINTER(fw_headers), I64, P, P, P]),
+    "fw_classify_ex": (ctypes.c_int, [P, ctypes.POINTER(fw_headers), I64, P, P, P, ctypes.POINTER(fw_config)]),
+    "fw_host_pipeline_create": (ctypes.c_int, [I64, ctypes.c_int, ctypes.POINTER(P)]),
+    "fw_host_pipeline_destroy": (None, [P]),
+    "fw_classify_host": (ctypes.c_int, [P, P, ctypes.POINTER(fw_headers), I64, P, P, ctypes.c_int,
+                                        ctypes.POINTER(fw_config)]),
+    "fw_last_status": (ctypes.c_int, []),
+    "fw_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "fw_abi_version": (ctypes.c_int, []),
+    "fw_rule_size": (ctypes.c_int, []),
+}
+
+
+def lib(path: str | None = None):
+    """Load ``libfw.so`` (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"CUDA library not built: {p} is missing (run paper_1312_4188_gb300.build.build())")
+        L = ctypes.CDLL(p)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        if L.fw_rule_size() != RULE_DTYPE.itemsize:
+            raise RuntimeError("fw_rule layout mismatch between library and binding")
+        if path is None:
+            _lib = L
+        return L
+
+
+def status_string(s: int) -> str:
+    try:
+        return lib().fw_status_string(int(s)).decode()
+    except RuntimeError:
+        return f"status {s}"
+
+
+def _check(s: int, what: str):
+    if s != FW_OK:
+        raise FwError(s, what)
+
+
+def _as_rules(rules) -> np.ndarray:
+    rules = np.asarray(rules)
+    if rules.dtype != RULE_DTYPE:
+        rules = rules.astype(RULE_DTYPE)
+    return np.ascontiguousarray(rules)
+
+
+class Ruleset:
+    """Owning wrapper of an ``fw_ruleset*`` handle."""
+
+    def __init__(self, handle: int, n: int):
+        self.handle = ctypes.c_void_p(handle)
+        self.n = n
+
+    @property
+    def first_catch_all(self) -> int:
+        return int(lib().fw_ruleset_first_catch_all(self.handle))
+
+    def size(self) -> int:
+        return int(lib().fw_ruleset_size(self.handle))
+
+    def check(self) -> int:
+        return int(lib().fw_ruleset_check(self.handle))
+
+    def destroy(self):
+        if self.handle is not None and self.handle.value:
+            lib().fw_ruleset_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def fw_ruleset_create(rules) -> Ruleset:
+    r = _as_rules(rules)
+    out = ctypes.c_void_p()
+    s = lib().fw_ruleset_create_ex(r.ctypes.data_as(P) if r.size else None, int(r.shape[0]), ctypes.byref(out))
+    _check(s, "fw_ruleset_create")
+    return Ruleset(out.value, int(r.shape[0]))
+
+
+def headers_struct(h: dict) -> fw_headers:
+    """``fw_headers`` from a dict of tensors (or objects with data_ptr) keyed by field."""
+    return fw_headers(*[ctypes.c_void_p(int(h[f].data_ptr())) for f in HEADER_FIELDS])
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def headers_to_device(h: dict, device="cuda") -> dict:
+    """Copy numpy SoA headers to device tensors (same bytes, signed views for torch)."""
+    import torch
+    views = {"src": np.int32, "dst": np.int32, "sport": np.int16, "dport": np.int16, "proto": np.uint8}
+    return {f: torch.from_numpy(np.ascontiguousarray(h[f]).view(views[f])).to(device) for f in HEADER_FIELDS}
+
+
+def fw_classify(rs: Ruleset, hdrs: dict, n: int | None = None, out_idx=None, out_act=None, stream=None,
+                config: fw_config | None = None):
+    """Classify device headers; returns (out_idx int32 tensor, out_act uint8 tensor)."""
+    import torch
+    if n is None:
+        n = int(hdrs["src"].shape[0])
+    dev = hdrs["src"].device
+    if out_idx is None:
+        out_idx = torch.empty(n, dtype=torch.int32, device=dev)
+    if out_act is None:
+        out_act = torch.empty(n, dtype=torch.uint8, device=dev)
+    hs = headers_struct(hdrs)
+    st = _stream_handle(stream)
+    if config is None:
+        s = lib().fw_classify(rs.handle, ctypes.byref(hs), int(n), ctypes.c_void_p(out_idx.data_ptr()),
+                              ctypes.c_void_p(out_act.data_ptr()), st)
+    else:
+        s = lib().fw_classify_ex(rs.handle, ctypes.byref(hs), int(n), ctypes.c_void_p(out_idx.data_ptr()),
+                                 ctypes.c_void_p(out_act.data_ptr()), st, ctypes.byref(config))
+    _check(s, "fw_classify")
+    return out_idx, out_act
+
+
+fw_classify_ex = fw_classify
+
+
+class HostPipeline:
+    """Owning wrapper of an ``fw_host_pipeline*``."""
+
+    def __init__(self, handle: int):
+        self.handle = ctypes.c_void_p(handle)
+
+    def destroy(self):
+        if self.handle is not None and self.handle.value:
+            lib().fw_host_pipeline_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def fw_host_pipeline_create(chunk_packets: int = 0, n_streams: int = 0) -> HostPipeline:
+    out = ctypes.c_void_p()
+    _check(lib().fw_host_pipeline_create(int(chunk_packets), int(n_streams), ctypes.byref(out)),
+           "fw_host_pipeline_create")
+    return HostPipeline(out.value)
+
+
+def fw_classify_host(pl: HostPipeline, rs: Ruleset, host_hdrs: dict, out_idx, out_act, n: int | None = None,
+                     strategy: int = FW_HOST_COPY, config: fw_config | None = None):
+    """Classify headers held in host memory (tensors or numpy arrays); verdicts land in host ``out_*``."""
+    def ptr(a):
+        return ctypes.c_void_p(a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data)
+    if n is None:
+        n = int(host_hdrs["src"].shape[0])
+    hs = fw_headers(*[ptr(host_hdrs[f]) for f in HEADER_FIELDS])
+    s = lib().fw_classify_host(pl.handle, rs.handle, ctypes.byref(hs), int(n), ptr(out_idx), ptr(out_act),
+                               int(strategy), ctypes.byref(config) if config is not None else None)
+    _check(s, "fw_classify_host")
