@@ -43,7 +43,8 @@ BYTES_PER_PACKET = 18
 INT32_LANES_PER_SM_CLK = 128  # 4 schedulers x 32 lanes, one warp instruction per clock each
 FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "sms": 152}
 KERNEL_SOURCES = ["paper_1312_4188_gb300/csrc/fw_scan.cu", "paper_1312_4188_gb300/csrc/fw_internal.cuh"]
-TRAFFIC_RECORD = "profiles/k_packet_split_scan_10k_x_16m.md"
+KERNEL_NAME = "k_packet_split_compact"
+TRAFFIC_RECORD = "profiles/k_packet_split_compact_scan_10k_x_16m.md"
 
 
 def parse():
@@ -287,7 +288,7 @@ def main():
                      "frac": ops_per_s / alu_peak, "traffic": traffic,
                      "peak_source": f"derived: {sms} SMs x {INT32_LANES_PER_SM_CLK} INT32 lanes/clk x "
                                     f"{pk['sm_max_mhz']:.0f} MHz ({peak_src} max clock)",
-                     "ops_per_check": OPS_PER_CHECK, "kernel": "k_packet_split"},
+                     "ops_per_check": OPS_PER_CHECK, "kernel": KERNEL_NAME},
         "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": pk["hbm_gbs"], "frac": hbm_gbs / pk["hbm_gbs"],
                 "peak_source": peak_src, "bytes_per_packet": BYTES_PER_PACKET},
         "rule_checks_per_s": checks_per_s,
@@ -302,8 +303,14 @@ def main():
 
     if rank == 0 and not args.no_modes:
         modes = {}
-        for name in ("packet_split", "rule_split_warp", "rule_split_block", "rule_split_grid"):
-            c = fw.make_config(name)
+        variants = {"packet_split": ("packet_split", {}),
+                    "packet_split_lockstep": ("packet_split", {"compact": 2}),
+                    "packet_split_lockstep_clamp": ("packet_split", {"compact": 2, "predicate": fw.FW_PRED_CLAMP}),
+                    "rule_split_warp": ("rule_split_warp", {}),
+                    "rule_split_block": ("rule_split_block", {}),
+                    "rule_split_grid": ("rule_split_grid", {})}
+        for name, (mname, kw) in variants.items():
+            c = fw.make_config(mname, **kw)
             with torch.cuda.stream(stream):
                 for _ in range(3):
                     step(c)

@@ -99,6 +99,7 @@ typedef struct fw_headers {
 /* Encodings of the field tests (fw_config.predicate); both give identical results. */
 #define FW_PRED_CLAMP 1  /* port ranges as a 16x2 clamp, proto under a mask */
 #define FW_PRED_CMP   2  /* port ranges as unsigned subtract-and-compare */
+#define FW_PRED_ARITH 3  /* port ranges as multiply-add + compare, protocol folded into dport (default) */
 
 /*
  * Launch configuration. Zero in any field means "library default".
@@ -106,11 +107,15 @@ typedef struct fw_headers {
  *  block_threads:     threads per block (multiple of 32, <= 1024).
  *  blocks_per_sm:     resident blocks per SM for persistent launches.
  *  smem_rules:        rules kept resident in shared memory (packet split).
- *  packets_per_group: packets handled together by one warp/block (rule split).
+ *  packets_per_group: rule split: packets handled together by one warp/block;
+ *                     packet split with compaction: packets per warp batch
+ *                     (multiple of 128).
  *  rule_slices:       number of rule slices across the grid (RULE_SPLIT_GRID).
- *  compact:           packet split only: 1 = re-pack unresolved packets between
- *                     rule segments, 2 = do not (plain lockstep scan).
- *  predicate:         0 default, FW_PRED_CLAMP or FW_PRED_CMP.
+ *  compact:           packet split only: 1 = re-pack undecided packets between
+ *                     rule segments (default), 2 = plain lockstep scan.
+ *  predicate:         FW_PRED_CLAMP, FW_PRED_CMP or FW_PRED_ARITH (0 = default).
+ *  segment_rules:     packet split with compaction: rules in the first segment
+ *                     (multiple of 4; later segments double).
  */
 typedef struct fw_config {
     int32_t mode;
@@ -121,7 +126,8 @@ typedef struct fw_config {
     int32_t rule_slices;
     int32_t compact;
     int32_t predicate;
-    int32_t reserved[8];           /* must be zero */
+    int32_t segment_rules;
+    int32_t reserved[7];           /* must be zero */
 } fw_config;
 
 typedef struct fw_ruleset fw_ruleset;
@@ -217,6 +223,18 @@ void fw_host_pipeline_destroy(fw_host_pipeline *pl);
  */
 int fw_classify_host(fw_host_pipeline *pl, const fw_ruleset *rs, const fw_headers *host_hdrs, int64_t n,
                      int32_t *out_rule_idx, uint8_t *out_action, int strategy, const fw_config *cfg);
+
+/* ------------------------------------------------------------ self test */
+/*
+ * Failure-path check of the bounded device waits. Launches one block whose
+ * thread waits on an mbarrier that nothing will complete, with a limit of
+ * `limit_ns` nanoseconds (1e3..1e9); the wait gives up, records the timeout
+ * in the rule set's status word and the kernel returns normally, so the CUDA
+ * context stays usable. A following fw_ruleset_check(rs) returns FW_ETIMEOUT.
+ * The paper has no counterpart; this exists so that tests can exercise the
+ * timeout path of the kernels' waits without faulting or hanging a GPU.
+ */
+int fw_selftest_wait_timeout(fw_ruleset *rs, int64_t limit_ns, void *stream);
 
 /* ------------------------------------------------------------ misc */
 int fw_last_status(void);                 /* status of the last failed short-form call on this thread */

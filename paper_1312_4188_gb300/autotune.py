@@ -1,0 +1,129 @@
+"""Launch-configuration autotuner for the classification kernels.
+
+The paper studies how the launch configuration (threads per block, rules per
+thread) moves packet delay (Sec. IV results, B). Here the knobs are the
+fw_config fields: decomposition, predicate encoding, block size, resident
+blocks per SM, shared-memory rule prefix, warp batch size and first rule
+segment. ``sweep`` times each candidate with CUDA events on one stream and
+checks that every candidate returns the same verdicts as the first one
+(all forms compute the same function, so any difference is a bug).
+Results can be cached per (device, workload) in a JSON file.
+"""
+from __future__ import annotations
+
+import json
+import os
+import statistics
+import sys
+
+from . import fw
+
+PACKET_SPLIT_CANDIDATES = (
+    [dict(mode="packet_split", compact=2, predicate=p) for p in (fw.FW_PRED_CLAMP, fw.FW_PRED_CMP, fw.FW_PRED_ARITH)]
+    + [dict(mode="packet_split", compact=1, predicate=fw.FW_PRED_ARITH, block_threads=bt, blocks_per_sm=bps,
+            smem_rules=sr, packets_per_group=b, segment_rules=s0)
+       for (bt, bps, sr, b) in ((1024, 1, 2048, 256), (1024, 1, 2048, 128), (512, 2, 1024, 256), (768, 1, 2048, 256))
+       for s0 in (8, 16, 32)]
+    + [dict(mode="packet_split", compact=1, predicate=fw.FW_PRED_CLAMP, block_threads=1024, blocks_per_sm=1,
+            smem_rules=3072, packets_per_group=256, segment_rules=16)]
+)
+
+RULE_SPLIT_CANDIDATES = (
+    [dict(mode="rule_split_warp", block_threads=bt, packets_per_group=g) for bt in (128, 256) for g in (32, 64, 128)]
+    + [dict(mode="rule_split_block", block_threads=bt, packets_per_group=g) for bt in (128, 256) for g in (128, 256)]
+    + [dict(mode="rule_split_grid", rule_slices=s, packets_per_group=g) for s in (2, 4, 8) for g in (32, 64)]
+)
+
+
+def config_of(c: dict) -> fw.fw_config:
+    kw = dict(c)
+    return fw.make_config(kw.pop("mode"), **kw)
+
+
+def time_config(rs, dh, n, out_idx, out_act, cfg, reps=20, warmup=3, stream=None):
+    """Median per-launch milliseconds of fw_classify_ex with ``cfg`` (CUDA events on ``stream``)."""
+    import torch
+    stream = stream or torch.cuda.current_stream()
+    for _ in range(warmup):
+        fw.fw_classify(rs, dh, n, out_idx, out_act, stream=stream, config=cfg)
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fw.fw_classify(rs, dh, n, out_idx, out_act, stream=stream, config=cfg)
+        b.record(stream)
+        ts.append((a, b))
+    torch.cuda.synchronize()
+    return statistics.median(x.elapsed_time(y) for x, y in ts)
+
+
+def sweep(rs, dh, n, candidates, reps=20, warmup=3):
+    """Time every candidate; returns [(candidate, ms, same_as_first)] sorted by time."""
+    import torch
+    dev = dh["src"].device
+    ref_idx = ref_act = None
+    out = []
+    for c in candidates:
+        idx = torch.empty(n, dtype=torch.int32, device=dev)
+        act = torch.empty(n, dtype=torch.uint8, device=dev)
+        try:
+            ms = time_config(rs, dh, n, idx, act, config_of(c), reps=reps, warmup=warmup)
+        except fw.FwError as e:
+            out.append((c, float("inf"), f"rejected: {e}"))
+            continue
+        if ref_idx is None:
+            ref_idx, ref_act, same = idx, act, True
+        else:
+            same = bool(torch.equal(idx, ref_idx) and torch.equal(act, ref_act))
+        out.append((c, ms, same))
+    out.sort(key=lambda t: t[1])
+    return out
+
+
+def cache_path():
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
+
+
+def load_cache():
+    p = cache_path()
+    return json.load(open(p)) if os.path.exists(p) else {}
+
+
+def store(key: str, best: dict):
+    d = load_cache()
+    d[key] = best
+    os.makedirs(os.path.dirname(cache_path()), exist_ok=True)
+    json.dump(d, open(cache_path(), "w"), indent=1, sort_keys=True)
+
+
+def main(argv=None):
+    import argparse
+
+    import torch
+
+    from . import build, workload as W
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="scan_10k_x_16m_zipf", choices=sorted(W.WORKLOADS))
+    ap.add_argument("--set", default="packet_split", choices=["packet_split", "rule_split", "all"])
+    ap.add_argument("--reps", type=int, default=20)
+    a = ap.parse_args(argv)
+    build.build()
+    rules, hdr = W.make_workload(a.workload)
+    n = len(hdr["src"])
+    rs = fw.fw_ruleset_create(rules)
+    dh = fw.headers_to_device(hdr)
+    cands = {"packet_split": PACKET_SPLIT_CANDIDATES, "rule_split": RULE_SPLIT_CANDIDATES,
+             "all": PACKET_SPLIT_CANDIDATES + RULE_SPLIT_CANDIDATES}[a.set]
+    res = sweep(rs, dh, n, cands, reps=a.reps)
+    name = torch.cuda.get_device_name()
+    for c, ms, same in res:
+        print(json.dumps({"workload": a.workload, "device": name, "config": c, "ms": ms,
+                          "mpackets_s": n / (ms * 1e-3) / 1e6 if ms != float("inf") else 0.0, "same": same}))
+    if res and res[0][1] != float("inf"):
+        store(f"{name}|{a.workload}|{a.set}", res[0][0])
+    rs.destroy()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

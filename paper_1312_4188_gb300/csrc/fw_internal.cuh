@@ -39,6 +39,24 @@ struct RecCmp {
     uint4 c;  // pval, pmask, 0, 0
 };
 
+// Arithmetic-form record: 48 bytes = three uint4, of which c.y..c.w are unused.
+// The port tests are written as unsigned subtractions that the FMA pipe can
+// execute (IMAD), leaving only logic ops and compares on the ALU pipe:
+//   sport:        (sport + neg_slo) <= swidth            (neg_slo = -slo mod 2^32)
+//   dport, proto: (X * mul + add) <= wtop, X = proto << 17 | dport, where
+//     exact proto p: mul = 1,      add = -(p << 17 | dlo), wtop = dhi - dlo
+//     any proto:     mul = 2^15,   add = -(dlo << 15),      wtop = (dhi - dlo) << 15
+//   With mul = 1 the protocol sits 17 bits above the port, so any protocol
+//   difference moves the value at least 2^17 - 65535 > 65535 away from the
+//   port window (or wraps it past 2^32 - 2^25); with mul = 2^15 the protocol
+//   bits are shifted out of the 32-bit word and only the port difference,
+//   scaled by 2^15, remains, which cannot wrap into the window.
+struct RecArith {
+    uint4 a;  // saddr, smask, daddr, dmask
+    uint4 b;  // neg_slo, swidth, mul, add
+    uint4 c;  // wtop, 0, 0, 0
+};
+
 // A record that no packet matches (used to pad the device arrays): its
 // protocol value 0x100 differs from every 8-bit protocol under a full mask.
 constexpr uint32_t kNeverProto = 0x100u;
@@ -60,6 +78,23 @@ __device__ __forceinline__ bool match_cmp(const Pkt &p, const uint4 &a, const ui
     uint32_t mm = ((p.src ^ a.x) & a.y) | ((p.dst ^ a.z) & a.w) | ((p.proto ^ c.x) & c.y);
     uint32_t sp = p.ports >> 16, dp = p.ports & 0xFFFFu;
     return (mm == 0u) & ((sp - b.x) <= b.y) & ((dp - b.z) <= b.w);
+}
+
+// Packet form used with RecArith.
+struct PktA {
+    uint32_t src, dst, sport, x;  // x = proto << 17 | dport
+};
+
+__device__ __forceinline__ uint32_t x_of(uint32_t proto, uint32_t dport) { return (proto << 17) | dport; }
+
+// True exactly when the packet is outside the rule (arithmetic form). `one`
+// is the runtime constant 1, so that the sport subtraction is issued as a
+// multiply-add on the FMA pipe instead of an add on the ALU pipe.
+__device__ __forceinline__ bool mismatch_arith(const PktA &p, const uint4 &a, const uint4 &b, uint32_t wtop,
+                                               uint32_t one) {
+    const uint32_t ts = p.sport * one + b.x;
+    const uint32_t td = p.x * b.z + b.w;
+    return (((p.src ^ a.x) & a.y) != 0u) | (((p.dst ^ a.z) & a.w) != 0u) | (ts > b.y) | (td > wtop);
 }
 
 // ------------------------------------------------------------------ PTX helpers
@@ -134,6 +169,7 @@ struct fw_ruleset {
     int device;
     fwk::RecClamp *d_clamp;   // n_pad records
     fwk::RecCmp *d_cmp;       // n_pad records
+    fwk::RecArith *d_arith;   // n_pad records
     uint8_t *d_action;        // n_pad actions
     unsigned *d_status;       // device error flags (kStatus*)
 };

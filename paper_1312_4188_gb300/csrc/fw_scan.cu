@@ -35,11 +35,13 @@ struct HdrPtrs {
 };
 
 struct ScanParams {
-    const RecClamp *clamp;
-    const RecCmp *cmp;
+    const void *rec;       // records of the chosen form (RecClamp / RecCmp / RecArith)
     const uint8_t *action;
     int n_scan;   // rules scanned: n_eff rounded up to a multiple of 4 (padding never matches)
     int n_smem;   // rules resident in shared memory (multiple of kChunkRules, <= n_pad)
+    int batch;    // compacting kernel: packets per warp batch (multiple of 128)
+    int seg0;     // compacting kernel: rules in the first segment (multiple of 4)
+    uint32_t one; // the constant 1, opaque to the compiler (see mismatch_arith)
     HdrPtrs h;
     int64_t n;
     int32_t *out_idx;
@@ -47,9 +49,79 @@ struct ScanParams {
     unsigned *status;
 };
 
+// ------------------------------------------------------------ record policies
+// How a record form is fetched and tested, and how a packet is held.
+struct PolClamp {
+    using Rec = RecClamp;
+    using Pk = Pkt;
+    struct R {
+        uint4 a, b;
+    };
+    static __device__ __forceinline__ Pk make(uint32_t s, uint32_t d, uint32_t sp, uint32_t dp, uint32_t pr) {
+        return {s, d, ports_of(sp, dp), pr};
+    }
+    static __device__ __forceinline__ R lds(const Rec *r) { return {r->a, r->b}; }
+    static __device__ __forceinline__ R ldg(const Rec *r) { return {__ldg(&r->a), __ldg(&r->b)}; }
+    static __device__ __forceinline__ bool mism(const Pk &p, const R &r, uint32_t) {
+        return mismatch_clamp(p, r.a, r.b) != 0u;
+    }
+    // queue entry: the packet with its batch slot above the protocol byte
+    static __device__ __forceinline__ uint4 pack(const Pk &p, int slot) {
+        return make_uint4(p.src, p.dst, p.ports, p.proto | ((uint32_t)slot << 8));
+    }
+    static __device__ __forceinline__ Pk unpack(const uint4 &e, int &slot) {
+        slot = (int)(e.w >> 8);
+        return {e.x, e.y, e.z, e.w & 0xFFu};
+    }
+};
+
+struct PolCmp {
+    using Rec = RecCmp;
+    using Pk = Pkt;
+    struct R {
+        uint4 a, b, c;
+    };
+    static __device__ __forceinline__ Pk make(uint32_t s, uint32_t d, uint32_t sp, uint32_t dp, uint32_t pr) {
+        return {s, d, ports_of(sp, dp), pr};
+    }
+    static __device__ __forceinline__ R lds(const Rec *r) { return {r->a, r->b, r->c}; }
+    static __device__ __forceinline__ R ldg(const Rec *r) { return {__ldg(&r->a), __ldg(&r->b), __ldg(&r->c)}; }
+    static __device__ __forceinline__ bool mism(const Pk &p, const R &r, uint32_t) {
+        return !match_cmp(p, r.a, r.b, r.c);
+    }
+    static __device__ __forceinline__ uint4 pack(const Pk &p, int slot) { return PolClamp::pack(p, slot); }
+    static __device__ __forceinline__ Pk unpack(const uint4 &e, int &slot) { return PolClamp::unpack(e, slot); }
+};
+
+struct PolArith {
+    using Rec = RecArith;
+    using Pk = PktA;
+    struct R {
+        uint4 a, b;
+        uint32_t w;
+    };
+    static __device__ __forceinline__ Pk make(uint32_t s, uint32_t d, uint32_t sp, uint32_t dp, uint32_t pr) {
+        return {s, d, sp, x_of(pr, dp)};
+    }
+    static __device__ __forceinline__ R lds(const Rec *r) { return {r->a, r->b, r->c.x}; }
+    static __device__ __forceinline__ R ldg(const Rec *r) { return {__ldg(&r->a), __ldg(&r->b), __ldg(&r->c.x)}; }
+    static __device__ __forceinline__ bool mism(const Pk &p, const R &r, uint32_t one) {
+        return mismatch_arith(p, r.a, r.b, r.w, one);
+    }
+    // queue entry: the batch slot above the 16-bit source port
+    static __device__ __forceinline__ uint4 pack(const Pk &p, int slot) {
+        return make_uint4(p.src, p.dst, p.sport | ((uint32_t)slot << 16), p.x);
+    }
+    static __device__ __forceinline__ Pk unpack(const uint4 &e, int &slot) {
+        slot = (int)(e.z >> 16);
+        return {e.x, e.y, e.z & 0xFFFFu, e.w};
+    }
+};
+
 // ------------------------------------------------------------ packet loads
-template <bool VEC>
-__device__ __forceinline__ void load_quad(const HdrPtrs &h, int64_t n, int64_t q, Pkt pk[4], int &cnt) {
+template <class Pol, bool VEC>
+__device__ __forceinline__ void load_quad(const HdrPtrs &h, int64_t n, int64_t q, typename Pol::Pk pk[4],
+                                          int &cnt) {
     const int64_t base = q * 4;
     if (VEC && base + 3 < n) {
         uint4 s = __ldcs(reinterpret_cast<const uint4 *>(h.src) + q);
@@ -57,10 +129,10 @@ __device__ __forceinline__ void load_quad(const HdrPtrs &h, int64_t n, int64_t q
         uint2 sp = __ldcs(reinterpret_cast<const uint2 *>(h.sport) + q);
         uint2 dp = __ldcs(reinterpret_cast<const uint2 *>(h.dport) + q);
         uint32_t pr = __ldcs(reinterpret_cast<const unsigned int *>(h.proto) + q);
-        pk[0] = {s.x, d.x, (sp.x << 16) | (dp.x & 0xFFFFu), pr & 0xFFu};
-        pk[1] = {s.y, d.y, (sp.x & 0xFFFF0000u) | (dp.x >> 16), (pr >> 8) & 0xFFu};
-        pk[2] = {s.z, d.z, (sp.y << 16) | (dp.y & 0xFFFFu), (pr >> 16) & 0xFFu};
-        pk[3] = {s.w, d.w, (sp.y & 0xFFFF0000u) | (dp.y >> 16), pr >> 24};
+        pk[0] = Pol::make(s.x, d.x, sp.x & 0xFFFFu, dp.x & 0xFFFFu, pr & 0xFFu);
+        pk[1] = Pol::make(s.y, d.y, sp.x >> 16, dp.x >> 16, (pr >> 8) & 0xFFu);
+        pk[2] = Pol::make(s.z, d.z, sp.y & 0xFFFFu, dp.y & 0xFFFFu, (pr >> 16) & 0xFFu);
+        pk[3] = Pol::make(s.w, d.w, sp.y >> 16, dp.y >> 16, pr >> 24);
         cnt = 4;
     } else {
         cnt = 0;
@@ -68,10 +140,10 @@ __device__ __forceinline__ void load_quad(const HdrPtrs &h, int64_t n, int64_t q
         for (int j = 0; j < 4; ++j) {
             int64_t i = base + j;
             if (i < n) {
-                pk[j] = {h.src[i], h.dst[i], ports_of(h.sport[i], h.dport[i]), h.proto[i]};
+                pk[j] = Pol::make(h.src[i], h.dst[i], h.sport[i], h.dport[i], h.proto[i]);
                 cnt = j + 1;
             } else {
-                pk[j] = {0, 0, 0, 0};
+                pk[j] = Pol::make(0, 0, 0, 0, 0);
             }
         }
     }
@@ -95,71 +167,41 @@ __device__ __forceinline__ void store_quad(const ScanParams &p, int64_t q, const
 }
 
 // ------------------------------------------------------------ rule scans
-// First index in [0, n_scan) whose rule matches, or -1. Rules below n_smem come
-// from shared memory (chunk c usable once bars[c] completed), the rest from
-// global memory. Returns -2 if a chunk wait timed out.
-__device__ __forceinline__ int scan_clamp(const Pkt &pk, const RecClamp *__restrict__ sm, int n_smem,
-                                          const RecClamp *__restrict__ gm, int n_scan, uint64_t *bars,
-                                          unsigned *status) {
-    int k = 0;
-    const int lim = min(n_scan, n_smem);
+// First index in [k0, k1) whose rule matches, or -1 (k0, k1 multiples of 4).
+// Rules below n_smem come from shared memory (chunk c usable once bars[c]
+// completed), the rest from global memory. Returns -2 if a chunk wait timed out.
+template <class Pol>
+__device__ __forceinline__ int scan_range(const typename Pol::Pk &pk, int k0, int k1,
+                                          const typename Pol::Rec *__restrict__ sm, int n_smem,
+                                          const typename Pol::Rec *__restrict__ gm, uint64_t *bars, unsigned *status,
+                                          uint32_t one) {
+    int k = k0;
+    const int lim = min(k1, n_smem);
     while (k < lim) {
         if (!mbar_wait_bounded(&bars[k / kChunkRules], 0, status)) return -2;
-        const int kend = min(lim, k + kChunkRules);
+        const int kend = min(lim, (k / kChunkRules + 1) * kChunkRules);
         for (; k < kend; k += 4) {
-            const uint4 a0 = sm[k].a, b0 = sm[k].b, a1 = sm[k + 1].a, b1 = sm[k + 1].b;
-            const uint4 a2 = sm[k + 2].a, b2 = sm[k + 2].b, a3 = sm[k + 3].a, b3 = sm[k + 3].b;
-            const uint32_t m0 = mismatch_clamp(pk, a0, b0), m1 = mismatch_clamp(pk, a1, b1);
-            const uint32_t m2 = mismatch_clamp(pk, a2, b2), m3 = mismatch_clamp(pk, a3, b3);
-            if ((m0 == 0u) | (m1 == 0u) | (m2 == 0u) | (m3 == 0u))
-                return k + (m0 == 0u ? 0 : m1 == 0u ? 1 : m2 == 0u ? 2 : 3);
+            const typename Pol::R r0 = Pol::lds(sm + k), r1 = Pol::lds(sm + k + 1);
+            const typename Pol::R r2 = Pol::lds(sm + k + 2), r3 = Pol::lds(sm + k + 3);
+            const bool m0 = Pol::mism(pk, r0, one), m1 = Pol::mism(pk, r1, one);
+            const bool m2 = Pol::mism(pk, r2, one), m3 = Pol::mism(pk, r3, one);
+            if (!(m0 & m1 & m2 & m3)) return k + (!m0 ? 0 : !m1 ? 1 : !m2 ? 2 : 3);
         }
     }
-    for (; k < n_scan; k += 4) {
-        const uint4 a0 = __ldg(&gm[k].a), b0 = __ldg(&gm[k].b), a1 = __ldg(&gm[k + 1].a), b1 = __ldg(&gm[k + 1].b);
-        const uint4 a2 = __ldg(&gm[k + 2].a), b2 = __ldg(&gm[k + 2].b), a3 = __ldg(&gm[k + 3].a),
-                    b3 = __ldg(&gm[k + 3].b);
-        const uint32_t m0 = mismatch_clamp(pk, a0, b0), m1 = mismatch_clamp(pk, a1, b1);
-        const uint32_t m2 = mismatch_clamp(pk, a2, b2), m3 = mismatch_clamp(pk, a3, b3);
-        if ((m0 == 0u) | (m1 == 0u) | (m2 == 0u) | (m3 == 0u))
-            return k + (m0 == 0u ? 0 : m1 == 0u ? 1 : m2 == 0u ? 2 : 3);
+    for (; k < k1; k += 4) {
+        const typename Pol::R r0 = Pol::ldg(gm + k), r1 = Pol::ldg(gm + k + 1);
+        const typename Pol::R r2 = Pol::ldg(gm + k + 2), r3 = Pol::ldg(gm + k + 3);
+        const bool m0 = Pol::mism(pk, r0, one), m1 = Pol::mism(pk, r1, one);
+        const bool m2 = Pol::mism(pk, r2, one), m3 = Pol::mism(pk, r3, one);
+        if (!(m0 & m1 & m2 & m3)) return k + (!m0 ? 0 : !m1 ? 1 : !m2 ? 2 : 3);
     }
     return -1;
 }
 
-__device__ __forceinline__ int scan_cmp(const Pkt &pk, const RecCmp *__restrict__ sm, int n_smem,
-                                        const RecCmp *__restrict__ gm, int n_scan, uint64_t *bars,
-                                        unsigned *status) {
-    int k = 0;
-    const int lim = min(n_scan, n_smem);
-    while (k < lim) {
-        if (!mbar_wait_bounded(&bars[k / kChunkRules], 0, status)) return -2;
-        const int kend = min(lim, k + kChunkRules);
-        for (; k < kend; k += 4) {
-            const bool m0 = match_cmp(pk, sm[k].a, sm[k].b, sm[k].c);
-            const bool m1 = match_cmp(pk, sm[k + 1].a, sm[k + 1].b, sm[k + 1].c);
-            const bool m2 = match_cmp(pk, sm[k + 2].a, sm[k + 2].b, sm[k + 2].c);
-            const bool m3 = match_cmp(pk, sm[k + 3].a, sm[k + 3].b, sm[k + 3].c);
-            if (m0 | m1 | m2 | m3) return k + (m0 ? 0 : m1 ? 1 : m2 ? 2 : 3);
-        }
-    }
-    for (; k < n_scan; k += 4) {
-        const bool m0 = match_cmp(pk, __ldg(&gm[k].a), __ldg(&gm[k].b), __ldg(&gm[k].c));
-        const bool m1 = match_cmp(pk, __ldg(&gm[k + 1].a), __ldg(&gm[k + 1].b), __ldg(&gm[k + 1].c));
-        const bool m2 = match_cmp(pk, __ldg(&gm[k + 2].a), __ldg(&gm[k + 2].b), __ldg(&gm[k + 2].c));
-        const bool m3 = match_cmp(pk, __ldg(&gm[k + 3].a), __ldg(&gm[k + 3].b), __ldg(&gm[k + 3].c));
-        if (m0 | m1 | m2 | m3) return k + (m0 ? 0 : m1 ? 1 : m2 ? 2 : 3);
-    }
-    return -1;
-}
-
-// ------------------------------------------------------------ packet split kernel
-// Persistent grid; each thread takes packet quads (4 consecutive packets) in a
-// grid-stride loop and scans them one after another.
-template <int PRED, bool VEC>
-__global__ void __launch_bounds__(1024) k_packet_split(ScanParams p) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int rec_bytes = PRED == FW_PRED_CLAMP ? (int)sizeof(RecClamp) : (int)sizeof(RecCmp);
+// Shared-memory rule prefix: mbarrier init + TMA bulk copies, one per chunk.
+template <class Pol>
+__device__ __forceinline__ uint64_t *stage_rules(unsigned char *smem, const ScanParams &p) {
+    const int rec_bytes = (int)sizeof(typename Pol::Rec);
     const int n_chunks = p.n_smem / kChunkRules;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)p.n_smem * rec_bytes);
     if (threadIdx.x == 0) {
@@ -168,37 +210,111 @@ __global__ void __launch_bounds__(1024) k_packet_split(ScanParams p) {
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned char *src = PRED == FW_PRED_CLAMP ? reinterpret_cast<const unsigned char *>(p.clamp)
-                                                        : reinterpret_cast<const unsigned char *>(p.cmp);
+        const unsigned char *src = reinterpret_cast<const unsigned char *>(p.rec);
         const uint32_t bytes = kChunkRules * rec_bytes;
         for (int c = 0; c < n_chunks; ++c) {
             mbar_arrive_expect_tx(&bars[c], bytes);
             bulk_load(smem + (size_t)c * bytes, src + (size_t)c * bytes, bytes, &bars[c]);
         }
     }
+    return bars;
+}
+
+// Do not leave while a bulk copy into this block's shared memory may be in flight.
+__device__ __forceinline__ void drain_rules(uint64_t *bars, int n_smem, unsigned *status) {
+    if (threadIdx.x == 0)
+        for (int c = 0; c < n_smem / kChunkRules; ++c) mbar_wait_bounded(&bars[c], 0, status);
+}
+
+// ------------------------------------------------------------ packet split kernels
+// Lockstep form: persistent grid; each thread takes packet quads (4
+// consecutive packets) in a grid-stride loop and scans them one after another.
+template <class Pol, bool VEC>
+__global__ void __launch_bounds__(1024) k_packet_split(ScanParams p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    using Rec = typename Pol::Rec;
+    uint64_t *bars = stage_rules<Pol>(smem, p);
+    const Rec *sm = reinterpret_cast<const Rec *>(smem);
+    const Rec *gm = reinterpret_cast<const Rec *>(p.rec);
     const int64_t nq = (p.n + 3) / 4;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += stride) {
-        Pkt pk[4];
+        typename Pol::Pk pk[4];
         int cnt;
-        load_quad<VEC>(p.h, p.n, q, pk, cnt);
+        load_quad<Pol, VEC>(p.h, p.n, q, pk, cnt);
         int idx[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            int r;
-            if (PRED == FW_PRED_CLAMP)
-                r = scan_clamp(pk[j], reinterpret_cast<const RecClamp *>(smem), p.n_smem, p.clamp, p.n_scan, bars,
-                               p.status);
-            else
-                r = scan_cmp(pk[j], reinterpret_cast<const RecCmp *>(smem), p.n_smem, p.cmp, p.n_scan, bars,
-                             p.status);
+            const int r = scan_range<Pol>(pk[j], 0, p.n_scan, sm, p.n_smem, gm, bars, p.status, p.one);
             idx[j] = r < 0 ? -1 : r;
         }
         store_quad<VEC>(p, q, idx, cnt);
     }
-    // Do not leave while a bulk copy into this block's shared memory may be in flight.
-    if (threadIdx.x == 0)
-        for (int c = 0; c < n_chunks; ++c) mbar_wait_bounded(&bars[c], 0, p.status);
+    drain_rules(bars, p.n_smem, p.status);
+}
+
+// Compacting form. Each warp takes a batch of `batch` packets into its own
+// shared-memory queue and scans the queue segment by segment over the rule
+// list (first segment seg0 rules, then doubling). After each group of 32
+// queue entries, packets decided in the segment write their verdicts and the
+// undecided ones are packed to the front of the queue (ballot + popc), so the
+// next segment runs on dense groups of still-undecided packets instead of
+// lanes idling behind the slowest packet of a warp.
+template <class Pol, bool VEC>
+__global__ void __launch_bounds__(1024) k_packet_split_compact(ScanParams p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    using Rec = typename Pol::Rec;
+    uint64_t *bars = stage_rules<Pol>(smem, p);
+    const Rec *sm = reinterpret_cast<const Rec *>(smem);
+    const Rec *gm = reinterpret_cast<const Rec *>(p.rec);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int B = p.batch;
+    const size_t qoff = ((size_t)p.n_smem * sizeof(Rec) + (size_t)(p.n_smem / kChunkRules) * 8 + 15) / 16 * 16;
+    uint4 *Q = reinterpret_cast<uint4 *>(smem + qoff) + (size_t)warp * B;
+    const int64_t nb = (p.n + B - 1) / B;
+    for (int64_t b = (int64_t)blockIdx.x * nw + warp; b < nb; b += (int64_t)gridDim.x * nw) {
+        const int64_t base = b * B;
+        const int cnt = (int)min((int64_t)B, p.n - base);
+        for (int qq = lane; qq * 4 < cnt; qq += 32) {
+            typename Pol::Pk pk[4];
+            int c;
+            load_quad<Pol, VEC>(p.h, p.n, base / 4 + qq, pk, c);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (j < c) Q[qq * 4 + j] = Pol::pack(pk[j], qq * 4 + j);
+        }
+        __syncwarp();
+        int m = cnt, s0 = 0, s1 = p.seg0;
+        while (m > 0) {
+            s1 = min(s1, p.n_scan);
+            const bool last = s1 >= p.n_scan;
+            int w = 0;
+            for (int g0 = 0; g0 < m; g0 += 32) {
+                const int i = g0 + lane;
+                const bool valid = i < m;
+                const uint4 e = valid ? Q[i] : make_uint4(0, 0, 0, 0);
+                __syncwarp();
+                int slot;
+                const typename Pol::Pk pk = Pol::unpack(e, slot);
+                int r = -1;
+                if (valid && s0 < s1) r = scan_range<Pol>(pk, s0, s1, sm, p.n_smem, gm, bars, p.status, p.one);
+                const bool keep = valid && r == -1 && !last;
+                if (valid && !keep) {
+                    const int v = r >= 0 ? r : -1;
+                    p.out_idx[base + slot] = v;
+                    p.out_act[base + slot] = v >= 0 ? __ldg(p.action + v) : (uint8_t)FW_DROP;
+                }
+                const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
+                if (keep) Q[w + __popc(bal & ((1u << lane) - 1u))] = e;
+                w += __popc(bal);
+                __syncwarp();
+            }
+            m = w;
+            s0 = s1;
+            s1 = s1 * 2;
+        }
+    }
+    drain_rules(bars, p.n_smem, p.status);
 }
 
 // ------------------------------------------------------------ rule split kernel
@@ -325,44 +441,73 @@ static cudaError_t ensure_smem(K kernel, size_t bytes) {
 int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *out_idx, uint8_t *out_act,
                         cudaStream_t st, const fw_config &cfg) {
     ScanParams p;
-    p.clamp = rs->d_clamp;
-    p.cmp = rs->d_cmp;
+    const int pred = cfg.predicate == 0 ? FW_PRED_ARITH : cfg.predicate;
+    const bool compact = cfg.compact != 2;
+    int rec_bytes;
+    if (pred == FW_PRED_CLAMP) {
+        p.rec = rs->d_clamp;
+        rec_bytes = (int)sizeof(RecClamp);
+    } else if (pred == FW_PRED_CMP) {
+        p.rec = rs->d_cmp;
+        rec_bytes = (int)sizeof(RecCmp);
+    } else if (pred == FW_PRED_ARITH) {
+        p.rec = rs->d_arith;
+        rec_bytes = (int)sizeof(RecArith);
+    } else {
+        return FW_EINVAL;
+    }
+    if (cfg.compact < 0 || cfg.compact > 2) return FW_EINVAL;
     p.action = rs->d_action;
     p.n_scan = (int)((rs->n_eff + 3) / 4 * 4);
-    const int pred = cfg.predicate == 0 ? FW_PRED_CLAMP : cfg.predicate;
-    const int rec_bytes = pred == FW_PRED_CLAMP ? (int)sizeof(RecClamp) : (int)sizeof(RecCmp);
-    int want = cfg.smem_rules > 0 ? cfg.smem_rules : (cfg.smem_rules < 0 ? 0 : 3072);
+    const int threads = cfg.block_threads > 0 ? cfg.block_threads : (compact ? 1024 : 512);
+    const int per_sm = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : (compact ? 1 : 2);
+    if (threads % 32 != 0 || threads > 1024) return FW_EINVAL;
+    int want = cfg.smem_rules > 0 ? cfg.smem_rules : (cfg.smem_rules < 0 ? 0 : (compact ? 2048 : 3072));
     want = (want / kChunkRules) * kChunkRules;
     const int need = (int)((p.n_scan + kChunkRules - 1) / kChunkRules * kChunkRules);
     p.n_smem = std::min(want, need);
+    p.batch = cfg.packets_per_group > 0 ? cfg.packets_per_group : 128;
+    if (compact && (p.batch % 128 != 0 || p.batch > 65536)) return FW_EINVAL;
+    p.seg0 = cfg.segment_rules > 0 ? cfg.segment_rules : 16;
+    if (p.seg0 % 4 != 0) return FW_EINVAL;
+    p.one = 1u;
     p.h = h;
     p.n = n;
     p.out_idx = out_idx;
     p.out_act = out_act;
     p.status = rs->d_status;
-    const int threads = cfg.block_threads > 0 ? cfg.block_threads : 512;
-    const int per_sm = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : 2;
-    if (threads % 32 != 0 || threads > 1024) return FW_EINVAL;
-    const size_t smem = (size_t)p.n_smem * rec_bytes + (size_t)(p.n_smem / kChunkRules) * 8;
+    size_t smem = (size_t)p.n_smem * rec_bytes + (size_t)(p.n_smem / kChunkRules) * 8;
+    if (compact) smem = (smem + 15) / 16 * 16 + (size_t)(threads / 32) * p.batch * sizeof(uint4);
     if (smem > 227 * 1024) return FW_EINVAL;
     const bool vec = aligned(h.src, 16) && aligned(h.dst, 16) && aligned(h.sport, 8) && aligned(h.dport, 8) &&
                      aligned(h.proto, 4) && aligned(out_idx, 16) && aligned(out_act, 4);
-    const int64_t nq = (n + 3) / 4;
     int64_t blocks = (int64_t)sm_count(rs->device) * per_sm;
-    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (nq + threads - 1) / threads));
-    cudaError_t e;
-#define FW_LAUNCH_PS(PR, V)                                                                    \
-    do {                                                                                       \
-        e = ensure_smem(k_packet_split<PR, V>, smem);                                          \
-        if (e == cudaSuccess) k_packet_split<PR, V><<<(unsigned)blocks, threads, smem, st>>>(p); \
-    } while (0)
-    if (pred == FW_PRED_CLAMP) {
-        if (vec) FW_LAUNCH_PS(FW_PRED_CLAMP, true); else FW_LAUNCH_PS(FW_PRED_CLAMP, false);
-    } else if (pred == FW_PRED_CMP) {
-        if (vec) FW_LAUNCH_PS(FW_PRED_CMP, true); else FW_LAUNCH_PS(FW_PRED_CMP, false);
+    if (compact) {
+        const int64_t nb = (n + p.batch - 1) / p.batch;
+        blocks = std::min<int64_t>(blocks, (nb + threads / 32 - 1) / (threads / 32));
     } else {
-        return FW_EINVAL;
+        const int64_t nq = (n + 3) / 4;
+        blocks = std::min<int64_t>(blocks, (nq + threads - 1) / threads);
     }
+    blocks = std::max<int64_t>(1, blocks);
+    cudaError_t e = cudaSuccess;
+#define FW_LAUNCH_PS(KER, POL, V)                                                            \
+    do {                                                                                     \
+        e = ensure_smem(KER<POL, V>, smem);                                                  \
+        if (e == cudaSuccess) KER<POL, V><<<(unsigned)blocks, threads, smem, st>>>(p);         \
+    } while (0)
+#define FW_PICK(KER)                                                                         \
+    do {                                                                                     \
+        if (pred == FW_PRED_CLAMP) {                                                         \
+            if (vec) FW_LAUNCH_PS(KER, PolClamp, true); else FW_LAUNCH_PS(KER, PolClamp, false); \
+        } else if (pred == FW_PRED_CMP) {                                                    \
+            if (vec) FW_LAUNCH_PS(KER, PolCmp, true); else FW_LAUNCH_PS(KER, PolCmp, false);     \
+        } else {                                                                             \
+            if (vec) FW_LAUNCH_PS(KER, PolArith, true); else FW_LAUNCH_PS(KER, PolArith, false); \
+        }                                                                                    \
+    } while (0)
+    if (compact) FW_PICK(k_packet_split_compact); else FW_PICK(k_packet_split);
+#undef FW_PICK
 #undef FW_LAUNCH_PS
     if (e != cudaSuccess) return cuda_status(e);
     return cuda_status(cudaGetLastError());
@@ -446,7 +591,7 @@ static int classify_impl(const fw_ruleset *rs, const fw_headers *hdrs, int64_t n
     fw_config cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     if (cfg_in != nullptr) cfg = *cfg_in;
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 7; ++i)
         if (cfg.reserved[i] != 0) return FW_EINVAL;
     HdrPtrs h{hdrs->src, hdrs->dst, hdrs->sport, hdrs->dport, hdrs->proto};
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -471,4 +616,21 @@ extern "C" int fw_classify(const fw_ruleset *rs, const fw_headers *hdrs, int64_t
 extern "C" int fw_classify_ex(const fw_ruleset *rs, const fw_headers *hdrs, int64_t n, int32_t *out_rule_idx,
                               uint8_t *out_action, void *stream, const fw_config *cfg) {
     return set_status(classify_impl(rs, hdrs, n, out_rule_idx, out_action, stream, cfg));
+}
+
+// A wait that nothing completes: the bounded wait must give up and report.
+__global__ void k_selftest_wait(unsigned *status, uint64_t limit_ns) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_wait_bounded(&bar, 0, status, limit_ns);
+}
+
+extern "C" int fw_selftest_wait_timeout(fw_ruleset *rs, int64_t limit_ns, void *stream) {
+    if (rs == nullptr || limit_ns < 1000 || limit_ns > 1000000000) return set_status(FW_EINVAL);
+    k_selftest_wait<<<1, 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>(rs->d_status, (uint64_t)limit_ns);
+    return set_status(cuda_status(cudaGetLastError()));
 }

@@ -43,6 +43,7 @@ MODES = {
 }
 FW_PRED_CLAMP = 1
 FW_PRED_CMP = 2
+FW_PRED_ARITH = 3
 FW_HOST_COPY = 1
 FW_HOST_ZEROCOPY = 2
 
@@ -62,7 +63,7 @@ class fw_config(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("smem_rules", ctypes.c_int32), ("packets_per_group", ctypes.c_int32),
                 ("rule_slices", ctypes.c_int32), ("compact", ctypes.c_int32), ("predicate", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("segment_rules", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
 def make_config(mode=FW_MODE_AUTO, **kw) -> fw_config:
@@ -94,6 +95,7 @@ SIGNATURES = {
     "fw_host_pipeline_destroy": (None, [P]),
     "fw_classify_host": (ctypes.c_int, [P, P, ctypes.POINTER(fw_headers), I64, P, P, ctypes.c_int,
                                         ctypes.POINTER(fw_config)]),
+    "fw_selftest_wait_timeout": (ctypes.c_int, [P, I64, P]),
     "fw_last_status": (ctypes.c_int, []),
     "fw_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "fw_abi_version": (ctypes.c_int, []),
@@ -135,10 +137,16 @@ def _check(s: int, what: str):
 
 
 def _as_rules(rules) -> np.ndarray:
+    """Copy rules field by field into a zeroed 24-byte-record array.
+
+    numpy leaves the padding bytes of structured copies (fancy indexing,
+    concatenate) uninitialised; the library rejects non-zero reserved bytes.
+    """
     rules = np.asarray(rules)
-    if rules.dtype != RULE_DTYPE:
-        rules = rules.astype(RULE_DTYPE)
-    return np.ascontiguousarray(rules)
+    out = np.zeros(rules.shape[0], dtype=RULE_DTYPE)
+    for f in RULE_DTYPE.names:
+        out[f] = rules[f]
+    return out
 
 
 class Ruleset:

@@ -18,9 +18,14 @@ THREADS = os.cpu_count() or 1
 CONFIGS = [
     ("packet_split", {}),
     ("packet_split", {"predicate": fw.FW_PRED_CMP}),
-    ("packet_split", {"smem_rules": -1}),
-    ("packet_split", {"smem_rules": 256}),
-    ("packet_split", {"block_threads": 96, "blocks_per_sm": 1, "smem_rules": 512, "predicate": fw.FW_PRED_CMP}),
+    ("packet_split", {"predicate": fw.FW_PRED_CLAMP}),
+    ("packet_split", {"smem_rules": -1, "segment_rules": 8}),
+    ("packet_split", {"smem_rules": 256, "segment_rules": 4, "packets_per_group": 256, "block_threads": 512,
+                      "blocks_per_sm": 2}),
+    ("packet_split", {"compact": 2}),
+    ("packet_split", {"compact": 2, "predicate": fw.FW_PRED_CLAMP}),
+    ("packet_split", {"compact": 2, "smem_rules": -1, "predicate": fw.FW_PRED_CMP}),
+    ("packet_split", {"compact": 2, "block_threads": 96, "blocks_per_sm": 1, "smem_rules": 512}),
     ("rule_split_warp", {}),
     ("rule_split_warp", {"packets_per_group": 32, "block_threads": 64}),
     ("rule_split_block", {}),
@@ -94,7 +99,8 @@ def test_sizes_no_catch_all(torch_cuda, mode, kw, n_rules, n_pkts):
     assert_same(run_gpu(torch_cuda, rules, hdr, mode, kw), want, f"{mode} {n_rules}x{n_pkts}")
 
 
-@pytest.mark.parametrize("mode,kw", CONFIGS[:1] + CONFIGS[5:6] + CONFIGS[9:10], ids=["ps", "rsw", "rsg"])
+@pytest.mark.parametrize("mode,kw", [("packet_split", {}), ("packet_split", {"compact": 2}), ("rule_split_warp", {}),
+                                     ("rule_split_grid", {})], ids=["ps", "ps_lockstep", "rsw", "rsg"])
 @pytest.mark.parametrize("offset", [1, 2, 3])
 def test_misaligned_buffers(torch_cuda, mode, kw, offset):
     rules = no_catch_all(W.gen_rules(700, 5))
@@ -111,8 +117,9 @@ def test_golden_policy_on_gpu(torch_cuda, mode, kw):
     assert [(int(a), int(b)) for a, b in zip(gi, ga)] == expect
 
 
-@pytest.mark.parametrize("mode,kw", CONFIGS[:2] + CONFIGS[5:6] + CONFIGS[7:8] + CONFIGS[9:10],
-                         ids=["ps", "ps_cmp", "rsw", "rsb", "rsg"])
+@pytest.mark.parametrize("mode,kw", [("packet_split", {}), ("packet_split", {"compact": 2, "predicate": 2}),
+                                     ("rule_split_warp", {}), ("rule_split_block", {}), ("rule_split_grid", {})],
+                         ids=["ps", "ps_lockstep_cmp", "rsw", "rsb", "rsg"])
 def test_special_rule_sets(torch_cuda, mode, kw):
     import oracle_pins as P
     rng = np.random.default_rng(3)
@@ -157,9 +164,10 @@ def big(torch_cuda):
     return rules, hdr, fw.headers_to_device(hdr), want, pos
 
 
-@pytest.mark.parametrize("mode,kw", [("packet_split", {}), ("packet_split", {"predicate": fw.FW_PRED_CMP}),
+@pytest.mark.parametrize("mode,kw", [("packet_split", {}), ("packet_split", {"compact": 2}),
+                                     ("packet_split", {"compact": 2, "predicate": fw.FW_PRED_CLAMP}),
                                      ("rule_split_warp", {}), ("rule_split_block", {}), ("rule_split_grid", {})],
-                         ids=["ps", "ps_cmp", "rsw", "rsb", "rsg"])
+                         ids=["ps", "ps_lockstep", "ps_lockstep_clamp", "rsw", "rsb", "rsg"])
 def test_scan_10k_x_16m_sampled(torch_cuda, big, mode, kw):
     torch = torch_cuda
     rules, hdr, dh, want, pos = big
