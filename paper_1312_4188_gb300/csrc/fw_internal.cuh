@@ -39,8 +39,9 @@ struct RecCmp {
     uint4 c;  // pval, pmask, 0, 0
 };
 
-// Arithmetic-form record: 48 bytes = three uint4, of which c.y..c.w are unused.
-// The port tests are written as unsigned subtractions that the FMA pipe can
+// Arithmetic-form record: 32 bytes = two uint4, plus one word `wtop` per rule
+// kept in a separate array (so that four rules' wtop words come in one 16-byte
+// load). The port tests are written as unsigned subtractions that the FMA pipe can
 // execute (IMAD), leaving only logic ops and compares on the ALU pipe:
 //   sport:        (sport + neg_slo) <= swidth            (neg_slo = -slo mod 2^32)
 //   dport, proto: (X * mul + add) <= wtop, X = proto << 17 | dport, where
@@ -54,7 +55,6 @@ struct RecCmp {
 struct RecArith {
     uint4 a;  // saddr, smask, daddr, dmask
     uint4 b;  // neg_slo, swidth, mul, add
-    uint4 c;  // wtop, 0, 0, 0
 };
 
 // A record that no packet matches (used to pad the device arrays): its
@@ -89,9 +89,33 @@ __device__ __forceinline__ uint32_t x_of(uint32_t proto, uint32_t dport) { retur
 
 // True exactly when the packet is outside the rule (arithmetic form). `one`
 // is the runtime constant 1, so that the sport subtraction is issued as a
-// multiply-add on the FMA pipe instead of an add on the ALU pipe.
+// multiply-add on the FMA pipe instead of an add on the ALU pipe. The five
+// field tests are one chain of predicated ALU operations: two 3-input logic
+// ops (lop3 with LUT 0x28 = (a ^ b) & c) whose "result != 0" predicate is
+// OR-ed into the chain, then two unsigned compares OR-ed into it.
 __device__ __forceinline__ bool mismatch_arith(const PktA &p, const uint4 &a, const uint4 &b, uint32_t wtop,
                                                uint32_t one) {
+    const uint32_t ts = p.sport * one + b.x;
+    const uint32_t td = p.x * b.z + b.w;
+    uint32_t r;
+    asm("{\n\t"
+        ".reg .pred q;\n\t"
+        ".reg .b32 t;\n\t"
+        "setp.ne.u32 q, 0, 0;\n\t"
+        "lop3.or.b32 t|q, %1, %2, %3, 0x28, q;\n\t"
+        "lop3.or.b32 t|q, %4, %5, %6, 0x28, q;\n\t"
+        "setp.gt.or.u32 q, %7, %8, q;\n\t"
+        "setp.gt.or.u32 q, %9, %10, q;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t"
+        "}"
+        : "=r"(r)
+        : "r"(p.src), "r"(a.x), "r"(a.y), "r"(p.dst), "r"(a.z), "r"(a.w), "r"(ts), "r"(b.y), "r"(td), "r"(wtop));
+    return r != 0u;
+}
+
+// Plain C++ statement of the same test (used where the chained form is not needed).
+__device__ __forceinline__ bool mismatch_arith_c(const PktA &p, const uint4 &a, const uint4 &b, uint32_t wtop,
+                                                 uint32_t one) {
     const uint32_t ts = p.sport * one + b.x;
     const uint32_t td = p.x * b.z + b.w;
     return (((p.src ^ a.x) & a.y) != 0u) | (((p.dst ^ a.z) & a.w) != 0u) | (ts > b.y) | (td > wtop);
@@ -170,6 +194,7 @@ struct fw_ruleset {
     fwk::RecClamp *d_clamp;   // n_pad records
     fwk::RecCmp *d_cmp;       // n_pad records
     fwk::RecArith *d_arith;   // n_pad records
+    uint32_t *d_wtop;         // n_pad words (arithmetic form)
     uint8_t *d_action;        // n_pad actions
     unsigned *d_status;       // device error flags (kStatus*)
 };

@@ -44,7 +44,7 @@ static int validate(const fw_rule &r) {
     return FW_OK;
 }
 
-static void canon_arith(const fw_rule &r, RecArith *q) {
+static void canon_arith(const fw_rule &r, RecArith *q, uint32_t *wt) {
     uint32_t sm = prefix_mask(r.src_prefix), dm = prefix_mask(r.dst_prefix);
     q->a = make_uint4(r.src_addr & sm, sm, r.dst_addr & dm, dm);
     const uint32_t dw = uint32_t(r.dport_hi) - r.dport_lo;
@@ -59,14 +59,14 @@ static void canon_arith(const fw_rule &r, RecArith *q) {
         wtop = dw;
     }
     q->b = make_uint4(0u - uint32_t(r.sport_lo), uint32_t(r.sport_hi) - r.sport_lo, mul, add);
-    q->c = make_uint4(wtop, 0u, 0u, 0u);
+    *wt = wtop;
 }
 
-static void never_match_arith(RecArith *q) {
+static void never_match_arith(RecArith *q, uint32_t *wt) {
     q->a = make_uint4(0, 0, 0, 0);
     // exact protocol 0x100: no 8-bit protocol reaches the window
     q->b = make_uint4(0u, 0xFFFFFFFFu, 1u, 0u - (kNeverProto << 17));
-    q->c = make_uint4(0u, 0u, 0u, 0u);
+    *wt = 0u;
 }
 
 static void canon(const fw_rule &r, RecClamp *c, RecCmp *m) {
@@ -114,26 +114,29 @@ extern "C" int fw_ruleset_create_ex(const fw_rule *rules, int64_t n, fw_ruleset 
     std::vector<RecClamp> hc(rs->n_pad);
     std::vector<RecCmp> hm(rs->n_pad);
     std::vector<RecArith> hq(rs->n_pad);
+    std::vector<uint32_t> hw(rs->n_pad);
     std::vector<uint8_t> ha(rs->n_pad, FW_DROP);
     for (int64_t k = 0; k < rs->n_pad; ++k) {
         if (k < rs->n_eff) {
             canon(rules[k], &hc[k], &hm[k]);
-            canon_arith(rules[k], &hq[k]);
+            canon_arith(rules[k], &hq[k], &hw[k]);
             ha[k] = rules[k].action;
         } else {
             never_match(&hc[k], &hm[k]);
-            never_match_arith(&hq[k]);
+            never_match_arith(&hq[k], &hw[k]);
         }
     }
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMalloc(&rs->d_clamp, rs->n_pad * sizeof(RecClamp));
     if (e == cudaSuccess) e = cudaMalloc(&rs->d_cmp, rs->n_pad * sizeof(RecCmp));
     if (e == cudaSuccess) e = cudaMalloc(&rs->d_arith, rs->n_pad * sizeof(RecArith));
+    if (e == cudaSuccess) e = cudaMalloc(&rs->d_wtop, rs->n_pad * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&rs->d_action, rs->n_pad);
     if (e == cudaSuccess) e = cudaMalloc(&rs->d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemcpy(rs->d_clamp, hc.data(), rs->n_pad * sizeof(RecClamp), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(rs->d_cmp, hm.data(), rs->n_pad * sizeof(RecCmp), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(rs->d_arith, hq.data(), rs->n_pad * sizeof(RecArith), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(rs->d_wtop, hw.data(), rs->n_pad * sizeof(uint32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(rs->d_action, ha.data(), rs->n_pad, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(rs->d_status, 0, sizeof(unsigned));
     if (e != cudaSuccess) {
@@ -156,6 +159,7 @@ extern "C" void fw_ruleset_destroy(fw_ruleset *rs) {
     if (rs->d_clamp) cudaFree(rs->d_clamp);
     if (rs->d_cmp) cudaFree(rs->d_cmp);
     if (rs->d_arith) cudaFree(rs->d_arith);
+    if (rs->d_wtop) cudaFree(rs->d_wtop);
     if (rs->d_action) cudaFree(rs->d_action);
     if (rs->d_status) cudaFree(rs->d_status);
     delete rs;

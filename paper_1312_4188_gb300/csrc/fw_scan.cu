@@ -36,6 +36,7 @@ struct HdrPtrs {
 
 struct ScanParams {
     const void *rec;       // records of the chosen form (RecClamp / RecCmp / RecArith)
+    const uint32_t *wtop;  // arithmetic form: per-rule wtop words
     const uint8_t *action;
     int n_scan;   // rules scanned: n_eff rounded up to a multiple of 4 (padding never matches)
     int n_smem;   // rules resident in shared memory (multiple of kChunkRules, <= n_pad)
@@ -50,18 +51,41 @@ struct ScanParams {
 };
 
 // ------------------------------------------------------------ record policies
-// How a record form is fetched and tested, and how a packet is held.
+// How a record form is laid out, fetched and tested, and how a packet is held.
+// A View locates the records of rules [0, n) either in global memory or in
+// the block's shared-memory prefix (same layout in both).
 struct PolClamp {
     using Rec = RecClamp;
     using Pk = Pkt;
     struct R {
         uint4 a, b;
     };
+    struct View {
+        const Rec *rec;
+    };
+    static __host__ __device__ size_t bytes_per_rule() { return sizeof(Rec); }
+    static __device__ __forceinline__ View global_view(const ScanParams &p) {
+        return {reinterpret_cast<const Rec *>(p.rec)};
+    }
+    static __device__ __forceinline__ View smem_view(unsigned char *sm, int) { return {reinterpret_cast<const Rec *>(sm)}; }
+    // chunk c of the shared prefix: one bulk copy of kChunkRules records
+    static __device__ __forceinline__ uint32_t stage(unsigned char *sm, int, const ScanParams &p, int c, uint64_t *bar) {
+        const uint32_t bytes = kChunkRules * sizeof(Rec);
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_load(sm + (size_t)c * bytes, reinterpret_cast<const unsigned char *>(p.rec) + (size_t)c * bytes, bytes, bar);
+        return bytes;
+    }
+    template <bool SMEM>
+    static __device__ __forceinline__ void load4(const View &v, int k, R r[4]) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (SMEM) r[j] = {v.rec[k + j].a, v.rec[k + j].b};
+            else r[j] = {__ldg(&v.rec[k + j].a), __ldg(&v.rec[k + j].b)};
+        }
+    }
     static __device__ __forceinline__ Pk make(uint32_t s, uint32_t d, uint32_t sp, uint32_t dp, uint32_t pr) {
         return {s, d, ports_of(sp, dp), pr};
     }
-    static __device__ __forceinline__ R lds(const Rec *r) { return {r->a, r->b}; }
-    static __device__ __forceinline__ R ldg(const Rec *r) { return {__ldg(&r->a), __ldg(&r->b)}; }
     static __device__ __forceinline__ bool mism(const Pk &p, const R &r, uint32_t) {
         return mismatch_clamp(p, r.a, r.b) != 0u;
     }
@@ -81,11 +105,31 @@ struct PolCmp {
     struct R {
         uint4 a, b, c;
     };
+    struct View {
+        const Rec *rec;
+    };
+    static __host__ __device__ size_t bytes_per_rule() { return sizeof(Rec); }
+    static __device__ __forceinline__ View global_view(const ScanParams &p) {
+        return {reinterpret_cast<const Rec *>(p.rec)};
+    }
+    static __device__ __forceinline__ View smem_view(unsigned char *sm, int) { return {reinterpret_cast<const Rec *>(sm)}; }
+    static __device__ __forceinline__ uint32_t stage(unsigned char *sm, int, const ScanParams &p, int c, uint64_t *bar) {
+        const uint32_t bytes = kChunkRules * sizeof(Rec);
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_load(sm + (size_t)c * bytes, reinterpret_cast<const unsigned char *>(p.rec) + (size_t)c * bytes, bytes, bar);
+        return bytes;
+    }
+    template <bool SMEM>
+    static __device__ __forceinline__ void load4(const View &v, int k, R r[4]) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (SMEM) r[j] = {v.rec[k + j].a, v.rec[k + j].b, v.rec[k + j].c};
+            else r[j] = {__ldg(&v.rec[k + j].a), __ldg(&v.rec[k + j].b), __ldg(&v.rec[k + j].c)};
+        }
+    }
     static __device__ __forceinline__ Pk make(uint32_t s, uint32_t d, uint32_t sp, uint32_t dp, uint32_t pr) {
         return {s, d, ports_of(sp, dp), pr};
     }
-    static __device__ __forceinline__ R lds(const Rec *r) { return {r->a, r->b, r->c}; }
-    static __device__ __forceinline__ R ldg(const Rec *r) { return {__ldg(&r->a), __ldg(&r->b), __ldg(&r->c)}; }
     static __device__ __forceinline__ bool mism(const Pk &p, const R &r, uint32_t) {
         return !match_cmp(p, r.a, r.b, r.c);
     }
@@ -100,11 +144,49 @@ struct PolArith {
         uint4 a, b;
         uint32_t w;
     };
+    struct View {
+        const Rec *rec;
+        const uint32_t *wtop;
+    };
+    static __host__ __device__ size_t bytes_per_rule() { return sizeof(Rec) + sizeof(uint32_t); }
+    static __device__ __forceinline__ View global_view(const ScanParams &p) {
+        return {reinterpret_cast<const Rec *>(p.rec), p.wtop};
+    }
+    // shared layout: [n_smem records][n_smem wtop words]
+    static __device__ __forceinline__ View smem_view(unsigned char *sm, int n_smem) {
+        return {reinterpret_cast<const Rec *>(sm), reinterpret_cast<const uint32_t *>(sm + (size_t)n_smem * sizeof(Rec))};
+    }
+    static __device__ __forceinline__ uint32_t stage(unsigned char *sm, int n_smem, const ScanParams &p, int c,
+                                                     uint64_t *bar) {
+        const uint32_t rb = kChunkRules * sizeof(Rec), wb = kChunkRules * sizeof(uint32_t);
+        mbar_arrive_expect_tx(bar, rb + wb);
+        bulk_load(sm + (size_t)c * rb, reinterpret_cast<const unsigned char *>(p.rec) + (size_t)c * rb, rb, bar);
+        bulk_load(sm + (size_t)n_smem * sizeof(Rec) + (size_t)c * wb,
+                  reinterpret_cast<const unsigned char *>(p.wtop) + (size_t)c * wb, wb, bar);
+        return rb + wb;
+    }
+    template <bool SMEM>
+    static __device__ __forceinline__ void load4(const View &v, int k, R r[4]) {
+        const uint4 w = SMEM ? *reinterpret_cast<const uint4 *>(v.wtop + k)
+                             : __ldg(reinterpret_cast<const uint4 *>(v.wtop + k));
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (SMEM) {
+                r[j].a = v.rec[k + j].a;
+                r[j].b = v.rec[k + j].b;
+            } else {
+                r[j].a = __ldg(&v.rec[k + j].a);
+                r[j].b = __ldg(&v.rec[k + j].b);
+            }
+        }
+        r[0].w = w.x;
+        r[1].w = w.y;
+        r[2].w = w.z;
+        r[3].w = w.w;
+    }
     static __device__ __forceinline__ Pk make(uint32_t s, uint32_t d, uint32_t sp, uint32_t dp, uint32_t pr) {
         return {s, d, sp, x_of(pr, dp)};
     }
-    static __device__ __forceinline__ R lds(const Rec *r) { return {r->a, r->b, r->c.x}; }
-    static __device__ __forceinline__ R ldg(const Rec *r) { return {__ldg(&r->a), __ldg(&r->b), __ldg(&r->c.x)}; }
     static __device__ __forceinline__ bool mism(const Pk &p, const R &r, uint32_t one) {
         return mismatch_arith(p, r.a, r.b, r.w, one);
     }
@@ -170,10 +252,20 @@ __device__ __forceinline__ void store_quad(const ScanParams &p, int64_t q, const
 // First index in [k0, k1) whose rule matches, or -1 (k0, k1 multiples of 4).
 // Rules below n_smem come from shared memory (chunk c usable once bars[c]
 // completed), the rest from global memory. Returns -2 if a chunk wait timed out.
+template <class Pol, bool SMEM>
+__device__ __forceinline__ int scan_block4(const typename Pol::Pk &pk, const typename Pol::View &v, int k,
+                                           uint32_t one) {
+    typename Pol::R r[4];
+    Pol::template load4<SMEM>(v, k, r);
+    const bool m0 = Pol::mism(pk, r[0], one), m1 = Pol::mism(pk, r[1], one);
+    const bool m2 = Pol::mism(pk, r[2], one), m3 = Pol::mism(pk, r[3], one);
+    if (m0 & m1 & m2 & m3) return -1;
+    return k + (!m0 ? 0 : !m1 ? 1 : !m2 ? 2 : 3);
+}
+
 template <class Pol>
-__device__ __forceinline__ int scan_range(const typename Pol::Pk &pk, int k0, int k1,
-                                          const typename Pol::Rec *__restrict__ sm, int n_smem,
-                                          const typename Pol::Rec *__restrict__ gm, uint64_t *bars, unsigned *status,
+__device__ __forceinline__ int scan_range(const typename Pol::Pk &pk, int k0, int k1, const typename Pol::View &sv,
+                                          int n_smem, const typename Pol::View &gv, uint64_t *bars, unsigned *status,
                                           uint32_t one) {
     int k = k0;
     const int lim = min(k1, n_smem);
@@ -181,42 +273,29 @@ __device__ __forceinline__ int scan_range(const typename Pol::Pk &pk, int k0, in
         if (!mbar_wait_bounded(&bars[k / kChunkRules], 0, status)) return -2;
         const int kend = min(lim, (k / kChunkRules + 1) * kChunkRules);
         for (; k < kend; k += 4) {
-            const typename Pol::R r0 = Pol::lds(sm + k), r1 = Pol::lds(sm + k + 1);
-            const typename Pol::R r2 = Pol::lds(sm + k + 2), r3 = Pol::lds(sm + k + 3);
-            const bool m0 = Pol::mism(pk, r0, one), m1 = Pol::mism(pk, r1, one);
-            const bool m2 = Pol::mism(pk, r2, one), m3 = Pol::mism(pk, r3, one);
-            if (!(m0 & m1 & m2 & m3)) return k + (!m0 ? 0 : !m1 ? 1 : !m2 ? 2 : 3);
+            const int r = scan_block4<Pol, true>(pk, sv, k, one);
+            if (r >= 0) return r;
         }
     }
     for (; k < k1; k += 4) {
-        const typename Pol::R r0 = Pol::ldg(gm + k), r1 = Pol::ldg(gm + k + 1);
-        const typename Pol::R r2 = Pol::ldg(gm + k + 2), r3 = Pol::ldg(gm + k + 3);
-        const bool m0 = Pol::mism(pk, r0, one), m1 = Pol::mism(pk, r1, one);
-        const bool m2 = Pol::mism(pk, r2, one), m3 = Pol::mism(pk, r3, one);
-        if (!(m0 & m1 & m2 & m3)) return k + (!m0 ? 0 : !m1 ? 1 : !m2 ? 2 : 3);
+        const int r = scan_block4<Pol, false>(pk, gv, k, one);
+        if (r >= 0) return r;
     }
     return -1;
 }
 
-// Shared-memory rule prefix: mbarrier init + TMA bulk copies, one per chunk.
+// Shared-memory rule prefix: mbarrier init + TMA bulk copies, one barrier per chunk.
 template <class Pol>
 __device__ __forceinline__ uint64_t *stage_rules(unsigned char *smem, const ScanParams &p) {
-    const int rec_bytes = (int)sizeof(typename Pol::Rec);
     const int n_chunks = p.n_smem / kChunkRules;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)p.n_smem * rec_bytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)p.n_smem * Pol::bytes_per_rule());
     if (threadIdx.x == 0) {
         for (int c = 0; c < n_chunks; ++c) mbar_init(&bars[c], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned char *src = reinterpret_cast<const unsigned char *>(p.rec);
-        const uint32_t bytes = kChunkRules * rec_bytes;
-        for (int c = 0; c < n_chunks; ++c) {
-            mbar_arrive_expect_tx(&bars[c], bytes);
-            bulk_load(smem + (size_t)c * bytes, src + (size_t)c * bytes, bytes, &bars[c]);
-        }
-    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < n_chunks; ++c) Pol::stage(smem, p.n_smem, p, c, &bars[c]);
     return bars;
 }
 
@@ -232,10 +311,9 @@ __device__ __forceinline__ void drain_rules(uint64_t *bars, int n_smem, unsigned
 template <class Pol, bool VEC>
 __global__ void __launch_bounds__(1024) k_packet_split(ScanParams p) {
     extern __shared__ __align__(128) unsigned char smem[];
-    using Rec = typename Pol::Rec;
     uint64_t *bars = stage_rules<Pol>(smem, p);
-    const Rec *sm = reinterpret_cast<const Rec *>(smem);
-    const Rec *gm = reinterpret_cast<const Rec *>(p.rec);
+    const typename Pol::View sv = Pol::smem_view(smem, p.n_smem);
+    const typename Pol::View gv = Pol::global_view(p);
     const int64_t nq = (p.n + 3) / 4;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += stride) {
@@ -245,7 +323,7 @@ __global__ void __launch_bounds__(1024) k_packet_split(ScanParams p) {
         int idx[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int r = scan_range<Pol>(pk[j], 0, p.n_scan, sm, p.n_smem, gm, bars, p.status, p.one);
+            const int r = scan_range<Pol>(pk[j], 0, p.n_scan, sv, p.n_smem, gv, bars, p.status, p.one);
             idx[j] = r < 0 ? -1 : r;
         }
         store_quad<VEC>(p, q, idx, cnt);
@@ -263,13 +341,12 @@ __global__ void __launch_bounds__(1024) k_packet_split(ScanParams p) {
 template <class Pol, bool VEC>
 __global__ void __launch_bounds__(1024) k_packet_split_compact(ScanParams p) {
     extern __shared__ __align__(128) unsigned char smem[];
-    using Rec = typename Pol::Rec;
     uint64_t *bars = stage_rules<Pol>(smem, p);
-    const Rec *sm = reinterpret_cast<const Rec *>(smem);
-    const Rec *gm = reinterpret_cast<const Rec *>(p.rec);
+    const typename Pol::View sv = Pol::smem_view(smem, p.n_smem);
+    const typename Pol::View gv = Pol::global_view(p);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int B = p.batch;
-    const size_t qoff = ((size_t)p.n_smem * sizeof(Rec) + (size_t)(p.n_smem / kChunkRules) * 8 + 15) / 16 * 16;
+    const size_t qoff = ((size_t)p.n_smem * Pol::bytes_per_rule() + (size_t)(p.n_smem / kChunkRules) * 8 + 15) / 16 * 16;
     uint4 *Q = reinterpret_cast<uint4 *>(smem + qoff) + (size_t)warp * B;
     const int64_t nb = (p.n + B - 1) / B;
     for (int64_t b = (int64_t)blockIdx.x * nw + warp; b < nb; b += (int64_t)gridDim.x * nw) {
@@ -297,7 +374,7 @@ __global__ void __launch_bounds__(1024) k_packet_split_compact(ScanParams p) {
                 int slot;
                 const typename Pol::Pk pk = Pol::unpack(e, slot);
                 int r = -1;
-                if (valid && s0 < s1) r = scan_range<Pol>(pk, s0, s1, sm, p.n_smem, gm, bars, p.status, p.one);
+                if (valid && s0 < s1) r = scan_range<Pol>(pk, s0, s1, sv, p.n_smem, gv, bars, p.status, p.one);
                 const bool keep = valid && r == -1 && !last;
                 if (valid && !keep) {
                     const int v = r >= 0 ? r : -1;
@@ -332,6 +409,7 @@ struct SplitParams {
 };
 
 constexpr int kNoMatch = 0x7F7F7F7F;  // byte-fill sentinel, larger than any rule index
+constexpr int64_t kCompactMinPackets = int64_t(1) << 20;  // default packet split compacts from this batch size
 
 // BLOCK = true: all warps of the block share one packet group and split its
 // chunks round-robin. BLOCK = false: each warp owns a packet group alone.
@@ -442,7 +520,6 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
                         cudaStream_t st, const fw_config &cfg) {
     ScanParams p;
     const int pred = cfg.predicate == 0 ? FW_PRED_ARITH : cfg.predicate;
-    const bool compact = cfg.compact != 2;
     int rec_bytes;
     if (pred == FW_PRED_CLAMP) {
         p.rec = rs->d_clamp;
@@ -452,14 +529,24 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
         rec_bytes = (int)sizeof(RecCmp);
     } else if (pred == FW_PRED_ARITH) {
         p.rec = rs->d_arith;
-        rec_bytes = (int)sizeof(RecArith);
+        rec_bytes = (int)PolArith::bytes_per_rule();
     } else {
         return FW_EINVAL;
     }
     if (cfg.compact < 0 || cfg.compact > 2) return FW_EINVAL;
+    // Default: compaction for large batches; small batches need every thread
+    // they can get, so they take the lockstep form with smaller blocks.
+    const bool compact = cfg.compact == 1 || (cfg.compact == 0 && n >= kCompactMinPackets);
+    p.wtop = rs->d_wtop;
     p.action = rs->d_action;
     p.n_scan = (int)((rs->n_eff + 3) / 4 * 4);
-    const int threads = cfg.block_threads > 0 ? cfg.block_threads : (compact ? 1024 : 512);
+    int threads = cfg.block_threads > 0 ? cfg.block_threads : (compact ? 1024 : 512);
+    if (cfg.block_threads <= 0 && !compact) {
+        // at least two blocks per SM when the batch allows it
+        const int64_t nq = (n + 3) / 4;
+        const int64_t t = nq / (2 * (int64_t)sm_count(rs->device)) / 32 * 32;
+        threads = (int)std::max<int64_t>(64, std::min<int64_t>(512, t));
+    }
     const int per_sm = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : (compact ? 1 : 2);
     if (threads % 32 != 0 || threads > 1024) return FW_EINVAL;
     int want = cfg.smem_rules > 0 ? cfg.smem_rules : (cfg.smem_rules < 0 ? 0 : (compact ? 2048 : 3072));
