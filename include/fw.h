@@ -100,6 +100,7 @@ typedef struct fw_headers {
 #define FW_PRED_CLAMP 1  /* port ranges as a 16x2 clamp, proto under a mask */
 #define FW_PRED_CMP   2  /* port ranges as unsigned subtract-and-compare */
 #define FW_PRED_ARITH 3  /* port ranges as multiply-add + compare, protocol folded into dport (default) */
+#define FW_PRED_RANGE 4  /* every field (prefixes too) as multiply-add + compare */
 
 /*
  * Launch configuration. Zero in any field means "library default".
@@ -113,7 +114,8 @@ typedef struct fw_headers {
  *  rule_slices:       number of rule slices across the grid (RULE_SPLIT_GRID).
  *  compact:           packet split only: 1 = re-pack undecided packets between
  *                     rule segments (default), 2 = plain lockstep scan.
- *  predicate:         FW_PRED_CLAMP, FW_PRED_CMP or FW_PRED_ARITH (0 = default).
+ *  predicate:         FW_PRED_CLAMP, FW_PRED_CMP, FW_PRED_ARITH or FW_PRED_RANGE
+ *                     (0 = default).
  *  segment_rules:     packet split with compaction: rules in the first segment
  *                     (multiple of 4; later segments double).
  */

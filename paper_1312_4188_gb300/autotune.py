@@ -19,7 +19,10 @@ import sys
 from . import fw
 
 PACKET_SPLIT_CANDIDATES = (
-    [dict(mode="packet_split", compact=2, predicate=p) for p in (fw.FW_PRED_CLAMP, fw.FW_PRED_CMP, fw.FW_PRED_ARITH)]
+    [dict(mode="packet_split", compact=2, predicate=p)
+     for p in (fw.FW_PRED_CLAMP, fw.FW_PRED_CMP, fw.FW_PRED_ARITH, fw.FW_PRED_RANGE)]
+    + [dict(mode="packet_split", compact=1, predicate=fw.FW_PRED_RANGE, block_threads=1024, blocks_per_sm=1,
+            smem_rules=sr, packets_per_group=256, segment_rules=s0) for sr in (1024, 2048) for s0 in (16, 32)]
     + [dict(mode="packet_split", compact=1, predicate=fw.FW_PRED_ARITH, block_threads=bt, blocks_per_sm=bps,
             smem_rules=sr, packets_per_group=b, segment_rules=s0)
        for (bt, bps, sr, b) in ((1024, 1, 2048, 256), (1024, 1, 2048, 128), (512, 2, 1024, 256), (768, 1, 2048, 256),

@@ -113,6 +113,55 @@ __device__ __forceinline__ bool mismatch_arith(const PktA &p, const uint4 &a, co
     return r != 0u;
 }
 
+// Range-form record (32 bytes + one word in a separate array, like RecArith):
+// every field test is "value - lo <= width" in unsigned 32-bit arithmetic, a
+// prefix /len being the range [addr & mask, (addr & mask) + ~mask]:
+//   a = {-src_lo, src_width, -dst_lo, dst_width}, b = {-sport_lo, swidth, mul, add},
+//   wtop as in RecArith. Four multiply-adds (FMA pipe) produce the offsets and
+//   four compares chained with .or (ALU pipe) give the mismatch predicate.
+using RecRange = RecArith;
+
+// Four rules at once, range form: non-zero exactly when the packet is outside
+// all four. t[4k..4k+3] are rule k's four offsets, w[...] the four widths.
+__device__ __forceinline__ uint32_t all_mismatch4_range(const uint32_t t[16], const uint32_t w[16]) {
+    uint32_t r;
+    asm("{\n\t"
+        ".reg .pred q0, q1, q2, q3;\n\t"
+        "setp.gt.u32 q0, %1, %2;\n\t"
+        "setp.gt.or.u32 q0, %3, %4, q0;\n\t"
+        "setp.gt.or.u32 q0, %5, %6, q0;\n\t"
+        "setp.gt.or.u32 q0, %7, %8, q0;\n\t"
+        "setp.gt.u32 q1, %9, %10;\n\t"
+        "setp.gt.or.u32 q1, %11, %12, q1;\n\t"
+        "setp.gt.or.u32 q1, %13, %14, q1;\n\t"
+        "setp.gt.or.u32 q1, %15, %16, q1;\n\t"
+        "setp.gt.u32 q2, %17, %18;\n\t"
+        "setp.gt.or.u32 q2, %19, %20, q2;\n\t"
+        "setp.gt.or.u32 q2, %21, %22, q2;\n\t"
+        "setp.gt.or.u32 q2, %23, %24, q2;\n\t"
+        "setp.gt.u32 q3, %25, %26;\n\t"
+        "setp.gt.or.u32 q3, %27, %28, q3;\n\t"
+        "setp.gt.or.u32 q3, %29, %30, q3;\n\t"
+        "setp.gt.or.u32 q3, %31, %32, q3;\n\t"
+        "and.pred q0, q0, q1;\n\t"
+        "and.pred q2, q2, q3;\n\t"
+        "and.pred q0, q0, q2;\n\t"
+        "selp.u32 %0, 1, 0, q0;\n\t"
+        "}"
+        : "=r"(r)
+        : "r"(t[0]), "r"(w[0]), "r"(t[1]), "r"(w[1]), "r"(t[2]), "r"(w[2]), "r"(t[3]), "r"(w[3]),
+          "r"(t[4]), "r"(w[4]), "r"(t[5]), "r"(w[5]), "r"(t[6]), "r"(w[6]), "r"(t[7]), "r"(w[7]),
+          "r"(t[8]), "r"(w[8]), "r"(t[9]), "r"(w[9]), "r"(t[10]), "r"(w[10]), "r"(t[11]), "r"(w[11]),
+          "r"(t[12]), "r"(w[12]), "r"(t[13]), "r"(w[13]), "r"(t[14]), "r"(w[14]), "r"(t[15]), "r"(w[15]));
+    return r;
+}
+
+__device__ __forceinline__ bool mismatch_range_c(const PktA &p, const uint4 &a, const uint4 &b, uint32_t wtop,
+                                                 uint32_t one) {
+    return ((p.src * one + a.x) > a.y) | ((p.dst * one + a.z) > a.w) | ((p.sport * one + b.x) > b.y) |
+           ((p.x * b.z + b.w) > wtop);
+}
+
 // Plain C++ statement of the same test (used where the chained form is not needed).
 __device__ __forceinline__ bool mismatch_arith_c(const PktA &p, const uint4 &a, const uint4 &b, uint32_t wtop,
                                                  uint32_t one) {
@@ -195,6 +244,8 @@ struct fw_ruleset {
     fwk::RecCmp *d_cmp;       // n_pad records
     fwk::RecArith *d_arith;   // n_pad records
     uint32_t *d_wtop;         // n_pad words (arithmetic form)
+    fwk::RecArith *d_range;   // n_pad records (range form)
+    uint32_t *d_range_wtop;   // n_pad words (range form)
     uint8_t *d_action;        // n_pad actions
     unsigned *d_status;       // device error flags (kStatus*)
 };

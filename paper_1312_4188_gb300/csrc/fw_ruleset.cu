@@ -62,6 +62,13 @@ static void canon_arith(const fw_rule &r, RecArith *q, uint32_t *wt) {
     *wt = wtop;
 }
 
+static void canon_range(const fw_rule &r, RecRange *q, uint32_t *wt) {
+    canon_arith(r, q, wt);  // ports and protocol as in the arithmetic form
+    uint32_t sm = prefix_mask(r.src_prefix), dm = prefix_mask(r.dst_prefix);
+    const uint32_t slo = r.src_addr & sm, dlo = r.dst_addr & dm;
+    q->a = make_uint4(0u - slo, ~sm, 0u - dlo, ~dm);
+}
+
 static void never_match_arith(RecArith *q, uint32_t *wt) {
     q->a = make_uint4(0, 0, 0, 0);
     // exact protocol 0x100: no 8-bit protocol reaches the window
@@ -115,15 +122,20 @@ extern "C" int fw_ruleset_create_ex(const fw_rule *rules, int64_t n, fw_ruleset 
     std::vector<RecCmp> hm(rs->n_pad);
     std::vector<RecArith> hq(rs->n_pad);
     std::vector<uint32_t> hw(rs->n_pad);
+    std::vector<RecRange> hr(rs->n_pad);
+    std::vector<uint32_t> hrw(rs->n_pad);
     std::vector<uint8_t> ha(rs->n_pad, FW_DROP);
     for (int64_t k = 0; k < rs->n_pad; ++k) {
         if (k < rs->n_eff) {
             canon(rules[k], &hc[k], &hm[k]);
             canon_arith(rules[k], &hq[k], &hw[k]);
+            canon_range(rules[k], &hr[k], &hrw[k]);
             ha[k] = rules[k].action;
         } else {
             never_match(&hc[k], &hm[k]);
             never_match_arith(&hq[k], &hw[k]);
+            never_match_arith(&hr[k], &hrw[k]);
+            hr[k].a = make_uint4(0u, 0xFFFFFFFFu, 0u, 0xFFFFFFFFu);
         }
     }
     cudaError_t e = cudaSuccess;
@@ -131,12 +143,17 @@ extern "C" int fw_ruleset_create_ex(const fw_rule *rules, int64_t n, fw_ruleset 
     if (e == cudaSuccess) e = cudaMalloc(&rs->d_cmp, rs->n_pad * sizeof(RecCmp));
     if (e == cudaSuccess) e = cudaMalloc(&rs->d_arith, rs->n_pad * sizeof(RecArith));
     if (e == cudaSuccess) e = cudaMalloc(&rs->d_wtop, rs->n_pad * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&rs->d_range, rs->n_pad * sizeof(RecRange));
+    if (e == cudaSuccess) e = cudaMalloc(&rs->d_range_wtop, rs->n_pad * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&rs->d_action, rs->n_pad);
     if (e == cudaSuccess) e = cudaMalloc(&rs->d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemcpy(rs->d_clamp, hc.data(), rs->n_pad * sizeof(RecClamp), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(rs->d_cmp, hm.data(), rs->n_pad * sizeof(RecCmp), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(rs->d_arith, hq.data(), rs->n_pad * sizeof(RecArith), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(rs->d_wtop, hw.data(), rs->n_pad * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(rs->d_range, hr.data(), rs->n_pad * sizeof(RecRange), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(rs->d_range_wtop, hrw.data(), rs->n_pad * sizeof(uint32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(rs->d_action, ha.data(), rs->n_pad, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(rs->d_status, 0, sizeof(unsigned));
     if (e != cudaSuccess) {
@@ -160,6 +177,8 @@ extern "C" void fw_ruleset_destroy(fw_ruleset *rs) {
     if (rs->d_cmp) cudaFree(rs->d_cmp);
     if (rs->d_arith) cudaFree(rs->d_arith);
     if (rs->d_wtop) cudaFree(rs->d_wtop);
+    if (rs->d_range) cudaFree(rs->d_range);
+    if (rs->d_range_wtop) cudaFree(rs->d_range_wtop);
     if (rs->d_action) cudaFree(rs->d_action);
     if (rs->d_status) cudaFree(rs->d_status);
     delete rs;

@@ -89,6 +89,9 @@ struct PolClamp {
     static __device__ __forceinline__ bool mism(const Pk &p, const R &r, uint32_t) {
         return mismatch_clamp(p, r.a, r.b) != 0u;
     }
+    static __device__ __forceinline__ bool all_mismatch4(const Pk &p, const R r[4], uint32_t one) {
+        return mism(p, r[0], one) & mism(p, r[1], one) & mism(p, r[2], one) & mism(p, r[3], one);
+    }
     // queue entry: the packet with its batch slot above the protocol byte
     static __device__ __forceinline__ uint4 pack(const Pk &p, int slot) {
         return make_uint4(p.src, p.dst, p.ports, p.proto | ((uint32_t)slot << 8));
@@ -132,6 +135,9 @@ struct PolCmp {
     }
     static __device__ __forceinline__ bool mism(const Pk &p, const R &r, uint32_t) {
         return !match_cmp(p, r.a, r.b, r.c);
+    }
+    static __device__ __forceinline__ bool all_mismatch4(const Pk &p, const R r[4], uint32_t one) {
+        return mism(p, r[0], one) & mism(p, r[1], one) & mism(p, r[2], one) & mism(p, r[3], one);
     }
     static __device__ __forceinline__ uint4 pack(const Pk &p, int slot) { return PolClamp::pack(p, slot); }
     static __device__ __forceinline__ Pk unpack(const uint4 &e, int &slot) { return PolClamp::unpack(e, slot); }
@@ -190,6 +196,9 @@ struct PolArith {
     static __device__ __forceinline__ bool mism(const Pk &p, const R &r, uint32_t one) {
         return mismatch_arith(p, r.a, r.b, r.w, one);
     }
+    static __device__ __forceinline__ bool all_mismatch4(const Pk &p, const R r[4], uint32_t one) {
+        return mism(p, r[0], one) & mism(p, r[1], one) & mism(p, r[2], one) & mism(p, r[3], one);
+    }
     // queue entry: the batch slot above the 16-bit source port
     static __device__ __forceinline__ uint4 pack(const Pk &p, int slot) {
         return make_uint4(p.src, p.dst, p.sport | ((uint32_t)slot << 16), p.x);
@@ -197,6 +206,28 @@ struct PolArith {
     static __device__ __forceinline__ Pk unpack(const uint4 &e, int &slot) {
         slot = (int)(e.z >> 16);
         return {e.x, e.y, e.z & 0xFFFFu, e.w};
+    }
+};
+
+// Range form: the arithmetic-form layout with every field a range test.
+struct PolRange : PolArith {
+    static __device__ __forceinline__ bool mism(const Pk &p, const R &r, uint32_t one) {
+        return mismatch_range_c(p, r.a, r.b, r.w, one);
+    }
+    static __device__ __forceinline__ bool all_mismatch4(const Pk &p, const R r[4], uint32_t one) {
+        uint32_t t[16], w[16];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            t[4 * j + 0] = p.src * one + r[j].a.x;
+            w[4 * j + 0] = r[j].a.y;
+            t[4 * j + 1] = p.dst * one + r[j].a.z;
+            w[4 * j + 1] = r[j].a.w;
+            t[4 * j + 2] = p.sport * one + r[j].b.x;
+            w[4 * j + 2] = r[j].b.y;
+            t[4 * j + 3] = p.x * r[j].b.z + r[j].b.w;
+            w[4 * j + 3] = r[j].w;
+        }
+        return all_mismatch4_range(t, w) != 0u;
     }
 };
 
@@ -257,10 +288,9 @@ __device__ __forceinline__ int scan_block4(const typename Pol::Pk &pk, const typ
                                            uint32_t one) {
     typename Pol::R r[4];
     Pol::template load4<SMEM>(v, k, r);
-    const bool m0 = Pol::mism(pk, r[0], one), m1 = Pol::mism(pk, r[1], one);
-    const bool m2 = Pol::mism(pk, r[2], one), m3 = Pol::mism(pk, r[3], one);
-    if (m0 & m1 & m2 & m3) return -1;
-    return k + (!m0 ? 0 : !m1 ? 1 : !m2 ? 2 : 3);
+    if (Pol::all_mismatch4(pk, r, one)) return -1;
+    // once per decided packet: which of the four matched first
+    return k + (!Pol::mism(pk, r[0], one) ? 0 : !Pol::mism(pk, r[1], one) ? 1 : !Pol::mism(pk, r[2], one) ? 2 : 3);
 }
 
 template <class Pol>
@@ -530,6 +560,9 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
     } else if (pred == FW_PRED_ARITH) {
         p.rec = rs->d_arith;
         rec_bytes = (int)PolArith::bytes_per_rule();
+    } else if (pred == FW_PRED_RANGE) {
+        p.rec = rs->d_range;
+        rec_bytes = (int)PolRange::bytes_per_rule();
     } else {
         return FW_EINVAL;
     }
@@ -537,7 +570,7 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
     // Default: compaction for large batches; small batches need every thread
     // they can get, so they take the lockstep form with smaller blocks.
     const bool compact = cfg.compact == 1 || (cfg.compact == 0 && n >= kCompactMinPackets);
-    p.wtop = rs->d_wtop;
+    p.wtop = pred == FW_PRED_RANGE ? rs->d_range_wtop : rs->d_wtop;
     p.action = rs->d_action;
     p.n_scan = (int)((rs->n_eff + 3) / 4 * 4);
     int threads = cfg.block_threads > 0 ? cfg.block_threads : (compact ? 1024 : 512);
@@ -553,7 +586,7 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
     want = (want / kChunkRules) * kChunkRules;
     const int need = (int)((p.n_scan + kChunkRules - 1) / kChunkRules * kChunkRules);
     p.n_smem = std::min(want, need);
-    p.batch = cfg.packets_per_group > 0 ? cfg.packets_per_group : 128;
+    p.batch = cfg.packets_per_group > 0 ? cfg.packets_per_group : 256;
     if (compact && (p.batch % 128 != 0 || p.batch > 65536)) return FW_EINVAL;
     p.seg0 = cfg.segment_rules > 0 ? cfg.segment_rules : 16;
     if (p.seg0 % 4 != 0) return FW_EINVAL;
@@ -589,6 +622,8 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
             if (vec) FW_LAUNCH_PS(KER, PolClamp, true); else FW_LAUNCH_PS(KER, PolClamp, false); \
         } else if (pred == FW_PRED_CMP) {                                                    \
             if (vec) FW_LAUNCH_PS(KER, PolCmp, true); else FW_LAUNCH_PS(KER, PolCmp, false);     \
+        } else if (pred == FW_PRED_RANGE) {                                                  \
+            if (vec) FW_LAUNCH_PS(KER, PolRange, true); else FW_LAUNCH_PS(KER, PolRange, false); \
         } else {                                                                             \
             if (vec) FW_LAUNCH_PS(KER, PolArith, true); else FW_LAUNCH_PS(KER, PolArith, false); \
         }                                                                                    \

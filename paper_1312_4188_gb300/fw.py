@@ -44,6 +44,7 @@ MODES = {
 FW_PRED_CLAMP = 1
 FW_PRED_CMP = 2
 FW_PRED_ARITH = 3
+FW_PRED_RANGE = 4
 FW_HOST_COPY = 1
 FW_HOST_ZEROCOPY = 2
 

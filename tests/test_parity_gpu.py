@@ -19,6 +19,8 @@ CONFIGS = [
     ("packet_split", {}),
     ("packet_split", {"predicate": fw.FW_PRED_CMP}),
     ("packet_split", {"predicate": fw.FW_PRED_CLAMP}),
+    ("packet_split", {"predicate": fw.FW_PRED_RANGE}),
+    ("packet_split", {"predicate": fw.FW_PRED_RANGE, "compact": 2}),
     ("packet_split", {"smem_rules": -1, "segment_rules": 8}),
     ("packet_split", {"smem_rules": 256, "segment_rules": 4, "packets_per_group": 256, "block_threads": 512,
                       "blocks_per_sm": 2}),
@@ -166,8 +168,9 @@ def big(torch_cuda):
 
 @pytest.mark.parametrize("mode,kw", [("packet_split", {}), ("packet_split", {"compact": 2}),
                                      ("packet_split", {"compact": 2, "predicate": fw.FW_PRED_CLAMP}),
+                                     ("packet_split", {"predicate": fw.FW_PRED_RANGE}),
                                      ("rule_split_warp", {}), ("rule_split_block", {}), ("rule_split_grid", {})],
-                         ids=["ps", "ps_lockstep", "ps_lockstep_clamp", "rsw", "rsb", "rsg"])
+                         ids=["ps", "ps_lockstep", "ps_lockstep_clamp", "ps_range", "rsw", "rsb", "rsg"])
 def test_scan_10k_x_16m_sampled(torch_cuda, big, mode, kw):
     torch = torch_cuda
     rules, hdr, dh, want, pos = big
