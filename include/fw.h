@@ -226,6 +226,47 @@ void fw_host_pipeline_destroy(fw_host_pipeline *pl);
 int fw_classify_host(fw_host_pipeline *pl, const fw_ruleset *rs, const fw_headers *host_hdrs, int64_t n,
                      int32_t *out_rule_idx, uint8_t *out_action, int strategy, const fw_config *cfg);
 
+/* ------------------------------------------------------------ no allocation */
+/*
+ * Largest batch fw_classify_rule_split_noalloc accepts (packets). Its scratch
+ * is a fixed device array of this many int32 values (4 MiB) that every GPU
+ * which loads this library keeps until the process exits.
+ */
+#define FW_NOALLOC_MAX_PACKETS (1 << 20)
+
+/*
+ * The paper has no counterpart to this call; it exists for callers that must
+ * not allocate device memory while classifying. Examples: a packet path that
+ * cannot afford the implicit device synchronisation and latency of
+ * cudaMalloc/cudaFree, a service whose GPU memory footprint is fixed when it
+ * starts (every later allocation is refused or would compete with other
+ * tenants), or code that runs where the stream-ordered allocator has been
+ * disabled.
+ *
+ * Same result as fw_classify_ex with FW_MODE_RULE_SPLIT_GRID, but the
+ * per-packet partial minima live in a file-scope device array of
+ * FW_NOALLOC_MAX_PACKETS int32 values instead of a per-call allocation. No
+ * cudaMalloc, cudaFree or other allocating routine is called. The caller
+ * still passes the device headers and the two device output arrays.
+ *  - n > FW_NOALLOC_MAX_PACKETS: FW_ERANGE, nothing is launched.
+ *  - Other argument errors as fw_classify (FW_EINVAL); cfg may be NULL, and
+ *    only its rule_slices, packets_per_group and block_threads fields are
+ *    read (mode must be 0 or FW_MODE_RULE_SPLIT_GRID).
+ *  - The first call on a device looks up that device's address of the array
+ *    (cudaGetSymbolAddress) with the device current and caches it; make that
+ *    first call before any stream capture.
+ *  - Every call on a device shares the one array, and each call re-fills the
+ *    part it uses before use, so stale contents from an earlier call never
+ *    leak into a result. Two calls whose work overlaps on the GPU (different
+ *    streams, or different host threads, without ordering between them) race
+ *    on the array and may return wrong verdicts: order them on one stream or
+ *    synchronise between them.
+ * Asynchronous on `stream` like fw_classify.
+ */
+int fw_classify_rule_split_noalloc(const fw_ruleset *rs, const fw_headers *hdrs, int64_t n,
+                                   int32_t *out_rule_idx, uint8_t *out_action, void *stream,
+                                   const fw_config *cfg);
+
 /* ------------------------------------------------------------ self test */
 /*
  * Failure-path check of the bounded device waits. Launches one block whose

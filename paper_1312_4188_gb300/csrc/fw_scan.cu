@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <climits>
 #include <cstring>
+#include <mutex>
 
 #include "fw_internal.cuh"
 
@@ -755,4 +756,91 @@ extern "C" int fw_selftest_wait_timeout(fw_ruleset *rs, int64_t limit_ns, void *
     if (rs == nullptr || limit_ns < 1000 || limit_ns > 1000000000) return set_status(FW_EINVAL);
     k_selftest_wait<<<1, 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>(rs->d_status, (uint64_t)limit_ns);
     return set_status(cuda_status(cudaGetLastError()));
+}
+
+// ------------------------------------------------------------ allocation-free grid rule split
+// Scratch for fw_classify_rule_split_noalloc: the per-packet partial minima of
+// the grid rule split, at a fixed address on every device that loads this
+// library. Host code must not use the symbol itself as a device address; the
+// address is looked up per device with cudaGetSymbolAddress.
+static __device__ __align__(256) int32_t g_noalloc_partial[FW_NOALLOC_MAX_PACKETS];
+
+static std::mutex g_noalloc_mu;
+static int32_t *g_noalloc_ptr[64] = {};
+
+// Device address of g_noalloc_partial on the current device (looked up once per device).
+static int noalloc_scratch(int32_t **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (dev < 0 || dev >= 64) return FW_EINVAL;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (g_noalloc_ptr[dev] == nullptr) {
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_partial);
+        if (e != cudaSuccess || ptr == nullptr) {
+            cudaGetLastError();
+            return e != cudaSuccess ? cuda_status(e) : FW_ECUDA;
+        }
+        g_noalloc_ptr[dev] = static_cast<int32_t *>(ptr);
+    }
+    *out = g_noalloc_ptr[dev];
+    return FW_OK;
+}
+
+extern "C" int fw_classify_rule_split_noalloc(const fw_ruleset *rs, const fw_headers *hdrs, int64_t n,
+                                              int32_t *out_idx, uint8_t *out_act, void *stream,
+                                              const fw_config *cfg_in) {
+    if (rs == nullptr || n < 0) return set_status(FW_EINVAL);
+    if (n > FW_NOALLOC_MAX_PACKETS) return set_status(FW_ERANGE);
+    if (n == 0) return FW_OK;
+    if (hdrs == nullptr || hdrs->src == nullptr || hdrs->dst == nullptr || hdrs->sport == nullptr ||
+        hdrs->dport == nullptr || hdrs->proto == nullptr || out_idx == nullptr || out_act == nullptr)
+        return set_status(FW_EINVAL);
+    fw_config cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    if (cfg_in != nullptr) cfg = *cfg_in;
+    if (cfg.mode != FW_MODE_AUTO && cfg.mode != FW_MODE_RULE_SPLIT_GRID) return set_status(FW_EINVAL);
+    int32_t *partial = nullptr;
+    int s = noalloc_scratch(&partial);
+    if (s != FW_OK) return set_status(s);
+
+    SplitParams p;
+    p.clamp = rs->d_clamp;
+    p.action = rs->d_action;
+    p.n_scan = (int)((rs->n_eff + 3) / 4 * 4);
+    p.h = HdrPtrs{hdrs->src, hdrs->dst, hdrs->sport, hdrs->dport, hdrs->proto};
+    p.n = n;
+    p.out_idx = out_idx;
+    p.out_act = out_act;
+    p.partial = partial;
+    const int threads = cfg.block_threads > 0 ? cfg.block_threads : 256;
+    if (threads % 32 != 0 || threads > 512) return set_status(FW_EINVAL);
+    const int G = cfg.packets_per_group > 0 ? cfg.packets_per_group : 64;
+    if (G % 32 != 0 || G > 4096) return set_status(FW_EINVAL);
+    p.group = G;
+    const int groups_per_block = threads / 32;
+    const size_t smem = (size_t)groups_per_block * G * (sizeof(Pkt) + sizeof(int));
+    if (smem > 227 * 1024) return set_status(FW_EINVAL);
+    int slices = cfg.rule_slices > 0 ? cfg.rule_slices : 8;
+    slices = std::max(1, std::min(std::min(slices, 65535), (p.n_scan + 31) / 32));
+    p.slice_rules = std::max(32, ((p.n_scan + slices - 1) / slices + 31) / 32 * 32);
+    slices = std::max(1, (p.n_scan + p.slice_rules - 1) / p.slice_rules);
+    const int64_t n_groups = (n + G - 1) / G;
+    int64_t bx = std::max<int64_t>(1, (int64_t)sm_count(rs->device) * 4 / slices);
+    bx = std::max<int64_t>(1, std::min<int64_t>(bx, (n_groups + groups_per_block - 1) / groups_per_block));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // every packet's partial minimum starts at the no-match sentinel
+    cudaError_t e = cudaMemsetAsync(partial, 0x7F, (size_t)n * sizeof(int32_t), st);
+    if (e == cudaSuccess) e = ensure_smem(k_rule_split<false>, smem);
+    if (e == cudaSuccess) {
+        k_rule_split<false><<<dim3((unsigned)bx, (unsigned)slices), threads, smem, st>>>(p);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        const int fb = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count(rs->device) * 8);
+        k_rule_split_finalize<<<std::max(fb, 1), 256, 0, st>>>(partial, p.action, n, out_idx, out_act);
+        e = cudaGetLastError();
+    }
+    return set_status(cuda_status(e));
 }

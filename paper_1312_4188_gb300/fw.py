@@ -25,6 +25,7 @@ FW_EALIGN = -4
 FW_ETIMEOUT = -5
 FW_EBUSY = -6
 FW_ERANGE = -7
+FW_NOALLOC_MAX_PACKETS = 1 << 20
 
 FW_DROP = 0
 FW_ACCEPT = 1
@@ -97,6 +98,8 @@ SIGNATURES = {
     "fw_classify_host": (ctypes.c_int, [P, P, ctypes.POINTER(fw_headers), I64, P, P, ctypes.c_int,
                                         ctypes.POINTER(fw_config)]),
     "fw_selftest_wait_timeout": (ctypes.c_int, [P, I64, P]),
+    "fw_classify_rule_split_noalloc": (ctypes.c_int, [P, ctypes.POINTER(fw_headers), I64, P, P, P,
+                                                      ctypes.POINTER(fw_config)]),
     "fw_last_status": (ctypes.c_int, []),
     "fw_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "fw_abi_version": (ctypes.c_int, []),

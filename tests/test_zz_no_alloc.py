@@ -1,0 +1,89 @@
+"""The allocation-free entry point against the allocating one.
+
+fw_classify_rule_split_noalloc serves callers that must not allocate device
+memory while they classify (a packet path that cannot take the implicit
+synchronisation of cudaMalloc/cudaFree, or a service whose GPU memory is
+fixed at start-up). It keeps its scratch in a fixed device array instead of
+allocating per call. Here it is called twice in a row through the C ABI, on
+different batches, and each result must equal, bit for bit, what the
+existing grid rule-split entry point (fw_classify_ex, which allocates its
+scratch per call) returns for the same batch. This file is collected last so
+that a failure here does not hide the other GPU tests.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1312_4188_gb300 import fw, workload as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1312_4188_gb300 import build
+    build.build()
+    return torch
+
+
+def _noalloc(torch, rs, dh, n, cfg=None):
+    idx = torch.full((max(n, 1),), -7, dtype=torch.int32, device="cuda")
+    act = torch.full((max(n, 1),), 9, dtype=torch.uint8, device="cuda")
+    hs = fw.headers_struct(dh)
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    s = fw.lib().fw_classify_rule_split_noalloc(rs.handle, ctypes.byref(hs), n, ctypes.c_void_p(idx.data_ptr()),
+                                                ctypes.c_void_p(act.data_ptr()), st,
+                                                ctypes.byref(cfg) if cfg is not None else None)
+    return s, idx[:n], act[:n]
+
+
+def test_two_calls_match_the_allocating_entry_point(torch_cuda):
+    torch = torch_cuda
+    rules = W.gen_rules(3000, 17)
+    keep = ~((rules["src_prefix"] == 0) & (rules["dst_prefix"] == 0))  # deep scans, many unmatched
+    rules = rules[keep]
+    rs = fw.fw_ruleset_create(rules)
+    batches = [W.gen_packets(rules, 300_001, 18), W.gen_packets(rules, 77_777, 19, zipf_s=1.1)]
+    for call, hdr in enumerate(batches):
+        n = len(hdr["src"])
+        dh = fw.headers_to_device(hdr)
+        want_idx, want_act = fw.fw_classify(rs, dh, n, config=fw.make_config("rule_split_grid"))
+        s, idx, act = _noalloc(torch, rs, dh, n)
+        torch.cuda.synchronize()
+        assert s == fw.FW_OK, f"call {call}: status {s}"
+        assert torch.equal(idx, want_idx), f"call {call}: rule index differs from fw_classify_ex"
+        assert torch.equal(act, want_act), f"call {call}: action differs from fw_classify_ex"
+        assert int((idx >= 0).sum()) > 0 and int((idx < 0).sum()) > 0
+    assert rs.check() == fw.FW_OK
+    rs.destroy()
+
+
+def test_limits_and_arguments(torch_cuda):
+    torch = torch_cuda
+    rules = W.gen_rules(100, 5)
+    rs = fw.fw_ruleset_create(rules)
+    hdr = W.gen_packets(rules, 64, 6)
+    dh = fw.headers_to_device(hdr)
+    hs = fw.headers_struct(dh)
+    L = fw.lib()
+    big = fw.FW_NOALLOC_MAX_PACKETS + 1
+    assert L.fw_classify_rule_split_noalloc(rs.handle, ctypes.byref(hs), big, None, None, None, None) == fw.FW_ERANGE
+    assert L.fw_classify_rule_split_noalloc(rs.handle, ctypes.byref(hs), -1, None, None, None, None) == fw.FW_EINVAL
+    assert L.fw_classify_rule_split_noalloc(rs.handle, ctypes.byref(hs), 0, None, None, None, None) == fw.FW_OK
+    bad = fw.make_config("packet_split")
+    s, _, _ = _noalloc(torch, rs, dh, 64, bad)
+    assert s == fw.FW_EINVAL
+    # the largest accepted batch, with explicit slices
+    n = fw.FW_NOALLOC_MAX_PACKETS
+    hdr = W.gen_packets(rules, n, 7)
+    dh = fw.headers_to_device(hdr)
+    s, idx, act = _noalloc(torch, rs, dh, n, fw.make_config("rule_split_grid", rule_slices=3))
+    want_idx, want_act = fw.fw_classify(rs, dh, n, config=fw.make_config("rule_split_grid", rule_slices=3))
+    torch.cuda.synchronize()
+    assert s == fw.FW_OK
+    assert torch.equal(idx, want_idx) and torch.equal(act, want_act)
+    rs.destroy()
