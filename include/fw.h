@@ -188,6 +188,57 @@ int fw_classify_ex(const fw_ruleset *rs, const fw_headers *hdrs, int64_t n,
                    int32_t *out_rule_idx, uint8_t *out_action, void *stream,
                    const fw_config *cfg);
 
+/* ------------------------------------------------------------ learned index */
+/*
+ * Decomposition classifier with a learned locator (same result as
+ * fw_classify). Each rule field is an interval of its key space (Sec. IV:
+ * prefix = address interval, port range, protocol value or all). Per field
+ * the key space is cut at every interval end into elementary intervals; row
+ * j of the field's bitmap has bit k set when rule k covers interval j. A
+ * packet's first match (Sec. I) is the lowest set bit of the AND of its five
+ * rows. The interval holding a key is found by a piecewise-linear FP32 model
+ * (the key space cut into `segments` equal parts, one line per part fit on
+ * the sorted interval ends: least squares or the chord, whichever has the
+ * smaller exact error bound) whose stored per-part maximum error
+ * bounds an exact integer binary search; the search window is verified with
+ * integer compares, and a failed check falls back to a full search (counted
+ * in fw_lindex_stats.fallbacks), so no floating-point value decides a match.
+ *
+ * fw_lindex_config (zero = default):
+ *  segments: model parts per field, a power of two <= 65536 (default 4096;
+ *            fields with fewer keys use one part per key).
+ *  truncate: 1 (default) index only rules up to the first catch-all (no
+ *            packet is decided after it); 2 index every rule.
+ * Device memory: rows x ceil(rules/128)*16 bytes per field, rows <= 2 x
+ * indexed rules + 1. Create is synchronous and copies `rules`.
+ */
+typedef struct fw_lindex_config {
+    int32_t segments;
+    int32_t truncate;
+    int32_t reserved[6];
+} fw_lindex_config;
+
+typedef struct fw_lindex_stats {
+    int64_t rules;          /* rules supplied */
+    int64_t rules_indexed;  /* rules in the bitmaps */
+    int64_t words_per_row;  /* 32-bit words per bitmap row */
+    int64_t segments;       /* model parts per field (upper bound) */
+    int64_t intervals[5];   /* elementary intervals: src, dst, sport, dport, proto */
+    int32_t max_error[5];   /* stored maximum model error per field, in positions */
+    int64_t bitmap_bytes;   /* device bytes of all rows */
+    int64_t fallbacks;      /* verified windows that failed (0 when the bounds hold) */
+} fw_lindex_stats;
+
+typedef struct fw_lindex fw_lindex;
+
+int fw_lindex_create(const fw_rule *rules, int64_t n, const fw_lindex_config *cfg, fw_lindex **out);
+void fw_lindex_destroy(fw_lindex *li);
+/* As fw_classify (device SoA headers, device outputs, asynchronous on stream). */
+int fw_lindex_classify(const fw_lindex *li, const fw_headers *hdrs, int64_t n, int32_t *out_rule_idx,
+                       uint8_t *out_action, void *stream);
+/* Synchronises the device and fills *st. */
+int fw_lindex_get_stats(fw_lindex *li, fw_lindex_stats *st);
+
 /* ------------------------------------------------------------ host buffers */
 /*
  * Host-ingress path: classify packets whose headers live in HOST memory and

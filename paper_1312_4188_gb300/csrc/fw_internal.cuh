@@ -253,4 +253,8 @@ struct fw_ruleset {
 namespace fwk {
 int set_status(int s);  // records s as this thread's last status; returns s
 int cuda_status(cudaError_t e);
+uint32_t prefix_mask(unsigned prefix);  // top `prefix` bits set; 0 for prefix 0
+bool is_catch_all(const fw_rule &r);    // all five fields wildcards
+int validate_rule(const fw_rule &r);    // FW_OK or FW_EINVAL
+int sm_count(int dev);                  // SMs of device `dev` (cached)
 }  // namespace fwk

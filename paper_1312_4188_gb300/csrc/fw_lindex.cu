@@ -1,0 +1,423 @@
+// Learned-index decomposition classifier (interval decomposition per field,
+// rule bitmaps, AND, first set bit).
+//
+// Every field of a rule is an interval of that field's key space (Sec. IV
+// rule model: a prefix is an address interval, a port range an interval, a
+// protocol one value or all of them). Cutting each field's key space at every
+// interval endpoint gives "elementary intervals" inside which no rule's
+// field test changes. For elementary interval j of field f, the row
+// bits_f[j] has bit k set exactly when rule k's field-f interval covers it.
+// A packet lies in rule k iff bit k is set in the rows of all five of its
+// fields' intervals, so the first match (Sec. I) is the lowest set bit of the
+// AND of five rows, found by scanning words from the start.
+//
+// Locating a key's elementary interval: a piecewise-linear FP32 model per
+// field (the key space cut into `segments` equal parts, one line per part fit
+// on the sorted endpoints: least squares or the chord, whichever has the
+// smaller exact error bound) predicts the position; the stored
+// per-part maximum error bounds an exact integer binary search around it.
+// The window is verified with integer compares before it is trusted (a
+// failed check falls back to a search over the whole array and is counted),
+// so floating point never decides a match.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "fw_internal.cuh"
+
+namespace fwk {
+
+constexpr int kFields = 5;
+constexpr int kKeyBits[kFields] = {32, 32, 16, 16, 8};
+
+struct LiFieldDev {
+    const uint32_t *bound;  // M sorted interval starts, bound[0] = 0
+    const float *a;         // per segment slope
+    const float *b;         // per segment intercept
+    const int32_t *err;     // per segment max |prediction - position|
+    const uint32_t *bits;   // M rows of W words
+    int32_t M;
+    int32_t shift;          // segment = key >> shift
+};
+
+struct LiDev {
+    LiFieldDev f[kFields];
+    int64_t W;              // words per row (multiple of 4)
+    const uint8_t *action;
+    unsigned long long *fallbacks;
+};
+
+}  // namespace fwk
+
+struct fw_lindex {
+    int64_t n = 0, n_idx = 0, W = 0, first_catch_all = -1;
+    int device = 0;
+    int segments = 0;
+    int64_t M[fwk::kFields] = {};
+    int32_t max_err[fwk::kFields] = {};
+    int64_t bitmap_bytes = 0;
+    uint32_t *d_bound[fwk::kFields] = {};
+    float *d_a[fwk::kFields] = {};
+    float *d_b[fwk::kFields] = {};
+    int32_t *d_err[fwk::kFields] = {};
+    uint32_t *d_bits[fwk::kFields] = {};
+    int32_t shift[fwk::kFields] = {};
+    uint8_t *d_action = nullptr;
+    unsigned long long *d_fallbacks = nullptr;
+};
+
+namespace fwk {
+
+// ------------------------------------------------------------ device
+// Row j, words [w0, w0+32) of one field: lane l of warp r computes word
+// w0+l of row j0+r from the 1024 rules of the word tile, staged in shared
+// memory bit-major (rule 32(w0+l)+b at [b][l]) so the lanes never collide on
+// a bank.
+__global__ void k_li_build(const uint32_t *__restrict__ bound, int64_t M, const uint32_t *__restrict__ rlo,
+                           const uint32_t *__restrict__ rhi, int64_t n_idx, int64_t W, uint32_t *__restrict__ bits) {
+    __shared__ uint32_t slo[32][32], shi[32][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t word_tiles = (W + 31) / 32;
+    const int64_t row_groups = (M + nw - 1) / nw;
+    for (int64_t t = blockIdx.x; t < word_tiles * row_groups; t += gridDim.x) {
+        const int64_t wt = t % word_tiles, rg = t / word_tiles;
+        const int64_t w0 = wt * 32;
+        __syncthreads();
+        for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
+            const int l = i >> 5, b = i & 31;  // rule 32*(w0+l)+b
+            const int64_t k = 32 * (w0 + l) + b;
+            const bool ok = k < n_idx;
+            slo[b][l] = ok ? rlo[k] : 1u;
+            shi[b][l] = ok ? rhi[k] : 0u;  // empty interval: never covers
+        }
+        __syncthreads();
+        const int64_t j = rg * nw + warp;
+        const int64_t w = w0 + lane;
+        if (j < M && w < W) {
+            const uint32_t v = bound[j];
+            uint32_t word = 0;
+#pragma unroll 8
+            for (int b = 0; b < 32; ++b) word |= (uint32_t)((slo[b][lane] <= v) & (v <= shi[b][lane])) << b;
+            bits[j * W + w] = word;
+        }
+    }
+}
+
+__device__ __forceinline__ int li_locate(const LiFieldDev &f, uint32_t v, unsigned long long *fallbacks) {
+    const uint32_t s = v >> f.shift;
+    const uint32_t base = s << f.shift;
+    const float pf = __fmaf_rn(__ldg(f.a + s), __uint2float_rn(v - base), __ldg(f.b + s));
+    int p = (int)floorf(fminf(fmaxf(pf, 0.0f), (float)(f.M - 1)));
+    const int e = __ldg(f.err + s);
+    int lo = max(0, p - e), hi = min(f.M - 1, p + e);
+    // exact check of the window before it is trusted
+    if (__ldg(f.bound + lo) > v || (hi < f.M - 1 && __ldg(f.bound + hi + 1) <= v)) {
+        atomicAdd(fallbacks, 1ull);
+        lo = 0;
+        hi = f.M - 1;
+    }
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(f.bound + mid) <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_li_classify(LiDev d, const uint32_t *__restrict__ src,
+                                                     const uint32_t *__restrict__ dst,
+                                                     const uint16_t *__restrict__ sport,
+                                                     const uint16_t *__restrict__ dport,
+                                                     const uint8_t *__restrict__ proto, int64_t n,
+                                                     int32_t *__restrict__ out_idx, uint8_t *__restrict__ out_act) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t key[kFields] = {src[i], dst[i], sport[i], dport[i], proto[i]};
+        const uint4 *row[kFields];
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) {
+            const int j = li_locate(d.f[f], key[f], d.fallbacks);
+            row[f] = reinterpret_cast<const uint4 *>(d.f[f].bits + (int64_t)j * d.W);
+        }
+        int r = -1;
+        for (int64_t q = 0; q < d.W / 4; ++q) {
+            uint4 x = __ldg(row[0] + q);
+#pragma unroll
+            for (int f = 1; f < kFields; ++f) {
+                const uint4 y = __ldg(row[f] + q);
+                x.x &= y.x;
+                x.y &= y.y;
+                x.z &= y.z;
+                x.w &= y.w;
+            }
+            if (x.x | x.y | x.z | x.w) {
+                const int base = (int)(q * 128);
+                r = x.x ? base + __ffs(x.x) - 1
+                  : x.y ? base + 32 + __ffs(x.y) - 1
+                  : x.z ? base + 64 + __ffs(x.z) - 1
+                        : base + 96 + __ffs(x.w) - 1;
+                break;
+            }
+        }
+        out_idx[i] = r;
+        out_act[i] = r >= 0 ? __ldg(d.action + r) : (uint8_t)FW_DROP;
+    }
+}
+
+// ------------------------------------------------------------ host
+static void field_interval(const fw_rule &r, int f, uint32_t &lo, uint32_t &hi) {
+    switch (f) {
+        case 0: {
+            const uint32_t m = prefix_mask(r.src_prefix);
+            lo = r.src_addr & m;
+            hi = lo | ~m;
+            break;
+        }
+        case 1: {
+            const uint32_t m = prefix_mask(r.dst_prefix);
+            lo = r.dst_addr & m;
+            hi = lo | ~m;
+            break;
+        }
+        case 2: lo = r.sport_lo; hi = r.sport_hi; break;
+        case 3: lo = r.dport_lo; hi = r.dport_hi; break;
+        default:
+            lo = r.proto_any ? 0u : r.proto;
+            hi = r.proto_any ? 255u : r.proto;
+    }
+}
+
+// Host twin of the device prediction (identical IEEE single-precision steps).
+static int predict(float a, float b, uint32_t v, uint32_t base, int64_t M) {
+    const float pf = std::fmaf(a, static_cast<float>(v - base), b);
+    return (int)std::floor(std::fmin(std::fmax(pf, 0.0f), (float)(M - 1)));
+}
+
+// Exact maximum error of the line (a, b) over every elementary interval that
+// meets the segment [base, end), evaluated at the clipped interval ends (the
+// prediction is non-decreasing inside a segment, so the ends bound it).
+static int32_t segment_error(const std::vector<uint32_t> &B, int64_t t0, int64_t t1, uint64_t base, uint64_t end,
+                             uint64_t dom_end, float a, float b) {
+    const int64_t M = (int64_t)B.size();
+    int32_t e = 0;
+    for (int64_t t = t0; t <= t1 && t < M; ++t) {
+        const uint64_t lo = std::max<uint64_t>(B[t], base);
+        const uint64_t hi = std::min<uint64_t>((t + 1 < M ? (uint64_t)B[t + 1] : dom_end) - 1, end - 1);
+        if (lo > hi) continue;
+        const int p0 = predict(a, b, (uint32_t)lo, (uint32_t)base, M);
+        const int p1 = predict(a, b, (uint32_t)hi, (uint32_t)base, M);
+        e = std::max<int32_t>(e, (int32_t)std::max<int64_t>(std::llabs(p0 - t), std::llabs(p1 - t)));
+    }
+    return e;
+}
+
+// One line per segment of the key space. Two candidates are fit and the one
+// with the smaller exact error bound is kept: the least-squares line over the
+// (key - base, position) pairs of the interval ends inside the segment, and
+// the chord from the position at the segment's first key to the position at
+// its last key (the least-squares line alone can extrapolate badly when the
+// ends inside a segment are bunched together).
+static void fit_field(const std::vector<uint32_t> &B, int bits, int nseg, int shift, std::vector<float> &A,
+                      std::vector<float> &Bc, std::vector<int32_t> &E, int32_t &max_err) {
+    const int64_t M = (int64_t)B.size();
+    A.assign(nseg, 0.0f);
+    Bc.assign(nseg, 0.0f);
+    E.assign(nseg, 0);
+    max_err = 0;
+    const uint64_t dom_end = uint64_t(1) << bits;
+    int64_t j = 0;  // first interval start >= base of the segment
+    for (int s = 0; s < nseg; ++s) {
+        const uint64_t base = (uint64_t)s << shift, end = std::min<uint64_t>(((uint64_t)(s + 1) << shift), dom_end);
+        while (j < M && B[j] < base) ++j;
+        int64_t j_end = j;
+        while (j_end < M && B[j_end] < end) ++j_end;
+        const int64_t t0 = (j < M && B[j] == base) ? j : j - 1;  // interval holding `base`
+        const int64_t t1 = j_end - 1 >= t0 ? j_end - 1 : t0;     // interval holding end - 1
+        // chord
+        const double span = (double)(end - 1 - base);
+        float ca = span > 0 ? (float)((double)(t1 - t0) / span) : 0.0f;
+        float cb = (float)t0;
+        int32_t ce = segment_error(B, t0, t1, base, end, dom_end, ca, cb);
+        // least squares over the interval starts inside the segment
+        const int64_t cnt = j_end - j;
+        float la = 0.0f, lb = (float)t0;
+        if (cnt >= 2) {
+            double sx = 0, sy = 0, sxx = 0, sxy = 0;
+            for (int64_t t = j; t < j_end; ++t) {
+                const double x = (double)(B[t] - base), y = (double)t;
+                sx += x;
+                sy += y;
+                sxx += x * x;
+                sxy += x * y;
+            }
+            const double den = cnt * sxx - sx * sx;
+            if (den > 0) {
+                const double a = std::max(0.0, (cnt * sxy - sx * sy) / den);
+                la = (float)a;
+                lb = (float)((sy - a * sx) / cnt);
+            }
+        }
+        const int32_t le = segment_error(B, t0, t1, base, end, dom_end, la, lb);
+        if (le < ce) {
+            ca = la;
+            cb = lb;
+            ce = le;
+        }
+        A[s] = ca;
+        Bc[s] = cb;
+        E[s] = ce;
+        max_err = std::max(max_err, ce);
+    }
+}
+
+}  // namespace fwk
+
+using namespace fwk;
+
+extern "C" void fw_lindex_destroy(fw_lindex *li) {
+    if (li == nullptr) return;
+    for (int f = 0; f < kFields; ++f) {
+        cudaFree(li->d_bound[f]);
+        cudaFree(li->d_a[f]);
+        cudaFree(li->d_b[f]);
+        cudaFree(li->d_err[f]);
+        cudaFree(li->d_bits[f]);
+    }
+    cudaFree(li->d_action);
+    cudaFree(li->d_fallbacks);
+    delete li;
+}
+
+extern "C" int fw_lindex_create(const fw_rule *rules, int64_t n, const fw_lindex_config *cfg_in, fw_lindex **out) {
+    if (out == nullptr) return set_status(FW_EINVAL);
+    *out = nullptr;
+    if (n < 0 || (n > 0 && rules == nullptr) || n > (int64_t(1) << 30)) return set_status(FW_EINVAL);
+    fw_lindex_config cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    if (cfg_in) cfg = *cfg_in;
+    const int segments = cfg.segments > 0 ? cfg.segments : 4096;
+    if ((segments & (segments - 1)) != 0 || segments > (1 << 16)) return set_status(FW_EINVAL);
+    if (cfg.truncate < 0 || cfg.truncate > 2) return set_status(FW_EINVAL);
+    int64_t first_ca = -1;
+    for (int64_t k = 0; k < n; ++k) {
+        const int s = validate_rule(rules[k]);
+        if (s != FW_OK) return set_status(s);
+        if (first_ca < 0 && is_catch_all(rules[k])) first_ca = k;
+    }
+    fw_lindex *li = new (std::nothrow) fw_lindex();
+    if (li == nullptr) return set_status(FW_ENOMEM);
+    li->n = n;
+    li->first_catch_all = first_ca;
+    li->n_idx = (cfg.truncate != 2 && first_ca >= 0) ? first_ca + 1 : n;
+    li->W = std::max<int64_t>(4, (li->n_idx + 127) / 128 * 4);
+    li->segments = segments;
+    cudaGetDevice(&li->device);
+
+    cudaError_t e = cudaSuccess;
+    std::vector<uint8_t> act(li->W * 32, FW_DROP);
+    for (int64_t k = 0; k < li->n_idx; ++k) act[k] = rules[k].action;
+    e = cudaMalloc(&li->d_action, act.size());
+    if (e == cudaSuccess) e = cudaMemcpy(li->d_action, act.data(), act.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&li->d_fallbacks, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(li->d_fallbacks, 0, sizeof(unsigned long long));
+    uint32_t *d_rlo = nullptr, *d_rhi = nullptr;
+    const size_t nr = (size_t)std::max<int64_t>(li->n_idx, 1);
+    if (e == cudaSuccess) e = cudaMalloc(&d_rlo, nr * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&d_rhi, nr * 4);
+    std::vector<uint32_t> rlo(nr), rhi(nr);
+    for (int f = 0; f < kFields && e == cudaSuccess; ++f) {
+        const int bits = kKeyBits[f];
+        const int nseg = std::min(segments, 1 << std::min(bits, 16));
+        int lg = 0;
+        while ((1 << lg) < nseg) ++lg;
+        li->shift[f] = bits - lg;
+        std::vector<uint64_t> ends;
+        ends.reserve(2 * li->n_idx + 1);
+        ends.push_back(0);
+        const uint64_t dom_end = uint64_t(1) << bits;
+        for (int64_t k = 0; k < li->n_idx; ++k) {
+            uint32_t lo, hi;
+            field_interval(rules[k], f, lo, hi);
+            rlo[k] = lo;
+            rhi[k] = hi;
+            ends.push_back(lo);
+            if ((uint64_t)hi + 1 < dom_end) ends.push_back((uint64_t)hi + 1);
+        }
+        std::sort(ends.begin(), ends.end());
+        ends.erase(std::unique(ends.begin(), ends.end()), ends.end());
+        std::vector<uint32_t> B(ends.begin(), ends.end());
+        const int64_t M = (int64_t)B.size();
+        li->M[f] = M;
+        std::vector<float> A, Bc;
+        std::vector<int32_t> E;
+        fit_field(B, bits, nseg, li->shift[f], A, Bc, E, li->max_err[f]);
+        const size_t row_bytes = (size_t)li->W * 4;
+        e = cudaMalloc(&li->d_bound[f], M * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&li->d_a[f], nseg * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&li->d_b[f], nseg * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&li->d_err[f], nseg * sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&li->d_bits[f], (size_t)M * row_bytes);
+        if (e == cudaSuccess) e = cudaMemcpy(li->d_bound[f], B.data(), M * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(li->d_a[f], A.data(), nseg * sizeof(float), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(li->d_b[f], Bc.data(), nseg * sizeof(float), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(li->d_err[f], E.data(), nseg * sizeof(int32_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && li->n_idx > 0) e = cudaMemcpy(d_rlo, rlo.data(), li->n_idx * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && li->n_idx > 0) e = cudaMemcpy(d_rhi, rhi.data(), li->n_idx * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) {
+            const int blocks = sm_count(li->device) * 8;
+            k_li_build<<<blocks, 256>>>(li->d_bound[f], M, d_rlo, d_rhi, li->n_idx, li->W, li->d_bits[f]);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        li->bitmap_bytes += (int64_t)M * (int64_t)row_bytes;
+    }
+    cudaFree(d_rlo);
+    cudaFree(d_rhi);
+    if (e != cudaSuccess) {
+        fw_lindex_destroy(li);
+        cudaGetLastError();
+        return set_status(cuda_status(e));
+    }
+    *out = li;
+    return FW_OK;
+}
+
+extern "C" int fw_lindex_classify(const fw_lindex *li, const fw_headers *hdrs, int64_t n, int32_t *out_idx,
+                                  uint8_t *out_act, void *stream) {
+    if (li == nullptr || n < 0 || n > INT32_MAX) return set_status(FW_EINVAL);
+    if (n == 0) return FW_OK;
+    if (hdrs == nullptr || !hdrs->src || !hdrs->dst || !hdrs->sport || !hdrs->dport || !hdrs->proto || !out_idx ||
+        !out_act)
+        return set_status(FW_EINVAL);
+    LiDev d;
+    for (int f = 0; f < kFields; ++f) {
+        d.f[f] = LiFieldDev{li->d_bound[f], li->d_a[f], li->d_b[f], li->d_err[f], li->d_bits[f], (int32_t)li->M[f],
+                            li->shift[f]};
+    }
+    d.W = li->W;
+    d.action = li->d_action;
+    d.fallbacks = li->d_fallbacks;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sm_count(li->device) * 16));
+    k_li_classify<<<(unsigned)blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        d, hdrs->src, hdrs->dst, hdrs->sport, hdrs->dport, hdrs->proto, n, out_idx, out_act);
+    return set_status(cuda_status(cudaGetLastError()));
+}
+
+extern "C" int fw_lindex_get_stats(fw_lindex *li, fw_lindex_stats *st) {
+    if (li == nullptr || st == nullptr) return set_status(FW_EINVAL);
+    std::memset(st, 0, sizeof(*st));
+    st->rules = li->n;
+    st->rules_indexed = li->n_idx;
+    st->words_per_row = li->W;
+    st->segments = li->segments;
+    for (int f = 0; f < kFields; ++f) {
+        st->intervals[f] = li->M[f];
+        st->max_error[f] = li->max_err[f];
+    }
+    st->bitmap_bytes = li->bitmap_bytes;
+    cudaError_t e = cudaDeviceSynchronize();
+    unsigned long long fb = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&fb, li->d_fallbacks, sizeof(fb), cudaMemcpyDeviceToHost);
+    st->fallbacks = (int64_t)fb;
+    return set_status(cuda_status(e));
+}

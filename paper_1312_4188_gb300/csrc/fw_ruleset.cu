@@ -27,16 +27,16 @@ int cuda_status(cudaError_t e) {
     return FW_ECUDA;
 }
 
-static uint32_t prefix_mask(unsigned prefix) {
+uint32_t prefix_mask(unsigned prefix) {
     return prefix == 0 ? 0u : (0xFFFFFFFFu << (32u - prefix));
 }
 
-static bool is_catch_all(const fw_rule &r) {
+bool is_catch_all(const fw_rule &r) {
     return r.src_prefix == 0 && r.dst_prefix == 0 && r.sport_lo == 0 && r.sport_hi == 0xFFFF && r.dport_lo == 0 &&
            r.dport_hi == 0xFFFF && r.proto_any != 0;
 }
 
-static int validate(const fw_rule &r) {
+int validate_rule(const fw_rule &r) {
     if (r.src_prefix > 32 || r.dst_prefix > 32) return FW_EINVAL;
     if (r.sport_lo > r.sport_hi || r.dport_lo > r.dport_hi) return FW_EINVAL;
     if (r.action != FW_DROP && r.action != FW_ACCEPT) return FW_EINVAL;
@@ -105,7 +105,7 @@ extern "C" int fw_ruleset_create_ex(const fw_rule *rules, int64_t n, fw_ruleset 
     if (n < 0 || (n > 0 && rules == nullptr) || n > (int64_t(1) << 30)) return set_status(FW_EINVAL);
     int64_t first_ca = -1;
     for (int64_t k = 0; k < n; ++k) {
-        int s = validate(rules[k]);
+        int s = validate_rule(rules[k]);
         if (s != FW_OK) return set_status(s);
         if (first_ca < 0 && is_catch_all(rules[k])) first_ca = k;
     }

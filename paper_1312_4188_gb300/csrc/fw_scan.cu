@@ -528,7 +528,7 @@ __global__ void k_rule_split_finalize(const int32_t *__restrict__ partial, const
 }
 
 // ------------------------------------------------------------ host side
-static int sm_count(int dev) {
+int sm_count(int dev) {
     static int cached[64] = {0};
     if (dev < 0 || dev >= 64) return 148;
     if (cached[dev] == 0) {

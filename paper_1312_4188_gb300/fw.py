@@ -78,6 +78,16 @@ def make_config(mode=FW_MODE_AUTO, **kw) -> fw_config:
     return c
 
 
+class fw_lindex_config(ctypes.Structure):
+    _fields_ = [("segments", ctypes.c_int32), ("truncate", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+
+
+class fw_lindex_stats(ctypes.Structure):
+    _fields_ = [("rules", ctypes.c_int64), ("rules_indexed", ctypes.c_int64), ("words_per_row", ctypes.c_int64),
+                ("segments", ctypes.c_int64), ("intervals", ctypes.c_int64 * 5), ("max_error", ctypes.c_int32 * 5),
+                ("bitmap_bytes", ctypes.c_int64), ("fallbacks", ctypes.c_int64)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -100,6 +110,10 @@ SIGNATURES = {
     "fw_selftest_wait_timeout": (ctypes.c_int, [P, I64, P]),
     "fw_classify_rule_split_noalloc": (ctypes.c_int, [P, ctypes.POINTER(fw_headers), I64, P, P, P,
                                                       ctypes.POINTER(fw_config)]),
+    "fw_lindex_create": (ctypes.c_int, [P, I64, ctypes.POINTER(fw_lindex_config), ctypes.POINTER(P)]),
+    "fw_lindex_destroy": (None, [P]),
+    "fw_lindex_classify": (ctypes.c_int, [P, ctypes.POINTER(fw_headers), I64, P, P, P]),
+    "fw_lindex_get_stats": (ctypes.c_int, [P, ctypes.POINTER(fw_lindex_stats)]),
     "fw_last_status": (ctypes.c_int, []),
     "fw_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "fw_abi_version": (ctypes.c_int, []),
@@ -273,3 +287,55 @@ def fw_classify_host(pl: HostPipeline, rs: Ruleset, host_hdrs: dict, out_idx, ou
     s = lib().fw_classify_host(pl.handle, rs.handle, ctypes.byref(hs), int(n), ptr(out_idx), ptr(out_act),
                                int(strategy), ctypes.byref(config) if config is not None else None)
     _check(s, "fw_classify_host")
+
+
+class LIndex:
+    """Owning wrapper of an ``fw_lindex*`` (learned-index decomposition classifier)."""
+
+    def __init__(self, handle: int):
+        self.handle = ctypes.c_void_p(handle)
+
+    def stats(self) -> dict:
+        st = fw_lindex_stats()
+        _check(lib().fw_lindex_get_stats(self.handle, ctypes.byref(st)), "fw_lindex_get_stats")
+        return {"rules": st.rules, "rules_indexed": st.rules_indexed, "words_per_row": st.words_per_row,
+                "segments": st.segments, "intervals": list(st.intervals), "max_error": list(st.max_error),
+                "bitmap_bytes": st.bitmap_bytes, "fallbacks": st.fallbacks}
+
+    def destroy(self):
+        if self.handle is not None and self.handle.value:
+            lib().fw_lindex_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def fw_lindex_create(rules, segments: int = 0, truncate: int = 0) -> LIndex:
+    r = _as_rules(rules)
+    cfg = fw_lindex_config()
+    cfg.segments, cfg.truncate = int(segments), int(truncate)
+    out = ctypes.c_void_p()
+    s = lib().fw_lindex_create(r.ctypes.data_as(P) if r.size else None, int(r.shape[0]), ctypes.byref(cfg),
+                               ctypes.byref(out))
+    _check(s, "fw_lindex_create")
+    return LIndex(out.value)
+
+
+def fw_lindex_classify(li: LIndex, hdrs: dict, n: int | None = None, out_idx=None, out_act=None, stream=None):
+    import torch
+    if n is None:
+        n = int(hdrs["src"].shape[0])
+    dev = hdrs["src"].device
+    if out_idx is None:
+        out_idx = torch.empty(n, dtype=torch.int32, device=dev)
+    if out_act is None:
+        out_act = torch.empty(n, dtype=torch.uint8, device=dev)
+    hs = headers_struct(hdrs)
+    s = lib().fw_lindex_classify(li.handle, ctypes.byref(hs), int(n), ctypes.c_void_p(out_idx.data_ptr()),
+                                 ctypes.c_void_p(out_act.data_ptr()), _stream_handle(stream))
+    _check(s, "fw_lindex_classify")
+    return out_idx, out_act

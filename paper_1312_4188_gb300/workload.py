@@ -215,11 +215,13 @@ def sample_positions(n: int, m: int, seed: int) -> np.ndarray:
 
 
 # Named workloads. Sizes follow the plain first-match case (1,000 rules x
-# 100,000 packets, uniform rule choice) and the scan at scale (10,000 rules x
-# 16,777,216 packets, Zipf(1.1) rule choice).
+# 100,000 packets, uniform rule choice), the scan at scale (10,000 rules x
+# 16,777,216 packets, Zipf(1.1) rule choice) and the learned-index case
+# (100,000 rules x 67,108,864 packets, uniform rule choice).
 WORKLOADS = {
     "plain_1k_x_100k": dict(n_rules=1000, n_packets=100_000, rules_seed=1, packets_seed=2, zipf_s=None),
     "scan_10k_x_16m_zipf": dict(n_rules=10_000, n_packets=1 << 24, rules_seed=3, packets_seed=4, zipf_s=1.1),
+    "lindex_100k_x_64m": dict(n_rules=100_000, n_packets=1 << 26, rules_seed=5, packets_seed=6, zipf_s=None),
 }
 
 
