@@ -188,6 +188,65 @@ int fw_classify_ex(const fw_ruleset *rs, const fw_headers *hdrs, int64_t n,
                    int32_t *out_rule_idx, uint8_t *out_action, void *stream,
                    const fw_config *cfg);
 
+/* ------------------------------------------------------------ batched plans */
+/*
+ * Many (rule set, packet batch) jobs in one persistent launch. The paper
+ * accumulates a set of packets and checks them in parallel against one rule
+ * set (Sec. IV.A) and suggests asynchronous launches to cut per-batch delay
+ * (Sec. V); a plan covers any number of rule sets and batches at once. It is
+ * built once (device work list of items: runs of up to packets_per_item
+ * packets of one job, longest rule sets first) and launched as often as
+ * needed; a persistent grid takes items from a counter, so uneven jobs
+ * balance. Each job's result is exactly fw_classify's.
+ *
+ * A job's buffers must stay valid, and keep their addresses, for the life of
+ * the plan (the plan stores the pointers; relaunching re-reads the headers and
+ * rewrites the outputs).
+ */
+typedef struct fw_job {
+    const fw_ruleset *rs;
+    fw_headers hdrs;         /* device SoA headers */
+    int64_t n;               /* packets, 0 <= n <= 2^31-1 */
+    int32_t *out_rule_idx;   /* device int32[n] */
+    uint8_t *out_action;     /* device uint8[n] */
+} fw_job;
+
+/*
+ * Plan configuration (zero = default). Rule sets fall into n_classes (1..4)
+ * size classes by reachable rules: class c takes sets with at most
+ * class_max_rules[c] rules (the last class takes the rest). Per class:
+ * packets_per_item (multiple of 128, <= 4096, default 256) and segment_rules
+ * (first rule segment of the compacting scan, multiple of 4, default 16).
+ * block_threads (default 1024) x max packets_per_item x 16 bytes of shared
+ * memory per block must fit in 227 KB.
+ */
+typedef struct fw_plan_config {
+    int32_t block_threads;
+    int32_t blocks_per_sm;
+    int32_t n_classes;
+    int32_t class_max_rules[4];
+    int32_t packets_per_item[4];
+    int32_t segment_rules[4];
+    int32_t reserved[5];
+} fw_plan_config;
+
+typedef struct fw_plan fw_plan;
+
+/* Build a plan (synchronous; copies the job list). Errors: FW_EINVAL, FW_ENOMEM, FW_ECUDA. */
+int fw_plan_create(const fw_job *jobs, int64_t n_jobs, const fw_plan_config *cfg, fw_plan **out);
+/* Enqueue the whole plan on `stream` (a counter reset and one persistent kernel). */
+int fw_plan_launch(fw_plan *plan, void *stream);
+/*
+ * Same work, replayed from a CUDA graph: the first call captures the launch
+ * on an internal stream and instantiates the graph (make it outside any
+ * capture of the caller's own); every call launches the graph on `stream`.
+ */
+int fw_plan_launch_graph(fw_plan *plan, void *stream);
+/* Number of work items in the plan (-1 for NULL). */
+int64_t fw_plan_items(const fw_plan *plan);
+/* Free the plan; no launch of it may still be in flight. */
+void fw_plan_destroy(fw_plan *plan);
+
 /* ------------------------------------------------------------ learned index */
 /*
  * Decomposition classifier with a learned locator (same result as

@@ -84,6 +84,61 @@ def sweep(rs, dh, n, candidates, reps=20, warmup=3):
     return out
 
 
+PLAN_CANDIDATES = [(ppi, seg) for ppi in (128, 256) for seg in (8, 16, 32)]
+CLASS_LIMITS = (256, 4096)  # reachable rules: <= 256, <= 4096, larger
+
+
+def time_plan(plan, reps=10, warmup=3):
+    """Median milliseconds of one graph launch of ``plan`` (CUDA events)."""
+    import torch
+    s = torch.cuda.current_stream()
+    for _ in range(warmup):
+        plan.launch(s)
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        plan.launch(s)
+        b.record(s)
+        ts.append((a, b))
+    torch.cuda.synchronize()
+    return statistics.median(x.elapsed_time(y) for x, y in ts)
+
+
+def tune_plan_classes(jobs, limits=CLASS_LIMITS, candidates=PLAN_CANDIDATES, reps=10):
+    """Pick (packets_per_item, segment_rules) per rule-set size class by timing plans of each class alone.
+
+    ``jobs``: list of (Ruleset, device headers, out_idx, out_act). Returns
+    (classes for fw.make_plan_config, per-class timing table).
+    """
+    classes, table = [], []
+    bounds = list(limits) + [1 << 30]
+    lo = -1
+    for c, hi in enumerate(bounds):
+        sub = [j for j in jobs if lo < _reach(j[0]) <= hi]
+        lo = hi
+        if not sub:
+            classes.append((hi, 256, 16))
+            continue
+        best = None
+        for ppi, seg in candidates:
+            plan = fw.fw_plan_create(sub, fw.make_plan_config([(hi, ppi, seg)]))
+            ms = time_plan(plan, reps=reps)
+            plan.destroy()
+            table.append({"class": c, "max_rules": hi, "jobs": len(sub), "packets_per_item": ppi,
+                          "segment_rules": seg, "ms": ms})
+            if best is None or ms < best[0]:
+                best = (ms, ppi, seg)
+        classes.append((hi, best[1], best[2]))
+    return classes, table
+
+
+def _reach(rs) -> int:
+    """Rules a scan of ``rs`` can reach (first catch-all + 1, else all)."""
+    ca = rs.first_catch_all
+    return ca + 1 if ca >= 0 else rs.size()
+
+
 def cache_path():
     return os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 

@@ -1,0 +1,289 @@
+// Batched classification: many (rule set, packet batch) jobs in one
+// persistent launch, optionally replayed from a CUDA graph.
+//
+// The paper's data-parallel firewall accumulates a set of packets and checks
+// them in parallel against one rule set (Sec. IV.A); its conclusions point to
+// asynchronous launches to cut per-batch delay (Sec. V). Here a plan turns a
+// list of jobs into a device work list of items, each a run of up to
+// `packets_per_item` packets of one job. A persistent grid of warps takes
+// items from a global counter (dynamic scheduling, so cheap and expensive
+// items balance), and each warp runs the compacting first-match scan of
+// fw_scan.cuh on its item against the item's own rule set, read through L1.
+// Items are ordered by decreasing rule-set size so the long scans start
+// first. Per size class of rule set (by reachable rules) the plan carries its
+// own item size and first rule segment, chosen by the autotuner.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "fw_scan.cuh"
+
+namespace fwk {
+
+struct BatchJobDev {
+    const RecArith *rec;
+    const uint32_t *wtop;
+    const uint8_t *action;
+    int32_t n_scan;
+    int32_t vec;  // 1 when the job's buffers allow the vector loads
+    HdrPtrs h;
+    int64_t n;
+    int32_t *out_idx;
+    uint8_t *out_act;
+};
+
+struct BatchItem {
+    int64_t start;
+    int32_t job;
+    int32_t count;  // <= packets_per_item of its class
+    int32_t seg0;   // first rule segment of its class
+    int32_t pad;
+};
+
+struct BatchParams {
+    const BatchJobDev *jobs;
+    const BatchItem *items;
+    int64_t n_items;
+    unsigned long long *next;  // item counter, zeroed before each launch
+    int32_t qcap;              // queue capacity per warp (packets)
+    uint32_t one;
+};
+
+template <bool VEC>
+__device__ __forceinline__ void batch_item(const BatchJobDev &J, const BatchItem &it, uint4 *Q, uint32_t one,
+                                           int lane) {
+    using Pol = PolArith;
+    const int64_t base = it.start;
+    const int cnt = it.count;
+    const int64_t nloc = J.n;
+    for (int qq = lane; qq * 4 < cnt; qq += 32) {
+        Pol::Pk pk[4];
+        int c;
+        load_quad<Pol, VEC>(J.h, nloc, base / 4 + qq, pk, c);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (j < c && qq * 4 + j < cnt) Q[qq * 4 + j] = Pol::pack(pk[j], qq * 4 + j);
+    }
+    __syncwarp();
+    const Pol::View gv{J.rec, J.wtop};
+    int m = cnt, s0 = 0, s1 = it.seg0;
+    while (m > 0) {
+        s1 = min(s1, J.n_scan);
+        const bool last = s1 >= J.n_scan;
+        int w = 0;
+        for (int g0 = 0; g0 < m; g0 += 32) {
+            const int i = g0 + lane;
+            const bool valid = i < m;
+            const uint4 e = valid ? Q[i] : make_uint4(0, 0, 0, 0);
+            __syncwarp();
+            int slot;
+            const Pol::Pk pk = Pol::unpack(e, slot);
+            int r = -1;
+            if (valid && s0 < s1) r = scan_range<Pol>(pk, s0, s1, gv, 0, gv, nullptr, nullptr, one);
+            const bool keep = valid && r == -1 && !last;
+            if (valid && !keep) {
+                const int v = r >= 0 ? r : -1;
+                J.out_idx[base + slot] = v;
+                J.out_act[base + slot] = v >= 0 ? __ldg(J.action + v) : (uint8_t)FW_DROP;
+            }
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
+            if (keep) Q[w + __popc(bal & ((1u << lane) - 1u))] = e;
+            w += __popc(bal);
+            __syncwarp();
+        }
+        m = w;
+        s0 = s1;
+        s1 = s1 * 2;
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(1024) k_batch(BatchParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint4 *Q = reinterpret_cast<uint4 *>(smem) + (size_t)warp * p.qcap;
+    for (;;) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(p.next, 1ull);
+        it = __shfl_sync(0xFFFFFFFFu, it, 0);
+        if (it >= (unsigned long long)p.n_items) break;
+        const BatchItem item = p.items[it];
+        const BatchJobDev &J = p.jobs[item.job];
+        if (J.vec) batch_item<true>(J, item, Q, p.one, lane);
+        else batch_item<false>(J, item, Q, p.one, lane);
+    }
+}
+
+}  // namespace fwk
+
+struct fw_plan {
+    int device = 0;
+    int threads = 1024;
+    int64_t blocks = 1;
+    size_t smem = 0;
+    int64_t n_items = 0;
+    int64_t n_jobs = 0;
+    int64_t packets = 0;
+    fwk::BatchJobDev *d_jobs = nullptr;
+    fwk::BatchItem *d_items = nullptr;
+    unsigned long long *d_next = nullptr;
+    int32_t qcap = 256;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+using namespace fwk;
+
+static bool al(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+extern "C" void fw_plan_destroy(fw_plan *pl) {
+    if (pl == nullptr) return;
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+    cudaFree(pl->d_jobs);
+    cudaFree(pl->d_items);
+    cudaFree(pl->d_next);
+    delete pl;
+}
+
+extern "C" int fw_plan_create(const fw_job *jobs, int64_t n_jobs, const fw_plan_config *cfg_in, fw_plan **out) {
+    if (out == nullptr) return set_status(FW_EINVAL);
+    *out = nullptr;
+    if (n_jobs < 0 || (n_jobs > 0 && jobs == nullptr) || n_jobs > (1 << 24)) return set_status(FW_EINVAL);
+    fw_plan_config cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    if (cfg_in) cfg = *cfg_in;
+    const int n_classes = cfg.n_classes > 0 ? cfg.n_classes : 1;
+    if (n_classes > 4) return set_status(FW_EINVAL);
+    int32_t per_item[4], seg0[4];
+    int32_t qcap = 0;
+    for (int c = 0; c < n_classes; ++c) {
+        per_item[c] = cfg.packets_per_item[c] > 0 ? cfg.packets_per_item[c] : 256;
+        seg0[c] = cfg.segment_rules[c] > 0 ? cfg.segment_rules[c] : 16;
+        if (per_item[c] % 128 != 0 || per_item[c] > 4096 || seg0[c] % 4 != 0) return set_status(FW_EINVAL);
+        qcap = std::max(qcap, per_item[c]);
+    }
+    const int threads = cfg.block_threads > 0 ? cfg.block_threads : 1024;
+    if (threads % 32 != 0 || threads > 1024) return set_status(FW_EINVAL);
+    const size_t smem = (size_t)(threads / 32) * qcap * sizeof(uint4);
+    if (smem > 227 * 1024) return set_status(FW_EINVAL);
+
+    std::vector<BatchJobDev> hj((size_t)n_jobs);
+    std::vector<int> cls((size_t)n_jobs);
+    int64_t packets = 0;
+    for (int64_t j = 0; j < n_jobs; ++j) {
+        const fw_job &J = jobs[j];
+        if (J.rs == nullptr || J.n < 0 || J.n > INT32_MAX) return set_status(FW_EINVAL);
+        if (J.n > 0 && (!J.hdrs.src || !J.hdrs.dst || !J.hdrs.sport || !J.hdrs.dport || !J.hdrs.proto ||
+                        !J.out_rule_idx || !J.out_action))
+            return set_status(FW_EINVAL);
+        BatchJobDev &d = hj[j];
+        d.rec = J.rs->d_arith;
+        d.wtop = J.rs->d_wtop;
+        d.action = J.rs->d_action;
+        d.n_scan = (int32_t)((J.rs->n_eff + 3) / 4 * 4);
+        d.vec = al(J.hdrs.src, 16) && al(J.hdrs.dst, 16) && al(J.hdrs.sport, 8) && al(J.hdrs.dport, 8) &&
+                al(J.hdrs.proto, 4);
+        d.h = HdrPtrs{J.hdrs.src, J.hdrs.dst, J.hdrs.sport, J.hdrs.dport, J.hdrs.proto};
+        d.n = J.n;
+        d.out_idx = J.out_rule_idx;
+        d.out_act = J.out_action;
+        int c = 0;
+        while (c < n_classes - 1 && J.rs->n_eff > cfg.class_max_rules[c]) ++c;
+        cls[j] = c;
+        packets += J.n;
+    }
+    // items, longest scans first
+    std::vector<int64_t> order((size_t)n_jobs);
+    for (int64_t j = 0; j < n_jobs; ++j) order[j] = j;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return hj[a].n_scan > hj[b].n_scan; });
+    std::vector<BatchItem> items;
+    for (int64_t j : order) {
+        const int B = per_item[cls[j]];
+        for (int64_t s = 0; s < hj[j].n; s += B) {
+            BatchItem it;
+            it.start = s;
+            it.job = (int32_t)j;
+            it.count = (int32_t)std::min<int64_t>(B, hj[j].n - s);
+            it.seg0 = seg0[cls[j]];
+            it.pad = 0;
+            items.push_back(it);
+        }
+    }
+    fw_plan *pl = new (std::nothrow) fw_plan();
+    if (pl == nullptr) return set_status(FW_ENOMEM);
+    cudaGetDevice(&pl->device);
+    pl->threads = threads;
+    pl->smem = smem;
+    pl->qcap = qcap;
+    pl->n_items = (int64_t)items.size();
+    pl->n_jobs = n_jobs;
+    pl->packets = packets;
+    const int per_sm = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : 1;
+    pl->blocks = std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)sm_count(pl->device) * per_sm, (pl->n_items + threads / 32 - 1) / (threads / 32)));
+    cudaError_t e = cudaMalloc(&pl->d_jobs, std::max<size_t>(1, hj.size()) * sizeof(BatchJobDev));
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_items, std::max<size_t>(1, items.size()) * sizeof(BatchItem));
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_next, sizeof(unsigned long long));
+    if (e == cudaSuccess && !hj.empty())
+        e = cudaMemcpy(pl->d_jobs, hj.data(), hj.size() * sizeof(BatchJobDev), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !items.empty())
+        e = cudaMemcpy(pl->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) {
+        fw_plan_destroy(pl);
+        cudaGetLastError();
+        return set_status(cuda_status(e));
+    }
+    *out = pl;
+    return FW_OK;
+}
+
+static cudaError_t enqueue_plan(fw_plan *pl, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(pl->d_next, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess || pl->n_items == 0) return e;
+    BatchParams p;
+    p.jobs = pl->d_jobs;
+    p.items = pl->d_items;
+    p.n_items = pl->n_items;
+    p.next = pl->d_next;
+    p.qcap = pl->qcap;
+    p.one = 1u;
+    k_batch<<<(unsigned)pl->blocks, pl->threads, pl->smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+extern "C" int fw_plan_launch(fw_plan *pl, void *stream) {
+    if (pl == nullptr) return set_status(FW_EINVAL);
+    return set_status(cuda_status(enqueue_plan(pl, reinterpret_cast<cudaStream_t>(stream))));
+}
+
+extern "C" int fw_plan_launch_graph(fw_plan *pl, void *stream) {
+    if (pl == nullptr) return set_status(FW_EINVAL);
+    cudaError_t e = cudaSuccess;
+    if (pl->exec == nullptr) {
+        if (pl->cap_stream == nullptr) e = cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t eq = enqueue_plan(pl, pl->cap_stream);
+            cudaGraph_t g = nullptr;
+            e = cudaStreamEndCapture(pl->cap_stream, &g);
+            if (eq != cudaSuccess) e = eq;
+            if (e == cudaSuccess) {
+                pl->graph = g;
+                e = cudaGraphInstantiate(&pl->exec, pl->graph, 0);
+            } else if (g) {
+                cudaGraphDestroy(g);
+            }
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_status(cuda_status(e));
+        }
+    }
+    return set_status(cuda_status(cudaGraphLaunch(pl->exec, reinterpret_cast<cudaStream_t>(stream))));
+}
+
+extern "C" int64_t fw_plan_items(const fw_plan *pl) { return pl ? pl->n_items : -1; }

@@ -1,0 +1,318 @@
+// Record policies, packet loads and rule-scan helpers shared by the scan
+// kernels (fw_scan.cu) and the batched persistent kernel (fw_batch.cu).
+#pragma once
+
+#include "fw_internal.cuh"
+
+namespace fwk {
+
+struct HdrPtrs {
+    const uint32_t *src;
+    const uint32_t *dst;
+    const uint16_t *sport;
+    const uint16_t *dport;
+    const uint8_t *proto;
+};
+
+struct ScanParams {
+    const void *rec;       // records of the chosen form (RecClamp / RecCmp / RecArith)
+    const uint32_t *wtop;  // arithmetic form: per-rule wtop words
+    const uint8_t *action;
+    int n_scan;   // rules scanned: n_eff rounded up to a multiple of 4 (padding never matches)
+    int n_smem;   // rules resident in shared memory (multiple of kChunkRules, <= n_pad)
+    int batch;    // compacting kernel: packets per warp batch (multiple of 128)
+    int seg0;     // compacting kernel: rules in the first segment (multiple of 4)
+    uint32_t one; // the constant 1, opaque to the compiler (see mismatch_arith)
+    HdrPtrs h;
+    int64_t n;
+    int32_t *out_idx;
+    uint8_t *out_act;
+    unsigned *status;
+};
+
+// ------------------------------------------------------------ record policies
+// How a record form is laid out, fetched and tested, and how a packet is held.
+// A View locates the records of rules [0, n) either in global memory or in
+// the block's shared-memory prefix (same layout in both).
+struct PolClamp {
+    using Rec = RecClamp;
+    using Pk = Pkt;
+    struct R {
+        uint4 a, b;
+    };
+    struct View {
+        const Rec *rec;
+    };
+    static __host__ __device__ size_t bytes_per_rule() { return sizeof(Rec); }
+    static __device__ __forceinline__ View global_view(const ScanParams &p) {
+        return {reinterpret_cast<const Rec *>(p.rec)};
+    }
+    static __device__ __forceinline__ View smem_view(unsigned char *sm, int) { return {reinterpret_cast<const Rec *>(sm)}; }
+    // chunk c of the shared prefix: one bulk copy of kChunkRules records
+    static __device__ __forceinline__ uint32_t stage(unsigned char *sm, int, const ScanParams &p, int c, uint64_t *bar) {
+        const uint32_t bytes = kChunkRules * sizeof(Rec);
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_load(sm + (size_t)c * bytes, reinterpret_cast<const unsigned char *>(p.rec) + (size_t)c * bytes, bytes, bar);
+        return bytes;
+    }
+    template <bool SMEM>
+    static __device__ __forceinline__ void load4(const View &v, int k, R r[4]) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (SMEM) r[j] = {v.rec[k + j].a, v.rec[k + j].b};
+            else r[j] = {__ldg(&v.rec[k + j].a), __ldg(&v.rec[k + j].b)};
+        }
+    }
+    static __device__ __forceinline__ Pk make(uint32_t s, uint32_t d, uint32_t sp, uint32_t dp, uint32_t pr) {
+        return {s, d, ports_of(sp, dp), pr};
+    }
+    static __device__ __forceinline__ bool mism(const Pk &p, const R &r, uint32_t) {
+        return mismatch_clamp(p, r.a, r.b) != 0u;
+    }
+    static __device__ __forceinline__ bool all_mismatch4(const Pk &p, const R r[4], uint32_t one) {
+        return mism(p, r[0], one) & mism(p, r[1], one) & mism(p, r[2], one) & mism(p, r[3], one);
+    }
+    // queue entry: the packet with its batch slot above the protocol byte
+    static __device__ __forceinline__ uint4 pack(const Pk &p, int slot) {
+        return make_uint4(p.src, p.dst, p.ports, p.proto | ((uint32_t)slot << 8));
+    }
+    static __device__ __forceinline__ Pk unpack(const uint4 &e, int &slot) {
+        slot = (int)(e.w >> 8);
+        return {e.x, e.y, e.z, e.w & 0xFFu};
+    }
+};
+
+struct PolCmp {
+    using Rec = RecCmp;
+    using Pk = Pkt;
+    struct R {
+        uint4 a, b, c;
+    };
+    struct View {
+        const Rec *rec;
+    };
+    static __host__ __device__ size_t bytes_per_rule() { return sizeof(Rec); }
+    static __device__ __forceinline__ View global_view(const ScanParams &p) {
+        return {reinterpret_cast<const Rec *>(p.rec)};
+    }
+    static __device__ __forceinline__ View smem_view(unsigned char *sm, int) { return {reinterpret_cast<const Rec *>(sm)}; }
+    static __device__ __forceinline__ uint32_t stage(unsigned char *sm, int, const ScanParams &p, int c, uint64_t *bar) {
+        const uint32_t bytes = kChunkRules * sizeof(Rec);
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_load(sm + (size_t)c * bytes, reinterpret_cast<const unsigned char *>(p.rec) + (size_t)c * bytes, bytes, bar);
+        return bytes;
+    }
+    template <bool SMEM>
+    static __device__ __forceinline__ void load4(const View &v, int k, R r[4]) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (SMEM) r[j] = {v.rec[k + j].a, v.rec[k + j].b, v.rec[k + j].c};
+            else r[j] = {__ldg(&v.rec[k + j].a), __ldg(&v.rec[k + j].b), __ldg(&v.rec[k + j].c)};
+        }
+    }
+    static __device__ __forceinline__ Pk make(uint32_t s, uint32_t d, uint32_t sp, uint32_t dp, uint32_t pr) {
+        return {s, d, ports_of(sp, dp), pr};
+    }
+    static __device__ __forceinline__ bool mism(const Pk &p, const R &r, uint32_t) {
+        return !match_cmp(p, r.a, r.b, r.c);
+    }
+    static __device__ __forceinline__ bool all_mismatch4(const Pk &p, const R r[4], uint32_t one) {
+        return mism(p, r[0], one) & mism(p, r[1], one) & mism(p, r[2], one) & mism(p, r[3], one);
+    }
+    static __device__ __forceinline__ uint4 pack(const Pk &p, int slot) { return PolClamp::pack(p, slot); }
+    static __device__ __forceinline__ Pk unpack(const uint4 &e, int &slot) { return PolClamp::unpack(e, slot); }
+};
+
+struct PolArith {
+    using Rec = RecArith;
+    using Pk = PktA;
+    struct R {
+        uint4 a, b;
+        uint32_t w;
+    };
+    struct View {
+        const Rec *rec;
+        const uint32_t *wtop;
+    };
+    static __host__ __device__ size_t bytes_per_rule() { return sizeof(Rec) + sizeof(uint32_t); }
+    static __device__ __forceinline__ View global_view(const ScanParams &p) {
+        return {reinterpret_cast<const Rec *>(p.rec), p.wtop};
+    }
+    // shared layout: [n_smem records][n_smem wtop words]
+    static __device__ __forceinline__ View smem_view(unsigned char *sm, int n_smem) {
+        return {reinterpret_cast<const Rec *>(sm), reinterpret_cast<const uint32_t *>(sm + (size_t)n_smem * sizeof(Rec))};
+    }
+    static __device__ __forceinline__ uint32_t stage(unsigned char *sm, int n_smem, const ScanParams &p, int c,
+                                                     uint64_t *bar) {
+        const uint32_t rb = kChunkRules * sizeof(Rec), wb = kChunkRules * sizeof(uint32_t);
+        mbar_arrive_expect_tx(bar, rb + wb);
+        bulk_load(sm + (size_t)c * rb, reinterpret_cast<const unsigned char *>(p.rec) + (size_t)c * rb, rb, bar);
+        bulk_load(sm + (size_t)n_smem * sizeof(Rec) + (size_t)c * wb,
+                  reinterpret_cast<const unsigned char *>(p.wtop) + (size_t)c * wb, wb, bar);
+        return rb + wb;
+    }
+    template <bool SMEM>
+    static __device__ __forceinline__ void load4(const View &v, int k, R r[4]) {
+        const uint4 w = SMEM ? *reinterpret_cast<const uint4 *>(v.wtop + k)
+                             : __ldg(reinterpret_cast<const uint4 *>(v.wtop + k));
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (SMEM) {
+                r[j].a = v.rec[k + j].a;
+                r[j].b = v.rec[k + j].b;
+            } else {
+                r[j].a = __ldg(&v.rec[k + j].a);
+                r[j].b = __ldg(&v.rec[k + j].b);
+            }
+        }
+        r[0].w = w.x;
+        r[1].w = w.y;
+        r[2].w = w.z;
+        r[3].w = w.w;
+    }
+    static __device__ __forceinline__ Pk make(uint32_t s, uint32_t d, uint32_t sp, uint32_t dp, uint32_t pr) {
+        return {s, d, sp, x_of(pr, dp)};
+    }
+    static __device__ __forceinline__ bool mism(const Pk &p, const R &r, uint32_t one) {
+        return mismatch_arith(p, r.a, r.b, r.w, one);
+    }
+    static __device__ __forceinline__ bool all_mismatch4(const Pk &p, const R r[4], uint32_t one) {
+        return mism(p, r[0], one) & mism(p, r[1], one) & mism(p, r[2], one) & mism(p, r[3], one);
+    }
+    // queue entry: the batch slot above the 16-bit source port
+    static __device__ __forceinline__ uint4 pack(const Pk &p, int slot) {
+        return make_uint4(p.src, p.dst, p.sport | ((uint32_t)slot << 16), p.x);
+    }
+    static __device__ __forceinline__ Pk unpack(const uint4 &e, int &slot) {
+        slot = (int)(e.z >> 16);
+        return {e.x, e.y, e.z & 0xFFFFu, e.w};
+    }
+};
+
+// Range form: the arithmetic-form layout with every field a range test.
+struct PolRange : PolArith {
+    static __device__ __forceinline__ bool mism(const Pk &p, const R &r, uint32_t one) {
+        return mismatch_range_c(p, r.a, r.b, r.w, one);
+    }
+    static __device__ __forceinline__ bool all_mismatch4(const Pk &p, const R r[4], uint32_t one) {
+        uint32_t t[16], w[16];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            t[4 * j + 0] = p.src * one + r[j].a.x;
+            w[4 * j + 0] = r[j].a.y;
+            t[4 * j + 1] = p.dst * one + r[j].a.z;
+            w[4 * j + 1] = r[j].a.w;
+            t[4 * j + 2] = p.sport * one + r[j].b.x;
+            w[4 * j + 2] = r[j].b.y;
+            t[4 * j + 3] = p.x * r[j].b.z + r[j].b.w;
+            w[4 * j + 3] = r[j].w;
+        }
+        return all_mismatch4_range(t, w) != 0u;
+    }
+};
+
+// ------------------------------------------------------------ packet loads
+template <class Pol, bool VEC>
+__device__ __forceinline__ void load_quad(const HdrPtrs &h, int64_t n, int64_t q, typename Pol::Pk pk[4],
+                                          int &cnt) {
+    const int64_t base = q * 4;
+    if (VEC && base + 3 < n) {
+        uint4 s = __ldcs(reinterpret_cast<const uint4 *>(h.src) + q);
+        uint4 d = __ldcs(reinterpret_cast<const uint4 *>(h.dst) + q);
+        uint2 sp = __ldcs(reinterpret_cast<const uint2 *>(h.sport) + q);
+        uint2 dp = __ldcs(reinterpret_cast<const uint2 *>(h.dport) + q);
+        uint32_t pr = __ldcs(reinterpret_cast<const unsigned int *>(h.proto) + q);
+        pk[0] = Pol::make(s.x, d.x, sp.x & 0xFFFFu, dp.x & 0xFFFFu, pr & 0xFFu);
+        pk[1] = Pol::make(s.y, d.y, sp.x >> 16, dp.x >> 16, (pr >> 8) & 0xFFu);
+        pk[2] = Pol::make(s.z, d.z, sp.y & 0xFFFFu, dp.y & 0xFFFFu, (pr >> 16) & 0xFFu);
+        pk[3] = Pol::make(s.w, d.w, sp.y >> 16, dp.y >> 16, pr >> 24);
+        cnt = 4;
+    } else {
+        cnt = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int64_t i = base + j;
+            if (i < n) {
+                pk[j] = Pol::make(h.src[i], h.dst[i], h.sport[i], h.dport[i], h.proto[i]);
+                cnt = j + 1;
+            } else {
+                pk[j] = Pol::make(0, 0, 0, 0, 0);
+            }
+        }
+    }
+}
+
+template <bool VEC>
+__device__ __forceinline__ void store_quad(const ScanParams &p, int64_t q, const int idx[4], int cnt) {
+    const int64_t base = q * 4;
+    uint32_t a[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a[j] = idx[j] >= 0 ? __ldg(p.action + idx[j]) : (uint32_t)FW_DROP;
+    if (VEC && cnt == 4) {
+        __stcs(reinterpret_cast<int4 *>(p.out_idx) + q, make_int4(idx[0], idx[1], idx[2], idx[3]));
+        __stcs(reinterpret_cast<unsigned int *>(p.out_act) + q, a[0] | (a[1] << 8) | (a[2] << 16) | (a[3] << 24));
+    } else {
+        for (int j = 0; j < cnt; ++j) {
+            p.out_idx[base + j] = idx[j];
+            p.out_act[base + j] = (uint8_t)a[j];
+        }
+    }
+}
+
+// ------------------------------------------------------------ rule scans
+// First index in [k0, k1) whose rule matches, or -1 (k0, k1 multiples of 4).
+// Rules below n_smem come from shared memory (chunk c usable once bars[c]
+// completed), the rest from global memory. Returns -2 if a chunk wait timed out.
+template <class Pol, bool SMEM>
+__device__ __forceinline__ int scan_block4(const typename Pol::Pk &pk, const typename Pol::View &v, int k,
+                                           uint32_t one) {
+    typename Pol::R r[4];
+    Pol::template load4<SMEM>(v, k, r);
+    if (Pol::all_mismatch4(pk, r, one)) return -1;
+    // once per decided packet: which of the four matched first
+    return k + (!Pol::mism(pk, r[0], one) ? 0 : !Pol::mism(pk, r[1], one) ? 1 : !Pol::mism(pk, r[2], one) ? 2 : 3);
+}
+
+template <class Pol>
+__device__ __forceinline__ int scan_range(const typename Pol::Pk &pk, int k0, int k1, const typename Pol::View &sv,
+                                          int n_smem, const typename Pol::View &gv, uint64_t *bars, unsigned *status,
+                                          uint32_t one) {
+    int k = k0;
+    const int lim = min(k1, n_smem);
+    while (k < lim) {
+        if (!mbar_wait_bounded(&bars[k / kChunkRules], 0, status)) return -2;
+        const int kend = min(lim, (k / kChunkRules + 1) * kChunkRules);
+        for (; k < kend; k += 4) {
+            const int r = scan_block4<Pol, true>(pk, sv, k, one);
+            if (r >= 0) return r;
+        }
+    }
+    for (; k < k1; k += 4) {
+        const int r = scan_block4<Pol, false>(pk, gv, k, one);
+        if (r >= 0) return r;
+    }
+    return -1;
+}
+
+// Shared-memory rule prefix: mbarrier init + TMA bulk copies, one barrier per chunk.
+template <class Pol>
+__device__ __forceinline__ uint64_t *stage_rules(unsigned char *smem, const ScanParams &p) {
+    const int n_chunks = p.n_smem / kChunkRules;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)p.n_smem * Pol::bytes_per_rule());
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < n_chunks; ++c) mbar_init(&bars[c], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int c = 0; c < n_chunks; ++c) Pol::stage(smem, p.n_smem, p, c, &bars[c]);
+    return bars;
+}
+
+// Do not leave while a bulk copy into this block's shared memory may be in flight.
+__device__ __forceinline__ void drain_rules(uint64_t *bars, int n_smem, unsigned *status) {
+    if (threadIdx.x == 0)
+        for (int c = 0; c < n_smem / kChunkRules; ++c) mbar_wait_bounded(&bars[c], 0, status);
+}
+
+}  // namespace fwk

@@ -88,6 +88,17 @@ class fw_lindex_stats(ctypes.Structure):
                 ("bitmap_bytes", ctypes.c_int64), ("fallbacks", ctypes.c_int64)]
 
 
+class fw_job(ctypes.Structure):
+    _fields_ = [("rs", ctypes.c_void_p), ("hdrs", fw_headers), ("n", ctypes.c_int64),
+                ("out_rule_idx", ctypes.c_void_p), ("out_action", ctypes.c_void_p)]
+
+
+class fw_plan_config(ctypes.Structure):
+    _fields_ = [("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("n_classes", ctypes.c_int32),
+                ("class_max_rules", ctypes.c_int32 * 4), ("packets_per_item", ctypes.c_int32 * 4),
+                ("segment_rules", ctypes.c_int32 * 4), ("reserved", ctypes.c_int32 * 5)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -114,6 +125,12 @@ SIGNATURES = {
     "fw_lindex_destroy": (None, [P]),
     "fw_lindex_classify": (ctypes.c_int, [P, ctypes.POINTER(fw_headers), I64, P, P, P]),
     "fw_lindex_get_stats": (ctypes.c_int, [P, ctypes.POINTER(fw_lindex_stats)]),
+    "fw_plan_create": (ctypes.c_int, [ctypes.POINTER(fw_job), I64, ctypes.POINTER(fw_plan_config),
+                                      ctypes.POINTER(P)]),
+    "fw_plan_launch": (ctypes.c_int, [P, P]),
+    "fw_plan_launch_graph": (ctypes.c_int, [P, P]),
+    "fw_plan_items": (I64, [P]),
+    "fw_plan_destroy": (None, [P]),
     "fw_last_status": (ctypes.c_int, []),
     "fw_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "fw_abi_version": (ctypes.c_int, []),
@@ -339,3 +356,52 @@ def fw_lindex_classify(li: LIndex, hdrs: dict, n: int | None = None, out_idx=Non
                                  ctypes.c_void_p(out_act.data_ptr()), _stream_handle(stream))
     _check(s, "fw_lindex_classify")
     return out_idx, out_act
+
+
+def make_plan_config(classes=None, block_threads=0, blocks_per_sm=0) -> fw_plan_config:
+    """``classes``: list of (max_rules, packets_per_item, segment_rules); the last max_rules is ignored."""
+    c = fw_plan_config()
+    c.block_threads, c.blocks_per_sm = int(block_threads), int(blocks_per_sm)
+    classes = classes or []
+    c.n_classes = len(classes)
+    for i, (mx, ppi, seg) in enumerate(classes):
+        c.class_max_rules[i], c.packets_per_item[i], c.segment_rules[i] = int(mx), int(ppi), int(seg)
+    return c
+
+
+class Plan:
+    """Owning wrapper of an ``fw_plan*``; keeps the jobs' tensors alive."""
+
+    def __init__(self, handle: int, keep):
+        self.handle = ctypes.c_void_p(handle)
+        self._keep = keep
+
+    def items(self) -> int:
+        return int(lib().fw_plan_items(self.handle))
+
+    def launch(self, stream=None, graph: bool = True):
+        fn = lib().fw_plan_launch_graph if graph else lib().fw_plan_launch
+        _check(fn(self.handle, _stream_handle(stream)), "fw_plan_launch")
+
+    def destroy(self):
+        if self.handle is not None and self.handle.value:
+            lib().fw_plan_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def fw_plan_create(jobs, config: fw_plan_config | None = None) -> Plan:
+    """``jobs``: list of (Ruleset, device header dict, out_idx tensor, out_act tensor)."""
+    arr = (fw_job * max(1, len(jobs)))()
+    for i, (rs, h, oi, oa) in enumerate(jobs):
+        n = int(h["src"].shape[0])
+        arr[i] = fw_job(rs.handle, headers_struct(h), n, ctypes.c_void_p(oi.data_ptr()), ctypes.c_void_p(oa.data_ptr()))
+    out = ctypes.c_void_p()
+    s = lib().fw_plan_create(arr, len(jobs), ctypes.byref(config) if config is not None else None, ctypes.byref(out))
+    _check(s, "fw_plan_create")
+    return Plan(out.value, list(jobs))

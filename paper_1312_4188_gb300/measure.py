@@ -67,7 +67,55 @@ def lindex(args):
     return out
 
 
-COMMANDS = {"lindex": lindex}
+def batched(args):
+    import torch
+
+    from . import autotune
+    data = W.gen_batched(256, seed=7)
+    jobs = []
+    for rules, hdr in data:
+        n = len(hdr["src"])
+        jobs.append((fw.fw_ruleset_create(rules), fw.headers_to_device(hdr),
+                     torch.empty(n, dtype=torch.int32, device="cuda"), torch.empty(n, dtype=torch.uint8, device="cuda")))
+    total = sum(len(h["src"]) for _, h in data)
+    n_rules = sum(len(r) for r, _ in data)
+    ref = [(torch.empty_like(j[2]), torch.empty_like(j[3])) for j in jobs]
+
+    def sequential():
+        for (rs, dh, _, _), (oi, oa) in zip(jobs, ref):
+            fw.fw_classify(rs, dh, int(dh["src"].shape[0]), oi, oa)
+
+    t_seq = _events_ms(sequential, reps=5, warmup=2)
+    depth_sum = 0
+    for (rs, _, _, _), (oi, _) in zip(jobs, ref):
+        depth_sum += int(torch.where(oi >= 0, oi.to(torch.int64) + 1,
+                                     torch.full_like(oi, rs.size(), dtype=torch.int64)).sum())
+    out = [{"form": "sequential_fw_classify", "workload": "batched_256_sets", "sets": len(jobs), "packets": total,
+            "rules": n_rules, "ms": t_seq, "mpackets_s": total / t_seq / 1e3, "rule_checks_per_s": depth_sum / t_seq * 1e3,
+            "launches": len(jobs)}]
+    t0 = time.perf_counter()
+    classes, table = autotune.tune_plan_classes(jobs, reps=3)
+    tune_s = time.perf_counter() - t0
+    for label, cfg in (("plan_default_graph", None), ("plan_autotuned_graph", fw.make_plan_config(classes))):
+        plan = fw.fw_plan_create(jobs, cfg)
+        t = _events_ms(lambda: plan.launch(graph=True), reps=10, warmup=3)
+        torch.cuda.synchronize()
+        same = all(torch.equal(j[2], r[0]) and torch.equal(j[3], r[1]) for j, r in zip(jobs, ref))
+        line = {"form": label, "ms": t, "mpackets_s": total / t / 1e3, "rule_checks_per_s": depth_sum / t * 1e3,
+                "speedup_vs_sequential": t_seq / t, "same_as_sequential": same, "items": plan.items(),
+                "graph_nodes": "memset + persistent kernel"}
+        if cfg is not None:
+            line["classes"] = classes
+            line["tune_s"] = tune_s
+            line["tune_table"] = table
+        out.append(line)
+        plan.destroy()
+    for j in jobs:
+        j[0].destroy()
+    return out
+
+
+COMMANDS = {"lindex": lindex, "batched": batched}
 
 
 def main(argv=None):

@@ -231,3 +231,26 @@ def make_workload(name: str, n_packets: int | None = None):
     n = w["n_packets"] if n_packets is None else n_packets
     hdr = gen_packets(rules, n, w["packets_seed"], zipf_s=w["zipf_s"])
     return rules, hdr
+
+
+def log_uniform_int(rng: np.random.Generator, lo: int, hi: int, size: int) -> np.ndarray:
+    """Integers log-uniform on [lo, hi]."""
+    return np.floor(np.exp(rng.uniform(np.log(lo), np.log(hi + 1), size=size))).astype(np.int64).clip(lo, hi)
+
+
+def gen_batched(n_sets: int = 256, seed: int = 7, rules_range=(64, 65536), packets_range=(1024, 1 << 20),
+                zipf_s: float | None = None):
+    """``n_sets`` independent (rules, headers) jobs with log-uniform rule and packet counts.
+
+    Every set is drawn with the rule generator above from its own seed, and its
+    batch with the packet generator (same 60/40 in-rule / uniform mix).
+    """
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence((int(seed), 0x42415443))))
+    nr = log_uniform_int(rng, rules_range[0], rules_range[1], n_sets)
+    npk = log_uniform_int(rng, packets_range[0], packets_range[1], n_sets)
+    jobs = []
+    for i in range(n_sets):
+        rules = gen_rules(int(nr[i]), 1_000_000 + 1000 * int(seed) + i)
+        hdr = gen_packets(rules, int(npk[i]), 2_000_000 + 1000 * int(seed) + i, zipf_s=zipf_s)
+        jobs.append((rules, hdr))
+    return jobs
