@@ -247,6 +247,92 @@ int64_t fw_plan_items(const fw_plan *plan);
 /* Free the plan; no launch of it may still be in flight. */
 void fw_plan_destroy(fw_plan *plan);
 
+/* ------------------------------------------------------------ serving */
+/*
+ * Continuous batching of classification requests (a packet batch for one of
+ * the server's device-resident rule sets). A scheduler thread owns `slots`
+ * streams; whenever one is free it admits the queued requests that fit (at
+ * most max_group_requests requests and max_group_packets packets and, in
+ * copy mode, free space in a device staging arena of arena_bytes) and
+ * launches them together as one persistent batched kernel. A finished group
+ * releases its slot and memory at once, so requests that arrive while others
+ * run join the next launch and groups overlap on the device. Each request's
+ * result is exactly fw_classify's for its batch.
+ *
+ * Modes: FW_HOST_COPY (default): request buffers are ordinary host memory
+ * (pinned for speed); headers are copied in and verdicts out through the
+ * arena. FW_HOST_ZEROCOPY: request buffers must be device memory or pinned
+ * host memory; the kernel reads and writes them in place (over the host link
+ * for host memory) and no arena is used.
+ * A request's buffers must stay valid until it is waited for. The server
+ * stands in for the paper's queue-to-user-space and reinject loop (Sec. IV,
+ * Fig. 1) and realises its asynchronous launches (Sec. V).
+ */
+typedef struct fw_server_config {
+    int32_t mode;                /* FW_HOST_COPY (0 = default) or FW_HOST_ZEROCOPY */
+    int32_t slots;               /* groups in flight at once, 1..16 (default 4) */
+    int32_t max_group_requests;  /* requests per launch (default 256) */
+    int32_t max_pending;         /* queue capacity; submit returns FW_EBUSY beyond it (default 65536) */
+    int64_t max_group_packets;   /* packets per launch (default 2^20); also the largest request */
+    int64_t arena_bytes;         /* copy mode device staging budget (default 256 MiB) */
+    int32_t packets_per_item;    /* kernel work item (multiple of 128, default 256) */
+    int32_t segment_rules;       /* first rule segment of the compacting scan (default 16) */
+    int32_t block_threads;       /* kernel block size (default 512) */
+    int32_t reserved[5];
+} fw_server_config;
+
+typedef struct fw_server_stats {
+    int64_t submitted, completed, failed, packets;
+    int64_t groups;               /* launches */
+    int64_t max_group_requests;   /* largest group admitted */
+    int64_t max_inflight_groups;  /* most groups on the device at once */
+    int64_t arena_high_water;     /* most arena bytes in use at once */
+    int64_t pending;              /* queued now */
+} fw_server_stats;
+
+/* One request of a replayed arrival schedule (fw_server_replay). */
+typedef struct fw_request {
+    int32_t set;             /* rule set index */
+    int32_t status;          /* out: FW_OK or an error */
+    fw_headers hdrs;         /* request buffers, as for fw_server_submit */
+    int64_t n;
+    int32_t *out_rule_idx;
+    uint8_t *out_action;
+    double arrival_us;       /* in: arrival time after the replay starts */
+    double latency_us;       /* out: completion time minus scheduled arrival */
+} fw_request;
+
+typedef struct fw_server fw_server;
+
+/* Start a server over n_sets rule sets (the caller keeps them alive until destroy). */
+int fw_server_create(const fw_ruleset *const *sets, int n_sets, const fw_server_config *cfg, fw_server **out);
+/* Finish all queued and running requests, stop the scheduler, free everything. */
+void fw_server_destroy(fw_server *sv);
+/*
+ * Queue a request of n (1..max_group_packets) packets for rule set `set`;
+ * *ticket identifies it. Returns at once. FW_EBUSY when the queue is full,
+ * FW_ERANGE when the request can never fit (too many packets, or more arena
+ * bytes than the arena has), FW_EINVAL for bad arguments (in zero-copy mode
+ * also for buffers the device cannot reach).
+ */
+int fw_server_submit(fw_server *sv, int set, const fw_headers *hdrs, int64_t n, int32_t *out_rule_idx,
+                     uint8_t *out_action, uint64_t *ticket);
+/*
+ * Wait for a request (timeout_us < 0: no limit); on return other than
+ * FW_ETIMEOUT the ticket is released and *latency_us (may be NULL) holds
+ * completion minus submit time in microseconds. Returns the request's status.
+ */
+int fw_server_wait(fw_server *sv, uint64_t ticket, int64_t timeout_us, double *latency_us);
+/* Wait until nothing is queued or running (tickets stay valid for fw_server_wait). */
+int fw_server_drain(fw_server *sv, int64_t timeout_us);
+int fw_server_get_stats(fw_server *sv, fw_server_stats *st);
+/*
+ * Open-loop replay: submit reqs[i] at arrival_us[i] after the call starts
+ * (retrying while the queue is full), then wait for all of them and fill
+ * status and latency_us. Returns FW_OK when every request succeeded.
+ */
+int fw_server_replay(fw_server *sv, fw_request *reqs, int64_t n, int64_t timeout_us);
+
 /* ------------------------------------------------------------ learned index */
 /*
  * Decomposition classifier with a learned locator (same result as

@@ -16,38 +16,9 @@
 #include <cstring>
 #include <vector>
 
-#include "fw_scan.cuh"
+#include "fw_batch.cuh"
 
 namespace fwk {
-
-struct BatchJobDev {
-    const RecArith *rec;
-    const uint32_t *wtop;
-    const uint8_t *action;
-    int32_t n_scan;
-    int32_t vec;  // 1 when the job's buffers allow the vector loads
-    HdrPtrs h;
-    int64_t n;
-    int32_t *out_idx;
-    uint8_t *out_act;
-};
-
-struct BatchItem {
-    int64_t start;
-    int32_t job;
-    int32_t count;  // <= packets_per_item of its class
-    int32_t seg0;   // first rule segment of its class
-    int32_t pad;
-};
-
-struct BatchParams {
-    const BatchJobDev *jobs;
-    const BatchItem *items;
-    int64_t n_items;
-    unsigned long long *next;  // item counter, zeroed before each launch
-    int32_t qcap;              // queue capacity per warp (packets)
-    uint32_t one;
-};
 
 template <bool VEC>
 __device__ __forceinline__ void batch_item(const BatchJobDev &J, const BatchItem &it, uint4 *Q, uint32_t one,
@@ -114,6 +85,40 @@ __global__ void __launch_bounds__(1024) k_batch(BatchParams p) {
     }
 }
 
+static bool al(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+void fill_batch_job(BatchJobDev &d, const fw_ruleset *rs, const fw_headers &h, int64_t n, int32_t *out_idx,
+                    uint8_t *out_act) {
+    d.rec = rs->d_arith;
+    d.wtop = rs->d_wtop;
+    d.action = rs->d_action;
+    d.n_scan = (int32_t)((rs->n_eff + 3) / 4 * 4);
+    d.vec = al(h.src, 16) && al(h.dst, 16) && al(h.sport, 8) && al(h.dport, 8) && al(h.proto, 4);
+    d.h = HdrPtrs{h.src, h.dst, h.sport, h.dport, h.proto};
+    d.n = n;
+    d.out_idx = out_idx;
+    d.out_act = out_act;
+}
+
+cudaError_t prepare_batch_kernel(size_t smem_bytes) {
+    return cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+}
+
+cudaError_t launch_batch(const BatchJobDev *d_jobs, const BatchItem *d_items, int64_t n_items,
+                         unsigned long long *d_next, int32_t qcap, int threads, int64_t blocks, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(d_next, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess || n_items == 0) return e;
+    BatchParams p;
+    p.jobs = d_jobs;
+    p.items = d_items;
+    p.n_items = n_items;
+    p.next = d_next;
+    p.qcap = qcap;
+    p.one = 1u;
+    k_batch<<<(unsigned)blocks, threads, (size_t)(threads / 32) * qcap * sizeof(uint4), st>>>(p);
+    return cudaGetLastError();
+}
+
 }  // namespace fwk
 
 struct fw_plan {
@@ -134,8 +139,6 @@ struct fw_plan {
 };
 
 using namespace fwk;
-
-static bool al(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 extern "C" void fw_plan_destroy(fw_plan *pl) {
     if (pl == nullptr) return;
@@ -179,17 +182,7 @@ extern "C" int fw_plan_create(const fw_job *jobs, int64_t n_jobs, const fw_plan_
         if (J.n > 0 && (!J.hdrs.src || !J.hdrs.dst || !J.hdrs.sport || !J.hdrs.dport || !J.hdrs.proto ||
                         !J.out_rule_idx || !J.out_action))
             return set_status(FW_EINVAL);
-        BatchJobDev &d = hj[j];
-        d.rec = J.rs->d_arith;
-        d.wtop = J.rs->d_wtop;
-        d.action = J.rs->d_action;
-        d.n_scan = (int32_t)((J.rs->n_eff + 3) / 4 * 4);
-        d.vec = al(J.hdrs.src, 16) && al(J.hdrs.dst, 16) && al(J.hdrs.sport, 8) && al(J.hdrs.dport, 8) &&
-                al(J.hdrs.proto, 4);
-        d.h = HdrPtrs{J.hdrs.src, J.hdrs.dst, J.hdrs.sport, J.hdrs.dport, J.hdrs.proto};
-        d.n = J.n;
-        d.out_idx = J.out_rule_idx;
-        d.out_act = J.out_action;
+        fill_batch_job(hj[j], J.rs, J.hdrs, J.n, J.out_rule_idx, J.out_action);
         int c = 0;
         while (c < n_classes - 1 && J.rs->n_eff > cfg.class_max_rules[c]) ++c;
         cls[j] = c;
@@ -231,7 +224,7 @@ extern "C" int fw_plan_create(const fw_job *jobs, int64_t n_jobs, const fw_plan_
         e = cudaMemcpy(pl->d_jobs, hj.data(), hj.size() * sizeof(BatchJobDev), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !items.empty())
         e = cudaMemcpy(pl->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = prepare_batch_kernel(smem);
     if (e != cudaSuccess) {
         fw_plan_destroy(pl);
         cudaGetLastError();
@@ -242,17 +235,7 @@ extern "C" int fw_plan_create(const fw_job *jobs, int64_t n_jobs, const fw_plan_
 }
 
 static cudaError_t enqueue_plan(fw_plan *pl, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(pl->d_next, 0, sizeof(unsigned long long), st);
-    if (e != cudaSuccess || pl->n_items == 0) return e;
-    BatchParams p;
-    p.jobs = pl->d_jobs;
-    p.items = pl->d_items;
-    p.n_items = pl->n_items;
-    p.next = pl->d_next;
-    p.qcap = pl->qcap;
-    p.one = 1u;
-    k_batch<<<(unsigned)pl->blocks, pl->threads, pl->smem, st>>>(p);
-    return cudaGetLastError();
+    return launch_batch(pl->d_jobs, pl->d_items, pl->n_items, pl->d_next, pl->qcap, pl->threads, pl->blocks, st);
 }
 
 extern "C" int fw_plan_launch(fw_plan *pl, void *stream) {

@@ -1,0 +1,49 @@
+// Work-list types of the batched persistent kernel (fw_batch.cu), shared with
+// the serving scheduler (fw_serve.cu).
+#pragma once
+
+#include "fw_scan.cuh"
+
+namespace fwk {
+
+struct BatchJobDev {
+    const RecArith *rec;
+    const uint32_t *wtop;
+    const uint8_t *action;
+    int32_t n_scan;
+    int32_t vec;  // 1 when the job's buffers allow the vector loads
+    HdrPtrs h;
+    int64_t n;
+    int32_t *out_idx;
+    uint8_t *out_act;
+};
+
+struct BatchItem {
+    int64_t start;
+    int32_t job;
+    int32_t count;  // <= packets_per_item of its class
+    int32_t seg0;   // first rule segment of its class
+    int32_t pad;
+};
+
+struct BatchParams {
+    const BatchJobDev *jobs;
+    const BatchItem *items;
+    int64_t n_items;
+    unsigned long long *next;  // item counter, zeroed before each launch
+    int32_t qcap;              // queue capacity per warp (packets)
+    uint32_t one;
+};
+
+// Fill a job entry from a rule set and device-accessible buffers.
+void fill_batch_job(BatchJobDev &d, const fw_ruleset *rs, const fw_headers &h, int64_t n, int32_t *out_idx,
+                    uint8_t *out_act);
+
+// Zero the item counter and launch the persistent kernel on `st` (nothing but
+// the counter reset when n_items is 0). The kernel's shared-memory limit must
+// have been raised with prepare_batch_kernel for `qcap` and `threads`.
+cudaError_t launch_batch(const BatchJobDev *d_jobs, const BatchItem *d_items, int64_t n_items,
+                         unsigned long long *d_next, int32_t qcap, int threads, int64_t blocks, cudaStream_t st);
+cudaError_t prepare_batch_kernel(size_t smem_bytes);
+
+}  // namespace fwk

@@ -99,6 +99,25 @@ class fw_plan_config(ctypes.Structure):
                 ("segment_rules", ctypes.c_int32 * 4), ("reserved", ctypes.c_int32 * 5)]
 
 
+class fw_server_config(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("slots", ctypes.c_int32), ("max_group_requests", ctypes.c_int32),
+                ("max_pending", ctypes.c_int32), ("max_group_packets", ctypes.c_int64),
+                ("arena_bytes", ctypes.c_int64), ("packets_per_item", ctypes.c_int32),
+                ("segment_rules", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+
+class fw_server_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "completed", "failed", "packets", "groups",
+                                               "max_group_requests", "max_inflight_groups", "arena_high_water",
+                                               "pending")]
+
+
+class fw_request(ctypes.Structure):
+    _fields_ = [("set", ctypes.c_int32), ("status", ctypes.c_int32), ("hdrs", fw_headers), ("n", ctypes.c_int64),
+                ("out_rule_idx", ctypes.c_void_p), ("out_action", ctypes.c_void_p), ("arrival_us", ctypes.c_double),
+                ("latency_us", ctypes.c_double)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -131,6 +150,15 @@ SIGNATURES = {
     "fw_plan_launch_graph": (ctypes.c_int, [P, P]),
     "fw_plan_items": (I64, [P]),
     "fw_plan_destroy": (None, [P]),
+    "fw_server_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(fw_server_config),
+                                        ctypes.POINTER(P)]),
+    "fw_server_destroy": (None, [P]),
+    "fw_server_submit": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(fw_headers), I64, P, P,
+                                        ctypes.POINTER(ctypes.c_uint64)]),
+    "fw_server_wait": (ctypes.c_int, [P, ctypes.c_uint64, I64, ctypes.POINTER(ctypes.c_double)]),
+    "fw_server_drain": (ctypes.c_int, [P, I64]),
+    "fw_server_get_stats": (ctypes.c_int, [P, ctypes.POINTER(fw_server_stats)]),
+    "fw_server_replay": (ctypes.c_int, [P, ctypes.POINTER(fw_request), I64, I64]),
     "fw_last_status": (ctypes.c_int, []),
     "fw_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "fw_abi_version": (ctypes.c_int, []),
@@ -405,3 +433,72 @@ def fw_plan_create(jobs, config: fw_plan_config | None = None) -> Plan:
     s = lib().fw_plan_create(arr, len(jobs), ctypes.byref(config) if config is not None else None, ctypes.byref(out))
     _check(s, "fw_plan_create")
     return Plan(out.value, list(jobs))
+
+
+class Server:
+    """Owning wrapper of an ``fw_server*`` (continuous-batching classification service)."""
+
+    def __init__(self, rulesets, **cfg):
+        self._sets = list(rulesets)
+        arr = (ctypes.c_void_p * len(self._sets))(*[r.handle.value for r in self._sets])
+        c = fw_server_config()
+        for k, v in cfg.items():
+            setattr(c, k, int(v))
+        out = ctypes.c_void_p()
+        _check(lib().fw_server_create(arr, len(self._sets), ctypes.byref(c), ctypes.byref(out)), "fw_server_create")
+        self.handle = out
+
+    def submit(self, set_index: int, hdrs: dict, out_idx, out_act, n: int | None = None) -> int:
+        """Queue a request; returns its ticket. Raises FwError (e.g. FW_EBUSY when the queue is full)."""
+        if n is None:
+            n = int(hdrs["src"].shape[0])
+        hs = headers_struct(hdrs)
+        t = ctypes.c_uint64()
+        s = lib().fw_server_submit(self.handle, int(set_index), ctypes.byref(hs), int(n),
+                                   ctypes.c_void_p(out_idx.data_ptr()), ctypes.c_void_p(out_act.data_ptr()),
+                                   ctypes.byref(t))
+        _check(s, "fw_server_submit")
+        return int(t.value)
+
+    def wait(self, ticket: int, timeout_us: int = -1):
+        """(status, latency_us) of a request; releases the ticket."""
+        lat = ctypes.c_double()
+        s = lib().fw_server_wait(self.handle, ctypes.c_uint64(ticket), int(timeout_us), ctypes.byref(lat))
+        return int(s), float(lat.value)
+
+    def drain(self, timeout_us: int = -1) -> int:
+        return int(lib().fw_server_drain(self.handle, int(timeout_us)))
+
+    def stats(self) -> dict:
+        st = fw_server_stats()
+        _check(lib().fw_server_get_stats(self.handle, ctypes.byref(st)), "fw_server_get_stats")
+        return {k: int(getattr(st, k)) for k, _ in fw_server_stats._fields_}
+
+    def replay(self, specs, timeout_us: int = 60_000_000):
+        """``specs``: list of (set, hdrs dict, out_idx, out_act, arrival_us). Returns (status array, latency array)."""
+        arr = (fw_request * len(specs))()
+        for i, (st, h, oi, oa, t) in enumerate(specs):
+            arr[i] = fw_request(int(st), 0, headers_struct(h), int(h["src"].shape[0]), ctypes.c_void_p(oi.data_ptr()),
+                                ctypes.c_void_p(oa.data_ptr()), float(t), 0.0)
+        s = lib().fw_server_replay(self.handle, arr, len(specs), int(timeout_us))
+        status = np.array([r.status for r in arr], dtype=np.int32)
+        lat = np.array([r.latency_us for r in arr], dtype=np.float64)
+        return int(s), status, lat
+
+    def destroy(self):
+        if self.handle is not None and self.handle.value:
+            lib().fw_server_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def pinned_headers(h: dict) -> dict:
+    """Pinned host tensors holding the bytes of numpy SoA headers."""
+    import torch
+    views = {"src": np.int32, "dst": np.int32, "sport": np.int16, "dport": np.int16, "proto": np.uint8}
+    return {f: torch.from_numpy(np.ascontiguousarray(h[f]).view(views[f])).pin_memory() for f in HEADER_FIELDS}

@@ -115,7 +115,67 @@ def batched(args):
     return out
 
 
-COMMANDS = {"lindex": lindex, "batched": batched}
+def serving(args):
+    """Poisson arrivals of log-uniform 64..65536-packet batches against 4 rule sets (1K/10K/50K/100K rules)."""
+    import numpy as np
+    import torch
+    sizes = [1000, 10_000, 50_000, 100_000]
+    rules = [W.gen_rules(n, 40 + i) for i, n in enumerate(sizes)]
+    sets = [fw.fw_ruleset_create(r) for r in rules]
+    pool_n = 1 << 20
+    pools = [fw.pinned_headers(W.gen_packets(r, pool_n, 50 + i)) for i, r in enumerate(rules)]
+    dpools = [{f: t.cuda() for f, t in p.items()} for p in pools]
+    rng = np.random.default_rng(5)
+    n_req = 4000
+    req_set = rng.integers(0, 4, size=n_req)
+    req_n = W.log_uniform_int(rng, 64, 65536, n_req)
+    req_off = (rng.integers(0, pool_n - 65536, size=n_req) // 4) * 4
+    total = int(req_n.sum())
+    out_i = torch.empty(total, dtype=torch.int32).pin_memory()
+    out_a = torch.empty(total, dtype=torch.uint8).pin_memory()
+    offs = np.concatenate([[0], np.cumsum(req_n)[:-1]])
+    # the plain scan of every request, for the check
+    ref_i = torch.empty(total, dtype=torch.int32, device="cuda")
+    ref_a = torch.empty(total, dtype=torch.uint8, device="cuda")
+    for k in range(n_req):
+        s, o, n, off = int(req_set[k]), int(req_off[k]), int(req_n[k]), int(offs[k])
+        fw.fw_classify(sets[s], {f: t[o:o + n] for f, t in dpools[s].items()}, n, ref_i[off:off + n], ref_a[off:off + n])
+    torch.cuda.synchronize()
+    ref_i, ref_a = ref_i.cpu(), ref_a.cpu()
+    mean_n = float(req_n.mean())
+    out = []
+    for mode, mname, slots in ((fw.FW_HOST_ZEROCOPY, "zerocopy", 4), (fw.FW_HOST_ZEROCOPY, "zerocopy", 8),
+                               (fw.FW_HOST_COPY, "copy", 4)):
+        sv = fw.Server(sets, mode=mode, slots=slots, max_group_requests=256, arena_bytes=1 << 30)
+        for load_gpps in (0.1, 0.25, 0.5, 1, 2, 4, 8, 16, 32):
+            rate = load_gpps * 1e9 / mean_n  # requests per second
+            arrivals = np.cumsum(rng.exponential(1e6 / rate, size=n_req))
+            specs = []
+            for k in range(n_req):
+                s, o, n, off = int(req_set[k]), int(req_off[k]), int(req_n[k]), int(offs[k])
+                specs.append((s, {f: t[o:o + n] for f, t in pools[s].items()}, out_i[off:off + n], out_a[off:off + n],
+                              float(arrivals[k])))
+            out_i.fill_(-7)
+            st0 = sv.stats()
+            t0 = time.perf_counter()
+            rc, status, lat = sv.replay(specs)
+            wall = time.perf_counter() - t0
+            st1 = sv.stats()
+            same = bool(torch.equal(out_i, ref_i) and torch.equal(out_a, ref_a))
+            groups = st1["groups"] - st0["groups"]
+            out.append({"form": f"serve_{mname}_slots{slots}", "offered_gpackets_s": load_gpps, "requests": n_req,
+                        "packets": total, "achieved_mpackets_s": total / wall / 1e6, "wall_s": wall,
+                        "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
+                        "mean_us": float(lat.mean()), "ok": bool(rc == fw.FW_OK and np.all(status == 0)),
+                        "same_as_scan": same, "groups": groups, "requests_per_group": n_req / max(groups, 1),
+                        "max_inflight_groups": st1["max_inflight_groups"], "arena_high_water": st1["arena_high_water"]})
+        sv.destroy()
+    for r in sets:
+        r.destroy()
+    return out
+
+
+COMMANDS = {"lindex": lindex, "batched": batched, "serving": serving}
 
 
 def main(argv=None):
