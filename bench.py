@@ -42,7 +42,8 @@ OPS_PER_CHECK = 8
 BYTES_PER_PACKET = 18
 INT32_LANES_PER_SM_CLK = 128  # 4 schedulers x 32 lanes, one warp instruction per clock each
 FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "sms": 152}
-KERNEL_SOURCES = ["paper_1312_4188_gb300/csrc/fw_scan.cu", "paper_1312_4188_gb300/csrc/fw_internal.cuh"]
+KERNEL_SOURCES = ["paper_1312_4188_gb300/csrc/fw_scan.cu", "paper_1312_4188_gb300/csrc/fw_scan.cuh",
+                  "paper_1312_4188_gb300/csrc/fw_internal.cuh"]
 KERNEL_NAME = "k_packet_split_compact"
 TRAFFIC_RECORD = "profiles/k_packet_split_compact_scan_10k_x_16m.md"
 
@@ -56,7 +57,7 @@ def parse():
     ap.add_argument("--workload", default="scan_10k_x_16m_zipf", choices=sorted(W.WORKLOADS))
     ap.add_argument("--mode", default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-modes", action="store_true", help="skip the per-decomposition side measurements")
+    ap.add_argument("--modes", action="store_true", help="also time every decomposition / record form (side lines)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     return ap.parse_args()
 
@@ -301,7 +302,7 @@ def main():
         "gpu_launches": launches_per_step * args.steps,
     }
 
-    if rank == 0 and not args.no_modes:
+    if rank == 0 and args.modes:
         modes = {}
         variants = {"packet_split": ("packet_split", {}),
                     "packet_split_lockstep": ("packet_split", {"compact": 2}),

@@ -50,7 +50,7 @@ __device__ __forceinline__ void batch_item(const BatchJobDev &J, const BatchItem
             int slot;
             const Pol::Pk pk = Pol::unpack(e, slot);
             int r = -1;
-            if (valid && s0 < s1) r = scan_range<Pol>(pk, s0, s1, gv, 0, gv, nullptr, nullptr, one);
+            if (valid && s0 < s1) r = scan_range<Pol>(pk, s0, s1, gv, 0, gv, one);
             const bool keep = valid && r == -1 && !last;
             if (valid && !keep) {
                 const int v = r >= 0 ? r : -1;

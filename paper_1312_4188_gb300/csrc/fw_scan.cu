@@ -33,7 +33,9 @@ namespace fwk {
 template <class Pol, bool VEC>
 __global__ void __launch_bounds__(1024) k_packet_split(ScanParams p) {
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *bars = stage_rules<Pol>(smem, p);
+    // a failed prefix wait leaves every rule to be read from global memory
+    const bool staged = stage_rules<Pol>(smem, p);
+    const int n_smem = staged ? p.n_smem : 0;
     const typename Pol::View sv = Pol::smem_view(smem, p.n_smem);
     const typename Pol::View gv = Pol::global_view(p);
     const int64_t nq = (p.n + 3) / 4;
@@ -45,12 +47,12 @@ __global__ void __launch_bounds__(1024) k_packet_split(ScanParams p) {
         int idx[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int r = scan_range<Pol>(pk[j], 0, p.n_scan, sv, p.n_smem, gv, bars, p.status, p.one);
+            const int r = scan_range<Pol>(pk[j], 0, p.n_scan, sv, n_smem, gv, p.one);
             idx[j] = r < 0 ? -1 : r;
         }
         store_quad<VEC>(p, q, idx, cnt);
     }
-    drain_rules(bars, p.n_smem, p.status);
+    if (!staged) drain_rules<Pol>(smem, p);
 }
 
 // Compacting form. Each warp takes a batch of `batch` packets into its own
@@ -63,7 +65,8 @@ __global__ void __launch_bounds__(1024) k_packet_split(ScanParams p) {
 template <class Pol, bool VEC>
 __global__ void __launch_bounds__(1024) k_packet_split_compact(ScanParams p) {
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *bars = stage_rules<Pol>(smem, p);
+    const bool staged = stage_rules<Pol>(smem, p);
+    const int n_smem = staged ? p.n_smem : 0;
     const typename Pol::View sv = Pol::smem_view(smem, p.n_smem);
     const typename Pol::View gv = Pol::global_view(p);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -96,7 +99,7 @@ __global__ void __launch_bounds__(1024) k_packet_split_compact(ScanParams p) {
                 int slot;
                 const typename Pol::Pk pk = Pol::unpack(e, slot);
                 int r = -1;
-                if (valid && s0 < s1) r = scan_range<Pol>(pk, s0, s1, sv, p.n_smem, gv, bars, p.status, p.one);
+                if (valid && s0 < s1) r = scan_range<Pol>(pk, s0, s1, sv, n_smem, gv, p.one);
                 const bool keep = valid && r == -1 && !last;
                 if (valid && !keep) {
                     const int v = r >= 0 ? r : -1;
@@ -113,7 +116,7 @@ __global__ void __launch_bounds__(1024) k_packet_split_compact(ScanParams p) {
             s1 = s1 * 2;
         }
     }
-    drain_rules(bars, p.n_smem, p.status);
+    if (!staged) drain_rules<Pol>(smem, p);
 }
 
 // ------------------------------------------------------------ rule split kernel

@@ -260,9 +260,7 @@ __device__ __forceinline__ void store_quad(const ScanParams &p, int64_t q, const
 }
 
 // ------------------------------------------------------------ rule scans
-// First index in [k0, k1) whose rule matches, or -1 (k0, k1 multiples of 4).
-// Rules below n_smem come from shared memory (chunk c usable once bars[c]
-// completed), the rest from global memory. Returns -2 if a chunk wait timed out.
+// Rules k..k+3 against one packet: k + (first of the four that matches), or -1.
 template <class Pol, bool SMEM>
 __device__ __forceinline__ int scan_block4(const typename Pol::Pk &pk, const typename Pol::View &v, int k,
                                            uint32_t one) {
@@ -273,19 +271,17 @@ __device__ __forceinline__ int scan_block4(const typename Pol::Pk &pk, const typ
     return k + (!Pol::mism(pk, r[0], one) ? 0 : !Pol::mism(pk, r[1], one) ? 1 : !Pol::mism(pk, r[2], one) ? 2 : 3);
 }
 
+// First index in [k0, k1) whose rule matches, or -1 (k0, k1 multiples of 4).
+// Rules below n_smem come from the block's shared-memory prefix (already
+// resident: see stage_rules), the rest from global memory.
 template <class Pol>
 __device__ __forceinline__ int scan_range(const typename Pol::Pk &pk, int k0, int k1, const typename Pol::View &sv,
-                                          int n_smem, const typename Pol::View &gv, uint64_t *bars, unsigned *status,
-                                          uint32_t one) {
+                                          int n_smem, const typename Pol::View &gv, uint32_t one) {
     int k = k0;
     const int lim = min(k1, n_smem);
-    while (k < lim) {
-        if (!mbar_wait_bounded(&bars[k / kChunkRules], 0, status)) return -2;
-        const int kend = min(lim, (k / kChunkRules + 1) * kChunkRules);
-        for (; k < kend; k += 4) {
-            const int r = scan_block4<Pol, true>(pk, sv, k, one);
-            if (r >= 0) return r;
-        }
+    for (; k < lim; k += 4) {
+        const int r = scan_block4<Pol, true>(pk, sv, k, one);
+        if (r >= 0) return r;
     }
     for (; k < k1; k += 4) {
         const int r = scan_block4<Pol, false>(pk, gv, k, one);
@@ -294,9 +290,13 @@ __device__ __forceinline__ int scan_range(const typename Pol::Pk &pk, int k0, in
     return -1;
 }
 
-// Shared-memory rule prefix: mbarrier init + TMA bulk copies, one barrier per chunk.
+// Shared-memory rule prefix: one mbarrier per 256-rule chunk, the chunks
+// brought in by 1-D TMA bulk copies issued by thread 0, then every thread
+// waits (bounded) until all chunks have landed. A persistent block does this
+// once and then serves millions of packets from the prefix. Returns false if
+// a wait gave up (the status word is set; the caller must not use the prefix).
 template <class Pol>
-__device__ __forceinline__ uint64_t *stage_rules(unsigned char *smem, const ScanParams &p) {
+__device__ __forceinline__ bool stage_rules(unsigned char *smem, const ScanParams &p) {
     const int n_chunks = p.n_smem / kChunkRules;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)p.n_smem * Pol::bytes_per_rule());
     if (threadIdx.x == 0) {
@@ -306,13 +306,18 @@ __device__ __forceinline__ uint64_t *stage_rules(unsigned char *smem, const Scan
     __syncthreads();
     if (threadIdx.x == 0)
         for (int c = 0; c < n_chunks; ++c) Pol::stage(smem, p.n_smem, p, c, &bars[c]);
-    return bars;
+    bool ok = true;
+    for (int c = 0; c < n_chunks; ++c) ok = mbar_wait_bounded(&bars[c], 0, p.status) && ok;
+    return __syncthreads_and(ok) != 0;
 }
 
-// Do not leave while a bulk copy into this block's shared memory may be in flight.
-__device__ __forceinline__ void drain_rules(uint64_t *bars, int n_smem, unsigned *status) {
+// After a failed stage_rules: before the block exits, give copies that may
+// still be in flight into its shared memory a second bounded wait.
+template <class Pol>
+__device__ __forceinline__ void drain_rules(unsigned char *smem, const ScanParams &p) {
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)p.n_smem * Pol::bytes_per_rule());
     if (threadIdx.x == 0)
-        for (int c = 0; c < n_smem / kChunkRules; ++c) mbar_wait_bounded(&bars[c], 0, status);
+        for (int c = 0; c < p.n_smem / kChunkRules; ++c) mbar_wait_bounded(&bars[c], 0, p.status);
 }
 
 }  // namespace fwk
