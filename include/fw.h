@@ -118,6 +118,14 @@ typedef struct fw_headers {
  *                     (0 = default).
  *  segment_rules:     packet split with compaction: rules in the first segment
  *                     (multiple of 4; later segments double).
+ *  partition:         packet split, arithmetic form: 1 = scan the protocol
+ *                     partition (default), 2 = scan the whole list. A rule set
+ *                     keeps, per protocol class (the exact protocols its rules
+ *                     use most, plus "every other protocol"), the sub-list of
+ *                     rules whose protocol can match that class, in list order;
+ *                     a packet scans only its class's sub-list, which contains
+ *                     every rule that can match it, so the first match is the
+ *                     same.
  */
 typedef struct fw_config {
     int32_t mode;
@@ -129,7 +137,8 @@ typedef struct fw_config {
     int32_t compact;
     int32_t predicate;
     int32_t segment_rules;
-    int32_t reserved[7];           /* must be zero */
+    int32_t partition;
+    int32_t reserved[6];           /* must be zero */
 } fw_config;
 
 typedef struct fw_ruleset fw_ruleset;
@@ -216,7 +225,7 @@ typedef struct fw_job {
  * size classes by reachable rules: class c takes sets with at most
  * class_max_rules[c] rules (the last class takes the rest). Per class:
  * packets_per_item (multiple of 128, <= 4096, default 256) and segment_rules
- * (first rule segment of the compacting scan, multiple of 4, default 16).
+ * (first rule segment of the compacting scan, multiple of 4, default 64).
  * block_threads (default 1024) x max packets_per_item x 16 bytes of shared
  * memory per block must fit in 227 KB.
  */
@@ -276,7 +285,7 @@ typedef struct fw_server_config {
     int64_t max_group_packets;   /* packets per launch (default 2^20); also the largest request */
     int64_t arena_bytes;         /* copy mode device staging budget (default 256 MiB) */
     int32_t packets_per_item;    /* kernel work item (multiple of 128, default 256) */
-    int32_t segment_rules;       /* first rule segment of the compacting scan (default 16) */
+    int32_t segment_rules;       /* first rule segment of the compacting scan (default 64) */
     int32_t block_threads;       /* kernel block size (default 512) */
     int32_t reserved[5];
 } fw_server_config;

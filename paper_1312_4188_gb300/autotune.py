@@ -19,12 +19,18 @@ import sys
 from . import fw
 
 PACKET_SPLIT_CANDIDATES = (
-    [dict(mode="packet_split", compact=2, predicate=p)
+    [dict(mode="packet_split", compact=c, partition=1, block_threads=bt, blocks_per_sm=bps, smem_rules=sr,
+          packets_per_group=b, segment_rules=s0)
+     for c in (1,) for (bt, bps, sr, b) in ((1024, 1, 2048, 256), (1024, 1, 2048, 128), (768, 1, 2048, 256),
+                                           (512, 2, 1024, 256), (512, 1, 2048, 512))
+     for s0 in (8, 16, 32, 64, 128)]
+    + [dict(mode="packet_split", compact=2, partition=1)]
+    + [dict(mode="packet_split", compact=2, predicate=p, partition=2)
      for p in (fw.FW_PRED_CLAMP, fw.FW_PRED_CMP, fw.FW_PRED_ARITH, fw.FW_PRED_RANGE)]
     + [dict(mode="packet_split", compact=1, predicate=fw.FW_PRED_RANGE, block_threads=1024, blocks_per_sm=1,
             smem_rules=sr, packets_per_group=256, segment_rules=s0) for sr in (1024, 2048) for s0 in (16, 32)]
-    + [dict(mode="packet_split", compact=1, predicate=fw.FW_PRED_ARITH, block_threads=bt, blocks_per_sm=bps,
-            smem_rules=sr, packets_per_group=b, segment_rules=s0)
+    + [dict(mode="packet_split", compact=1, predicate=fw.FW_PRED_ARITH, partition=2, block_threads=bt,
+            blocks_per_sm=bps, smem_rules=sr, packets_per_group=b, segment_rules=s0)
        for (bt, bps, sr, b) in ((1024, 1, 2048, 256), (1024, 1, 2048, 128), (512, 2, 1024, 256), (768, 1, 2048, 256),
                                 (768, 1, 3072, 256), (1024, 1, 1024, 256))
        for s0 in (8, 16, 32)]
@@ -84,7 +90,7 @@ def sweep(rs, dh, n, candidates, reps=20, warmup=3):
     return out
 
 
-PLAN_CANDIDATES = [(ppi, seg) for ppi in (128, 256) for seg in (8, 16, 32)]
+PLAN_CANDIDATES = [(ppi, seg) for ppi in (128, 256) for seg in (16, 64, 256)]
 CLASS_LIMITS = (256, 4096)  # reachable rules: <= 256, <= 4096, larger
 
 
@@ -118,7 +124,7 @@ def tune_plan_classes(jobs, limits=CLASS_LIMITS, candidates=PLAN_CANDIDATES, rep
         sub = [j for j in jobs if lo < _reach(j[0]) <= hi]
         lo = hi
         if not sub:
-            classes.append((hi, 256, 16))
+            classes.append((hi, 256, 64))
             continue
         best = None
         for ppi, seg in candidates:

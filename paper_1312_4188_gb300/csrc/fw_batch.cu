@@ -20,59 +20,11 @@
 
 namespace fwk {
 
-template <bool VEC>
-__device__ __forceinline__ void batch_item(const BatchJobDev &J, const BatchItem &it, uint4 *Q, uint32_t one,
-                                           int lane) {
-    using Pol = PolArith;
-    const int64_t base = it.start;
-    const int cnt = it.count;
-    const int64_t nloc = J.n;
-    for (int qq = lane; qq * 4 < cnt; qq += 32) {
-        Pol::Pk pk[4];
-        int c;
-        load_quad<Pol, VEC>(J.h, nloc, base / 4 + qq, pk, c);
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (j < c && qq * 4 + j < cnt) Q[qq * 4 + j] = Pol::pack(pk[j], qq * 4 + j);
-    }
-    __syncwarp();
-    const Pol::View gv{J.rec, J.wtop};
-    int m = cnt, s0 = 0, s1 = it.seg0;
-    while (m > 0) {
-        s1 = min(s1, J.n_scan);
-        const bool last = s1 >= J.n_scan;
-        int w = 0;
-        for (int g0 = 0; g0 < m; g0 += 32) {
-            const int i = g0 + lane;
-            const bool valid = i < m;
-            const uint4 e = valid ? Q[i] : make_uint4(0, 0, 0, 0);
-            __syncwarp();
-            int slot;
-            const Pol::Pk pk = Pol::unpack(e, slot);
-            int r = -1;
-            if (valid && s0 < s1) r = scan_range<Pol>(pk, s0, s1, gv, 0, gv, one);
-            const bool keep = valid && r == -1 && !last;
-            if (valid && !keep) {
-                const int v = r >= 0 ? r : -1;
-                J.out_idx[base + slot] = v;
-                J.out_act[base + slot] = v >= 0 ? __ldg(J.action + v) : (uint8_t)FW_DROP;
-            }
-            const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
-            if (keep) Q[w + __popc(bal & ((1u << lane) - 1u))] = e;
-            w += __popc(bal);
-            __syncwarp();
-        }
-        m = w;
-        s0 = s1;
-        s1 = s1 * 2;
-    }
-    __syncwarp();
-}
-
 __global__ void __launch_bounds__(1024) k_batch(BatchParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     uint4 *Q = reinterpret_cast<uint4 *>(smem) + (size_t)warp * p.qcap;
+    int *wc = reinterpret_cast<int *>(smem + (size_t)nw * p.qcap * sizeof(uint4)) + warp * 2 * kMaxClasses;
     for (;;) {
         unsigned long long it = 0;
         if (lane == 0) it = atomicAdd(p.next, 1ull);
@@ -80,8 +32,25 @@ __global__ void __launch_bounds__(1024) k_batch(BatchParams p) {
         if (it >= (unsigned long long)p.n_items) break;
         const BatchItem item = p.items[it];
         const BatchJobDev &J = p.jobs[item.job];
-        if (J.vec) batch_item<true>(J, item, Q, p.one, lane);
-        else batch_item<false>(J, item, Q, p.one, lane);
+        BatchTarget<PolArith> t;
+        t.h = J.h;
+        t.n = J.n;
+        t.gv = PolArith::View{J.rec, J.wtop};
+        t.sv = t.gv;
+        t.n_smem = 0;  // rules come through L1: jobs of one launch use different rule sets
+        t.n_scan = 0;
+        t.n_classes = J.n_classes;
+        t.class_off = J.class_off;
+        t.class_len = J.class_len;
+        t.class_of = J.class_of;
+        t.orig = J.orig;
+        t.action = J.action;
+        t.out_idx = J.out_idx;
+        t.out_act = J.out_act;
+        t.seg0 = item.seg0;
+        t.one = p.one;
+        if (J.vec) run_batch<PolArith, true, true>(t, item.start, item.count, Q, wc, lane);
+        else run_batch<PolArith, false, true>(t, item.start, item.count, Q, wc, lane);
     }
 }
 
@@ -89,15 +58,25 @@ static bool al(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p)
 
 void fill_batch_job(BatchJobDev &d, const fw_ruleset *rs, const fw_headers &h, int64_t n, int32_t *out_idx,
                     uint8_t *out_act) {
-    d.rec = rs->d_arith;
-    d.wtop = rs->d_wtop;
+    d.rec = rs->d_part;
+    d.wtop = rs->d_part_wtop;
     d.action = rs->d_action;
-    d.n_scan = (int32_t)((rs->n_eff + 3) / 4 * 4);
+    d.orig = rs->d_part_orig;
+    d.class_of = rs->d_class_of;
+    d.n_classes = rs->n_classes;
+    for (int c = 0; c < kMaxClasses; ++c) {
+        d.class_off[c] = rs->class_off[c];
+        d.class_len[c] = rs->class_len[c];
+    }
     d.vec = al(h.src, 16) && al(h.dst, 16) && al(h.sport, 8) && al(h.dport, 8) && al(h.proto, 4);
     d.h = HdrPtrs{h.src, h.dst, h.sport, h.dport, h.proto};
     d.n = n;
     d.out_idx = out_idx;
     d.out_act = out_act;
+}
+
+size_t batch_smem_bytes(int threads, int32_t qcap) {
+    return (size_t)(threads / 32) * ((size_t)qcap * sizeof(uint4) + 2 * kMaxClasses * sizeof(int));
 }
 
 cudaError_t prepare_batch_kernel(size_t smem_bytes) {
@@ -115,7 +94,7 @@ cudaError_t launch_batch(const BatchJobDev *d_jobs, const BatchItem *d_items, in
     p.next = d_next;
     p.qcap = qcap;
     p.one = 1u;
-    k_batch<<<(unsigned)blocks, threads, (size_t)(threads / 32) * qcap * sizeof(uint4), st>>>(p);
+    k_batch<<<(unsigned)blocks, threads, batch_smem_bytes(threads, qcap), st>>>(p);
     return cudaGetLastError();
 }
 
@@ -164,13 +143,13 @@ extern "C" int fw_plan_create(const fw_job *jobs, int64_t n_jobs, const fw_plan_
     int32_t qcap = 0;
     for (int c = 0; c < n_classes; ++c) {
         per_item[c] = cfg.packets_per_item[c] > 0 ? cfg.packets_per_item[c] : 256;
-        seg0[c] = cfg.segment_rules[c] > 0 ? cfg.segment_rules[c] : 16;
+        seg0[c] = cfg.segment_rules[c] > 0 ? cfg.segment_rules[c] : 64;
         if (per_item[c] % 128 != 0 || per_item[c] > 4096 || seg0[c] % 4 != 0) return set_status(FW_EINVAL);
         qcap = std::max(qcap, per_item[c]);
     }
     const int threads = cfg.block_threads > 0 ? cfg.block_threads : 1024;
     if (threads % 32 != 0 || threads > 1024) return set_status(FW_EINVAL);
-    const size_t smem = (size_t)(threads / 32) * qcap * sizeof(uint4);
+    const size_t smem = batch_smem_bytes(threads, qcap);
     if (smem > 227 * 1024) return set_status(FW_EINVAL);
 
     std::vector<BatchJobDev> hj((size_t)n_jobs);
@@ -191,7 +170,7 @@ extern "C" int fw_plan_create(const fw_job *jobs, int64_t n_jobs, const fw_plan_
     // items, longest scans first
     std::vector<int64_t> order((size_t)n_jobs);
     for (int64_t j = 0; j < n_jobs; ++j) order[j] = j;
-    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return hj[a].n_scan > hj[b].n_scan; });
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return jobs[a].rs->n_eff > jobs[b].rs->n_eff; });
     std::vector<BatchItem> items;
     for (int64_t j : order) {
         const int B = per_item[cls[j]];

@@ -6,12 +6,18 @@
 
 namespace fwk {
 
+// One job of a batched launch: its rule set's protocol partition (the
+// concatenated sub-lists in the arithmetic form), its headers and outputs.
 struct BatchJobDev {
     const RecArith *rec;
     const uint32_t *wtop;
     const uint8_t *action;
-    int32_t n_scan;
+    const int32_t *orig;
+    const uint8_t *class_of;
+    int32_t n_classes;
     int32_t vec;  // 1 when the job's buffers allow the vector loads
+    int32_t class_off[kMaxClasses];
+    int32_t class_len[kMaxClasses];
     HdrPtrs h;
     int64_t n;
     int32_t *out_idx;
@@ -45,5 +51,6 @@ void fill_batch_job(BatchJobDev &d, const fw_ruleset *rs, const fw_headers &h, i
 cudaError_t launch_batch(const BatchJobDev *d_jobs, const BatchItem *d_items, int64_t n_items,
                          unsigned long long *d_next, int32_t qcap, int threads, int64_t blocks, cudaStream_t st);
 cudaError_t prepare_batch_kernel(size_t smem_bytes);
+size_t batch_smem_bytes(int threads, int32_t qcap);  // dynamic shared memory of k_batch
 
 }  // namespace fwk

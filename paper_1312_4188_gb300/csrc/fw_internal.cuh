@@ -23,6 +23,7 @@
 namespace fwk {
 
 constexpr int kChunkRules = 256;          // rules per TMA chunk / padding granule
+constexpr int kMaxClasses = 8;            // protocol classes of the partitioned rule lists
 constexpr uint32_t kStatusTimeout = 1u;   // a bounded wait gave up
 constexpr uint32_t kStatusBadArgs = 2u;   // device-side sanity check failed
 
@@ -246,6 +247,17 @@ struct fw_ruleset {
     uint32_t *d_wtop;         // n_pad words (arithmetic form)
     fwk::RecArith *d_range;   // n_pad records (range form)
     uint32_t *d_range_wtop;   // n_pad words (range form)
+    // Protocol partition (arithmetic form): class c's sub-list holds, in list
+    // order, the reachable rules whose protocol set can contain a packet of
+    // class c; the sub-lists are stored one after another.
+    int32_t n_classes;                 // 1..kMaxClasses; the last class is "other"
+    int32_t class_off[8];              // first record of each sub-list (multiple of 4)
+    int32_t class_len[8];              // records in each sub-list (multiple of 4, padding never matches)
+    int64_t part_pad;                  // records stored (multiple of kChunkRules)
+    uint8_t *d_class_of;               // 256 entries: protocol -> class
+    fwk::RecArith *d_part;             // part_pad records
+    uint32_t *d_part_wtop;             // part_pad words
+    int32_t *d_part_orig;              // part_pad original rule indices (-1 for padding)
     uint8_t *d_action;        // n_pad actions
     unsigned *d_status;       // device error flags (kStatus*)
 };

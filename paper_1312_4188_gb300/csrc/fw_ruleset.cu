@@ -6,6 +6,7 @@
 // two device record forms described in fw_internal.cuh and records the first
 // catch-all rule (all five fields wildcards): under first match (Sec. I) no
 // packet is ever decided by a rule after it, so scans stop there.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -120,7 +121,10 @@ extern "C" int fw_ruleset_create_ex(const fw_rule *rules, int64_t n, fw_ruleset 
 
     std::vector<RecClamp> hc(rs->n_pad);
     std::vector<RecCmp> hm(rs->n_pad);
-    std::vector<RecArith> hq(rs->n_pad);
+    std::vector<RecArith> hq(rs->n_pad), part_rec;
+    std::vector<uint32_t> part_wtop;
+    std::vector<int32_t> part_orig;
+    std::vector<uint8_t> part_class_of;
     std::vector<uint32_t> hw(rs->n_pad);
     std::vector<RecRange> hr(rs->n_pad);
     std::vector<uint32_t> hrw(rs->n_pad);
@@ -138,6 +142,53 @@ extern "C" int fw_ruleset_create_ex(const fw_rule *rules, int64_t n, fw_ruleset 
             hr[k].a = make_uint4(0u, 0xFFFFFFFFu, 0u, 0xFFFFFFFFu);
         }
     }
+    // Protocol partition: up to kMaxClasses - 1 classes for the exact
+    // protocols most used by reachable rules, plus "other" for every other
+    // protocol value. Sub-list c keeps, in list order, the rules with
+    // protocol "any" or with class c's protocol ("other": any, or an exact
+    // protocol without a class of its own).
+    {
+        std::vector<int64_t> cnt(256, 0);
+        for (int64_t k = 0; k < rs->n_eff; ++k)
+            if (!rules[k].proto_any) cnt[rules[k].proto]++;
+        std::vector<int> order;
+        for (int p = 0; p < 256; ++p)
+            if (cnt[p] > 0) order.push_back(p);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cnt[a] > cnt[b]; });
+        if ((int)order.size() > kMaxClasses - 1) order.resize(kMaxClasses - 1);
+        rs->n_classes = (int)order.size() + 1;
+        std::vector<uint8_t> class_of(256, (uint8_t)(rs->n_classes - 1));
+        for (size_t c = 0; c < order.size(); ++c) class_of[order[c]] = (uint8_t)c;
+        std::vector<std::vector<int64_t>> lists(rs->n_classes);
+        for (int64_t k = 0; k < rs->n_eff; ++k) {
+            const fw_rule &r = rules[k];
+            for (int c = 0; c < rs->n_classes; ++c) {
+                const bool other = c == rs->n_classes - 1;
+                if (r.proto_any || (!other && r.proto == order[c]) || (other && class_of[r.proto] == c))
+                    lists[c].push_back(k);
+            }
+        }
+        int64_t off = 0;
+        for (int c = 0; c < kMaxClasses; ++c) {
+            const int64_t len = c < rs->n_classes ? (int64_t)(lists[c].size() + 3) / 4 * 4 : 0;
+            rs->class_off[c] = (int32_t)off;
+            rs->class_len[c] = (int32_t)len;
+            off += len;
+        }
+        rs->part_pad = std::max<int64_t>(kChunkRules, (off + kChunkRules - 1) / kChunkRules * kChunkRules);
+        part_rec.resize(rs->part_pad);
+        part_wtop.resize(rs->part_pad);
+        part_orig.assign(rs->part_pad, -1);
+        for (int64_t k = 0; k < rs->part_pad; ++k) never_match_arith(&part_rec[k], &part_wtop[k]);
+        for (int c = 0; c < rs->n_classes; ++c)
+            for (size_t j = 0; j < lists[c].size(); ++j) {
+                const int64_t k = lists[c][j], at = rs->class_off[c] + (int64_t)j;
+                part_rec[at] = hq[k];
+                part_wtop[at] = hw[k];
+                part_orig[at] = (int32_t)k;
+            }
+        part_class_of = class_of;
+    }
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMalloc(&rs->d_clamp, rs->n_pad * sizeof(RecClamp));
     if (e == cudaSuccess) e = cudaMalloc(&rs->d_cmp, rs->n_pad * sizeof(RecCmp));
@@ -145,6 +196,10 @@ extern "C" int fw_ruleset_create_ex(const fw_rule *rules, int64_t n, fw_ruleset 
     if (e == cudaSuccess) e = cudaMalloc(&rs->d_wtop, rs->n_pad * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&rs->d_range, rs->n_pad * sizeof(RecRange));
     if (e == cudaSuccess) e = cudaMalloc(&rs->d_range_wtop, rs->n_pad * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&rs->d_part, rs->part_pad * sizeof(RecArith));
+    if (e == cudaSuccess) e = cudaMalloc(&rs->d_part_wtop, rs->part_pad * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&rs->d_part_orig, rs->part_pad * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&rs->d_class_of, 256);
     if (e == cudaSuccess) e = cudaMalloc(&rs->d_action, rs->n_pad);
     if (e == cudaSuccess) e = cudaMalloc(&rs->d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemcpy(rs->d_clamp, hc.data(), rs->n_pad * sizeof(RecClamp), cudaMemcpyHostToDevice);
@@ -154,6 +209,13 @@ extern "C" int fw_ruleset_create_ex(const fw_rule *rules, int64_t n, fw_ruleset 
     if (e == cudaSuccess) e = cudaMemcpy(rs->d_range, hr.data(), rs->n_pad * sizeof(RecRange), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(rs->d_range_wtop, hrw.data(), rs->n_pad * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(rs->d_part, part_rec.data(), rs->part_pad * sizeof(RecArith), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(rs->d_part_wtop, part_wtop.data(), rs->part_pad * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(rs->d_part_orig, part_orig.data(), rs->part_pad * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(rs->d_class_of, part_class_of.data(), 256, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(rs->d_action, ha.data(), rs->n_pad, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(rs->d_status, 0, sizeof(unsigned));
     if (e != cudaSuccess) {
@@ -179,6 +241,10 @@ extern "C" void fw_ruleset_destroy(fw_ruleset *rs) {
     if (rs->d_wtop) cudaFree(rs->d_wtop);
     if (rs->d_range) cudaFree(rs->d_range);
     if (rs->d_range_wtop) cudaFree(rs->d_range_wtop);
+    if (rs->d_part) cudaFree(rs->d_part);
+    if (rs->d_part_wtop) cudaFree(rs->d_part_wtop);
+    if (rs->d_part_orig) cudaFree(rs->d_part_orig);
+    if (rs->d_class_of) cudaFree(rs->d_class_of);
     if (rs->d_action) cudaFree(rs->d_action);
     if (rs->d_status) cudaFree(rs->d_status);
     delete rs;

@@ -30,7 +30,7 @@ namespace fwk {
 // ------------------------------------------------------------ packet split kernels
 // Lockstep form: persistent grid; each thread takes packet quads (4
 // consecutive packets) in a grid-stride loop and scans them one after another.
-template <class Pol, bool VEC>
+template <class Pol, bool VEC, bool PART>
 __global__ void __launch_bounds__(1024) k_packet_split(ScanParams p) {
     extern __shared__ __align__(128) unsigned char smem[];
     // a failed prefix wait leaves every rule to be read from global memory
@@ -47,8 +47,17 @@ __global__ void __launch_bounds__(1024) k_packet_split(ScanParams p) {
         int idx[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int r = scan_range<Pol>(pk[j], 0, p.n_scan, sv, n_smem, gv, p.one);
-            idx[j] = r < 0 ? -1 : r;
+            if constexpr (PART) {
+                // the packet's protocol class picks its sub-list
+                const int c = __ldg(p.class_of + (pkt_proto<Pol>(pk[j]) & 0xFFu));
+                const int off = p.class_off[c];
+                const int r = scan_range<Pol>(pk[j], 0, p.class_len[c], shifted_view<Pol>(sv, off),
+                                              max(0, n_smem - off), shifted_view<Pol>(gv, off), p.one);
+                idx[j] = r < 0 ? -1 : __ldg(p.orig + off + r);
+            } else {
+                const int r = scan_range<Pol>(pk[j], 0, p.n_scan, sv, n_smem, gv, p.one);
+                idx[j] = r < 0 ? -1 : r;
+            }
         }
         store_quad<VEC>(p, q, idx, cnt);
     }
@@ -62,60 +71,48 @@ __global__ void __launch_bounds__(1024) k_packet_split(ScanParams p) {
 // undecided ones are packed to the front of the queue (ballot + popc), so the
 // next segment runs on dense groups of still-undecided packets instead of
 // lanes idling behind the slowest packet of a warp.
-template <class Pol, bool VEC>
+template <class Pol, bool VEC, bool PART>
 __global__ void __launch_bounds__(1024) k_packet_split_compact(ScanParams p) {
     extern __shared__ __align__(128) unsigned char smem[];
     const bool staged = stage_rules<Pol>(smem, p);
-    const int n_smem = staged ? p.n_smem : 0;
-    const typename Pol::View sv = Pol::smem_view(smem, p.n_smem);
-    const typename Pol::View gv = Pol::global_view(p);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int B = p.batch;
     const size_t qoff = ((size_t)p.n_smem * Pol::bytes_per_rule() + (size_t)(p.n_smem / kChunkRules) * 8 + 15) / 16 * 16;
     uint4 *Q = reinterpret_cast<uint4 *>(smem + qoff) + (size_t)warp * B;
-    const int64_t nb = (p.n + B - 1) / B;
-    for (int64_t b = (int64_t)blockIdx.x * nw + warp; b < nb; b += (int64_t)gridDim.x * nw) {
-        const int64_t base = b * B;
-        const int cnt = (int)min((int64_t)B, p.n - base);
-        for (int qq = lane; qq * 4 < cnt; qq += 32) {
-            typename Pol::Pk pk[4];
-            int c;
-            load_quad<Pol, VEC>(p.h, p.n, base / 4 + qq, pk, c);
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (j < c) Q[qq * 4 + j] = Pol::pack(pk[j], qq * 4 + j);
+    int *wc = reinterpret_cast<int *>(smem + qoff + (size_t)nw * B * sizeof(uint4)) + warp * 2 * kMaxClasses;
+    // block-shared tables (PART only): protocol -> class, and the sub-list offsets / lengths
+    uint8_t *tabs = smem + qoff + (size_t)nw * (B * sizeof(uint4) + 2 * kMaxClasses * sizeof(int));
+    int32_t *cls_off = reinterpret_cast<int32_t *>(tabs);
+    int32_t *cls_len = cls_off + kMaxClasses;
+    uint8_t *class_tab = tabs + 2 * kMaxClasses * sizeof(int32_t);
+    if constexpr (PART) {
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) class_tab[i] = p.class_of[i];
+        if (threadIdx.x < kMaxClasses) {
+            cls_off[threadIdx.x] = p.class_off[threadIdx.x];
+            cls_len[threadIdx.x] = p.class_len[threadIdx.x];
         }
-        __syncwarp();
-        int m = cnt, s0 = 0, s1 = p.seg0;
-        while (m > 0) {
-            s1 = min(s1, p.n_scan);
-            const bool last = s1 >= p.n_scan;
-            int w = 0;
-            for (int g0 = 0; g0 < m; g0 += 32) {
-                const int i = g0 + lane;
-                const bool valid = i < m;
-                const uint4 e = valid ? Q[i] : make_uint4(0, 0, 0, 0);
-                __syncwarp();
-                int slot;
-                const typename Pol::Pk pk = Pol::unpack(e, slot);
-                int r = -1;
-                if (valid && s0 < s1) r = scan_range<Pol>(pk, s0, s1, sv, n_smem, gv, p.one);
-                const bool keep = valid && r == -1 && !last;
-                if (valid && !keep) {
-                    const int v = r >= 0 ? r : -1;
-                    p.out_idx[base + slot] = v;
-                    p.out_act[base + slot] = v >= 0 ? __ldg(p.action + v) : (uint8_t)FW_DROP;
-                }
-                const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
-                if (keep) Q[w + __popc(bal & ((1u << lane) - 1u))] = e;
-                w += __popc(bal);
-                __syncwarp();
-            }
-            m = w;
-            s0 = s1;
-            s1 = s1 * 2;
-        }
+        __syncthreads();
     }
+    BatchTarget<Pol> t;
+    t.h = p.h;
+    t.n = p.n;
+    t.sv = Pol::smem_view(smem, p.n_smem);
+    t.gv = Pol::global_view(p);
+    t.n_smem = staged ? p.n_smem : 0;  // a failed prefix wait leaves every rule to global memory
+    t.n_scan = p.n_scan;
+    t.n_classes = p.n_classes;
+    t.class_off = cls_off;
+    t.class_len = cls_len;
+    t.class_of = class_tab;
+    t.orig = p.orig;
+    t.action = p.action;
+    t.out_idx = p.out_idx;
+    t.out_act = p.out_act;
+    t.seg0 = p.seg0;
+    t.one = p.one;
+    const int64_t nb = (p.n + B - 1) / B;
+    for (int64_t b = (int64_t)blockIdx.x * nw + warp; b < nb; b += (int64_t)gridDim.x * nw)
+        run_batch<Pol, VEC, PART>(t, b * B, (int)min((int64_t)B, p.n - b * B), Q, wc, lane);
     if (!staged) drain_rules<Pol>(smem, p);
 }
 
@@ -244,7 +241,19 @@ static cudaError_t ensure_smem(K kernel, size_t bytes) {
 int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *out_idx, uint8_t *out_act,
                         cudaStream_t st, const fw_config &cfg) {
     ScanParams p;
+    std::memset(&p, 0, sizeof(p));
     const int pred = cfg.predicate == 0 ? FW_PRED_ARITH : cfg.predicate;
+    if (cfg.partition < 0 || cfg.partition > 2) return FW_EINVAL;
+    if (cfg.partition == 1 && pred != FW_PRED_ARITH) return FW_EINVAL;
+    if (cfg.compact < 0 || cfg.compact > 2) return FW_EINVAL;
+    // Default: compaction for large batches; small batches need every thread
+    // they can get, so they take the lockstep form with smaller blocks.
+    const bool compact = cfg.compact == 1 || (cfg.compact == 0 && n >= kCompactMinPackets);
+    // Protocol partition (stored for the arithmetic form only): default on in
+    // the compacting kernel, which sorts each warp's batch by class so that a
+    // warp's lanes share one sub-list; in the lockstep kernel lanes of a warp
+    // would walk different sub-lists, so there it is used only on request.
+    const bool part = pred == FW_PRED_ARITH && (cfg.partition == 1 || (cfg.partition == 0 && compact));
     int rec_bytes;
     if (pred == FW_PRED_CLAMP) {
         p.rec = rs->d_clamp;
@@ -253,7 +262,7 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
         p.rec = rs->d_cmp;
         rec_bytes = (int)sizeof(RecCmp);
     } else if (pred == FW_PRED_ARITH) {
-        p.rec = rs->d_arith;
+        p.rec = part ? (const void *)rs->d_part : (const void *)rs->d_arith;
         rec_bytes = (int)PolArith::bytes_per_rule();
     } else if (pred == FW_PRED_RANGE) {
         p.rec = rs->d_range;
@@ -261,13 +270,20 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
     } else {
         return FW_EINVAL;
     }
-    if (cfg.compact < 0 || cfg.compact > 2) return FW_EINVAL;
-    // Default: compaction for large batches; small batches need every thread
-    // they can get, so they take the lockstep form with smaller blocks.
-    const bool compact = cfg.compact == 1 || (cfg.compact == 0 && n >= kCompactMinPackets);
-    p.wtop = pred == FW_PRED_RANGE ? rs->d_range_wtop : rs->d_wtop;
+    p.wtop = pred == FW_PRED_RANGE ? rs->d_range_wtop : (part ? rs->d_part_wtop : rs->d_wtop);
     p.action = rs->d_action;
-    p.n_scan = (int)((rs->n_eff + 3) / 4 * 4);
+    const int64_t stored = part ? rs->class_off[kMaxClasses - 1] + rs->class_len[kMaxClasses - 1]
+                                : (rs->n_eff + 3) / 4 * 4;
+    p.n_scan = (int)stored;
+    if (part) {
+        p.n_classes = rs->n_classes;
+        for (int c = 0; c < kMaxClasses; ++c) {
+            p.class_off[c] = rs->class_off[c];
+            p.class_len[c] = rs->class_len[c];
+        }
+        p.class_of = rs->d_class_of;
+        p.orig = rs->d_part_orig;
+    }
     int threads = cfg.block_threads > 0 ? cfg.block_threads : (compact ? 1024 : 512);
     if (cfg.block_threads <= 0 && !compact) {
         // at least two blocks per SM when the batch allows it
@@ -283,7 +299,8 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
     p.n_smem = std::min(want, need);
     p.batch = cfg.packets_per_group > 0 ? cfg.packets_per_group : 256;
     if (compact && (p.batch % 128 != 0 || p.batch > 65536)) return FW_EINVAL;
-    p.seg0 = cfg.segment_rules > 0 ? cfg.segment_rules : 16;
+    // protocol sub-lists are short, so one long first segment beats early compaction there
+    p.seg0 = cfg.segment_rules > 0 ? cfg.segment_rules : (part ? 64 : 16);
     if (p.seg0 % 4 != 0) return FW_EINVAL;
     p.one = 1u;
     p.h = h;
@@ -292,7 +309,9 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
     p.out_act = out_act;
     p.status = rs->d_status;
     size_t smem = (size_t)p.n_smem * rec_bytes + (size_t)(p.n_smem / kChunkRules) * 8;
-    if (compact) smem = (smem + 15) / 16 * 16 + (size_t)(threads / 32) * p.batch * sizeof(uint4);
+    if (compact)
+        smem = (smem + 15) / 16 * 16 + (size_t)(threads / 32) * (p.batch * sizeof(uint4) + 2 * kMaxClasses * sizeof(int)) +
+               2 * kMaxClasses * sizeof(int32_t) + 256;
     if (smem > 227 * 1024) return FW_EINVAL;
     const bool vec = aligned(h.src, 16) && aligned(h.dst, 16) && aligned(h.sport, 8) && aligned(h.dport, 8) &&
                      aligned(h.proto, 4) && aligned(out_idx, 16) && aligned(out_act, 4);
@@ -306,21 +325,23 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
     }
     blocks = std::max<int64_t>(1, blocks);
     cudaError_t e = cudaSuccess;
-#define FW_LAUNCH_PS(KER, POL, V)                                                            \
+#define FW_LAUNCH_PS(KER, POL, V, PT)                                                        \
     do {                                                                                     \
-        e = ensure_smem(KER<POL, V>, smem);                                                  \
-        if (e == cudaSuccess) KER<POL, V><<<(unsigned)blocks, threads, smem, st>>>(p);         \
+        e = ensure_smem(KER<POL, V, PT>, smem);                                              \
+        if (e == cudaSuccess) KER<POL, V, PT><<<(unsigned)blocks, threads, smem, st>>>(p);     \
     } while (0)
 #define FW_PICK(KER)                                                                         \
     do {                                                                                     \
         if (pred == FW_PRED_CLAMP) {                                                         \
-            if (vec) FW_LAUNCH_PS(KER, PolClamp, true); else FW_LAUNCH_PS(KER, PolClamp, false); \
+            if (vec) FW_LAUNCH_PS(KER, PolClamp, true, false); else FW_LAUNCH_PS(KER, PolClamp, false, false); \
         } else if (pred == FW_PRED_CMP) {                                                    \
-            if (vec) FW_LAUNCH_PS(KER, PolCmp, true); else FW_LAUNCH_PS(KER, PolCmp, false);     \
+            if (vec) FW_LAUNCH_PS(KER, PolCmp, true, false); else FW_LAUNCH_PS(KER, PolCmp, false, false); \
         } else if (pred == FW_PRED_RANGE) {                                                  \
-            if (vec) FW_LAUNCH_PS(KER, PolRange, true); else FW_LAUNCH_PS(KER, PolRange, false); \
+            if (vec) FW_LAUNCH_PS(KER, PolRange, true, false); else FW_LAUNCH_PS(KER, PolRange, false, false); \
+        } else if (part) {                                                                   \
+            if (vec) FW_LAUNCH_PS(KER, PolArith, true, true); else FW_LAUNCH_PS(KER, PolArith, false, true); \
         } else {                                                                             \
-            if (vec) FW_LAUNCH_PS(KER, PolArith, true); else FW_LAUNCH_PS(KER, PolArith, false); \
+            if (vec) FW_LAUNCH_PS(KER, PolArith, true, false); else FW_LAUNCH_PS(KER, PolArith, false, false); \
         }                                                                                    \
     } while (0)
     if (compact) FW_PICK(k_packet_split_compact); else FW_PICK(k_packet_split);
@@ -408,7 +429,7 @@ static int classify_impl(const fw_ruleset *rs, const fw_headers *hdrs, int64_t n
     fw_config cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     if (cfg_in != nullptr) cfg = *cfg_in;
-    for (int i = 0; i < 7; ++i)
+    for (int i = 0; i < 6; ++i)
         if (cfg.reserved[i] != 0) return FW_EINVAL;
     HdrPtrs h{hdrs->src, hdrs->dst, hdrs->sport, hdrs->dport, hdrs->proto};
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

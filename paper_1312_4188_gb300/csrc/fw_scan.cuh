@@ -28,6 +28,13 @@ struct ScanParams {
     int32_t *out_idx;
     uint8_t *out_act;
     unsigned *status;
+    // protocol partition (used by the PART kernels; records are then the
+    // concatenated sub-lists and n_scan / n_smem refer to that array)
+    int32_t n_classes;
+    int32_t class_off[kMaxClasses];
+    int32_t class_len[kMaxClasses];
+    const uint8_t *class_of;  // 256 entries
+    const int32_t *orig;      // original rule index of each stored record
 };
 
 // ------------------------------------------------------------ record policies
@@ -138,6 +145,8 @@ struct PolArith {
     static __device__ __forceinline__ View global_view(const ScanParams &p) {
         return {reinterpret_cast<const Rec *>(p.rec), p.wtop};
     }
+    // the same records seen from record `off` on (a sub-list of the partition)
+    static __device__ __forceinline__ View shifted(const View &v, int off) { return {v.rec + off, v.wtop + off}; }
     // shared layout: [n_smem records][n_smem wtop words]
     static __device__ __forceinline__ View smem_view(unsigned char *sm, int n_smem) {
         return {reinterpret_cast<const Rec *>(sm), reinterpret_cast<const uint32_t *>(sm + (size_t)n_smem * sizeof(Rec))};
@@ -318,6 +327,169 @@ __device__ __forceinline__ void drain_rules(unsigned char *smem, const ScanParam
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)p.n_smem * Pol::bytes_per_rule());
     if (threadIdx.x == 0)
         for (int c = 0; c < p.n_smem / kChunkRules; ++c) mbar_wait_bounded(&bars[c], 0, p.status);
+}
+
+// Protocol bytes of quad q (packets 4q..4q+3) packed little-endian into pr4;
+// nv = how many of the four exist (0 when !in_batch).
+template <bool VEC>
+__device__ __forceinline__ void load_protos(const HdrPtrs &h, int64_t n, int64_t q, bool in_batch, uint32_t &pr4,
+                                            int &nv) {
+    pr4 = 0;
+    nv = 0;
+    if (!in_batch) return;
+    const int64_t b = q * 4;
+    if (VEC && b + 3 < n) {
+        pr4 = __ldg(reinterpret_cast<const unsigned int *>(h.proto) + q);
+        nv = 4;
+        return;
+    }
+    for (int j = 0; j < 4 && b + j < n; ++j) {
+        pr4 |= (uint32_t)h.proto[b + j] << (8 * j);
+        nv = j + 1;
+    }
+}
+
+// Protocol of a packet held in a policy's packet form (the partition key).
+template <class Pol>
+__device__ __forceinline__ uint32_t pkt_proto(const typename Pol::Pk &p);
+template <>
+__device__ __forceinline__ uint32_t pkt_proto<PolArith>(const PolArith::Pk &p) { return p.x >> 17; }
+template <>
+__device__ __forceinline__ uint32_t pkt_proto<PolRange>(const PolRange::Pk &p) { return p.x >> 17; }
+template <>
+__device__ __forceinline__ uint32_t pkt_proto<PolClamp>(const PolClamp::Pk &p) { return p.proto; }
+template <>
+__device__ __forceinline__ uint32_t pkt_proto<PolCmp>(const PolCmp::Pk &p) { return p.proto; }
+
+// View of a sub-list that starts `off` records into the stored array (arithmetic form only).
+template <class Pol>
+__device__ __forceinline__ typename Pol::View shifted_view(const typename Pol::View &v, int off) {
+    return PolArith::shifted(v, off);
+}
+
+
+// ------------------------------------------------------------ one warp batch
+// What a warp needs to classify a batch: the headers, the rule records (the
+// shared prefix and the global array, or the protocol partition), and where
+// the verdicts go.
+template <class Pol>
+struct BatchTarget {
+    HdrPtrs h;
+    int64_t n;                        // packets in the whole array
+    typename Pol::View sv, gv;        // shared-memory prefix / global records
+    int n_smem;                       // records resident in the shared prefix
+    int n_scan;                       // records of the whole list (unpartitioned)
+    int n_classes;                    // partition: classes, sub-list offsets and lengths,
+    const int32_t *class_off;         //   protocol -> class table, original rule index
+    const int32_t *class_len;
+    const uint8_t *class_of;
+    const int32_t *orig;
+    const uint8_t *action;
+    int32_t *out_idx;
+    uint8_t *out_act;
+    int seg0;                         // first rule segment; later segments double
+    uint32_t one;
+};
+
+// Classify packets [base, base + cnt) with one warp. The batch goes into the
+// warp's shared queue Q (PART: counting-sorted by protocol class, one region
+// per class; wc = 2 * kMaxClasses ints of per-warp counters). Each region is
+// scanned segment by segment over its rule list; after each group of 32
+// queue entries, packets decided in the segment write their verdicts and the
+// undecided ones are packed to the front of the region (ballot + popc), so
+// the next segment runs on dense groups of still-undecided packets instead of
+// lanes idling behind the slowest packet of a warp.
+template <class Pol, bool VEC, bool PART>
+__device__ __forceinline__ void run_batch(const BatchTarget<Pol> &t, int64_t base, int cnt, uint4 *Q, int *wc,
+                                          int lane) {
+    int n_groups = 1;
+    if constexpr (PART) {
+        // count (shared atomics, one per packet), exclusive prefix, scatter
+        n_groups = t.n_classes;
+        if (lane < 2 * kMaxClasses) wc[lane] = 0;
+        __syncwarp();
+        for (int qq = lane; qq * 4 < cnt; qq += 32) {
+            uint32_t pr4;
+            int nv;
+            load_protos<VEC>(t.h, t.n, base / 4 + qq, true, pr4, nv);
+            for (int j = 0; j < nv; ++j) atomicAdd(&wc[t.class_of[(pr4 >> (8 * j)) & 0xFFu]], 1);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            int acc = 0;
+            for (int c = 0; c < t.n_classes; ++c) {
+                wc[kMaxClasses + c] = acc;  // region start; advanced by the scatter below
+                acc += wc[c];
+            }
+        }
+        __syncwarp();
+        for (int qq = lane; qq * 4 < cnt; qq += 32) {
+            typename Pol::Pk pk[4];
+            int nv;
+            load_quad<Pol, VEC>(t.h, t.n, base / 4 + qq, pk, nv);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (j >= nv) continue;
+                const int pos = atomicAdd(&wc[kMaxClasses + t.class_of[pkt_proto<Pol>(pk[j]) & 0xFFu]], 1);
+                Q[pos] = Pol::pack(pk[j], qq * 4 + j);
+            }
+        }
+    } else {
+        for (int qq = lane; qq * 4 < cnt; qq += 32) {
+            typename Pol::Pk pk[4];
+            int c;
+            load_quad<Pol, VEC>(t.h, t.n, base / 4 + qq, pk, c);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (j < c) Q[qq * 4 + j] = Pol::pack(pk[j], qq * 4 + j);
+        }
+    }
+    __syncwarp();
+    for (int g = 0; g < n_groups; ++g) {
+        int m = cnt, R = 0, off = 0, len = t.n_scan;
+        typename Pol::View svg = t.sv, gvg = t.gv;
+        if constexpr (PART) {
+            m = wc[g];
+            R = wc[kMaxClasses + g] - m;  // region of class g (the scatter left its pointer at the end)
+            off = t.class_off[g];
+            len = t.class_len[g];
+            svg = shifted_view<Pol>(t.sv, off);
+            gvg = shifted_view<Pol>(t.gv, off);
+        }
+        const int n_smem_g = max(0, t.n_smem - off);
+        int s0 = 0, s1 = t.seg0;
+        while (m > 0) {
+            s1 = min(s1, len);
+            const bool last = s1 >= len;
+            int w = 0;
+            for (int g0 = 0; g0 < m; g0 += 32) {
+                const int i = g0 + lane;
+                const bool valid = i < m;
+                const uint4 e = valid ? Q[R + i] : make_uint4(0, 0, 0, 0);
+                __syncwarp();
+                int slot;
+                const typename Pol::Pk pk = Pol::unpack(e, slot);
+                int r = -1;
+                if (valid && s0 < s1) r = scan_range<Pol>(pk, s0, s1, svg, n_smem_g, gvg, t.one);
+                const bool keep = valid && r == -1 && !last;
+                if (valid && !keep) {
+                    int v = r;
+                    if constexpr (PART) v = r >= 0 ? __ldg(t.orig + off + r) : -1;
+                    v = v >= 0 ? v : -1;
+                    t.out_idx[base + slot] = v;
+                    t.out_act[base + slot] = v >= 0 ? __ldg(t.action + v) : (uint8_t)FW_DROP;
+                }
+                const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
+                if (keep) Q[R + w + __popc(bal & ((1u << lane) - 1u))] = e;
+                w += __popc(bal);
+                __syncwarp();
+            }
+            m = w;
+            s0 = s1;
+            s1 = s1 * 2;
+        }
+    }
+    __syncwarp();
 }
 
 }  // namespace fwk

@@ -360,13 +360,13 @@ extern "C" int fw_server_create(const fw_ruleset *const *sets, int n_sets, const
     if (c.max_group_packets == 0) c.max_group_packets = int64_t(1) << 20;
     if (c.arena_bytes == 0) c.arena_bytes = int64_t(256) << 20;
     if (c.packets_per_item == 0) c.packets_per_item = 256;
-    if (c.segment_rules == 0) c.segment_rules = 16;
+    if (c.segment_rules == 0) c.segment_rules = 64;
     if (c.block_threads == 0) c.block_threads = 512;
     if (c.slots < 1 || c.slots > 16 || c.max_group_requests < 1 || c.max_pending < 1 || c.max_group_packets < 1 ||
         c.arena_bytes < 4096 || c.packets_per_item % 128 != 0 || c.packets_per_item > 4096 ||
         c.segment_rules % 4 != 0 || c.segment_rules < 4 || c.block_threads % 32 != 0 || c.block_threads > 1024)
         return set_status(FW_EINVAL);
-    const size_t smem = (size_t)(c.block_threads / 32) * c.packets_per_item * sizeof(uint4);
+    const size_t smem = batch_smem_bytes(c.block_threads, c.packets_per_item);
     if (smem > 227 * 1024) return set_status(FW_EINVAL);
     fw_server *sv = new (std::nothrow) fw_server();
     if (sv == nullptr) return set_status(FW_ENOMEM);

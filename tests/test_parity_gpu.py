@@ -17,6 +17,9 @@ THREADS = os.cpu_count() or 1
 
 CONFIGS = [
     ("packet_split", {}),
+    ("packet_split", {"partition": 2}),
+    ("packet_split", {"compact": 2, "partition": 1}),
+    ("packet_split", {"compact": 1, "partition": 1, "smem_rules": 256, "segment_rules": 4, "block_threads": 256}),
     ("packet_split", {"predicate": fw.FW_PRED_CMP}),
     ("packet_split", {"predicate": fw.FW_PRED_CLAMP}),
     ("packet_split", {"predicate": fw.FW_PRED_RANGE}),
@@ -120,12 +123,19 @@ def test_golden_policy_on_gpu(torch_cuda, mode, kw):
 
 
 @pytest.mark.parametrize("mode,kw", [("packet_split", {}), ("packet_split", {"compact": 2, "predicate": 2}),
+                                     ("packet_split", {"compact": 2}), ("packet_split", {"partition": 2}),
+                                     ("packet_split", {"compact": 1, "packets_per_group": 128}),
                                      ("rule_split_warp", {}), ("rule_split_block", {}), ("rule_split_grid", {})],
-                         ids=["ps", "ps_lockstep_cmp", "rsw", "rsb", "rsg"])
+                         ids=["ps", "ps_lockstep_cmp", "ps_lockstep_part", "ps_nopart", "ps_compact_part",
+                              "rsw", "rsb", "rsg"])
 def test_special_rule_sets(torch_cuda, mode, kw):
     import oracle_pins as P
     rng = np.random.default_rng(3)
+    many = no_catch_all(W.gen_rules(2000, 6))
+    many["proto_any"] = (rng.random(len(many)) < 0.1).astype(np.uint8)
+    many["proto"] = rng.integers(0, 256, size=len(many))  # far more exact protocols than classes
     cases = {
+        "many_protocols": many,
         "catch_all_first": np.concatenate([P.catch_all(W.DROP), W.gen_rules(100, 1)]).astype(W.RULE_DTYPE),
         "catch_all_last": np.concatenate([no_catch_all(W.gen_rules(600, 2)), P.catch_all(W.ACCEPT)]).astype(
             W.RULE_DTYPE),
@@ -167,10 +177,11 @@ def big(torch_cuda):
 
 
 @pytest.mark.parametrize("mode,kw", [("packet_split", {}), ("packet_split", {"compact": 2}),
+                                     ("packet_split", {"partition": 2}),
                                      ("packet_split", {"compact": 2, "predicate": fw.FW_PRED_CLAMP}),
                                      ("packet_split", {"predicate": fw.FW_PRED_RANGE}),
                                      ("rule_split_warp", {}), ("rule_split_block", {}), ("rule_split_grid", {})],
-                         ids=["ps", "ps_lockstep", "ps_lockstep_clamp", "ps_range", "rsw", "rsb", "rsg"])
+                         ids=["ps", "ps_lockstep", "ps_nopart", "ps_lockstep_clamp", "ps_range", "rsw", "rsb", "rsg"])
 def test_scan_10k_x_16m_sampled(torch_cuda, big, mode, kw):
     torch = torch_cuda
     rules, hdr, dh, want, pos = big
