@@ -334,6 +334,15 @@ int fw_server_submit(fw_server *sv, int set, const fw_headers *hdrs, int64_t n, 
 int fw_server_wait(fw_server *sv, uint64_t ticket, int64_t timeout_us, double *latency_us);
 /* Wait until nothing is queued or running (tickets stay valid for fw_server_wait). */
 int fw_server_drain(fw_server *sv, int64_t timeout_us);
+/*
+ * Zero-copy mode: declare that [p, p + bytes) (device memory or pinned host
+ * memory) will hold request buffers, so submits whose arrays lie inside it
+ * skip the per-call pointer lookups. The buffer must stay allocated until it
+ * is unregistered (by its start address) or the server is destroyed.
+ * FW_EINVAL if the range is not device accessible as one piece.
+ */
+int fw_server_register_buffer(fw_server *sv, const void *p, size_t bytes);
+int fw_server_unregister_buffer(fw_server *sv, const void *p);
 int fw_server_get_stats(fw_server *sv, fw_server_stats *st);
 /*
  * Open-loop replay: submit reqs[i] at arrival_us[i] after the call starts

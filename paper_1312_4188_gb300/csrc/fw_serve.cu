@@ -74,8 +74,17 @@ struct SvSlot {
 
 }  // namespace fwk
 
+// A caller buffer registered for zero-copy use: [lo, hi) is device
+// accessible at address + delta.
+struct SvRange {
+    uintptr_t lo, hi;
+    intptr_t delta;
+};
+
 struct fw_server {
     fw_server_config cfg{};
+    std::mutex reg_mu;
+    std::vector<SvRange> ranges;
     std::vector<const fw_ruleset *> sets;
     int device = 0;
     int threads = 512;
@@ -315,9 +324,46 @@ static const void *device_alias(const void *p) {
     return nullptr;
 }
 
+// Device alias of [p, p + bytes): from a registered range when one covers it,
+// else looked up now.
+static const void *resolve(fw_server *sv, const void *p, size_t bytes) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    {
+        std::lock_guard<std::mutex> lk(sv->reg_mu);
+        for (const SvRange &r : sv->ranges)
+            if (a >= r.lo && a + bytes <= r.hi) return reinterpret_cast<const void *>(a + r.delta);
+    }
+    return device_alias(p);
+}
+
 }  // namespace fwk
 
 using namespace fwk;
+
+extern "C" int fw_server_register_buffer(fw_server *sv, const void *p, size_t bytes) {
+    if (sv == nullptr || p == nullptr || bytes == 0) return set_status(FW_EINVAL);
+    const void *d0 = device_alias(p);
+    const void *d1 = device_alias(static_cast<const uint8_t *>(p) + bytes - 1);
+    const intptr_t delta0 = reinterpret_cast<intptr_t>(d0) - reinterpret_cast<intptr_t>(p);
+    const intptr_t delta1 = reinterpret_cast<intptr_t>(d1) - reinterpret_cast<intptr_t>(p) - (intptr_t)(bytes - 1);
+    if (d0 == nullptr || d1 == nullptr || delta0 != delta1) return set_status(FW_EINVAL);
+    std::lock_guard<std::mutex> lk(sv->reg_mu);
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    sv->ranges.push_back(SvRange{a, a + bytes, delta0});
+    return FW_OK;
+}
+
+extern "C" int fw_server_unregister_buffer(fw_server *sv, const void *p) {
+    if (sv == nullptr) return set_status(FW_EINVAL);
+    std::lock_guard<std::mutex> lk(sv->reg_mu);
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    for (size_t i = 0; i < sv->ranges.size(); ++i)
+        if (sv->ranges[i].lo == a) {
+            sv->ranges.erase(sv->ranges.begin() + (int64_t)i);
+            return FW_OK;
+        }
+    return set_status(FW_EINVAL);
+}
 
 extern "C" void fw_server_destroy(fw_server *sv) {
     if (sv == nullptr) return;
@@ -418,13 +464,14 @@ extern "C" int fw_server_submit(fw_server *sv, int set, const fw_headers *h, int
     r->out_idx = out_idx;
     r->out_act = out_act;
     if (sv->cfg.mode == FW_HOST_ZEROCOPY) {
-        r->dh.src = static_cast<const uint32_t *>(device_alias(h->src));
-        r->dh.dst = static_cast<const uint32_t *>(device_alias(h->dst));
-        r->dh.sport = static_cast<const uint16_t *>(device_alias(h->sport));
-        r->dh.dport = static_cast<const uint16_t *>(device_alias(h->dport));
-        r->dh.proto = static_cast<const uint8_t *>(device_alias(h->proto));
-        r->d_idx = static_cast<int32_t *>(const_cast<void *>(device_alias(out_idx)));
-        r->d_act = static_cast<uint8_t *>(const_cast<void *>(device_alias(out_act)));
+        const size_t m = (size_t)n;
+        r->dh.src = static_cast<const uint32_t *>(resolve(sv, h->src, 4 * m));
+        r->dh.dst = static_cast<const uint32_t *>(resolve(sv, h->dst, 4 * m));
+        r->dh.sport = static_cast<const uint16_t *>(resolve(sv, h->sport, 2 * m));
+        r->dh.dport = static_cast<const uint16_t *>(resolve(sv, h->dport, 2 * m));
+        r->dh.proto = static_cast<const uint8_t *>(resolve(sv, h->proto, m));
+        r->d_idx = static_cast<int32_t *>(const_cast<void *>(resolve(sv, out_idx, 4 * m)));
+        r->d_act = static_cast<uint8_t *>(const_cast<void *>(resolve(sv, out_act, m)));
         if (!r->dh.src || !r->dh.dst || !r->dh.sport || !r->dh.dport || !r->dh.proto || !r->d_idx || !r->d_act) {
             delete r;
             return set_status(FW_EINVAL);

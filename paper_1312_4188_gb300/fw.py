@@ -157,6 +157,8 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_uint64)]),
     "fw_server_wait": (ctypes.c_int, [P, ctypes.c_uint64, I64, ctypes.POINTER(ctypes.c_double)]),
     "fw_server_drain": (ctypes.c_int, [P, I64]),
+    "fw_server_register_buffer": (ctypes.c_int, [P, P, ctypes.c_size_t]),
+    "fw_server_unregister_buffer": (ctypes.c_int, [P, P]),
     "fw_server_get_stats": (ctypes.c_int, [P, ctypes.POINTER(fw_server_stats)]),
     "fw_server_replay": (ctypes.c_int, [P, ctypes.POINTER(fw_request), I64, I64]),
     "fw_last_status": (ctypes.c_int, []),
@@ -465,6 +467,11 @@ class Server:
         lat = ctypes.c_double()
         s = lib().fw_server_wait(self.handle, ctypes.c_uint64(ticket), int(timeout_us), ctypes.byref(lat))
         return int(s), float(lat.value)
+
+    def register(self, tensor):
+        """Zero-copy mode: register a tensor's storage as a request buffer (see fw_server_register_buffer)."""
+        _check(lib().fw_server_register_buffer(self.handle, ctypes.c_void_p(tensor.data_ptr()),
+                                               tensor.numel() * tensor.element_size()), "fw_server_register_buffer")
 
     def drain(self, timeout_us: int = -1) -> int:
         return int(lib().fw_server_drain(self.handle, int(timeout_us)))

@@ -104,6 +104,31 @@ def test_poisson_replay_and_memory_admission(env):
     sv.destroy()
 
 
+def test_registered_buffers(env):
+    torch, rules, sets, reqs, want = env
+    sv = fw.Server(sets, mode=fw.FW_HOST_ZEROCOPY)
+    bufs = buffers(torch, reqs[:50], fw.FW_HOST_ZEROCOPY)
+    for s, h, oi, oa in bufs:
+        for t in list(h.values()) + [oi, oa]:
+            sv.register(t)
+    tickets = [sv.submit(s, h, oi, oa) for s, h, oi, oa in bufs]
+    assert all(sv.wait(t)[0] == fw.FW_OK for t in tickets)
+    for b, w in zip(bufs, want):
+        assert np.array_equal(b[2].numpy(), w[0]) and np.array_equal(b[3].numpy(), w[1])
+    L = fw.lib()
+    assert L.fw_server_unregister_buffer(sv.handle, ctypes_ptr(bufs[0][2])) == fw.FW_OK
+    assert L.fw_server_unregister_buffer(sv.handle, ctypes_ptr(bufs[0][2])) == fw.FW_EINVAL
+    pageable = torch.empty(100, dtype=torch.int32)
+    with pytest.raises(fw.FwError):
+        sv.register(pageable)
+    sv.destroy()
+
+
+def ctypes_ptr(t):
+    import ctypes
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def test_bad_arguments(env):
     torch, rules, sets, reqs, want = env
     sv = fw.Server(sets)
