@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(1024) k_packet_split(ScanParams p) {
 // next segment runs on dense groups of still-undecided packets instead of
 // lanes idling behind the slowest packet of a warp.
 template <class Pol, bool VEC, bool PART>
-__global__ void __launch_bounds__(1024) k_packet_split_compact(ScanParams p) {
+__device__ __forceinline__ void compact_body(const ScanParams &p) {
     extern __shared__ __align__(128) unsigned char smem[];
     const bool staged = stage_rules<Pol>(smem, p);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -114,6 +114,18 @@ __global__ void __launch_bounds__(1024) k_packet_split_compact(ScanParams p) {
     for (int64_t b = (int64_t)blockIdx.x * nw + warp; b < nb; b += (int64_t)gridDim.x * nw)
         run_batch<Pol, VEC, PART>(t, b * B, (int)min((int64_t)B, p.n - b * B), Q, wc, lane);
     if (!staged) drain_rules<Pol>(smem, p);
+}
+
+template <class Pol, bool VEC, bool PART>
+__global__ void __launch_bounds__(1024) k_packet_split_compact(ScanParams p) {
+    compact_body<Pol, VEC, PART>(p);
+}
+
+// Dense form: two 768-thread blocks per SM (48 resident warps, at most 42
+// registers a thread) instead of one 1,024-thread block (32 warps).
+template <class Pol, bool VEC, bool PART>
+__global__ void __launch_bounds__(768, 2) k_packet_split_compact_dense(ScanParams p) {
+    compact_body<Pol, VEC, PART>(p);
 }
 
 // ------------------------------------------------------------ rule split kernel
@@ -284,19 +296,23 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
         p.class_of = rs->d_class_of;
         p.orig = rs->d_part_orig;
     }
-    int threads = cfg.block_threads > 0 ? cfg.block_threads : (compact ? 1024 : 512);
+    const int need_all = (int)((p.n_scan + kChunkRules - 1) / kChunkRules * kChunkRules);
+    // Short partitioned lists leave shared memory for two 768-thread blocks per SM (48 warps
+    // instead of 32), which hides more of the rule-load latency.
+    const bool auto_dense = compact && part && cfg.block_threads <= 0 && cfg.blocks_per_sm <= 0 &&
+                            cfg.smem_rules == 0 && need_all <= 1024;
+    int threads = cfg.block_threads > 0 ? cfg.block_threads : (auto_dense ? 768 : (compact ? 1024 : 512));
     if (cfg.block_threads <= 0 && !compact) {
         // at least two blocks per SM when the batch allows it
         const int64_t nq = (n + 3) / 4;
         const int64_t t = nq / (2 * (int64_t)sm_count(rs->device)) / 32 * 32;
         threads = (int)std::max<int64_t>(64, std::min<int64_t>(512, t));
     }
-    const int per_sm = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : (compact ? 1 : 2);
+    const int per_sm = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : ((compact && !auto_dense) ? 1 : 2);
     if (threads % 32 != 0 || threads > 1024) return FW_EINVAL;
     int want = cfg.smem_rules > 0 ? cfg.smem_rules : (cfg.smem_rules < 0 ? 0 : (compact ? 2048 : 3072));
     want = (want / kChunkRules) * kChunkRules;
-    const int need = (int)((p.n_scan + kChunkRules - 1) / kChunkRules * kChunkRules);
-    p.n_smem = std::min(want, need);
+    p.n_smem = std::min(want, need_all);
     p.batch = cfg.packets_per_group > 0 ? cfg.packets_per_group : 256;
     if (compact && (p.batch % 128 != 0 || p.batch > 65536)) return FW_EINVAL;
     // protocol sub-lists are short, so one long first segment beats early compaction there
@@ -324,11 +340,17 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
         blocks = std::min<int64_t>(blocks, (nq + threads - 1) / threads);
     }
     blocks = std::max<int64_t>(1, blocks);
+    const bool dense = compact && threads <= 768 && per_sm >= 2;
     cudaError_t e = cudaSuccess;
 #define FW_LAUNCH_PS(KER, POL, V, PT)                                                        \
     do {                                                                                     \
         e = ensure_smem(KER<POL, V, PT>, smem);                                              \
         if (e == cudaSuccess) KER<POL, V, PT><<<(unsigned)blocks, threads, smem, st>>>(p);     \
+    } while (0)
+#define FW_LAUNCH_PSD(POL, V, PT)                                                            \
+    do {                                                                                     \
+        if (dense) FW_LAUNCH_PS(k_packet_split_compact_dense, POL, V, PT);                   \
+        else FW_LAUNCH_PS(k_packet_split_compact, POL, V, PT);                               \
     } while (0)
 #define FW_PICK(KER)                                                                         \
     do {                                                                                     \
@@ -344,7 +366,22 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
             if (vec) FW_LAUNCH_PS(KER, PolArith, true, false); else FW_LAUNCH_PS(KER, PolArith, false, false); \
         }                                                                                    \
     } while (0)
-    if (compact) FW_PICK(k_packet_split_compact); else FW_PICK(k_packet_split);
+    if (compact) {
+        if (pred == FW_PRED_CLAMP) {
+            if (vec) FW_LAUNCH_PSD(PolClamp, true, false); else FW_LAUNCH_PSD(PolClamp, false, false);
+        } else if (pred == FW_PRED_CMP) {
+            if (vec) FW_LAUNCH_PSD(PolCmp, true, false); else FW_LAUNCH_PSD(PolCmp, false, false);
+        } else if (pred == FW_PRED_RANGE) {
+            if (vec) FW_LAUNCH_PSD(PolRange, true, false); else FW_LAUNCH_PSD(PolRange, false, false);
+        } else if (part) {
+            if (vec) FW_LAUNCH_PSD(PolArith, true, true); else FW_LAUNCH_PSD(PolArith, false, true);
+        } else {
+            if (vec) FW_LAUNCH_PSD(PolArith, true, false); else FW_LAUNCH_PSD(PolArith, false, false);
+        }
+    } else {
+        FW_PICK(k_packet_split);
+    }
+#undef FW_LAUNCH_PSD
 #undef FW_PICK
 #undef FW_LAUNCH_PS
     if (e != cudaSuccess) return cuda_status(e);

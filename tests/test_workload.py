@@ -1,0 +1,74 @@
+"""The seeded generator draws what its recipe states (determinism, slices, in-rule packets, shares)."""
+import numpy as np
+import pytest
+
+import oracle_pins as P
+from paper_1312_4188_gb300 import workload as W
+
+
+def test_rules_are_deterministic_and_valid():
+    a, b = W.gen_rules(5000, 42), W.gen_rules(5000, 42)
+    assert a.tobytes() == b.tobytes()
+    assert a.tobytes() != W.gen_rules(5000, 43).tobytes()
+    assert np.all(a["src_prefix"] <= 32) and np.all(a["dst_prefix"] <= 32)
+    assert np.all(a["sport_lo"] <= a["sport_hi"]) and np.all(a["dport_lo"] <= a["dport_hi"])
+    assert set(np.unique(a["action"])) <= {0, 1}
+
+
+def test_rule_distribution_shares():
+    r = W.gen_rules(200_000, 7)
+    n = len(r)
+    assert abs((r["src_prefix"] == 0).mean() - 0.2) < 0.01
+    nz = r["src_prefix"][r["src_prefix"] > 0]
+    assert nz.min() == 8 and nz.max() == 32
+    wild = (r["sport_lo"] == 0) & (r["sport_hi"] == 65535)
+    exact = r["sport_lo"] == r["sport_hi"]
+    assert abs(wild.mean() - 0.5) < 0.01 and abs(exact.mean() - 0.3) < 0.01
+    width = r["sport_hi"].astype(int) - r["sport_lo"].astype(int) + 1
+    rng_ = ~wild & ~exact
+    assert width[rng_].max() <= 1024
+    assert abs(r["proto_any"].mean() - 0.25) < 0.01
+    assert set(np.unique(r["proto"][r["proto_any"] == 0])) == {1, 6, 17}
+    assert abs(r["action"].mean() - 0.5) < 0.01
+    assert n == 200_000
+
+
+def test_packet_slices_match_the_whole_batch():
+    rules = W.gen_rules(300, 1)
+    whole = W.gen_packets(rules, 3 * W.BLOCK // 2, 5, zipf_s=1.1)
+    part = W.gen_packets(rules, 1000, 5, zipf_s=1.1, start=W.BLOCK - 400)
+    for f in W.HEADER_FIELDS:
+        assert np.array_equal(part[f], whole[f][W.BLOCK - 400:W.BLOCK + 600])
+
+
+def test_in_rule_packets_lie_in_some_rule():
+    rules = W.gen_rules(200, 3)
+    h = W.gen_packets(rules, 20_000, 4, in_rule_frac=1.0)
+    sets = [P.rule_sets(r) for r in rules]
+    for i in range(0, 20_000, 97):
+        p = tuple(int(h[f][i]) for f in W.HEADER_FIELDS)
+        assert any(P.contains(s, p) for s in sets), f"packet {i} is in no rule"
+
+
+def test_zipf_favours_early_rules():
+    cdf = W.zipf_cdf(10_000, 1.1)
+    assert cdf[-1] == pytest.approx(1.0) and np.all(np.diff(cdf) > 0)
+    w = np.arange(1, 10_001, dtype=float) ** -1.1
+    assert cdf[0] == pytest.approx(w[0] / w.sum())
+
+
+def test_log_uniform_and_batched_shapes():
+    rng = np.random.default_rng(0)
+    x = W.log_uniform_int(rng, 64, 65536, 100_000)
+    assert x.min() >= 64 and x.max() <= 65536
+    # log-uniform: the median is near the geometric mean
+    assert 1500 < np.median(x) < 2600
+    jobs = W.gen_batched(4, seed=1, rules_range=(64, 128), packets_range=(1024, 2048))
+    assert len(jobs) == 4 and all(64 <= len(r) <= 128 and 1024 <= len(h["src"]) <= 2048 for r, h in jobs)
+
+
+def test_sample_positions():
+    pos = W.sample_positions(1000, 100, 3)
+    assert len(np.unique(pos)) == 100 and pos.min() >= 0 and pos.max() < 1000
+    assert np.array_equal(pos, W.sample_positions(1000, 100, 3))
+    assert np.array_equal(W.sample_positions(10, 100, 3), np.arange(10))
