@@ -44,8 +44,10 @@ INT32_LANES_PER_SM_CLK = 128  # 4 schedulers x 32 lanes, one warp instruction pe
 FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "sms": 152}
 KERNEL_SOURCES = ["paper_1312_4188_gb300/csrc/fw_scan.cu", "paper_1312_4188_gb300/csrc/fw_scan.cuh",
                   "paper_1312_4188_gb300/csrc/fw_internal.cuh"]
-KERNEL_NAME = "k_packet_split_compact"
-TRAFFIC_RECORD = "profiles/k_packet_split_compact_scan_10k_x_16m.md"
+# the kernel the default (auto) configuration launches for this workload: the partitioned rule
+# lists are short, so the library picks the dense compacting kernel (two blocks per SM)
+KERNEL_NAME = "k_packet_split_compact_dense"
+TRAFFIC_RECORD = "profiles/k_packet_split_compact_dense_scan_10k_x_16m.md"
 
 
 def parse():
