@@ -44,10 +44,10 @@ INT32_LANES_PER_SM_CLK = 128  # 4 schedulers x 32 lanes, one warp instruction pe
 FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "sms": 152}
 KERNEL_SOURCES = ["paper_1312_4188_gb300/csrc/fw_scan.cu", "paper_1312_4188_gb300/csrc/fw_scan.cuh",
                   "paper_1312_4188_gb300/csrc/fw_internal.cuh"]
-# the kernel the default (auto) configuration launches for this workload: the partitioned rule
-# lists are short, so the library picks the dense compacting kernel (two blocks per SM)
-KERNEL_NAME = "k_packet_split_compact_dense"
-TRAFFIC_RECORD = "profiles/k_packet_split_compact_dense_scan_10k_x_16m.md"
+# the kernel the default (auto) configuration launches for this workload: the compacting scan of
+# the protocol-partitioned lists with two packets per lane
+KERNEL_NAME = "k_packet_split_compact_x2"
+TRAFFIC_RECORD = "profiles/k_packet_split_compact_x2_scan_10k_x_16m.md"
 
 
 def parse():
@@ -344,6 +344,8 @@ def main():
     if rank == 0 and args.modes:
         modes = {}
         variants = {"packet_split": ("packet_split", {}),
+                    "packet_split_one_lane": ("packet_split", {"lane_packets": 1}),
+                    "packet_split_dense": ("packet_split", {"block_threads": 768, "blocks_per_sm": 2, "smem_rules": 1024}),
                     "packet_split_whole_list": ("packet_split", {"partition": 2}),
                     "packet_split_lockstep": ("packet_split", {"compact": 2}),
                     "packet_split_lockstep_whole_list": ("packet_split", {"compact": 2, "partition": 2}),

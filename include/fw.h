@@ -126,6 +126,10 @@ typedef struct fw_headers {
  *                     a packet scans only its class's sub-list, which contains
  *                     every rule that can match it, so the first match is the
  *                     same.
+ *  lane_packets:      compacting packet split with the partition: packets each
+ *                     lane scans at once (1 = one, 2 = two sharing every rule
+ *                     load; 0 = default: two, or one when block_threads <= 768
+ *                     and blocks_per_sm >= 2 select the dense form).
  */
 typedef struct fw_config {
     int32_t mode;
@@ -138,7 +142,8 @@ typedef struct fw_config {
     int32_t predicate;
     int32_t segment_rules;
     int32_t partition;
-    int32_t reserved[6];           /* must be zero */
+    int32_t lane_packets;
+    int32_t reserved[5];           /* must be zero */
 } fw_config;
 
 typedef struct fw_ruleset fw_ruleset;

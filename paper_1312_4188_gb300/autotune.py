@@ -19,14 +19,16 @@ import sys
 from . import fw
 
 PACKET_SPLIT_CANDIDATES = (
-    [dict(mode="packet_split", compact=c, partition=1, block_threads=bt, blocks_per_sm=bps, smem_rules=sr,
-          packets_per_group=b, segment_rules=s0)
+    [dict(mode="packet_split", compact=c, partition=1, lane_packets=1, block_threads=bt, blocks_per_sm=bps,
+          smem_rules=sr, packets_per_group=b, segment_rules=s0)
      for c in (1,) for (bt, bps, sr, b) in ((1024, 1, 2048, 256), (1024, 1, 2048, 128), (768, 1, 2048, 256),
                                            (512, 2, 1024, 256), (512, 1, 2048, 512))
      for s0 in (8, 16, 32, 64, 128)]
     + [dict(mode="packet_split", compact=1, partition=1, block_threads=768, blocks_per_sm=2, smem_rules=sr,
             packets_per_group=b, segment_rules=s0)
        for sr in (256, 1024) for b in (128, 256) for s0 in (32, 64)]
+    + [dict(mode="packet_split", compact=1, partition=1, lane_packets=2, block_threads=1024, blocks_per_sm=1,
+            smem_rules=2048, packets_per_group=b, segment_rules=s0) for b in (256, 512) for s0 in (32, 64, 128)]
     + [dict(mode="packet_split", compact=2, partition=1)]
     + [dict(mode="packet_split", compact=2, predicate=p, partition=2)
      for p in (fw.FW_PRED_CLAMP, fw.FW_PRED_CMP, fw.FW_PRED_ARITH, fw.FW_PRED_RANGE)]

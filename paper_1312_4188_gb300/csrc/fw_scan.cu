@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(1024) k_packet_split(ScanParams p) {
 // undecided ones are packed to the front of the queue (ballot + popc), so the
 // next segment runs on dense groups of still-undecided packets instead of
 // lanes idling behind the slowest packet of a warp.
-template <class Pol, bool VEC, bool PART>
+template <class Pol, bool VEC, bool PART, int PPL>
 __device__ __forceinline__ void compact_body(const ScanParams &p) {
     extern __shared__ __align__(128) unsigned char smem[];
     const bool staged = stage_rules<Pol>(smem, p);
@@ -112,20 +112,27 @@ __device__ __forceinline__ void compact_body(const ScanParams &p) {
     t.one = p.one;
     const int64_t nb = (p.n + B - 1) / B;
     for (int64_t b = (int64_t)blockIdx.x * nw + warp; b < nb; b += (int64_t)gridDim.x * nw)
-        run_batch<Pol, VEC, PART>(t, b * B, (int)min((int64_t)B, p.n - b * B), Q, wc, lane);
+        run_batch<Pol, VEC, PART, PPL>(t, b * B, (int)min((int64_t)B, p.n - b * B), Q, wc, lane);
     if (!staged) drain_rules<Pol>(smem, p);
 }
 
 template <class Pol, bool VEC, bool PART>
 __global__ void __launch_bounds__(1024) k_packet_split_compact(ScanParams p) {
-    compact_body<Pol, VEC, PART>(p);
+    compact_body<Pol, VEC, PART, 1>(p);
 }
 
 // Dense form: two 768-thread blocks per SM (48 resident warps, at most 42
 // registers a thread) instead of one 1,024-thread block (32 warps).
 template <class Pol, bool VEC, bool PART>
 __global__ void __launch_bounds__(768, 2) k_packet_split_compact_dense(ScanParams p) {
-    compact_body<Pol, VEC, PART>(p);
+    compact_body<Pol, VEC, PART, 1>(p);
+}
+
+// Two packets per lane in every scan group (each rule load feeds both; two
+// independent test chains per lane), one 1,024-thread block per SM.
+template <class Pol, bool VEC, bool PART>
+__global__ void __launch_bounds__(1024) k_packet_split_compact_x2(ScanParams p) {
+    compact_body<Pol, VEC, PART, 2>(p);
 }
 
 // ------------------------------------------------------------ rule split kernel
@@ -297,26 +304,29 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
         p.orig = rs->d_part_orig;
     }
     const int need_all = (int)((p.n_scan + kChunkRules - 1) / kChunkRules * kChunkRules);
-    // Short partitioned lists leave shared memory for two 768-thread blocks per SM (48 warps
-    // instead of 32), which hides more of the rule-load latency.
-    const bool auto_dense = compact && part && cfg.block_threads <= 0 && cfg.blocks_per_sm <= 0 &&
-                            cfg.smem_rules == 0 && need_all <= 1024;
-    int threads = cfg.block_threads > 0 ? cfg.block_threads : (auto_dense ? 768 : (compact ? 1024 : 512));
+    int threads = cfg.block_threads > 0 ? cfg.block_threads : (compact ? 1024 : 512);
     if (cfg.block_threads <= 0 && !compact) {
         // at least two blocks per SM when the batch allows it
         const int64_t nq = (n + 3) / 4;
         const int64_t t = nq / (2 * (int64_t)sm_count(rs->device)) / 32 * 32;
         threads = (int)std::max<int64_t>(64, std::min<int64_t>(512, t));
     }
-    const int per_sm = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : ((compact && !auto_dense) ? 1 : 2);
+    const int per_sm = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : (compact ? 1 : 2);
     if (threads % 32 != 0 || threads > 1024) return FW_EINVAL;
+    if (cfg.lane_packets < 0 || cfg.lane_packets > 2) return FW_EINVAL;
+    // Compacting forms: one 1,024-thread block per SM by default; "dense" = two blocks of at
+    // most 768 threads. With the protocol partition the default gives each lane two packets
+    // per group (every rule load feeds two checks); the dense form keeps one.
+    const bool dense = compact && threads <= 768 && per_sm >= 2;
+    const bool lane2 = compact && part && (cfg.lane_packets == 2 || (cfg.lane_packets == 0 && !dense));
+    if (lane2 && dense) return FW_EINVAL;  // the two-packet form is built for one 1,024-thread block per SM
     int want = cfg.smem_rules > 0 ? cfg.smem_rules : (cfg.smem_rules < 0 ? 0 : (compact ? 2048 : 3072));
     want = (want / kChunkRules) * kChunkRules;
     p.n_smem = std::min(want, need_all);
     p.batch = cfg.packets_per_group > 0 ? cfg.packets_per_group : 256;
     if (compact && (p.batch % 128 != 0 || p.batch > 65536)) return FW_EINVAL;
     // protocol sub-lists are short, so one long first segment beats early compaction there
-    p.seg0 = cfg.segment_rules > 0 ? cfg.segment_rules : (part ? 64 : 16);
+    p.seg0 = cfg.segment_rules > 0 ? cfg.segment_rules : (part ? (lane2 ? 128 : 64) : 16);
     if (p.seg0 % 4 != 0) return FW_EINVAL;
     p.one = 1u;
     p.h = h;
@@ -340,7 +350,6 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
         blocks = std::min<int64_t>(blocks, (nq + threads - 1) / threads);
     }
     blocks = std::max<int64_t>(1, blocks);
-    const bool dense = compact && threads <= 768 && per_sm >= 2;
     cudaError_t e = cudaSuccess;
 #define FW_LAUNCH_PS(KER, POL, V, PT)                                                        \
     do {                                                                                     \
@@ -351,6 +360,11 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
     do {                                                                                     \
         if (dense) FW_LAUNCH_PS(k_packet_split_compact_dense, POL, V, PT);                   \
         else FW_LAUNCH_PS(k_packet_split_compact, POL, V, PT);                               \
+    } while (0)
+#define FW_LAUNCH_PSX(POL, V, PT)                                                            \
+    do {                                                                                     \
+        if (lane2) FW_LAUNCH_PS(k_packet_split_compact_x2, POL, V, PT);                      \
+        else FW_LAUNCH_PSD(POL, V, PT);                                                      \
     } while (0)
 #define FW_PICK(KER)                                                                         \
     do {                                                                                     \
@@ -374,13 +388,14 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
         } else if (pred == FW_PRED_RANGE) {
             if (vec) FW_LAUNCH_PSD(PolRange, true, false); else FW_LAUNCH_PSD(PolRange, false, false);
         } else if (part) {
-            if (vec) FW_LAUNCH_PSD(PolArith, true, true); else FW_LAUNCH_PSD(PolArith, false, true);
+            if (vec) FW_LAUNCH_PSX(PolArith, true, true); else FW_LAUNCH_PSX(PolArith, false, true);
         } else {
             if (vec) FW_LAUNCH_PSD(PolArith, true, false); else FW_LAUNCH_PSD(PolArith, false, false);
         }
     } else {
         FW_PICK(k_packet_split);
     }
+#undef FW_LAUNCH_PSX
 #undef FW_LAUNCH_PSD
 #undef FW_PICK
 #undef FW_LAUNCH_PS
@@ -466,7 +481,7 @@ static int classify_impl(const fw_ruleset *rs, const fw_headers *hdrs, int64_t n
     fw_config cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     if (cfg_in != nullptr) cfg = *cfg_in;
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < 5; ++i)
         if (cfg.reserved[i] != 0) return FW_EINVAL;
     HdrPtrs h{hdrs->src, hdrs->dst, hdrs->sport, hdrs->dport, hdrs->proto};
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

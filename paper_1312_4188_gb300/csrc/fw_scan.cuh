@@ -299,6 +299,52 @@ __device__ __forceinline__ int scan_range(const typename Pol::Pk &pk, int k0, in
     return -1;
 }
 
+// Two packets against the same rules: each rule record is loaded once for
+// both, and the two packets' tests are independent chains the scheduler can
+// overlap. ra / rb as scan_range for packets a / b (a packet that is not
+// valid is not scanned and returns -1). The loop runs until both are decided.
+template <class Pol, bool SMEM>
+__device__ __forceinline__ int first_of4(const typename Pol::Pk &pk, const typename Pol::R r[4], int k, uint32_t one) {
+    return k + (!Pol::mism(pk, r[0], one) ? 0 : !Pol::mism(pk, r[1], one) ? 1 : !Pol::mism(pk, r[2], one) ? 2 : 3);
+}
+
+template <class Pol>
+__device__ __forceinline__ void scan_range2(const typename Pol::Pk &a, const typename Pol::Pk &b, bool va, bool vb,
+                                            int k0, int k1, const typename Pol::View &sv, int n_smem,
+                                            const typename Pol::View &gv, uint32_t one, int &ra, int &rb) {
+    ra = -1;
+    rb = -1;
+    bool da = !va, db = !vb;
+    int k = k0;
+    const int lim = min(k1, n_smem);
+    for (; k < lim && !(da && db); k += 4) {
+        typename Pol::R r[4];
+        Pol::template load4<true>(sv, k, r);
+        const bool ma = Pol::all_mismatch4(a, r, one), mb = Pol::all_mismatch4(b, r, one);
+        if (!da && !ma) {
+            ra = first_of4<Pol, true>(a, r, k, one);
+            da = true;
+        }
+        if (!db && !mb) {
+            rb = first_of4<Pol, true>(b, r, k, one);
+            db = true;
+        }
+    }
+    for (; k < k1 && !(da && db); k += 4) {
+        typename Pol::R r[4];
+        Pol::template load4<false>(gv, k, r);
+        const bool ma = Pol::all_mismatch4(a, r, one), mb = Pol::all_mismatch4(b, r, one);
+        if (!da && !ma) {
+            ra = first_of4<Pol, false>(a, r, k, one);
+            da = true;
+        }
+        if (!db && !mb) {
+            rb = first_of4<Pol, false>(b, r, k, one);
+            db = true;
+        }
+    }
+}
+
 // Shared-memory rule prefix: one mbarrier per 256-rule chunk, the chunks
 // brought in by 1-D TMA bulk copies issued by thread 0, then every thread
 // waits (bounded) until all chunks have landed. A persistent block does this
@@ -399,7 +445,7 @@ struct BatchTarget {
 // undecided ones are packed to the front of the region (ballot + popc), so
 // the next segment runs on dense groups of still-undecided packets instead of
 // lanes idling behind the slowest packet of a warp.
-template <class Pol, bool VEC, bool PART>
+template <class Pol, bool VEC, bool PART, int PPL = 1>
 __device__ __forceinline__ void run_batch(const BatchTarget<Pol> &t, int64_t base, int cnt, uint4 *Q, int *wc,
                                           int lane) {
     int n_groups = 1;
@@ -462,27 +508,58 @@ __device__ __forceinline__ void run_batch(const BatchTarget<Pol> &t, int64_t bas
             s1 = min(s1, len);
             const bool last = s1 >= len;
             int w = 0;
-            for (int g0 = 0; g0 < m; g0 += 32) {
-                const int i = g0 + lane;
-                const bool valid = i < m;
-                const uint4 e = valid ? Q[R + i] : make_uint4(0, 0, 0, 0);
-                __syncwarp();
-                int slot;
-                const typename Pol::Pk pk = Pol::unpack(e, slot);
-                int r = -1;
-                if (valid && s0 < s1) r = scan_range<Pol>(pk, s0, s1, svg, n_smem_g, gvg, t.one);
-                const bool keep = valid && r == -1 && !last;
-                if (valid && !keep) {
-                    int v = r;
-                    if constexpr (PART) v = r >= 0 ? __ldg(t.orig + off + r) : -1;
-                    v = v >= 0 ? v : -1;
-                    t.out_idx[base + slot] = v;
-                    t.out_act[base + slot] = v >= 0 ? __ldg(t.action + v) : (uint8_t)FW_DROP;
+            if constexpr (PPL == 1) {
+                for (int g0 = 0; g0 < m; g0 += 32) {
+                    const int i = g0 + lane;
+                    const bool valid = i < m;
+                    const uint4 e = valid ? Q[R + i] : make_uint4(0, 0, 0, 0);
+                    __syncwarp();
+                    int slot;
+                    const typename Pol::Pk pk = Pol::unpack(e, slot);
+                    int r = -1;
+                    if (valid && s0 < s1) r = scan_range<Pol>(pk, s0, s1, svg, n_smem_g, gvg, t.one);
+                    const bool keep = valid && r == -1 && !last;
+                    if (valid && !keep) {
+                        int v = r;
+                        if constexpr (PART) v = r >= 0 ? __ldg(t.orig + off + r) : -1;
+                        v = v >= 0 ? v : -1;
+                        t.out_idx[base + slot] = v;
+                        t.out_act[base + slot] = v >= 0 ? __ldg(t.action + v) : (uint8_t)FW_DROP;
+                    }
+                    const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
+                    if (keep) Q[R + w + __popc(bal & ((1u << lane) - 1u))] = e;
+                    w += __popc(bal);
+                    __syncwarp();
                 }
-                const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
-                if (keep) Q[R + w + __popc(bal & ((1u << lane) - 1u))] = e;
-                w += __popc(bal);
-                __syncwarp();
+            } else {
+                // two queue entries per lane: g0 + lane and g0 + 32 + lane
+                for (int g0 = 0; g0 < m; g0 += 64) {
+                    const int i0 = g0 + lane, i1 = g0 + 32 + lane;
+                    const bool v0 = i0 < m, v1 = i1 < m;
+                    const uint4 e0 = v0 ? Q[R + i0] : make_uint4(0, 0, 0, 0);
+                    const uint4 e1 = v1 ? Q[R + i1] : make_uint4(0, 0, 0, 0);
+                    __syncwarp();
+                    int slot0, slot1, r0 = -1, r1 = -1;
+                    const typename Pol::Pk pk0 = Pol::unpack(e0, slot0), pk1 = Pol::unpack(e1, slot1);
+                    if (s0 < s1) scan_range2<Pol>(pk0, pk1, v0, v1, s0, s1, svg, n_smem_g, gvg, t.one, r0, r1);
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const bool valid = u ? v1 : v0;
+                        const int r = u ? r1 : r0, slot = u ? slot1 : slot0;
+                        const bool keep = valid && r == -1 && !last;
+                        if (valid && !keep) {
+                            int v = r;
+                            if constexpr (PART) v = r >= 0 ? __ldg(t.orig + off + r) : -1;
+                            v = v >= 0 ? v : -1;
+                            t.out_idx[base + slot] = v;
+                            t.out_act[base + slot] = v >= 0 ? __ldg(t.action + v) : (uint8_t)FW_DROP;
+                        }
+                        const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
+                        if (keep) Q[R + w + __popc(bal & ((1u << lane) - 1u))] = u ? e1 : e0;
+                        w += __popc(bal);
+                    }
+                    __syncwarp();
+                }
             }
             m = w;
             s0 = s1;

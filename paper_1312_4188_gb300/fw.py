@@ -65,7 +65,8 @@ class fw_config(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("smem_rules", ctypes.c_int32), ("packets_per_group", ctypes.c_int32),
                 ("rule_slices", ctypes.c_int32), ("compact", ctypes.c_int32), ("predicate", ctypes.c_int32),
-                ("segment_rules", ctypes.c_int32), ("partition", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("segment_rules", ctypes.c_int32), ("partition", ctypes.c_int32), ("lane_packets", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 def make_config(mode=FW_MODE_AUTO, **kw) -> fw_config:

@@ -19,8 +19,13 @@ CONFIGS = [
     ("packet_split", {}),
     ("packet_split", {"partition": 2}),
     ("packet_split", {"compact": 2, "partition": 1}),
-    ("packet_split", {"compact": 1, "partition": 1, "smem_rules": 256, "segment_rules": 4, "block_threads": 256}),
+    ("packet_split", {"compact": 1, "partition": 1, "lane_packets": 1}),
+    ("packet_split", {"compact": 1, "partition": 1, "lane_packets": 1, "smem_rules": 256, "segment_rules": 4,
+                      "block_threads": 256}),
     ("packet_split", {"compact": 1, "partition": 1, "block_threads": 768, "blocks_per_sm": 2, "smem_rules": 256}),
+    ("packet_split", {"compact": 1, "partition": 1, "lane_packets": 2, "block_threads": 1024, "blocks_per_sm": 1}),
+    ("packet_split", {"compact": 1, "partition": 1, "lane_packets": 2, "block_threads": 256, "blocks_per_sm": 1,
+                      "segment_rules": 4, "smem_rules": -1}),
     ("packet_split", {"compact": 1, "partition": 2, "block_threads": 512, "blocks_per_sm": 2, "segment_rules": 8}),
     ("packet_split", {"predicate": fw.FW_PRED_CMP}),
     ("packet_split", {"predicate": fw.FW_PRED_CLAMP}),
