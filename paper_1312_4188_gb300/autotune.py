@@ -28,7 +28,8 @@ PACKET_SPLIT_CANDIDATES = (
             packets_per_group=b, segment_rules=s0)
        for sr in (256, 1024) for b in (128, 256) for s0 in (32, 64)]
     + [dict(mode="packet_split", compact=1, partition=1, lane_packets=2, block_threads=1024, blocks_per_sm=1,
-            smem_rules=2048, packets_per_group=b, segment_rules=s0) for b in (256, 512) for s0 in (32, 64, 128)]
+            smem_rules=sr, packets_per_group=b, segment_rules=s0)
+       for (b, sr) in ((256, 2048), (384, 512)) for s0 in (32, 64, 128)]
     + [dict(mode="packet_split", compact=2, partition=1)]
     + [dict(mode="packet_split", compact=2, predicate=p, partition=2)
      for p in (fw.FW_PRED_CLAMP, fw.FW_PRED_CMP, fw.FW_PRED_ARITH, fw.FW_PRED_RANGE)]

@@ -110,9 +110,18 @@ __device__ __forceinline__ void compact_body(const ScanParams &p) {
     t.out_act = p.out_act;
     t.seg0 = p.seg0;
     t.one = p.one;
-    const int64_t nb = (p.n + B - 1) / B;
-    for (int64_t b = (int64_t)blockIdx.x * nw + warp; b < nb; b += (int64_t)gridDim.x * nw)
-        run_batch<Pol, VEC, PART, PPL>(t, b * B, (int)min((int64_t)B, p.n - b * B), Q, wc, lane);
+    // packets per batch: the two-packet form keeps queue room for one pad per class
+    const int P = PPL == 2 ? B - ((p.n_classes + 3) & ~3) : B;
+    const int64_t nb = (p.n + P - 1) / P;
+    for (int64_t b = (int64_t)blockIdx.x * nw + warp; b < nb; b += (int64_t)gridDim.x * nw) {
+        const int cnt = (int)min((int64_t)P, p.n - b * P);
+        if constexpr (PPL == 2) {
+            static_assert(PART, "two packets per lane needs the protocol partition");
+            run_batch_pairs<Pol, VEC>(t, b * P, cnt, Q, wc, lane);
+        } else {
+            run_batch<Pol, VEC, PART>(t, b * P, cnt, Q, wc, lane);
+        }
+    }
     if (!staged) drain_rules<Pol>(smem, p);
 }
 
@@ -343,7 +352,8 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
                      aligned(h.proto, 4) && aligned(out_idx, 16) && aligned(out_act, 4);
     int64_t blocks = (int64_t)sm_count(rs->device) * per_sm;
     if (compact) {
-        const int64_t nb = (n + p.batch - 1) / p.batch;
+        const int per_batch = lane2 ? p.batch - ((p.n_classes + 3) & ~3) : p.batch;
+        const int64_t nb = (n + per_batch - 1) / per_batch;
         blocks = std::min<int64_t>(blocks, (nb + threads / 32 - 1) / (threads / 32));
     } else {
         const int64_t nq = (n + 3) / 4;

@@ -445,7 +445,7 @@ struct BatchTarget {
 // undecided ones are packed to the front of the region (ballot + popc), so
 // the next segment runs on dense groups of still-undecided packets instead of
 // lanes idling behind the slowest packet of a warp.
-template <class Pol, bool VEC, bool PART, int PPL = 1>
+template <class Pol, bool VEC, bool PART>
 __device__ __forceinline__ void run_batch(const BatchTarget<Pol> &t, int64_t base, int cnt, uint4 *Q, int *wc,
                                           int lane) {
     int n_groups = 1;
@@ -508,63 +508,171 @@ __device__ __forceinline__ void run_batch(const BatchTarget<Pol> &t, int64_t bas
             s1 = min(s1, len);
             const bool last = s1 >= len;
             int w = 0;
-            if constexpr (PPL == 1) {
-                for (int g0 = 0; g0 < m; g0 += 32) {
-                    const int i = g0 + lane;
-                    const bool valid = i < m;
-                    const uint4 e = valid ? Q[R + i] : make_uint4(0, 0, 0, 0);
-                    __syncwarp();
-                    int slot;
-                    const typename Pol::Pk pk = Pol::unpack(e, slot);
-                    int r = -1;
-                    if (valid && s0 < s1) r = scan_range<Pol>(pk, s0, s1, svg, n_smem_g, gvg, t.one);
-                    const bool keep = valid && r == -1 && !last;
-                    if (valid && !keep) {
-                        int v = r;
-                        if constexpr (PART) v = r >= 0 ? __ldg(t.orig + off + r) : -1;
-                        v = v >= 0 ? v : -1;
-                        t.out_idx[base + slot] = v;
-                        t.out_act[base + slot] = v >= 0 ? __ldg(t.action + v) : (uint8_t)FW_DROP;
-                    }
-                    const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
-                    if (keep) Q[R + w + __popc(bal & ((1u << lane) - 1u))] = e;
-                    w += __popc(bal);
-                    __syncwarp();
+            for (int g0 = 0; g0 < m; g0 += 32) {
+                const int i = g0 + lane;
+                const bool valid = i < m;
+                const uint4 e = valid ? Q[R + i] : make_uint4(0, 0, 0, 0);
+                __syncwarp();
+                int slot;
+                const typename Pol::Pk pk = Pol::unpack(e, slot);
+                int r = -1;
+                if (valid && s0 < s1) r = scan_range<Pol>(pk, s0, s1, svg, n_smem_g, gvg, t.one);
+                const bool keep = valid && r == -1 && !last;
+                if (valid && !keep) {
+                    int v = r;
+                    if constexpr (PART) v = r >= 0 ? __ldg(t.orig + off + r) : -1;
+                    v = v >= 0 ? v : -1;
+                    t.out_idx[base + slot] = v;
+                    t.out_act[base + slot] = v >= 0 ? __ldg(t.action + v) : (uint8_t)FW_DROP;
                 }
-            } else {
-                // two queue entries per lane: g0 + lane and g0 + 32 + lane
-                for (int g0 = 0; g0 < m; g0 += 64) {
-                    const int i0 = g0 + lane, i1 = g0 + 32 + lane;
-                    const bool v0 = i0 < m, v1 = i1 < m;
-                    const uint4 e0 = v0 ? Q[R + i0] : make_uint4(0, 0, 0, 0);
-                    const uint4 e1 = v1 ? Q[R + i1] : make_uint4(0, 0, 0, 0);
-                    __syncwarp();
-                    int slot0, slot1, r0 = -1, r1 = -1;
-                    const typename Pol::Pk pk0 = Pol::unpack(e0, slot0), pk1 = Pol::unpack(e1, slot1);
-                    if (s0 < s1) scan_range2<Pol>(pk0, pk1, v0, v1, s0, s1, svg, n_smem_g, gvg, t.one, r0, r1);
-#pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        const bool valid = u ? v1 : v0;
-                        const int r = u ? r1 : r0, slot = u ? slot1 : slot0;
-                        const bool keep = valid && r == -1 && !last;
-                        if (valid && !keep) {
-                            int v = r;
-                            if constexpr (PART) v = r >= 0 ? __ldg(t.orig + off + r) : -1;
-                            v = v >= 0 ? v : -1;
-                            t.out_idx[base + slot] = v;
-                            t.out_act[base + slot] = v >= 0 ? __ldg(t.action + v) : (uint8_t)FW_DROP;
-                        }
-                        const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
-                        if (keep) Q[R + w + __popc(bal & ((1u << lane) - 1u))] = u ? e1 : e0;
-                        w += __popc(bal);
-                    }
-                    __syncwarp();
-                }
+                const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
+                if (keep) Q[R + w + __popc(bal & ((1u << lane) - 1u))] = e;
+                w += __popc(bal);
+                __syncwarp();
             }
             m = w;
             s0 = s1;
             s1 = s1 * 2;
         }
+    }
+    __syncwarp();
+}
+
+// Queue index of sorted position `pos` in the two-packets-per-lane layout: lane l
+// of a 64-entry group holds sorted entries 2l and 2l+1, stored at l and 32 + l,
+// so each of the group's two loads reads 32 consecutive 16-byte entries.
+__device__ __forceinline__ int pair_slot(int pos) { return (pos & ~63) + ((pos & 1) << 5) + ((pos >> 1) & 31); }
+
+// Slot value of a queue entry that holds no packet to scan: the pad that makes a
+// class region even, or a packet decided in the last segment. Real slots are
+// below the queue capacity, which shared memory bounds far below 0xFFFF.
+constexpr uint32_t kNoSlot = 0xFFFFu;
+
+// Lane 0 sets cur[c] to the start of class c's region, each region padded to an
+// even count; returns the padded total (every lane).
+__device__ __forceinline__ int even_region_starts(int n_classes, const int *cnt, int *cur, int lane) {
+    int acc = 0;
+    for (int c = 0; c < n_classes; ++c) {
+        if (lane == 0) cur[c] = acc;
+        acc += (cnt[c] + 1) & ~1;
+    }
+    __syncwarp();
+    return acc;
+}
+
+// After the regions are filled (cur[c] = start + count): one pad entry behind
+// every odd-sized region.
+__device__ __forceinline__ void write_pads(int n_classes, const int *cnt, const int *cur, uint4 *Q, int lane) {
+    if (lane < n_classes && (cnt[lane] & 1)) Q[pair_slot(cur[lane])] = make_uint4(0, 0, kNoSlot << 16, 0);
+    __syncwarp();
+}
+
+// run_batch with two packets per lane (partitioned arithmetic form). The batch
+// is counting-sorted by protocol class, every class region padded to an even
+// count, so the two entries a lane holds always share a class: one rule load
+// from their sub-list feeds both tests. A 64-entry group may span classes; each
+// lane follows its own class's sub-list (the loads of a group then have as many
+// distinct addresses as it has classes). The queue holds cnt plus at most
+// n_classes pads. After a segment that is not the last for every class, the
+// undecided packets are re-sorted by class, padded again, in place: regions only
+// shrink, so a packet's new position never lies past the group being read.
+template <class Pol, bool VEC>
+__device__ __forceinline__ void run_batch_pairs(const BatchTarget<Pol> &t, int64_t base, int cnt, uint4 *Q, int *wc,
+                                                int lane) {
+    int *cnt_c = wc, *cur_c = wc + kMaxClasses;
+    const int nc = t.n_classes;
+    if (lane < kMaxClasses) cnt_c[lane] = 0;
+    __syncwarp();
+    for (int qq = lane; qq * 4 < cnt; qq += 32) {
+        uint32_t pr4;
+        int nv;
+        load_protos<VEC>(t.h, t.n, base / 4 + qq, true, pr4, nv);
+        for (int j = 0; j < nv; ++j) atomicAdd(&cnt_c[t.class_of[(pr4 >> (8 * j)) & 0xFFu]], 1);
+    }
+    __syncwarp();
+    int m = even_region_starts(nc, cnt_c, cur_c, lane);
+    for (int qq = lane; qq * 4 < cnt; qq += 32) {
+        typename Pol::Pk pk[4];
+        int nv;
+        load_quad<Pol, VEC>(t.h, t.n, base / 4 + qq, pk, nv);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (j >= nv) continue;
+            const int pos = atomicAdd(&cur_c[t.class_of[pkt_proto<Pol>(pk[j]) & 0xFFu]], 1);
+            Q[pair_slot(pos)] = Pol::pack(pk[j], qq * 4 + j);
+        }
+    }
+    __syncwarp();
+    write_pads(nc, cnt_c, cur_c, Q, lane);
+    int max_len = 0;
+    for (int c = 0; c < nc; ++c) max_len = max(max_len, t.class_len[c]);
+    int s0 = 0, s1 = t.seg0;
+    while (m > 0) {
+        const bool final_seg = s1 >= max_len;  // every class's sub-list ends in this segment
+        if (!final_seg) {
+            if (lane < kMaxClasses) cnt_c[lane] = 0;
+            __syncwarp();
+        }
+        for (int g0 = 0; g0 < m; g0 += 64) {
+            const bool in = g0 + 2 * lane < m;  // m is even: both entries of the lane or neither
+            const uint4 e0 = in ? Q[g0 + lane] : make_uint4(0, 0, kNoSlot << 16, 0);
+            const uint4 e1 = in ? Q[g0 + 32 + lane] : make_uint4(0, 0, kNoSlot << 16, 0);
+            int slot0, slot1;
+            const typename Pol::Pk a = Pol::unpack(e0, slot0), b = Pol::unpack(e1, slot1);
+            const bool v0 = slot0 != (int)kNoSlot, v1 = slot1 != (int)kNoSlot;  // a pad is only ever second
+            int cls = 0, off = 0, len = 0;
+            if (v0) {
+                cls = t.class_of[pkt_proto<Pol>(a) & 0xFFu];
+                off = t.class_off[cls];
+                len = t.class_len[cls];
+            }
+            const int k1 = min(s1, len);
+            const bool last = s1 >= len;
+            int r0 = -1, r1 = -1;
+            if (v0 && s0 < k1)
+                scan_range2<Pol>(a, b, v0, v1, s0, k1, shifted_view<Pol>(t.sv, off), max(0, t.n_smem - off),
+                                 shifted_view<Pol>(t.gv, off), t.one, r0, r1);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const bool valid = u ? v1 : v0;
+                const int r = u ? r1 : r0, slot = u ? slot1 : slot0;
+                const bool decided = valid && (r >= 0 || last);
+                if (decided) {
+                    int v = r >= 0 ? __ldg(t.orig + off + r) : -1;
+                    v = v >= 0 ? v : -1;
+                    t.out_idx[base + slot] = v;
+                    t.out_act[base + slot] = v >= 0 ? __ldg(t.action + v) : (uint8_t)FW_DROP;
+                }
+                if (!final_seg) {
+                    if (valid && !decided) atomicAdd(&cnt_c[cls], 1);
+                    else if (decided) Q[g0 + 32 * u + lane].z = kNoSlot << 16;
+                }
+            }
+        }
+        if (final_seg) break;
+        __syncwarp();
+        const int m_old = m;
+        m = even_region_starts(nc, cnt_c, cur_c, lane);
+        for (int g0 = 0; g0 < m_old; g0 += 64) {
+            const bool in = g0 + 2 * lane < m_old;
+            const uint4 e0 = in ? Q[g0 + lane] : make_uint4(0, 0, kNoSlot << 16, 0);
+            const uint4 e1 = in ? Q[g0 + 32 + lane] : make_uint4(0, 0, kNoSlot << 16, 0);
+            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const uint4 e = u ? e1 : e0;
+                int slot;
+                const typename Pol::Pk pk = Pol::unpack(e, slot);
+                if (slot != (int)kNoSlot) {
+                    const int pos = atomicAdd(&cur_c[t.class_of[pkt_proto<Pol>(pk) & 0xFFu]], 1);
+                    Q[pair_slot(pos)] = e;
+                }
+            }
+            __syncwarp();
+        }
+        write_pads(nc, cnt_c, cur_c, Q, lane);
+        s0 = s1;
+        s1 = s1 * 2;
     }
     __syncwarp();
 }
