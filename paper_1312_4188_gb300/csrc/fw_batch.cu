@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(1024) k_batch(BatchParams p) {
         t.class_len = J.class_len;
         t.class_of = J.class_of;
         t.orig = J.orig;
+        t.verdict = nullptr;  // the batched kernel reads orig and action
         t.action = J.action;
         t.out_idx = J.out_idx;
         t.out_act = J.out_act;

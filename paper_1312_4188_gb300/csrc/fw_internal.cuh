@@ -258,6 +258,7 @@ struct fw_ruleset {
     fwk::RecArith *d_part;             // part_pad records
     uint32_t *d_part_wtop;             // part_pad words
     int32_t *d_part_orig;              // part_pad original rule indices (-1 for padding)
+    uint32_t *d_part_verdict;          // part_pad words: original index | action << 31
     uint8_t *d_action;        // n_pad actions
     unsigned *d_status;       // device error flags (kStatus*)
 };

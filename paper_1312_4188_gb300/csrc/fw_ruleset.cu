@@ -124,6 +124,7 @@ extern "C" int fw_ruleset_create_ex(const fw_rule *rules, int64_t n, fw_ruleset 
     std::vector<RecArith> hq(rs->n_pad), part_rec;
     std::vector<uint32_t> part_wtop;
     std::vector<int32_t> part_orig;
+    std::vector<uint32_t> part_verdict;
     std::vector<uint8_t> part_class_of;
     std::vector<uint32_t> hw(rs->n_pad);
     std::vector<RecRange> hr(rs->n_pad);
@@ -179,6 +180,7 @@ extern "C" int fw_ruleset_create_ex(const fw_rule *rules, int64_t n, fw_ruleset 
         part_rec.resize(rs->part_pad);
         part_wtop.resize(rs->part_pad);
         part_orig.assign(rs->part_pad, -1);
+        part_verdict.assign(rs->part_pad, 0u);
         for (int64_t k = 0; k < rs->part_pad; ++k) never_match_arith(&part_rec[k], &part_wtop[k]);
         for (int c = 0; c < rs->n_classes; ++c)
             for (size_t j = 0; j < lists[c].size(); ++j) {
@@ -186,6 +188,7 @@ extern "C" int fw_ruleset_create_ex(const fw_rule *rules, int64_t n, fw_ruleset 
                 part_rec[at] = hq[k];
                 part_wtop[at] = hw[k];
                 part_orig[at] = (int32_t)k;
+                part_verdict[at] = (uint32_t)k | ((uint32_t)(ha[k] & 1u) << 31);
             }
         part_class_of = class_of;
     }
@@ -199,6 +202,7 @@ extern "C" int fw_ruleset_create_ex(const fw_rule *rules, int64_t n, fw_ruleset 
     if (e == cudaSuccess) e = cudaMalloc(&rs->d_part, rs->part_pad * sizeof(RecArith));
     if (e == cudaSuccess) e = cudaMalloc(&rs->d_part_wtop, rs->part_pad * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&rs->d_part_orig, rs->part_pad * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&rs->d_part_verdict, rs->part_pad * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&rs->d_class_of, 256);
     if (e == cudaSuccess) e = cudaMalloc(&rs->d_action, rs->n_pad);
     if (e == cudaSuccess) e = cudaMalloc(&rs->d_status, sizeof(unsigned));
@@ -215,6 +219,9 @@ extern "C" int fw_ruleset_create_ex(const fw_rule *rules, int64_t n, fw_ruleset 
         e = cudaMemcpy(rs->d_part_wtop, part_wtop.data(), rs->part_pad * sizeof(uint32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(rs->d_part_orig, part_orig.data(), rs->part_pad * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(rs->d_part_verdict, part_verdict.data(), rs->part_pad * sizeof(uint32_t),
+                       cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(rs->d_class_of, part_class_of.data(), 256, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(rs->d_action, ha.data(), rs->n_pad, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(rs->d_status, 0, sizeof(unsigned));
@@ -244,6 +251,7 @@ extern "C" void fw_ruleset_destroy(fw_ruleset *rs) {
     if (rs->d_part) cudaFree(rs->d_part);
     if (rs->d_part_wtop) cudaFree(rs->d_part_wtop);
     if (rs->d_part_orig) cudaFree(rs->d_part_orig);
+    if (rs->d_part_verdict) cudaFree(rs->d_part_verdict);
     if (rs->d_class_of) cudaFree(rs->d_class_of);
     if (rs->d_action) cudaFree(rs->d_action);
     if (rs->d_status) cudaFree(rs->d_status);

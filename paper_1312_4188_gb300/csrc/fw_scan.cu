@@ -105,6 +105,7 @@ __device__ __forceinline__ void compact_body(const ScanParams &p) {
     t.class_len = cls_len;
     t.class_of = class_tab;
     t.orig = p.orig;
+    t.verdict = p.verdict;
     t.action = p.action;
     t.out_idx = p.out_idx;
     t.out_act = p.out_act;
@@ -311,6 +312,7 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
         }
         p.class_of = rs->d_class_of;
         p.orig = rs->d_part_orig;
+        p.verdict = rs->d_part_verdict;
     }
     const int need_all = (int)((p.n_scan + kChunkRules - 1) / kChunkRules * kChunkRules);
     int threads = cfg.block_threads > 0 ? cfg.block_threads : (compact ? 1024 : 512);

@@ -2,6 +2,8 @@
 // kernels (fw_scan.cu) and the batched persistent kernel (fw_batch.cu).
 #pragma once
 
+#include <type_traits>
+
 #include "fw_internal.cuh"
 
 namespace fwk {
@@ -35,6 +37,7 @@ struct ScanParams {
     int32_t class_len[kMaxClasses];
     const uint8_t *class_of;  // 256 entries
     const int32_t *orig;      // original rule index of each stored record
+    const uint32_t *verdict;  // the same index | action << 31 (one load per decided packet)
 };
 
 // ------------------------------------------------------------ record policies
@@ -188,6 +191,42 @@ struct PolArith {
     static __device__ __forceinline__ bool all_mismatch4(const Pk &p, const R r[4], uint32_t one) {
         return mism(p, r[0], one) & mism(p, r[1], one) & mism(p, r[2], one) & mism(p, r[3], one);
     }
+    // Bit j set exactly when rule j of the four matches. Each rule's four field
+    // tests form one predicate chain as in mismatch_arith, and a predicated OR
+    // records a match, so only one predicate is live and the first match is read
+    // from the mask instead of testing the rules again.
+    static __device__ __forceinline__ uint32_t match_mask4(const Pk &p, const R r[4], uint32_t one) {
+        uint32_t ts[4], td[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            ts[j] = p.sport * one + r[j].b.x;
+            td[j] = p.x * r[j].b.z + r[j].b.w;
+        }
+        uint32_t m;
+#define FW_RULE_TESTS(TS, SW, AX, AY, AZ, AW, TD, W, BIT)          \
+    "setp.gt.u32 q, %" #TS ", %" #SW ";\n\t"                       \
+    "lop3.or.b32 t|q, %1, %" #AX ", %" #AY ", 0x28, q;\n\t"        \
+    "lop3.or.b32 t|q, %2, %" #AZ ", %" #AW ", 0x28, q;\n\t"        \
+    "setp.gt.or.u32 q, %" #TD ", %" #W ", q;\n\t"                  \
+    "@!q or.b32 %0, %0, " #BIT ";\n\t"
+        asm("{\n\t"
+            ".reg .pred q;\n\t"
+            ".reg .b32 t;\n\t"
+            "mov.b32 %0, 0;\n\t"
+            FW_RULE_TESTS(3, 4, 5, 6, 7, 8, 9, 10, 1)
+            FW_RULE_TESTS(11, 12, 13, 14, 15, 16, 17, 18, 2)
+            FW_RULE_TESTS(19, 20, 21, 22, 23, 24, 25, 26, 4)
+            FW_RULE_TESTS(27, 28, 29, 30, 31, 32, 33, 34, 8)
+            "}"
+            : "=&r"(m)
+            : "r"(p.src), "r"(p.dst),
+              "r"(ts[0]), "r"(r[0].b.y), "r"(r[0].a.x), "r"(r[0].a.y), "r"(r[0].a.z), "r"(r[0].a.w), "r"(td[0]), "r"(r[0].w),
+              "r"(ts[1]), "r"(r[1].b.y), "r"(r[1].a.x), "r"(r[1].a.y), "r"(r[1].a.z), "r"(r[1].a.w), "r"(td[1]), "r"(r[1].w),
+              "r"(ts[2]), "r"(r[2].b.y), "r"(r[2].a.x), "r"(r[2].a.y), "r"(r[2].a.z), "r"(r[2].a.w), "r"(td[2]), "r"(r[2].w),
+              "r"(ts[3]), "r"(r[3].b.y), "r"(r[3].a.x), "r"(r[3].a.y), "r"(r[3].a.z), "r"(r[3].a.w), "r"(td[3]), "r"(r[3].w));
+#undef FW_RULE_TESTS
+        return m;
+    }
     // queue entry: the batch slot above the 16-bit source port
     static __device__ __forceinline__ uint4 pack(const Pk &p, int slot) {
         return make_uint4(p.src, p.dst, p.sport | ((uint32_t)slot << 16), p.x);
@@ -303,15 +342,11 @@ __device__ __forceinline__ int scan_range(const typename Pol::Pk &pk, int k0, in
 // both, and the two packets' tests are independent chains the scheduler can
 // overlap. ra / rb as scan_range for packets a / b (a packet that is not
 // valid is not scanned and returns -1). The loop runs until both are decided.
-template <class Pol, bool SMEM>
-__device__ __forceinline__ int first_of4(const typename Pol::Pk &pk, const typename Pol::R r[4], int k, uint32_t one) {
-    return k + (!Pol::mism(pk, r[0], one) ? 0 : !Pol::mism(pk, r[1], one) ? 1 : !Pol::mism(pk, r[2], one) ? 2 : 3);
-}
-
 template <class Pol>
 __device__ __forceinline__ void scan_range2(const typename Pol::Pk &a, const typename Pol::Pk &b, bool va, bool vb,
                                             int k0, int k1, const typename Pol::View &sv, int n_smem,
                                             const typename Pol::View &gv, uint32_t one, int &ra, int &rb) {
+    static_assert(std::is_same<Pol, PolArith>::value, "two-packet scan: arithmetic record form only");
     ra = -1;
     rb = -1;
     bool da = !va, db = !vb;
@@ -320,26 +355,26 @@ __device__ __forceinline__ void scan_range2(const typename Pol::Pk &a, const typ
     for (; k < lim && !(da && db); k += 4) {
         typename Pol::R r[4];
         Pol::template load4<true>(sv, k, r);
-        const bool ma = Pol::all_mismatch4(a, r, one), mb = Pol::all_mismatch4(b, r, one);
-        if (!da && !ma) {
-            ra = first_of4<Pol, true>(a, r, k, one);
+        const uint32_t ma = Pol::match_mask4(a, r, one), mb = Pol::match_mask4(b, r, one);
+        if (!da && ma) {
+            ra = k + __ffs(ma) - 1;
             da = true;
         }
-        if (!db && !mb) {
-            rb = first_of4<Pol, true>(b, r, k, one);
+        if (!db && mb) {
+            rb = k + __ffs(mb) - 1;
             db = true;
         }
     }
     for (; k < k1 && !(da && db); k += 4) {
         typename Pol::R r[4];
         Pol::template load4<false>(gv, k, r);
-        const bool ma = Pol::all_mismatch4(a, r, one), mb = Pol::all_mismatch4(b, r, one);
-        if (!da && !ma) {
-            ra = first_of4<Pol, false>(a, r, k, one);
+        const uint32_t ma = Pol::match_mask4(a, r, one), mb = Pol::match_mask4(b, r, one);
+        if (!da && ma) {
+            ra = k + __ffs(ma) - 1;
             da = true;
         }
-        if (!db && !mb) {
-            rb = first_of4<Pol, false>(b, r, k, one);
+        if (!db && mb) {
+            rb = k + __ffs(mb) - 1;
             db = true;
         }
     }
@@ -430,6 +465,7 @@ struct BatchTarget {
     const int32_t *class_len;
     const uint8_t *class_of;
     const int32_t *orig;
+    const uint32_t *verdict;          // partition: original index | action << 31 per record
     const uint8_t *action;
     int32_t *out_idx;
     uint8_t *out_act;
@@ -548,6 +584,28 @@ __device__ __forceinline__ int pair_slot(int pos) { return (pos & ~63) + ((pos &
 // below the queue capacity, which shared memory bounds far below 0xFFFF.
 constexpr uint32_t kNoSlot = 0xFFFFu;
 
+// Per-lane class counters: 16-bit fields, classes 0-3 in lo and 4-7 in hi.
+__device__ __forceinline__ uint32_t class_field(uint64_t lo, uint64_t hi, uint32_t c) {
+    return (uint32_t)((c < 4 ? lo : hi) >> (16 * (c & 3))) & 0xFFFFu;
+}
+__device__ __forceinline__ void class_bump(uint64_t &lo, uint64_t &hi, uint32_t c) {
+    const uint64_t inc = 1ull << (16 * (c & 3));
+    if (c < 4) lo += inc;
+    else hi += inc;
+}
+
+// Queue entries of the two-packet scan carry their class in bits 28-30 of the
+// fourth word, above the 25 bits of (protocol << 17 | dport).
+constexpr uint32_t kXMask = 0x01FFFFFFu;
+__device__ __forceinline__ uint32_t entry_class(const uint4 &e) { return e.w >> 28; }
+
+// After the re-sort (cur[c] = start + count): one pad entry behind every
+// odd-sized region.
+__device__ __forceinline__ void write_pads(int n_classes, const int *cnt, const int *cur, uint4 *Q, int lane) {
+    if (lane < n_classes && (cnt[lane] & 1)) Q[pair_slot(cur[lane])] = make_uint4(0, 0, kNoSlot << 16, 0);
+    __syncwarp();
+}
+
 // Lane 0 sets cur[c] to the start of class c's region, each region padded to an
 // even count; returns the padded total (every lane).
 __device__ __forceinline__ int even_region_starts(int n_classes, const int *cnt, int *cur, int lane) {
@@ -560,37 +618,54 @@ __device__ __forceinline__ int even_region_starts(int n_classes, const int *cnt,
     return acc;
 }
 
-// After the regions are filled (cur[c] = start + count): one pad entry behind
-// every odd-sized region.
-__device__ __forceinline__ void write_pads(int n_classes, const int *cnt, const int *cur, uint4 *Q, int lane) {
-    if (lane < n_classes && (cnt[lane] & 1)) Q[pair_slot(cur[lane])] = make_uint4(0, 0, kNoSlot << 16, 0);
-    __syncwarp();
-}
-
 // run_batch with two packets per lane (partitioned arithmetic form). The batch
-// is counting-sorted by protocol class, every class region padded to an even
-// count, so the two entries a lane holds always share a class: one rule load
-// from their sub-list feeds both tests. A 64-entry group may span classes; each
-// lane follows its own class's sub-list (the loads of a group then have as many
-// distinct addresses as it has classes). The queue holds cnt plus at most
-// n_classes pads. After a segment that is not the last for every class, the
-// undecided packets are re-sorted by class, padded again, in place: regions only
-// shrink, so a packet's new position never lies past the group being read.
+// is sorted by protocol class, every class region padded to an even count, so
+// the two entries a lane holds always share a class: one rule load from their
+// sub-list feeds both tests. A 64-entry group may span classes; each lane
+// follows its own class's sub-list (the loads of a group then have as many
+// distinct addresses as it has classes). The sort needs no atomics: each lane
+// counts its own packets per class in registers, one warp-wide exclusive scan
+// of those counters gives every lane its place in each region, and the lane
+// writes its packets there. The queue holds cnt plus at most n_classes pads.
+// After a segment that is not the last for every class, the undecided packets
+// are re-sorted by class, padded again, in place: regions only shrink, so a
+// packet's new position never lies past the group being read.
 template <class Pol, bool VEC>
 __device__ __forceinline__ void run_batch_pairs(const BatchTarget<Pol> &t, int64_t base, int cnt, uint4 *Q, int *wc,
                                                 int lane) {
     int *cnt_c = wc, *cur_c = wc + kMaxClasses;
     const int nc = t.n_classes;
-    if (lane < kMaxClasses) cnt_c[lane] = 0;
-    __syncwarp();
+    uint64_t lo = 0, hi = 0;
     for (int qq = lane; qq * 4 < cnt; qq += 32) {
         uint32_t pr4;
         int nv;
         load_protos<VEC>(t.h, t.n, base / 4 + qq, true, pr4, nv);
-        for (int j = 0; j < nv; ++j) atomicAdd(&cnt_c[t.class_of[(pr4 >> (8 * j)) & 0xFFu]], 1);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (j < nv) class_bump(lo, hi, t.class_of[(pr4 >> (8 * j)) & 0xFFu]);
+    }
+    uint64_t elo = lo, ehi = hi;  // inclusive scan over lanes, then exclusive
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint64_t a = __shfl_up_sync(0xFFFFFFFFu, elo, d), b = __shfl_up_sync(0xFFFFFFFFu, ehi, d);
+        if (lane >= d) {
+            elo += a;
+            ehi += b;
+        }
+    }
+    const uint64_t tlo = __shfl_sync(0xFFFFFFFFu, elo, 31), thi = __shfl_sync(0xFFFFFFFFu, ehi, 31);
+    elo -= lo;
+    ehi -= hi;
+    int m = 0;
+    for (int c = 0; c < nc; ++c) {
+        const int tc = (int)class_field(tlo, thi, (uint32_t)c);
+        if (lane == 0) {
+            cur_c[c] = m;
+            cnt_c[c] = tc;
+        }
+        m += (tc + 1) & ~1;
     }
     __syncwarp();
-    int m = even_region_starts(nc, cnt_c, cur_c, lane);
     for (int qq = lane; qq * 4 < cnt; qq += 32) {
         typename Pol::Pk pk[4];
         int nv;
@@ -598,12 +673,16 @@ __device__ __forceinline__ void run_batch_pairs(const BatchTarget<Pol> &t, int64
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (j >= nv) continue;
-            const int pos = atomicAdd(&cur_c[t.class_of[pkt_proto<Pol>(pk[j]) & 0xFFu]], 1);
-            Q[pair_slot(pos)] = Pol::pack(pk[j], qq * 4 + j);
+            const uint32_t c = t.class_of[pkt_proto<Pol>(pk[j]) & 0xFFu];
+            const int pos = cur_c[c] + (int)class_field(elo, ehi, c);
+            class_bump(elo, ehi, c);
+            uint4 e = Pol::pack(pk[j], qq * 4 + j);
+            e.w |= c << 28;
+            Q[pair_slot(pos)] = e;
         }
     }
+    if (lane < nc && (cnt_c[lane] & 1)) Q[pair_slot(cur_c[lane] + cnt_c[lane])] = make_uint4(0, 0, kNoSlot << 16, 0);
     __syncwarp();
-    write_pads(nc, cnt_c, cur_c, Q, lane);
     int max_len = 0;
     for (int c = 0; c < nc; ++c) max_len = max(max_len, t.class_len[c]);
     int s0 = 0, s1 = t.seg0;
@@ -615,33 +694,38 @@ __device__ __forceinline__ void run_batch_pairs(const BatchTarget<Pol> &t, int64
         }
         for (int g0 = 0; g0 < m; g0 += 64) {
             const bool in = g0 + 2 * lane < m;  // m is even: both entries of the lane or neither
-            const uint4 e0 = in ? Q[g0 + lane] : make_uint4(0, 0, kNoSlot << 16, 0);
-            const uint4 e1 = in ? Q[g0 + 32 + lane] : make_uint4(0, 0, kNoSlot << 16, 0);
-            int slot0, slot1;
-            const typename Pol::Pk a = Pol::unpack(e0, slot0), b = Pol::unpack(e1, slot1);
-            const bool v0 = slot0 != (int)kNoSlot, v1 = slot1 != (int)kNoSlot;  // a pad is only ever second
-            int cls = 0, off = 0, len = 0;
-            if (v0) {
-                cls = t.class_of[pkt_proto<Pol>(a) & 0xFFu];
-                off = t.class_off[cls];
-                len = t.class_len[cls];
-            }
-            const int k1 = min(s1, len);
-            const bool last = s1 >= len;
+            bool v0, v1, last;
             int r0 = -1, r1 = -1;
-            if (v0 && s0 < k1)
-                scan_range2<Pol>(a, b, v0, v1, s0, k1, shifted_view<Pol>(t.sv, off), max(0, t.n_smem - off),
-                                 shifted_view<Pol>(t.gv, off), t.one, r0, r1);
+            {
+                uint4 e0 = in ? Q[g0 + lane] : make_uint4(0, 0, kNoSlot << 16, 0);
+                uint4 e1 = in ? Q[g0 + 32 + lane] : make_uint4(0, 0, kNoSlot << 16, 0);
+                const uint32_t cls = entry_class(e0);  // a pad is only ever second; both share the class
+                e0.w &= kXMask;
+                e1.w &= kXMask;
+                int slot0, slot1;
+                const typename Pol::Pk a = Pol::unpack(e0, slot0), b = Pol::unpack(e1, slot1);
+                v0 = slot0 != (int)kNoSlot;
+                v1 = slot1 != (int)kNoSlot;
+                const int off = v0 ? t.class_off[cls] : 0, len = v0 ? t.class_len[cls] : 0;
+                const int k1 = min(s1, len);
+                last = s1 >= len;
+                if (v0 && s0 < k1)
+                    scan_range2<Pol>(a, b, v0, v1, s0, k1, shifted_view<Pol>(t.sv, off), max(0, t.n_smem - off),
+                                     shifted_view<Pol>(t.gv, off), t.one, r0, r1);
+            }
+            // slots and class again from the queue: fewer registers live across the scan
+            const uint32_t cls = v0 ? entry_class(Q[g0 + lane]) : 0u;
+            const int off = v0 ? t.class_off[cls] : 0;
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 const bool valid = u ? v1 : v0;
-                const int r = u ? r1 : r0, slot = u ? slot1 : slot0;
+                const int r = u ? r1 : r0;
+                const int slot = valid ? (int)(Q[g0 + 32 * u + lane].z >> 16) : 0;
                 const bool decided = valid && (r >= 0 || last);
                 if (decided) {
-                    int v = r >= 0 ? __ldg(t.orig + off + r) : -1;
-                    v = v >= 0 ? v : -1;
-                    t.out_idx[base + slot] = v;
-                    t.out_act[base + slot] = v >= 0 ? __ldg(t.action + v) : (uint8_t)FW_DROP;
+                    const uint32_t w = r >= 0 ? __ldg(t.verdict + off + r) : 0xFFFFFFFFu;
+                    t.out_idx[base + slot] = r >= 0 ? (int32_t)(w & 0x7FFFFFFFu) : -1;
+                    t.out_act[base + slot] = r >= 0 ? (uint8_t)(w >> 31) : (uint8_t)FW_DROP;
                 }
                 if (!final_seg) {
                     if (valid && !decided) atomicAdd(&cnt_c[cls], 1);
@@ -661,10 +745,8 @@ __device__ __forceinline__ void run_batch_pairs(const BatchTarget<Pol> &t, int64
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 const uint4 e = u ? e1 : e0;
-                int slot;
-                const typename Pol::Pk pk = Pol::unpack(e, slot);
-                if (slot != (int)kNoSlot) {
-                    const int pos = atomicAdd(&cur_c[t.class_of[pkt_proto<Pol>(pk) & 0xFFu]], 1);
+                if ((e.z >> 16) != kNoSlot) {
+                    const int pos = atomicAdd(&cur_c[entry_class(e)], 1);
                     Q[pair_slot(pos)] = e;
                 }
             }
