@@ -694,33 +694,25 @@ __device__ __forceinline__ void run_batch_pairs(const BatchTarget<Pol> &t, int64
         }
         for (int g0 = 0; g0 < m; g0 += 64) {
             const bool in = g0 + 2 * lane < m;  // m is even: both entries of the lane or neither
-            bool v0, v1, last;
+            uint4 e0 = in ? Q[g0 + lane] : make_uint4(0, 0, kNoSlot << 16, 0);
+            uint4 e1 = in ? Q[g0 + 32 + lane] : make_uint4(0, 0, kNoSlot << 16, 0);
+            const uint32_t cls = entry_class(e0);  // a pad is only ever second; both share the class
+            e0.w &= kXMask;
+            e1.w &= kXMask;
+            int slot0, slot1;
+            const typename Pol::Pk a = Pol::unpack(e0, slot0), b = Pol::unpack(e1, slot1);
+            const bool v0 = slot0 != (int)kNoSlot, v1 = slot1 != (int)kNoSlot;
+            const int off = v0 ? t.class_off[cls] : 0, len = v0 ? t.class_len[cls] : 0;
+            const int k1 = min(s1, len);
+            const bool last = s1 >= len;
             int r0 = -1, r1 = -1;
-            {
-                uint4 e0 = in ? Q[g0 + lane] : make_uint4(0, 0, kNoSlot << 16, 0);
-                uint4 e1 = in ? Q[g0 + 32 + lane] : make_uint4(0, 0, kNoSlot << 16, 0);
-                const uint32_t cls = entry_class(e0);  // a pad is only ever second; both share the class
-                e0.w &= kXMask;
-                e1.w &= kXMask;
-                int slot0, slot1;
-                const typename Pol::Pk a = Pol::unpack(e0, slot0), b = Pol::unpack(e1, slot1);
-                v0 = slot0 != (int)kNoSlot;
-                v1 = slot1 != (int)kNoSlot;
-                const int off = v0 ? t.class_off[cls] : 0, len = v0 ? t.class_len[cls] : 0;
-                const int k1 = min(s1, len);
-                last = s1 >= len;
-                if (v0 && s0 < k1)
-                    scan_range2<Pol>(a, b, v0, v1, s0, k1, shifted_view<Pol>(t.sv, off), max(0, t.n_smem - off),
-                                     shifted_view<Pol>(t.gv, off), t.one, r0, r1);
-            }
-            // slots and class again from the queue: fewer registers live across the scan
-            const uint32_t cls = v0 ? entry_class(Q[g0 + lane]) : 0u;
-            const int off = v0 ? t.class_off[cls] : 0;
+            if (v0 && s0 < k1)
+                scan_range2<Pol>(a, b, v0, v1, s0, k1, shifted_view<Pol>(t.sv, off), max(0, t.n_smem - off),
+                                 shifted_view<Pol>(t.gv, off), t.one, r0, r1);
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 const bool valid = u ? v1 : v0;
-                const int r = u ? r1 : r0;
-                const int slot = valid ? (int)(Q[g0 + 32 * u + lane].z >> 16) : 0;
+                const int r = u ? r1 : r0, slot = u ? slot1 : slot0;
                 const bool decided = valid && (r >= 0 || last);
                 if (decided) {
                     const uint32_t w = r >= 0 ? __ldg(t.verdict + off + r) : 0xFFFFFFFFu;
