@@ -208,7 +208,7 @@ int fw_classify_ex(const fw_ruleset *rs, const fw_headers *hdrs, int64_t n,
  * accumulates a set of packets and checks them in parallel against one rule
  * set (Sec. IV.A) and suggests asynchronous launches to cut per-batch delay
  * (Sec. V); a plan covers any number of rule sets and batches at once. It is
- * built once (device work list of items: runs of up to packets_per_item
+ * built once (device work list of items: runs of up to packets_per_item - 8
  * packets of one job, longest rule sets first) and launched as often as
  * needed; a persistent grid takes items from a counter, so uneven jobs
  * balance. Each job's result is exactly fw_classify's.
@@ -229,10 +229,12 @@ typedef struct fw_job {
  * Plan configuration (zero = default). Rule sets fall into n_classes (1..4)
  * size classes by reachable rules: class c takes sets with at most
  * class_max_rules[c] rules (the last class takes the rest). Per class:
- * packets_per_item (multiple of 128, <= 4096, default 256) and segment_rules
- * (first rule segment of the compacting scan, multiple of 4, default 64).
- * block_threads (default 1024) x max packets_per_item x 16 bytes of shared
- * memory per block must fit in 227 KB.
+ * packets_per_item (queue entries per warp: multiple of 128, <= 4096, default
+ * 256; an item carries up to packets_per_item - 8 packets, the rest holds the
+ * pads that keep each protocol class region even for the two-packet scan) and
+ * segment_rules (first rule segment of the compacting scan, multiple of 4,
+ * default 64). block_threads (default 1024) x max packets_per_item x 16 bytes
+ * of shared memory per block must fit in 227 KB.
  */
 typedef struct fw_plan_config {
     int32_t block_threads;
@@ -289,7 +291,7 @@ typedef struct fw_server_config {
     int32_t max_pending;         /* queue capacity; submit returns FW_EBUSY beyond it (default 65536) */
     int64_t max_group_packets;   /* packets per launch (default 2^20); also the largest request */
     int64_t arena_bytes;         /* copy mode device staging budget (default 256 MiB) */
-    int32_t packets_per_item;    /* kernel work item (multiple of 128, default 256) */
+    int32_t packets_per_item;    /* queue entries per warp (multiple of 128, default 256); an item carries 8 fewer packets */
     int32_t segment_rules;       /* first rule segment of the compacting scan (default 64) */
     int32_t block_threads;       /* kernel block size (default 512) */
     int32_t reserved[5];

@@ -7,8 +7,8 @@
 // list of jobs into a device work list of items, each a run of up to
 // `packets_per_item` packets of one job. A persistent grid of warps takes
 // items from a global counter (dynamic scheduling, so cheap and expensive
-// items balance), and each warp runs the compacting first-match scan of
-// fw_scan.cuh on its item against the item's own rule set, read through L1.
+// items balance), and each warp runs the two-packets-per-lane first-match scan
+// of fw_scan.cuh on its item against the item's own rule set, read through L1.
 // Items are ordered by decreasing rule-set size so the long scans start
 // first. Per size class of rule set (by reachable rules) the plan carries its
 // own item size and first rule segment, chosen by the autotuner.
@@ -44,14 +44,14 @@ __global__ void __launch_bounds__(1024) k_batch(BatchParams p) {
         t.class_len = J.class_len;
         t.class_of = J.class_of;
         t.orig = J.orig;
-        t.verdict = nullptr;  // the batched kernel reads orig and action
+        t.verdict = J.verdict;
         t.action = J.action;
         t.out_idx = J.out_idx;
         t.out_act = J.out_act;
         t.seg0 = item.seg0;
         t.one = p.one;
-        if (J.vec) run_batch<PolArith, true, true>(t, item.start, item.count, Q, wc, lane);
-        else run_batch<PolArith, false, true>(t, item.start, item.count, Q, wc, lane);
+        if (J.vec) run_batch_pairs<PolArith, true>(t, item.start, item.count, Q, wc, lane);
+        else run_batch_pairs<PolArith, false>(t, item.start, item.count, Q, wc, lane);
     }
 }
 
@@ -63,6 +63,7 @@ void fill_batch_job(BatchJobDev &d, const fw_ruleset *rs, const fw_headers &h, i
     d.wtop = rs->d_part_wtop;
     d.action = rs->d_action;
     d.orig = rs->d_part_orig;
+    d.verdict = rs->d_part_verdict;
     d.class_of = rs->d_class_of;
     d.n_classes = rs->n_classes;
     for (int c = 0; c < kMaxClasses; ++c) {
@@ -174,7 +175,7 @@ extern "C" int fw_plan_create(const fw_job *jobs, int64_t n_jobs, const fw_plan_
     std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return jobs[a].rs->n_eff > jobs[b].rs->n_eff; });
     std::vector<BatchItem> items;
     for (int64_t j : order) {
-        const int B = per_item[cls[j]];
+        const int B = item_packets(per_item[cls[j]]);
         for (int64_t s = 0; s < hj[j].n; s += B) {
             BatchItem it;
             it.start = s;

@@ -13,6 +13,7 @@ struct BatchJobDev {
     const uint32_t *wtop;
     const uint8_t *action;
     const int32_t *orig;
+    const uint32_t *verdict;  // original index | action << 31 per stored record
     const uint8_t *class_of;
     int32_t n_classes;
     int32_t vec;  // 1 when the job's buffers allow the vector loads
@@ -40,6 +41,11 @@ struct BatchParams {
     int32_t qcap;              // queue capacity per warp (packets)
     uint32_t one;
 };
+
+// Packets one item may carry with a queue of `qcap` entries per warp: the
+// two-packet scan pads every protocol class region to an even count, at most
+// one pad for each of up to kMaxClasses classes.
+inline int32_t item_packets(int32_t qcap) { return qcap - kMaxClasses; }
 
 // Fill a job entry from a rule set and device-accessible buffers.
 void fill_batch_job(BatchJobDev &d, const fw_ruleset *rs, const fw_headers &h, int64_t n, int32_t *out_idx,

@@ -143,7 +143,7 @@ static void arena_free(fw_server *sv, size_t off, size_t len) {
 // the persistent kernel, (copy mode) verdict copies out, the completion event.
 static cudaError_t launch_group(fw_server *sv, SvSlot &sl) {
     const bool copy = sv->cfg.mode != FW_HOST_ZEROCOPY;
-    const int B = sv->cfg.packets_per_item;
+    const int B = item_packets(sv->cfg.packets_per_item);
     cudaError_t e = cudaSuccess;
     size_t off = sl.arena_off;
     int64_t n_items = 0;
@@ -421,9 +421,9 @@ extern "C" int fw_server_create(const fw_ruleset *const *sets, int n_sets, const
     cudaGetDevice(&sv->device);
     sv->threads = c.block_threads;
     sv->qcap = c.packets_per_item;
-    // a request of n packets needs ceil(n / packets_per_item) items; a group
-    // holds at most max_group_packets packets plus one partial item per request
-    sv->item_cap = c.max_group_packets / c.packets_per_item + c.max_group_requests + 1;
+    // a request of n packets needs ceil(n / item_packets) items; a group holds
+    // at most max_group_packets packets plus one partial item per request
+    sv->item_cap = c.max_group_packets / item_packets(c.packets_per_item) + c.max_group_requests + 1;
     cudaError_t e = prepare_batch_kernel(smem);
     if (e == cudaSuccess && c.mode == FW_HOST_COPY) {
         sv->arena_bytes = (size_t)c.arena_bytes;
