@@ -96,7 +96,7 @@ def sweep(rs, dh, n, candidates, reps=20, warmup=3):
     return out
 
 
-PLAN_CANDIDATES = [(ppi, seg) for ppi in (128, 256) for seg in (16, 64, 256)]
+PLAN_CANDIDATES = [(ppi, seg) for ppi in (128, 256) for seg in (16, 64, 256, 1024)]
 CLASS_LIMITS = (256, 4096)  # reachable rules: <= 256, <= 4096, larger
 
 

@@ -337,7 +337,7 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
     p.batch = cfg.packets_per_group > 0 ? cfg.packets_per_group : 256;
     if (compact && (p.batch % 128 != 0 || p.batch > 65536)) return FW_EINVAL;
     // protocol sub-lists are short, so one long first segment beats early compaction there
-    p.seg0 = cfg.segment_rules > 0 ? cfg.segment_rules : (part ? (lane2 ? 128 : 64) : 16);
+    p.seg0 = cfg.segment_rules > 0 ? cfg.segment_rules : (part ? (lane2 ? 512 : 64) : 16);
     if (p.seg0 % 4 != 0) return FW_EINVAL;
     p.one = 1u;
     p.h = h;
