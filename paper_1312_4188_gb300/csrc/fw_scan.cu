@@ -152,6 +152,7 @@ struct SplitParams {
     int n_scan;        // rules scanned (multiple of 4; padded records never match)
     int slice_rules;   // rules per slice along gridDim.y (multiple of 32)
     int group;         // packets per group (multiple of 32)
+    int gw;            // block mode: warps sharing one packet group (<= warps per block)
     HdrPtrs h;
     int64_t n;
     int32_t *out_idx;
@@ -164,17 +165,29 @@ constexpr int64_t kCompactMinPackets = int64_t(1) << 20;  // default packet spli
 
 // BLOCK = true: all warps of the block share one packet group and split its
 // chunks round-robin. BLOCK = false: each warp owns a packet group alone.
+// Barrier over the gw warps of packet group g: the warp itself when gw is 1,
+// otherwise named barrier 1 + g (barrier 0 is __syncthreads'; at most 8 groups
+// share a block when gw >= 2).
+__device__ __forceinline__ void group_sync(int gw, int g) {
+    if (gw == 1) __syncwarp();
+    else asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(gw * 32) : "memory");
+}
+
 template <bool BLOCK>
 __global__ void __launch_bounds__(512) k_rule_split(SplitParams p) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
     const int G = p.group;
-    const int groups_per_block = BLOCK ? 1 : nwarps;
-    const int my_group = BLOCK ? 0 : warp;
-    const int gw = BLOCK ? nwarps : 1;          // warps sharing a group
-    const int w_in_group = BLOCK ? warp : 0;
-    const int gt = BLOCK ? threadIdx.x : lane;  // thread index within the group
+    // Block mode (the paper's hybrid): gw warps share a packet group and split its rule
+    // chunks; a block holds nwarps / gw such groups, each synchronised by its own named
+    // barrier (gw is the chunk count when the list is short, so no warp sits idle).
+    const int gw = BLOCK ? p.gw : 1;
+    const int groups_per_block = nwarps / gw;
+    const int my_group = warp / gw;
+    if (my_group >= groups_per_block) return;  // warps left over when gw does not divide nwarps
+    const int w_in_group = warp % gw;
+    const int gt = w_in_group * 32 + lane;  // thread index within the group
     const int gthreads = gw * 32;
     Pkt *stage = reinterpret_cast<Pkt *>(smem) + (size_t)my_group * G;
     int *best = reinterpret_cast<int *>(smem + (size_t)groups_per_block * G * sizeof(Pkt)) + (size_t)my_group * G;
@@ -195,7 +208,7 @@ __global__ void __launch_bounds__(512) k_rule_split(SplitParams p) {
                 best[t] = -1;  // no packet: never pending
             }
         }
-        if (BLOCK) __syncthreads(); else __syncwarp();
+        group_sync(gw, my_group);
         for (int c0 = r0 + w_in_group * 32; c0 < r1; c0 += gw * 32) {
             const int k = c0 + lane;
             uint4 a = make_uint4(0, 0, 0, 0), b = make_uint4(0, 0xFFFFFFFFu, kNeverProto, 0xFFFFFFFFu);
@@ -210,17 +223,33 @@ __global__ void __launch_bounds__(512) k_rule_split(SplitParams p) {
             for (int t0 = 0; t0 < G; t0 += 32) {
                 unsigned pend = __ballot_sync(0xFFFFFFFFu, *reinterpret_cast<volatile int *>(&best[t0 + lane]) > c0);
                 pending |= pend != 0u;
+                // up to four pending packets per pass: four independent test chains and
+                // ballots in flight instead of one load-test-vote chain at a time
                 while (pend != 0u) {
-                    const int t = t0 + __ffs(pend) - 1;
-                    pend &= pend - 1u;
-                    const Pkt pk = stage[t];
-                    const unsigned bal = __ballot_sync(0xFFFFFFFFu, mismatch_clamp(pk, a, b) == 0u);
-                    if (bal != 0u && lane == 0) atomicMin(&best[t], c0 + __ffs(bal) - 1);
+                    int t[4];
+                    bool has[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        has[j] = pend != 0u;
+                        t[j] = has[j] ? t0 + __ffs(pend) - 1 : t0;
+                        pend &= pend - 1u;  // no-op once empty
+                    }
+                    unsigned bal[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const Pkt pk = stage[t[j]];
+                        bal[j] = __ballot_sync(0xFFFFFFFFu, has[j] && mismatch_clamp(pk, a, b) == 0u);
+                    }
+                    if (lane == 0) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            if (bal[j] != 0u) atomicMin(&best[t[j]], c0 + __ffs(bal[j]) - 1);
+                    }
                 }
             }
             if (!pending) break;
         }
-        if (BLOCK) __syncthreads(); else __syncwarp();
+        group_sync(gw, my_group);
         for (int t = gt; t < G; t += gthreads) {
             const int64_t i = base + t;
             if (i >= p.n) break;
@@ -233,7 +262,7 @@ __global__ void __launch_bounds__(512) k_rule_split(SplitParams p) {
                 p.out_act[i] = r >= 0 ? __ldg(p.action + r) : (uint8_t)FW_DROP;
             }
         }
-        if (BLOCK) __syncthreads(); else __syncwarp();
+        group_sync(gw, my_group);
     }
 }
 
@@ -428,13 +457,15 @@ int launch_rule_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t
     p.partial = nullptr;
     const bool block_mode = cfg.mode == FW_MODE_RULE_SPLIT_BLOCK;
     const bool grid_mode = cfg.mode == FW_MODE_RULE_SPLIT_GRID;
-    const int threads = cfg.block_threads > 0 ? cfg.block_threads : 256;
+    const int threads = cfg.block_threads > 0 ? cfg.block_threads : (block_mode ? 512 : 256);
     if (threads % 32 != 0 || threads > 512) return FW_EINVAL;
     int G = cfg.packets_per_group > 0 ? cfg.packets_per_group : (block_mode ? 256 : 64);
     if (G % 32 != 0 || G > 4096) return FW_EINVAL;
     p.group = G;
     const int nwarps = threads / 32;
-    const int groups_per_block = block_mode ? 1 : nwarps;
+    // block mode: as many warps per group as the list has 32-rule chunks, up to the block
+    p.gw = block_mode ? std::max(1, std::min(nwarps, (p.n_scan + 31) / 32)) : 1;
+    const int groups_per_block = nwarps / p.gw;
     const size_t smem = (size_t)groups_per_block * G * (sizeof(Pkt) + sizeof(int));
     if (smem > 227 * 1024) return FW_EINVAL;
     int slices = 1;
@@ -593,6 +624,7 @@ extern "C" int fw_classify_rule_split_noalloc(const fw_ruleset *rs, const fw_hea
     p.out_idx = out_idx;
     p.out_act = out_act;
     p.partial = partial;
+    p.gw = 1;
     const int threads = cfg.block_threads > 0 ? cfg.block_threads : 256;
     if (threads % 32 != 0 || threads > 512) return set_status(FW_EINVAL);
     const int G = cfg.packets_per_group > 0 ? cfg.packets_per_group : 64;

@@ -42,6 +42,8 @@ CONFIGS = [
     ("rule_split_warp", {"packets_per_group": 32, "block_threads": 64}),
     ("rule_split_block", {}),
     ("rule_split_block", {"block_threads": 64, "packets_per_group": 96}),
+    ("rule_split_block", {"block_threads": 160}),
+    ("rule_split_block", {"block_threads": 512, "packets_per_group": 128}),
     ("rule_split_grid", {}),
     ("rule_split_grid", {"rule_slices": 3}),
     ("rule_split_grid", {"rule_slices": 64, "packets_per_group": 32}),
