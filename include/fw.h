@@ -363,10 +363,13 @@ int fw_server_replay(fw_server *sv, fw_request *reqs, int64_t n, int64_t timeout
  * Decomposition classifier with a learned locator (same result as
  * fw_classify). Each rule field is an interval of its key space (Sec. IV:
  * prefix = address interval, port range, protocol value or all). Per field
- * the key space is cut at every interval end into elementary intervals; row
- * j of the field's bitmap has bit k set when rule k covers interval j. A
- * packet's first match (Sec. I) is the lowest set bit of the AND of its five
- * rows. The interval holding a key is found by a piecewise-linear FP32 model
+ * the key space is cut at every interval end into elementary intervals. The
+ * protocol selects a class as in fw_classify's partition (the up to 7 exact
+ * protocols most used, plus "other"); per class, row j of a field's bitmap
+ * (src, dst, sport, dport) has bit b set when the b-th rule of the class's
+ * sub-list covers interval j. A packet's first match (Sec. I) is the rule
+ * behind the lowest set bit of the AND of its four rows in its class. The
+ * interval holding a key is found by a piecewise-linear FP32 model
  * (the key space cut into `segments` equal parts, one line per part fit on
  * the sorted interval ends: least squares or the chord, whichever has the
  * smaller exact error bound) whose stored per-part maximum error
@@ -379,8 +382,9 @@ int fw_server_replay(fw_server *sv, fw_request *reqs, int64_t n, int64_t timeout
  *            fields with fewer keys use one part per key).
  *  truncate: 1 (default) index only rules up to the first catch-all (no
  *            packet is decided after it); 2 index every rule.
- * Device memory: rows x ceil(rules/128)*16 bytes per field, rows <= 2 x
- * indexed rules + 1. Create is synchronous and copies `rules`.
+ * Device memory: per class and field (src, dst, sport, dport), rows x
+ * ceil(sub-list/128)*16 bytes, rows <= 2 x indexed rules + 1. Create is
+ * synchronous and copies `rules`.
  */
 typedef struct fw_lindex_config {
     int32_t segments;
@@ -391,12 +395,13 @@ typedef struct fw_lindex_config {
 typedef struct fw_lindex_stats {
     int64_t rules;          /* rules supplied */
     int64_t rules_indexed;  /* rules in the bitmaps */
-    int64_t words_per_row;  /* 32-bit words per bitmap row */
+    int64_t words_per_row;  /* 32-bit words per bitmap row (the longest class sub-list's) */
     int64_t segments;       /* model parts per field (upper bound) */
     int64_t intervals[5];   /* elementary intervals: src, dst, sport, dport, proto */
     int32_t max_error[5];   /* stored maximum model error per field, in positions */
     int64_t bitmap_bytes;   /* device bytes of all rows */
     int64_t fallbacks;      /* verified windows that failed (0 when the bounds hold) */
+    int64_t classes;        /* protocol classes (one set of rows each) */
 } fw_lindex_stats;
 
 typedef struct fw_lindex fw_lindex;

@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "fw.h"
 
 namespace fwk {
@@ -269,5 +271,12 @@ int cuda_status(cudaError_t e);
 uint32_t prefix_mask(unsigned prefix);  // top `prefix` bits set; 0 for prefix 0
 bool is_catch_all(const fw_rule &r);    // all five fields wildcards
 int validate_rule(const fw_rule &r);    // FW_OK or FW_EINVAL
+// Protocol partition of rules [0, n): up to kMaxClasses - 1 classes for the
+// exact protocols those rules use most, plus "other" for every other protocol
+// value. class_of[p] is protocol p's class; lists[c] holds, in list order, the
+// rules whose protocol set can contain a packet of class c (protocol "any", or
+// class c's protocol; for "other": any, or an exact protocol without a class).
+void protocol_classes(const fw_rule *rules, int64_t n, std::vector<uint8_t> &class_of,
+                      std::vector<std::vector<int64_t>> &lists);
 int sm_count(int dev);                  // SMs of device `dev` (cached)
 }  // namespace fwk

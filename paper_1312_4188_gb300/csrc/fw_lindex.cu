@@ -5,11 +5,16 @@
 // rule model: a prefix is an address interval, a port range an interval, a
 // protocol one value or all of them). Cutting each field's key space at every
 // interval endpoint gives "elementary intervals" inside which no rule's
-// field test changes. For elementary interval j of field f, the row
-// bits_f[j] has bit k set exactly when rule k's field-f interval covers it.
-// A packet lies in rule k iff bit k is set in the rows of all five of its
-// fields' intervals, so the first match (Sec. I) is the lowest set bit of the
-// AND of five rows, found by scanning words from the start.
+// field test changes. The protocol is handled by the same partition as the
+// scan: per protocol class, the sub-list of rules whose protocol can match a
+// packet of that class, in list order. For class c, field f (src, dst, sport,
+// dport) and elementary interval j, the row bits_{c,f}[j] has bit b set
+// exactly when the b-th rule of c's sub-list covers interval j in field f. A
+// packet of class c lies in that rule iff bit b is set in the rows of its four
+// fields' intervals, so the first match (Sec. I) is the rule behind the lowest
+// set bit of the AND of four rows, found by scanning words from the start.
+// The sub-list holds every rule that can match the packet, in order, so the
+// answer is the whole list's first match.
 //
 // Locating a key's elementary interval: a piecewise-linear FP32 model per
 // field (the key space cut into `segments` equal parts, one line per part fit
@@ -28,7 +33,8 @@
 
 namespace fwk {
 
-constexpr int kFields = 5;
+constexpr int kFields = 5;      // src, dst, sport, dport, proto (intervals and models)
+constexpr int kRowFields = 4;   // fields with bitmap rows; the protocol selects the class
 constexpr int kKeyBits[kFields] = {32, 32, 16, 16, 8};
 
 struct LiFieldDev {
@@ -36,14 +42,22 @@ struct LiFieldDev {
     const float *a;         // per segment slope
     const float *b;         // per segment intercept
     const int32_t *err;     // per segment max |prediction - position|
-    const uint32_t *bits;   // M rows of W words
     int32_t M;
     int32_t shift;          // segment = key >> shift
 };
 
+// One protocol class: its rows (per field, M_f rows of W words) and the
+// original rule index behind each bit (-1 past the sub-list).
+struct LiClassDev {
+    const uint32_t *bits[kRowFields];
+    const int32_t *orig;
+    int64_t W;              // words per row (multiple of 4)
+};
+
 struct LiDev {
     LiFieldDev f[kFields];
-    int64_t W;              // words per row (multiple of 4)
+    const LiClassDev *cls;  // n_classes entries (device memory)
+    const uint8_t *class_of;  // protocol -> class (256 entries)
     const uint8_t *action;
     unsigned long long *fallbacks;
 };
@@ -61,8 +75,12 @@ struct fw_lindex {
     float *d_a[fwk::kFields] = {};
     float *d_b[fwk::kFields] = {};
     int32_t *d_err[fwk::kFields] = {};
-    uint32_t *d_bits[fwk::kFields] = {};
     int32_t shift[fwk::kFields] = {};
+    int n_classes = 0;
+    uint32_t *d_bits[fwk::kMaxClasses][fwk::kRowFields] = {};
+    int32_t *d_orig[fwk::kMaxClasses] = {};
+    fwk::LiClassDev *d_cls = nullptr;
+    uint8_t *d_class_of = nullptr;
     uint8_t *d_action = nullptr;
     unsigned long long *d_fallbacks = nullptr;
 };
@@ -132,18 +150,20 @@ __global__ void __launch_bounds__(256) k_li_classify(LiDev d, const uint32_t *__
                                                      const uint8_t *__restrict__ proto, int64_t n,
                                                      int32_t *__restrict__ out_idx, uint8_t *__restrict__ out_act) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t key[kFields] = {src[i], dst[i], sport[i], dport[i], proto[i]};
-        const uint4 *row[kFields];
+        const uint32_t key[kRowFields] = {src[i], dst[i], sport[i], dport[i]};
+        const LiClassDev &c = d.cls[__ldg(d.class_of + proto[i])];
+        const int64_t W = c.W;
+        const uint4 *row[kRowFields];
 #pragma unroll
-        for (int f = 0; f < kFields; ++f) {
+        for (int f = 0; f < kRowFields; ++f) {
             const int j = li_locate(d.f[f], key[f], d.fallbacks);
-            row[f] = reinterpret_cast<const uint4 *>(d.f[f].bits + (int64_t)j * d.W);
+            row[f] = reinterpret_cast<const uint4 *>(c.bits[f] + (int64_t)j * W);
         }
         int r = -1;
-        for (int64_t q = 0; q < d.W / 4; ++q) {
+        for (int64_t q = 0; q < W / 4; ++q) {
             uint4 x = __ldg(row[0] + q);
 #pragma unroll
-            for (int f = 1; f < kFields; ++f) {
+            for (int f = 1; f < kRowFields; ++f) {
                 const uint4 y = __ldg(row[f] + q);
                 x.x &= y.x;
                 x.y &= y.y;
@@ -152,10 +172,11 @@ __global__ void __launch_bounds__(256) k_li_classify(LiDev d, const uint32_t *__
             }
             if (x.x | x.y | x.z | x.w) {
                 const int base = (int)(q * 128);
-                r = x.x ? base + __ffs(x.x) - 1
-                  : x.y ? base + 32 + __ffs(x.y) - 1
-                  : x.z ? base + 64 + __ffs(x.z) - 1
-                        : base + 96 + __ffs(x.w) - 1;
+                const int bit = x.x ? base + __ffs(x.x) - 1
+                              : x.y ? base + 32 + __ffs(x.y) - 1
+                              : x.z ? base + 64 + __ffs(x.z) - 1
+                                    : base + 96 + __ffs(x.w) - 1;
+                r = __ldg(c.orig + bit);
                 break;
             }
         }
@@ -281,8 +302,13 @@ extern "C" void fw_lindex_destroy(fw_lindex *li) {
         cudaFree(li->d_a[f]);
         cudaFree(li->d_b[f]);
         cudaFree(li->d_err[f]);
-        cudaFree(li->d_bits[f]);
     }
+    for (int c = 0; c < kMaxClasses; ++c) {
+        for (int f = 0; f < kRowFields; ++f) cudaFree(li->d_bits[c][f]);
+        cudaFree(li->d_orig[c]);
+    }
+    cudaFree(li->d_cls);
+    cudaFree(li->d_class_of);
     cudaFree(li->d_action);
     cudaFree(li->d_fallbacks);
     delete li;
@@ -309,22 +335,45 @@ extern "C" int fw_lindex_create(const fw_rule *rules, int64_t n, const fw_lindex
     li->n = n;
     li->first_catch_all = first_ca;
     li->n_idx = (cfg.truncate != 2 && first_ca >= 0) ? first_ca + 1 : n;
-    li->W = std::max<int64_t>(4, (li->n_idx + 127) / 128 * 4);
     li->segments = segments;
     cudaGetDevice(&li->device);
+    std::vector<uint8_t> class_of;
+    std::vector<std::vector<int64_t>> lists;
+    protocol_classes(rules, li->n_idx, class_of, lists);
+    li->n_classes = (int)lists.size();
+    std::vector<LiClassDev> hcls((size_t)li->n_classes);
+    for (int c = 0; c < li->n_classes; ++c) {
+        hcls[c].W = std::max<int64_t>(4, ((int64_t)lists[c].size() + 127) / 128 * 4);
+        li->W = std::max(li->W, hcls[c].W);
+    }
 
     cudaError_t e = cudaSuccess;
-    std::vector<uint8_t> act(li->W * 32, FW_DROP);
+    std::vector<uint8_t> act((size_t)std::max<int64_t>(li->n_idx, 1), FW_DROP);
     for (int64_t k = 0; k < li->n_idx; ++k) act[k] = rules[k].action;
-    e = cudaMalloc(&li->d_action, act.size());
+    e = cudaMalloc(&li->d_class_of, 256);
+    if (e == cudaSuccess) e = cudaMemcpy(li->d_class_of, class_of.data(), 256, cudaMemcpyHostToDevice);
+    for (int c = 0; c < li->n_classes && e == cudaSuccess; ++c) {
+        std::vector<int32_t> orig((size_t)hcls[c].W * 32, -1);
+        for (size_t b = 0; b < lists[c].size(); ++b) orig[b] = (int32_t)lists[c][b];
+        e = cudaMalloc(&li->d_orig[c], orig.size() * sizeof(int32_t));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(li->d_orig[c], orig.data(), orig.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        fw_lindex_destroy(li);
+        cudaGetLastError();
+        return set_status(cuda_status(e));
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&li->d_action, act.size());
     if (e == cudaSuccess) e = cudaMemcpy(li->d_action, act.data(), act.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&li->d_fallbacks, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(li->d_fallbacks, 0, sizeof(unsigned long long));
     uint32_t *d_rlo = nullptr, *d_rhi = nullptr;
-    const size_t nr = (size_t)std::max<int64_t>(li->n_idx, 1);
+    size_t nr = 1;
+    for (const auto &L : lists) nr = std::max(nr, L.size());
     if (e == cudaSuccess) e = cudaMalloc(&d_rlo, nr * 4);
     if (e == cudaSuccess) e = cudaMalloc(&d_rhi, nr * 4);
-    std::vector<uint32_t> rlo(nr), rhi(nr);
+    std::vector<uint32_t> rlo((size_t)std::max<int64_t>(li->n_idx, 1)), rhi(rlo.size()), clo(nr), chi(nr);
     for (int f = 0; f < kFields && e == cudaSuccess; ++f) {
         const int bits = kKeyBits[f];
         const int nseg = std::min(segments, 1 << std::min(bits, 16));
@@ -351,26 +400,38 @@ extern "C" int fw_lindex_create(const fw_rule *rules, int64_t n, const fw_lindex
         std::vector<float> A, Bc;
         std::vector<int32_t> E;
         fit_field(B, bits, nseg, li->shift[f], A, Bc, E, li->max_err[f]);
-        const size_t row_bytes = (size_t)li->W * 4;
         e = cudaMalloc(&li->d_bound[f], M * 4);
         if (e == cudaSuccess) e = cudaMalloc(&li->d_a[f], nseg * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc(&li->d_b[f], nseg * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc(&li->d_err[f], nseg * sizeof(int32_t));
-        if (e == cudaSuccess) e = cudaMalloc(&li->d_bits[f], (size_t)M * row_bytes);
         if (e == cudaSuccess) e = cudaMemcpy(li->d_bound[f], B.data(), M * 4, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(li->d_a[f], A.data(), nseg * sizeof(float), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(li->d_b[f], Bc.data(), nseg * sizeof(float), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(li->d_err[f], E.data(), nseg * sizeof(int32_t), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess && li->n_idx > 0) e = cudaMemcpy(d_rlo, rlo.data(), li->n_idx * 4, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess && li->n_idx > 0) e = cudaMemcpy(d_rhi, rhi.data(), li->n_idx * 4, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) {
-            const int blocks = sm_count(li->device) * 8;
-            k_li_build<<<blocks, 256>>>(li->d_bound[f], M, d_rlo, d_rhi, li->n_idx, li->W, li->d_bits[f]);
-            e = cudaGetLastError();
+        // rows of every class for this field (the protocol field has none: it picks the class)
+        for (int c = 0; c < li->n_classes && f < kRowFields && e == cudaSuccess; ++c) {
+            const int64_t nc = (int64_t)lists[c].size(), W = hcls[c].W;
+            for (int64_t b = 0; b < nc; ++b) {
+                clo[b] = rlo[lists[c][b]];
+                chi[b] = rhi[lists[c][b]];
+            }
+            e = cudaMalloc(&li->d_bits[c][f], (size_t)M * W * 4);
+            if (e == cudaSuccess && nc > 0) e = cudaMemcpy(d_rlo, clo.data(), nc * 4, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess && nc > 0) e = cudaMemcpy(d_rhi, chi.data(), nc * 4, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) {
+                const int blocks = sm_count(li->device) * 8;
+                k_li_build<<<blocks, 256>>>(li->d_bound[f], M, d_rlo, d_rhi, nc, W, li->d_bits[c][f]);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            hcls[c].bits[f] = li->d_bits[c][f];
+            hcls[c].orig = li->d_orig[c];
+            li->bitmap_bytes += (int64_t)M * W * 4;
         }
-        if (e == cudaSuccess) e = cudaDeviceSynchronize();
-        li->bitmap_bytes += (int64_t)M * (int64_t)row_bytes;
     }
+    if (e == cudaSuccess) e = cudaMalloc(&li->d_cls, hcls.size() * sizeof(LiClassDev));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(li->d_cls, hcls.data(), hcls.size() * sizeof(LiClassDev), cudaMemcpyHostToDevice);
     cudaFree(d_rlo);
     cudaFree(d_rhi);
     if (e != cudaSuccess) {
@@ -391,10 +452,10 @@ extern "C" int fw_lindex_classify(const fw_lindex *li, const fw_headers *hdrs, i
         return set_status(FW_EINVAL);
     LiDev d;
     for (int f = 0; f < kFields; ++f) {
-        d.f[f] = LiFieldDev{li->d_bound[f], li->d_a[f], li->d_b[f], li->d_err[f], li->d_bits[f], (int32_t)li->M[f],
-                            li->shift[f]};
+        d.f[f] = LiFieldDev{li->d_bound[f], li->d_a[f], li->d_b[f], li->d_err[f], (int32_t)li->M[f], li->shift[f]};
     }
-    d.W = li->W;
+    d.cls = li->d_cls;
+    d.class_of = li->d_class_of;
     d.action = li->d_action;
     d.fallbacks = li->d_fallbacks;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sm_count(li->device) * 16));
@@ -415,6 +476,7 @@ extern "C" int fw_lindex_get_stats(fw_lindex *li, fw_lindex_stats *st) {
         st->max_error[f] = li->max_err[f];
     }
     st->bitmap_bytes = li->bitmap_bytes;
+    st->classes = li->n_classes;
     cudaError_t e = cudaDeviceSynchronize();
     unsigned long long fb = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&fb, li->d_fallbacks, sizeof(fb), cudaMemcpyDeviceToHost);

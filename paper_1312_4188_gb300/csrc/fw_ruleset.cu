@@ -96,6 +96,30 @@ static void never_match(RecClamp *c, RecCmp *m) {
     m->c = make_uint4(kNeverProto, 0xFFFFFFFFu, 0, 0);
 }
 
+void protocol_classes(const fw_rule *rules, int64_t n, std::vector<uint8_t> &class_of,
+                      std::vector<std::vector<int64_t>> &lists) {
+    std::vector<int64_t> cnt(256, 0);
+    for (int64_t k = 0; k < n; ++k)
+        if (!rules[k].proto_any) cnt[rules[k].proto]++;
+    std::vector<int> order;
+    for (int p = 0; p < 256; ++p)
+        if (cnt[p] > 0) order.push_back(p);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cnt[a] > cnt[b]; });
+    if ((int)order.size() > kMaxClasses - 1) order.resize(kMaxClasses - 1);
+    const int n_classes = (int)order.size() + 1;
+    class_of.assign(256, (uint8_t)(n_classes - 1));
+    for (size_t c = 0; c < order.size(); ++c) class_of[order[c]] = (uint8_t)c;
+    lists.assign(n_classes, std::vector<int64_t>());
+    for (int64_t k = 0; k < n; ++k) {
+        const fw_rule &r = rules[k];
+        for (int c = 0; c < n_classes; ++c) {
+            const bool other = c == n_classes - 1;
+            if (r.proto_any || (!other && r.proto == order[c]) || (other && class_of[r.proto] == c))
+                lists[c].push_back(k);
+        }
+    }
+}
+
 }  // namespace fwk
 
 using namespace fwk;
@@ -149,26 +173,10 @@ extern "C" int fw_ruleset_create_ex(const fw_rule *rules, int64_t n, fw_ruleset 
     // protocol "any" or with class c's protocol ("other": any, or an exact
     // protocol without a class of its own).
     {
-        std::vector<int64_t> cnt(256, 0);
-        for (int64_t k = 0; k < rs->n_eff; ++k)
-            if (!rules[k].proto_any) cnt[rules[k].proto]++;
-        std::vector<int> order;
-        for (int p = 0; p < 256; ++p)
-            if (cnt[p] > 0) order.push_back(p);
-        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cnt[a] > cnt[b]; });
-        if ((int)order.size() > kMaxClasses - 1) order.resize(kMaxClasses - 1);
-        rs->n_classes = (int)order.size() + 1;
-        std::vector<uint8_t> class_of(256, (uint8_t)(rs->n_classes - 1));
-        for (size_t c = 0; c < order.size(); ++c) class_of[order[c]] = (uint8_t)c;
-        std::vector<std::vector<int64_t>> lists(rs->n_classes);
-        for (int64_t k = 0; k < rs->n_eff; ++k) {
-            const fw_rule &r = rules[k];
-            for (int c = 0; c < rs->n_classes; ++c) {
-                const bool other = c == rs->n_classes - 1;
-                if (r.proto_any || (!other && r.proto == order[c]) || (other && class_of[r.proto] == c))
-                    lists[c].push_back(k);
-            }
-        }
+        std::vector<uint8_t> class_of;
+        std::vector<std::vector<int64_t>> lists;
+        protocol_classes(rules, rs->n_eff, class_of, lists);
+        rs->n_classes = (int)lists.size();
         int64_t off = 0;
         for (int c = 0; c < kMaxClasses; ++c) {
             const int64_t len = c < rs->n_classes ? (int64_t)(lists[c].size() + 3) / 4 * 4 : 0;

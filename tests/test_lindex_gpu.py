@@ -75,10 +75,20 @@ def test_stats_shape(torch_cuda):
     li = fw.fw_lindex_create(rules, truncate=2)
     st = li.stats()
     assert st["rules_indexed"] == len(rules)
-    assert st["words_per_row"] % 4 == 0 and st["words_per_row"] * 32 >= len(rules)
     assert all(1 <= m <= 2 * len(rules) + 1 for m in st["intervals"])
     assert st["intervals"][4] <= 257
-    assert st["bitmap_bytes"] == sum(st["intervals"]) * st["words_per_row"] * 4
+    # classes: the exact protocols used (here 3, each with a class of its own) plus "other";
+    # a class's sub-list holds the protocol-any rules and the rules of its protocol
+    exact = [int(p) for p, a in zip(rules["proto"], rules["proto_any"]) if not a]
+    assert len(set(exact)) <= 7 and st["classes"] == len(set(exact)) + 1
+    n_any = int(rules["proto_any"].sum())
+    longest = n_any + max([exact.count(p) for p in set(exact)] + [0])
+    assert st["words_per_row"] == max(4, -(-longest // 128) * 4)
+    # one set of rows per class over the four address and port fields, each row at
+    # least 4 and at most words_per_row words
+    rows = sum(st["intervals"][:4])
+    assert rows * 16 * st["classes"] <= st["bitmap_bytes"] <= rows * st["words_per_row"] * 4 * st["classes"]
+    assert st["bitmap_bytes"] % (rows * 16) == 0
     li.destroy()
 
 
