@@ -39,9 +39,7 @@ constexpr int kKeyBits[kFields] = {32, 32, 16, 16, 8};
 
 struct LiFieldDev {
     const uint32_t *bound;  // M sorted interval starts, bound[0] = 0
-    const float *a;         // per segment slope
-    const float *b;         // per segment intercept
-    const int32_t *err;     // per segment max |prediction - position|
+    const float4 *model;    // per segment {slope, intercept, max |prediction - position| (int bits), 0}
     int32_t M;
     int32_t shift;          // segment = key >> shift
 };
@@ -57,6 +55,7 @@ struct LiClassDev {
 struct LiDev {
     LiFieldDev f[kFields];
     const LiClassDev *cls;  // n_classes entries (device memory)
+    int32_t n_classes;
     const uint8_t *class_of;  // protocol -> class (256 entries)
     const uint8_t *action;
     unsigned long long *fallbacks;
@@ -72,9 +71,7 @@ struct fw_lindex {
     int32_t max_err[fwk::kFields] = {};
     int64_t bitmap_bytes = 0;
     uint32_t *d_bound[fwk::kFields] = {};
-    float *d_a[fwk::kFields] = {};
-    float *d_b[fwk::kFields] = {};
-    int32_t *d_err[fwk::kFields] = {};
+    float4 *d_model[fwk::kFields] = {};
     int32_t shift[fwk::kFields] = {};
     int n_classes = 0;
     uint32_t *d_bits[fwk::kMaxClasses][fwk::kRowFields] = {};
@@ -122,41 +119,65 @@ __global__ void k_li_build(const uint32_t *__restrict__ bound, int64_t M, const 
     }
 }
 
-__device__ __forceinline__ int li_locate(const LiFieldDev &f, uint32_t v, unsigned long long *fallbacks) {
+template <bool SMEM>
+__device__ __forceinline__ int li_locate(const LiFieldDev &f, const uint32_t *bound, uint32_t v,
+                                         unsigned long long *fallbacks) {
     const uint32_t s = v >> f.shift;
     const uint32_t base = s << f.shift;
-    const float pf = __fmaf_rn(__ldg(f.a + s), __uint2float_rn(v - base), __ldg(f.b + s));
+    const float4 md = __ldg(f.model + s);
+    const float pf = __fmaf_rn(md.x, __uint2float_rn(v - base), md.y);
     int p = (int)floorf(fminf(fmaxf(pf, 0.0f), (float)(f.M - 1)));
-    const int e = __ldg(f.err + s);
+    const int e = __float_as_int(md.z);
     int lo = max(0, p - e), hi = min(f.M - 1, p + e);
+    auto at = [&](int i) { return SMEM ? bound[i] : __ldg(bound + i); };
     // exact check of the window before it is trusted
-    if (__ldg(f.bound + lo) > v || (hi < f.M - 1 && __ldg(f.bound + hi + 1) <= v)) {
+    if (at(lo) > v || (hi < f.M - 1 && at(hi + 1) <= v)) {
         atomicAdd(fallbacks, 1ull);
         lo = 0;
         hi = f.M - 1;
     }
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(f.bound + mid) <= v) lo = mid;
+        if (at(mid) <= v) lo = mid;
         else hi = mid - 1;
     }
     return lo;
 }
 
-__global__ void __launch_bounds__(256) k_li_classify(LiDev d, const uint32_t *__restrict__ src,
+// One packet per thread. The block first copies the class descriptors and,
+// when they fit (SMEM), the four fields' interval starts into shared memory,
+// which keeps the model windows and searches off the L1 path the rows use.
+template <bool SMEM>
+__global__ void __launch_bounds__(512) k_li_classify(LiDev d, const uint32_t *__restrict__ src,
                                                      const uint32_t *__restrict__ dst,
                                                      const uint16_t *__restrict__ sport,
                                                      const uint16_t *__restrict__ dport,
                                                      const uint8_t *__restrict__ proto, int64_t n,
                                                      int32_t *__restrict__ out_idx, uint8_t *__restrict__ out_act) {
+    __shared__ LiClassDev scls[kMaxClasses];
+    extern __shared__ __align__(16) uint32_t sbound[];
+    if (threadIdx.x < d.n_classes) scls[threadIdx.x] = d.cls[threadIdx.x];
+    const uint32_t *bound[kRowFields];
+    int off = 0;
+#pragma unroll
+    for (int f = 0; f < kRowFields; ++f) {
+        if (SMEM) {
+            for (int i = threadIdx.x; i < d.f[f].M; i += blockDim.x) sbound[off + i] = __ldg(d.f[f].bound + i);
+            bound[f] = sbound + off;
+            off += d.f[f].M;
+        } else {
+            bound[f] = d.f[f].bound;
+        }
+    }
+    __syncthreads();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t key[kRowFields] = {src[i], dst[i], sport[i], dport[i]};
-        const LiClassDev &c = d.cls[__ldg(d.class_of + proto[i])];
+        const LiClassDev &c = scls[__ldg(d.class_of + proto[i])];
         const int64_t W = c.W;
         const uint4 *row[kRowFields];
 #pragma unroll
         for (int f = 0; f < kRowFields; ++f) {
-            const int j = li_locate(d.f[f], key[f], d.fallbacks);
+            const int j = li_locate<SMEM>(d.f[f], bound[f], key[f], d.fallbacks);
             row[f] = reinterpret_cast<const uint4 *>(c.bits[f] + (int64_t)j * W);
         }
         int r = -1;
@@ -299,9 +320,7 @@ extern "C" void fw_lindex_destroy(fw_lindex *li) {
     if (li == nullptr) return;
     for (int f = 0; f < kFields; ++f) {
         cudaFree(li->d_bound[f]);
-        cudaFree(li->d_a[f]);
-        cudaFree(li->d_b[f]);
-        cudaFree(li->d_err[f]);
+        cudaFree(li->d_model[f]);
     }
     for (int c = 0; c < kMaxClasses; ++c) {
         for (int f = 0; f < kRowFields; ++f) cudaFree(li->d_bits[c][f]);
@@ -401,13 +420,15 @@ extern "C" int fw_lindex_create(const fw_rule *rules, int64_t n, const fw_lindex
         std::vector<int32_t> E;
         fit_field(B, bits, nseg, li->shift[f], A, Bc, E, li->max_err[f]);
         e = cudaMalloc(&li->d_bound[f], M * 4);
-        if (e == cudaSuccess) e = cudaMalloc(&li->d_a[f], nseg * sizeof(float));
-        if (e == cudaSuccess) e = cudaMalloc(&li->d_b[f], nseg * sizeof(float));
-        if (e == cudaSuccess) e = cudaMalloc(&li->d_err[f], nseg * sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&li->d_model[f], nseg * sizeof(float4));
         if (e == cudaSuccess) e = cudaMemcpy(li->d_bound[f], B.data(), M * 4, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(li->d_a[f], A.data(), nseg * sizeof(float), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(li->d_b[f], Bc.data(), nseg * sizeof(float), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(li->d_err[f], E.data(), nseg * sizeof(int32_t), cudaMemcpyHostToDevice);
+        std::vector<float4> model((size_t)nseg);
+        for (int s = 0; s < nseg; ++s) {
+            float eb;
+            std::memcpy(&eb, &E[s], sizeof(eb));
+            model[s] = make_float4(A[s], Bc[s], eb, 0.0f);
+        }
+        if (e == cudaSuccess) e = cudaMemcpy(li->d_model[f], model.data(), nseg * sizeof(float4), cudaMemcpyHostToDevice);
         // rows of every class for this field (the protocol field has none: it picks the class)
         for (int c = 0; c < li->n_classes && f < kRowFields && e == cudaSuccess; ++c) {
             const int64_t nc = (int64_t)lists[c].size(), W = hcls[c].W;
@@ -452,15 +473,25 @@ extern "C" int fw_lindex_classify(const fw_lindex *li, const fw_headers *hdrs, i
         return set_status(FW_EINVAL);
     LiDev d;
     for (int f = 0; f < kFields; ++f) {
-        d.f[f] = LiFieldDev{li->d_bound[f], li->d_a[f], li->d_b[f], li->d_err[f], (int32_t)li->M[f], li->shift[f]};
+        d.f[f] = LiFieldDev{li->d_bound[f], li->d_model[f], (int32_t)li->M[f], li->shift[f]};
     }
     d.cls = li->d_cls;
     d.class_of = li->d_class_of;
     d.action = li->d_action;
     d.fallbacks = li->d_fallbacks;
-    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sm_count(li->device) * 16));
-    k_li_classify<<<(unsigned)blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
-        d, hdrs->src, hdrs->dst, hdrs->sport, hdrs->dport, hdrs->proto, n, out_idx, out_act);
+    d.n_classes = li->n_classes;
+    // the four fields' interval starts in shared memory when they fit in 48 KB
+    int64_t nb = 0;
+    for (int f = 0; f < kRowFields; ++f) nb += li->M[f];
+    const size_t sbytes = (size_t)nb * sizeof(uint32_t);
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n + 511) / 512, (int64_t)sm_count(li->device) * 4));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (sbytes <= 48 * 1024)
+        k_li_classify<true><<<(unsigned)blocks, 512, sbytes, st>>>(d, hdrs->src, hdrs->dst, hdrs->sport, hdrs->dport,
+                                                                    hdrs->proto, n, out_idx, out_act);
+    else
+        k_li_classify<false><<<(unsigned)blocks, 512, 0, st>>>(d, hdrs->src, hdrs->dst, hdrs->sport, hdrs->dport,
+                                                                hdrs->proto, n, out_idx, out_act);
     return set_status(cuda_status(cudaGetLastError()));
 }
 
