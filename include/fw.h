@@ -368,7 +368,9 @@ int fw_server_replay(fw_server *sv, fw_request *reqs, int64_t n, int64_t timeout
  * protocols most used, plus "other"); per class, row j of a field's bitmap
  * (src, dst, sport, dport) has bit b set when the b-th rule of the class's
  * sub-list covers interval j. A packet's first match (Sec. I) is the rule
- * behind the lowest set bit of the AND of its four rows in its class. The
+ * behind the lowest set bit of the AND of its four rows in its class (five
+ * when the class is "other" and holds exact-protocol rules: then a protocol
+ * row is ANDed as well, since the class no longer implies the protocol). The
  * interval holding a key is found by a piecewise-linear FP32 model
  * (the key space cut into `segments` equal parts, one line per part fit on
  * the sorted interval ends: least squares or the chord, whichever has the

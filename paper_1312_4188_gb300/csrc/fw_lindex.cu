@@ -14,7 +14,9 @@
 // fields' intervals, so the first match (Sec. I) is the rule behind the lowest
 // set bit of the AND of four rows, found by scanning words from the start.
 // The sub-list holds every rule that can match the packet, in order, so the
-// answer is the whole list's first match.
+// answer is the whole list's first match. When more exact protocols are in use
+// than there are classes, the "other" class holds rules of several protocols
+// and gets protocol rows too, ANDed as a fifth row.
 //
 // Locating a key's elementary interval: a piecewise-linear FP32 model per
 // field (the key space cut into `segments` equal parts, one line per part fit
@@ -45,9 +47,12 @@ struct LiFieldDev {
 };
 
 // One protocol class: its rows (per field, M_f rows of W words) and the
-// original rule index behind each bit (-1 past the sub-list).
+// original rule index behind each bit (-1 past the sub-list). A class that
+// holds rules of several exact protocols ("other", when more protocols are in
+// use than there are classes) also has protocol rows (bits[4]); for every
+// other class the protocol test is implied by the class.
 struct LiClassDev {
-    const uint32_t *bits[kRowFields];
+    const uint32_t *bits[kFields];
     const int32_t *orig;
     int64_t W;              // words per row (multiple of 4)
 };
@@ -74,7 +79,7 @@ struct fw_lindex {
     float4 *d_model[fwk::kFields] = {};
     int32_t shift[fwk::kFields] = {};
     int n_classes = 0;
-    uint32_t *d_bits[fwk::kMaxClasses][fwk::kRowFields] = {};
+    uint32_t *d_bits[fwk::kMaxClasses][fwk::kFields] = {};
     int32_t *d_orig[fwk::kMaxClasses] = {};
     fwk::LiClassDev *d_cls = nullptr;
     uint8_t *d_class_of = nullptr;
@@ -157,10 +162,10 @@ __global__ void __launch_bounds__(512) k_li_classify(LiDev d, const uint32_t *__
     __shared__ LiClassDev scls[kMaxClasses];
     extern __shared__ __align__(16) uint32_t sbound[];
     if (threadIdx.x < d.n_classes) scls[threadIdx.x] = d.cls[threadIdx.x];
-    const uint32_t *bound[kRowFields];
+    const uint32_t *bound[kFields];
     int off = 0;
 #pragma unroll
-    for (int f = 0; f < kRowFields; ++f) {
+    for (int f = 0; f < kFields; ++f) {
         if (SMEM) {
             for (int i = threadIdx.x; i < d.f[f].M; i += blockDim.x) sbound[off + i] = __ldg(d.f[f].bound + i);
             bound[f] = sbound + off;
@@ -171,20 +176,28 @@ __global__ void __launch_bounds__(512) k_li_classify(LiDev d, const uint32_t *__
     }
     __syncthreads();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t pr = proto[i];
         const uint32_t key[kRowFields] = {src[i], dst[i], sport[i], dport[i]};
-        const LiClassDev &c = scls[__ldg(d.class_of + proto[i])];
+        const LiClassDev &c = scls[__ldg(d.class_of + pr)];
         const int64_t W = c.W;
-        const uint4 *row[kRowFields];
+        const uint4 *row[kFields];
 #pragma unroll
         for (int f = 0; f < kRowFields; ++f) {
             const int j = li_locate<SMEM>(d.f[f], bound[f], key[f], d.fallbacks);
             row[f] = reinterpret_cast<const uint4 *>(c.bits[f] + (int64_t)j * W);
         }
+        const bool prow = c.bits[kFields - 1] != nullptr;  // a class of mixed exact protocols
+        row[kFields - 1] = nullptr;
+        if (prow) {
+            const int j = li_locate<SMEM>(d.f[kFields - 1], bound[kFields - 1], pr, d.fallbacks);
+            row[kFields - 1] = reinterpret_cast<const uint4 *>(c.bits[kFields - 1] + (int64_t)j * W);
+        }
         int r = -1;
         for (int64_t q = 0; q < W / 4; ++q) {
             uint4 x = __ldg(row[0] + q);
 #pragma unroll
-            for (int f = 1; f < kRowFields; ++f) {
+            for (int f = 1; f < kFields; ++f) {
+                if (f == kFields - 1 && !prow) break;
                 const uint4 y = __ldg(row[f] + q);
                 x.x &= y.x;
                 x.y &= y.y;
@@ -323,7 +336,7 @@ extern "C" void fw_lindex_destroy(fw_lindex *li) {
         cudaFree(li->d_model[f]);
     }
     for (int c = 0; c < kMaxClasses; ++c) {
-        for (int f = 0; f < kRowFields; ++f) cudaFree(li->d_bits[c][f]);
+        for (int f = 0; f < kFields; ++f) cudaFree(li->d_bits[c][f]);
         cudaFree(li->d_orig[c]);
     }
     cudaFree(li->d_cls);
@@ -360,6 +373,17 @@ extern "C" int fw_lindex_create(const fw_rule *rules, int64_t n, const fw_lindex
     std::vector<std::vector<int64_t>> lists;
     protocol_classes(rules, li->n_idx, class_of, lists);
     li->n_classes = (int)lists.size();
+    std::vector<char> mixed((size_t)li->n_classes, 0);  // sub-list holds exact protocols of different values
+    for (int c = 0; c < li->n_classes; ++c) {
+        int first = -1;
+        for (int64_t k : lists[c])
+            if (!rules[k].proto_any) {
+                if (first < 0) first = rules[k].proto;
+                else if (rules[k].proto != first) mixed[c] = 1;
+            }
+        // the "other" class matches every protocol without a class: one exact rule is enough
+        if (c == li->n_classes - 1 && first >= 0) mixed[c] = 1;
+    }
     std::vector<LiClassDev> hcls((size_t)li->n_classes);
     for (int c = 0; c < li->n_classes; ++c) {
         hcls[c].W = std::max<int64_t>(4, ((int64_t)lists[c].size() + 127) / 128 * 4);
@@ -429,8 +453,10 @@ extern "C" int fw_lindex_create(const fw_rule *rules, int64_t n, const fw_lindex
             model[s] = make_float4(A[s], Bc[s], eb, 0.0f);
         }
         if (e == cudaSuccess) e = cudaMemcpy(li->d_model[f], model.data(), nseg * sizeof(float4), cudaMemcpyHostToDevice);
-        // rows of every class for this field (the protocol field has none: it picks the class)
-        for (int c = 0; c < li->n_classes && f < kRowFields && e == cudaSuccess; ++c) {
+        // rows of every class for this field; protocol rows only for a class whose
+        // sub-list mixes exact protocols (elsewhere the class implies the protocol)
+        for (int c = 0; c < li->n_classes && e == cudaSuccess; ++c) {
+            if (f == kFields - 1 && !mixed[c]) continue;
             const int64_t nc = (int64_t)lists[c].size(), W = hcls[c].W;
             for (int64_t b = 0; b < nc; ++b) {
                 clo[b] = rlo[lists[c][b]];
@@ -480,9 +506,9 @@ extern "C" int fw_lindex_classify(const fw_lindex *li, const fw_headers *hdrs, i
     d.action = li->d_action;
     d.fallbacks = li->d_fallbacks;
     d.n_classes = li->n_classes;
-    // the four fields' interval starts in shared memory when they fit in 48 KB
+    // the fields' interval starts in shared memory when they fit in 48 KB
     int64_t nb = 0;
-    for (int f = 0; f < kRowFields; ++f) nb += li->M[f];
+    for (int f = 0; f < kFields; ++f) nb += li->M[f];
     const size_t sbytes = (size_t)nb * sizeof(uint32_t);
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n + 511) / 512, (int64_t)sm_count(li->device) * 4));
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

@@ -111,3 +111,22 @@ def test_full_size_against_scan_and_oracle(torch_cuda):
     assert np.array_equal(l_idx[pt].cpu().numpy(), want[0]) and np.array_equal(l_act[pt].cpu().numpy(), want[1])
     li.destroy()
     rs.destroy()
+
+
+@pytest.mark.parametrize("truncate", [1, 2])
+def test_many_protocols_other_class(torch_cuda, truncate):
+    """More exact protocols than classes: the "other" class then also holds exact-protocol rules
+    (its rows must keep them, in list order, with the protocol-any rules)."""
+    rng = np.random.default_rng(11)
+    rules = no_catch_all(W.gen_rules(3000, 12))
+    rules["proto_any"] = (rng.random(len(rules)) < 0.1).astype(np.uint8)
+    rules["proto"] = rng.integers(0, 256, size=len(rules))
+    hdr = W.gen_packets(rules, 40_000, 13)
+    # half the packets get a random protocol, many of them without a class of their own
+    flip = rng.random(len(hdr["proto"])) < 0.5
+    hdr["proto"] = np.where(flip, rng.integers(0, 256, size=len(flip)), hdr["proto"]).astype(np.uint8)
+    want = oracle.classify(rules, hdr, threads=THREADS)
+    gi, ga, st = run_li(torch_cuda, rules, hdr, truncate=truncate)
+    assert st["classes"] == 8 and st["fallbacks"] == 0
+    assert np.array_equal(gi, want[0]) and np.array_equal(ga, want[1])
+    assert (want[0] >= 0).mean() > 0.2  # the case is not all default deny (here a third match)
