@@ -163,8 +163,9 @@ def serving(args):
             "first_catch_all": [r.first_catch_all for r in sets]}]
     dout_i = torch.empty(total, dtype=torch.int32, device="cuda")
     dout_a = torch.empty(total, dtype=torch.uint8, device="cuda")
-    for mode, mname, slots in ((fw.FW_HOST_ZEROCOPY, "device_buffers", 4), (fw.FW_HOST_ZEROCOPY, "zerocopy", 4),
-                               (fw.FW_HOST_ZEROCOPY, "zerocopy", 8), (fw.FW_HOST_COPY, "copy", 4)):
+    for mode, mname, slots in ((fw.FW_HOST_ZEROCOPY, "device_buffers", 4), (fw.FW_HOST_ZEROCOPY, "device_buffers", 8),
+                               (fw.FW_HOST_ZEROCOPY, "zerocopy", 4), (fw.FW_HOST_ZEROCOPY, "zerocopy", 8),
+                               (fw.FW_HOST_COPY, "copy", 4)):
         # "device_buffers": request headers and verdicts already in device memory (e.g. placed there
         # by the producer); the server reads and writes them in place
         on_dev = mname == "device_buffers"
