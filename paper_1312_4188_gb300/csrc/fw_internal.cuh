@@ -165,14 +165,6 @@ __device__ __forceinline__ bool mismatch_range_c(const PktA &p, const uint4 &a, 
            ((p.x * b.z + b.w) > wtop);
 }
 
-// Plain C++ statement of the same test (used where the chained form is not needed).
-__device__ __forceinline__ bool mismatch_arith_c(const PktA &p, const uint4 &a, const uint4 &b, uint32_t wtop,
-                                                 uint32_t one) {
-    const uint32_t ts = p.sport * one + b.x;
-    const uint32_t td = p.x * b.z + b.w;
-    return (((p.src ^ a.x) & a.y) != 0u) | (((p.dst ^ a.z) & a.w) != 0u) | (ts > b.y) | (td > wtop);
-}
-
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
