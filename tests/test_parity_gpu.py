@@ -150,7 +150,10 @@ def test_special_rule_sets(torch_cuda, mode, kw):
             W.RULE_DTYPE),
         "tiny_domain": P.random_tiny_rules(rng, 4),
         "exact_only": W.gen_rules(300, 4),
+        "any_protocol_only": W.gen_rules(500, 5),  # one protocol class
     }
+    cases["any_protocol_only"]["proto_any"] = 1
+    cases["any_protocol_only"]["proto"] = 0
     ex = cases["exact_only"]
     ex["src_prefix"] = ex["dst_prefix"] = 32
     ex["sport_hi"] = ex["sport_lo"]
