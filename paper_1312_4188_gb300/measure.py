@@ -3,6 +3,7 @@
   python -m paper_1312_4188_gb300.measure lindex   # learned index vs scan, 100K rules x 64M packets
   python -m paper_1312_4188_gb300.measure batched  # 256 rule sets in one persistent launch
   python -m paper_1312_4188_gb300.measure serving  # continuous batching, Poisson arrivals
+  python -m paper_1312_4188_gb300.measure variants # the 10K x 16M scan: permuted Zipf ranks, no catch-all
 
 Each prints JSON lines. Every form is compared bit for bit with the plain
 scan on the same inputs before its time is reported. Times are CUDA-event
@@ -210,7 +211,45 @@ def serving(args):
     return out
 
 
-COMMANDS = {"lindex": lindex, "batched": batched, "serving": serving}
+def variants(args):
+    """The 10K-rule x 16M-packet scan under two labelled variants of its traffic: the Zipf rank
+    order randomly permuted over the rule list (popular rules no longer at the top), and every
+    all-wildcard rule removed (deep scans, many default-deny packets). Each is timed with the
+    default configuration and checked bit for bit against the whole-list lockstep scan."""
+    import numpy as np
+    import torch
+
+    from .metrics import partition_depth
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    out = []
+    for name in ("scan_10k_x_16m_zipf_permuted", "scan_10k_x_16m_no_catch_all"):
+        rules, hdr = W.make_workload(name)
+        n = len(hdr["src"])
+        dh = fw.headers_to_device(hdr)
+        rs = fw.fw_ruleset_create(rules)
+        idx = torch.empty(n, dtype=torch.int32, device="cuda")
+        act = torch.empty(n, dtype=torch.uint8, device="cuda")
+        t = _events_ms(lambda: fw.fw_classify(rs, dh, n, idx, act), reps=10, warmup=2)
+        ref_i = torch.empty_like(idx)
+        ref_a = torch.empty_like(act)
+        fw.fw_classify(rs, dh, n, ref_i, ref_a, config=fw.make_config("packet_split", compact=2, partition=2))
+        torch.cuda.synchronize()
+        same = bool(torch.equal(idx, ref_i) and torch.equal(act, ref_a))
+        idx_np = idx.cpu().numpy()
+        depth = np.where(idx_np >= 0, idx_np.astype(np.int64) + 1, rs.size()).sum()
+        scan = partition_depth(rules, idx_np, hdr["proto"])
+        checks_s = scan / (t * 1e-3)
+        out.append({"form": "scan", "workload": name, "rules": int(len(rules)), "packets": n,
+                    "ms": t, "mpackets_s": n / t / 1e3, "mean_depth": float(depth / n),
+                    "mean_scan_depth": float(scan / n), "unmatched_frac": float((idx_np < 0).mean()),
+                    "first_catch_all": rs.first_catch_all, "scan_checks_per_s": checks_s,
+                    "int32_frac": checks_s * 8 / (sms * 128 * 2.07e9), "hbm_gbs": BYTES_PER_PACKET * n / t / 1e6,
+                    "same_as_lockstep_whole_list": same})
+        rs.destroy()
+    return out
+
+
+COMMANDS = {"lindex": lindex, "batched": batched, "serving": serving, "variants": variants}
 
 
 def main(argv=None):

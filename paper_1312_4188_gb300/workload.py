@@ -152,7 +152,7 @@ def _address_in(rng, addr, plen):
     return (base + (low % span)).astype(np.uint32)
 
 
-def _gen_block(rules, n_rules, m, seed, block, in_rule_frac, cdf):
+def _gen_block(rules, n_rules, m, seed, block, in_rule_frac, cdf, rank_perm=None):
     rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence((int(seed), int(block), 0x504B54))))
     h = {
         "src": rng.integers(0, 1 << 32, size=m, dtype=np.uint64).astype(np.uint32),
@@ -167,6 +167,8 @@ def _gen_block(rules, n_rules, m, seed, block, in_rule_frac, cdf):
     if inside.size == 0:
         return h
     k = _draw_rule_index(rng, inside.size, n_rules, cdf)
+    if rank_perm is not None:  # the drawn rank names rule rank_perm[rank]
+        k = rank_perm[k]
     rk = rules[k]
     h["src"][inside] = _address_in(rng, rk["src_addr"], rk["src_prefix"])
     h["dst"][inside] = _address_in(rng, rk["dst_addr"], rk["dst_prefix"])
@@ -179,11 +181,13 @@ def _gen_block(rules, n_rules, m, seed, block, in_rule_frac, cdf):
 
 
 def gen_packets(rules: np.ndarray, n: int, seed: int, in_rule_frac: float = 0.6,
-                zipf_s: float | None = None, start: int = 0) -> dict:
+                zipf_s: float | None = None, start: int = 0, rank_perm: np.ndarray | None = None) -> dict:
     """Draw packets ``start .. start+n-1`` of the batch defined by (rules, seed, ...).
 
     Returns SoA numpy arrays keyed by ``HEADER_FIELDS``. ``zipf_s=None`` picks the
-    rule of an in-rule packet uniformly; otherwise Zipf(zipf_s) over the index.
+    rule of an in-rule packet uniformly; otherwise Zipf(zipf_s) over the index, or,
+    with ``rank_perm`` (a permutation of the rule indices), over the ranks, rank r
+    naming rule ``rank_perm[r]`` (popular rules no longer sit at the top of the list).
     """
     n_rules = int(rules.shape[0])
     cdf = zipf_cdf(n_rules, zipf_s) if (zipf_s is not None and n_rules > 0) else None
@@ -194,12 +198,20 @@ def gen_packets(rules: np.ndarray, n: int, seed: int, in_rule_frac: float = 0.6,
     b0, b1 = start // BLOCK, (end - 1) // BLOCK
     for b in range(b0, b1 + 1):
         bs = b * BLOCK
-        blk = _gen_block(rules, n_rules, BLOCK, seed, b, in_rule_frac, cdf)
+        blk = _gen_block(rules, n_rules, BLOCK, seed, b, in_rule_frac, cdf, rank_perm)
         lo = max(start, bs)
         hi = min(end, bs + BLOCK)
         for f in HEADER_FIELDS:
             out[f][lo - start:hi - start] = blk[f][lo - bs:hi - bs]
     return out
+
+
+def without_catch_alls(rules: np.ndarray) -> np.ndarray:
+    """The rules minus every all-wildcard one (default deny then decides the unmatched packets)."""
+    ca = ((rules["src_prefix"] == 0) & (rules["dst_prefix"] == 0) & (rules["sport_lo"] == 0) &
+          (rules["sport_hi"] == 65535) & (rules["dport_lo"] == 0) & (rules["dport_hi"] == 65535) &
+          (rules["proto_any"] != 0))
+    return np.ascontiguousarray(rules[~ca])
 
 
 def take(headers: dict, idx: np.ndarray) -> dict:
@@ -222,14 +234,26 @@ WORKLOADS = {
     "plain_1k_x_100k": dict(n_rules=1000, n_packets=100_000, rules_seed=1, packets_seed=2, zipf_s=None),
     "scan_10k_x_16m_zipf": dict(n_rules=10_000, n_packets=1 << 24, rules_seed=3, packets_seed=4, zipf_s=1.1),
     "lindex_100k_x_64m": dict(n_rules=100_000, n_packets=1 << 26, rules_seed=5, packets_seed=6, zipf_s=None),
+    # labelled variants of the scan workload: the Zipf rank order permuted over the rule list,
+    # and every all-wildcard rule removed (deep scans, default deny for unmatched packets)
+    "scan_10k_x_16m_zipf_permuted": dict(n_rules=10_000, n_packets=1 << 24, rules_seed=3, packets_seed=4,
+                                         zipf_s=1.1, rank_perm_seed=0x5045524D),
+    "scan_10k_x_16m_no_catch_all": dict(n_rules=10_000, n_packets=1 << 24, rules_seed=3, packets_seed=4,
+                                        zipf_s=1.1, drop_catch_alls=True),
 }
 
 
 def make_workload(name: str, n_packets: int | None = None):
     w = WORKLOADS[name]
     rules = gen_rules(w["n_rules"], w["rules_seed"])
+    if w.get("drop_catch_alls"):
+        rules = without_catch_alls(rules)
+    perm = None
+    if "rank_perm_seed" in w:
+        rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence((w["rules_seed"], w["rank_perm_seed"]))))
+        perm = rng.permutation(len(rules))
     n = w["n_packets"] if n_packets is None else n_packets
-    hdr = gen_packets(rules, n, w["packets_seed"], zipf_s=w["zipf_s"])
+    hdr = gen_packets(rules, n, w["packets_seed"], zipf_s=w["zipf_s"], rank_perm=perm)
     return rules, hdr
 
 
