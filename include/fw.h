@@ -108,18 +108,28 @@ typedef struct fw_headers {
  *  block_threads:     threads per block (multiple of 32, <= 1024).
  *  blocks_per_sm:     resident blocks per SM for persistent launches.
  *  smem_rules:        rules kept resident in shared memory (packet split).
- *  packets_per_group: rule split: packets handled together by one warp/block;
- *                     packet split with compaction: packets per warp batch
- *                     (multiple of 128).
- *  rule_slices:       number of rule slices across the grid (RULE_SPLIT_GRID).
- *  compact:           packet split only: 1 = re-pack undecided packets between
- *                     rule segments (default), 2 = plain lockstep scan.
+ *  packets_per_group: rule split: packets handled together by one warp group
+ *                     (default 64 for warp and grid mode, 256 for block mode);
+ *                     packet split with compaction: queue entries per warp
+ *                     batch (multiple of 128, default 256; with two packets
+ *                     per lane a batch holds up to 4 or 8 fewer packets, room
+ *                     for the protocol class pads).
+ *  rule_slices:       number of rule slices across the grid (RULE_SPLIT_GRID,
+ *                     default 8).
+ *  compact:           packet split only: 1 = per-warp queues that re-pack
+ *                     undecided packets between rule segments, 2 = plain
+ *                     lockstep scan; default: 1 for batches of 2^20 packets or
+ *                     more, else 2.
  *  predicate:         FW_PRED_CLAMP, FW_PRED_CMP, FW_PRED_ARITH or FW_PRED_RANGE
- *                     (0 = default).
+ *                     (0 = default, the arithmetic form).
  *  segment_rules:     packet split with compaction: rules in the first segment
- *                     (multiple of 4; later segments double).
+ *                     (multiple of 4; later segments double). Default: with two
+ *                     packets per lane 512, or 32 when the longest protocol
+ *                     sub-list exceeds 2,048 rules; with one packet per lane 64
+ *                     (partitioned) or 16 (whole list).
  *  partition:         packet split, arithmetic form: 1 = scan the protocol
- *                     partition (default), 2 = scan the whole list. A rule set
+ *                     partition (default with compaction), 2 = scan the whole
+ *                     list (default for the lockstep scan). A rule set
  *                     keeps, per protocol class (the exact protocols its rules
  *                     use most, plus "every other protocol"), the sub-list of
  *                     rules whose protocol can match that class, in list order;
