@@ -105,8 +105,12 @@ typedef struct fw_headers {
 /*
  * Launch configuration. Zero in any field means "library default".
  *  mode:              one of FW_MODE_*.
- *  block_threads:     threads per block (multiple of 32, <= 1024).
- *  blocks_per_sm:     resident blocks per SM for persistent launches.
+ *  block_threads:     threads per block (multiple of 32; <= 1024 for packet
+ *                     split, <= 512 for rule split). Defaults: compacting packet
+ *                     split 1024, lockstep sized to the batch (<= 512), rule
+ *                     split 256 (block mode 512).
+ *  blocks_per_sm:     resident blocks per SM for persistent launches (defaults:
+ *                     compacting packet split 1, lockstep 2, rule split 4).
  *  smem_rules:        rules kept resident in shared memory (packet split).
  *  packets_per_group: rule split: packets handled together by one warp group
  *                     (default 64 for warp and grid mode, 256 for block mode);
