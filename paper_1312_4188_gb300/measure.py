@@ -1,6 +1,7 @@
 """Measurements of the extended forms beside the plain GPU scan, on the same GPU.
 
   python -m paper_1312_4188_gb300.measure lindex   # learned index vs scan, 100K rules x 64M packets
+  python -m paper_1312_4188_gb300.measure lindex_scan  # the same on 10K rules x 16M packets
   python -m paper_1312_4188_gb300.measure batched  # 256 rule sets in one persistent launch
   python -m paper_1312_4188_gb300.measure serving  # continuous batching, Poisson arrivals
   python -m paper_1312_4188_gb300.measure variants # the 10K x 16M scan: permuted Zipf ranks, no catch-all
@@ -37,9 +38,9 @@ def _events_ms(fn, reps=10, warmup=3):
     return statistics.median(x.elapsed_time(y) for x, y in ts)
 
 
-def lindex(args):
+def lindex(args, workload="lindex_100k_x_64m", full=True):
     import torch
-    rules, hdr = W.make_workload("lindex_100k_x_64m")
+    rules, hdr = W.make_workload(workload)
     n = len(hdr["src"])
     dh = fw.headers_to_device(hdr)
     rs = fw.fw_ruleset_create(rules)
@@ -48,10 +49,10 @@ def lindex(args):
     t_scan = _events_ms(lambda: fw.fw_classify(rs, dh, n, s_idx, s_act))
     depth = torch.where(s_idx >= 0, s_idx.to(torch.int64) + 1, torch.full_like(s_idx, len(rules), dtype=torch.int64))
     depth_sum = int(depth.sum())
-    out = [{"form": "scan", "workload": "lindex_100k_x_64m", "ms": t_scan, "mpackets_s": n / t_scan / 1e3,
+    out = [{"form": "scan", "workload": workload, "ms": t_scan, "mpackets_s": n / t_scan / 1e3,
             "mean_depth": depth_sum / n, "first_catch_all": rs.first_catch_all,
             "hbm_gbs": BYTES_PER_PACKET * n / t_scan / 1e6}]
-    for label, kw in (("lindex_truncated", {}), ("lindex_full_100k", {"truncate": 2})):
+    for label, kw in (("lindex_truncated", {}), ("lindex_full", {"truncate": 2}))[:2 if full else 1]:
         t0 = time.perf_counter()
         li = fw.fw_lindex_create(rules, **kw)
         torch.cuda.synchronize()
@@ -249,7 +250,13 @@ def variants(args):
     return out
 
 
-COMMANDS = {"lindex": lindex, "batched": batched, "serving": serving, "variants": variants}
+def lindex_scan_workload(args):
+    """The learned index on the 10K-rule x 16M-packet scan workload (69 reachable rules)."""
+    return lindex(args, "scan_10k_x_16m_zipf", full=False)
+
+
+COMMANDS = {"lindex": lindex, "lindex_scan": lindex_scan_workload, "batched": batched, "serving": serving,
+            "variants": variants}
 
 
 def main(argv=None):
