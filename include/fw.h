@@ -107,11 +107,16 @@ typedef struct fw_headers {
  *  mode:              one of FW_MODE_*.
  *  block_threads:     threads per block (multiple of 32; <= 1024 for packet
  *                     split, <= 512 for rule split). Defaults: compacting packet
- *                     split 1024, lockstep sized to the batch (<= 512), rule
+ *                     split 1024 (128 for partitioned batches of 98,304 to 2^22
+ *                     packets), lockstep sized to the batch (<= 512), rule
  *                     split 256 (block mode 512).
  *  blocks_per_sm:     resident blocks per SM for persistent launches (defaults:
- *                     compacting packet split 1, lockstep 2, rule split 4).
- *  smem_rules:        rules kept resident in shared memory (packet split).
+ *                     compacting packet split 1 (8 with 128-thread blocks),
+ *                     lockstep 2, rule split 4). The two-packet scan allows at
+ *                     most 1,024 threads per SM (block_threads x blocks_per_sm).
+ *  smem_rules:        rules kept resident in shared memory (packet split;
+ *                     defaults 2048 compacting, 256 with 128-thread blocks,
+ *                     3072 lockstep; -1 = none).
  *  packets_per_group: rule split: packets handled together by one warp group
  *                     (default 64 for warp and grid mode, 256 for block mode);
  *                     packet split with compaction: queue entries per warp
@@ -123,7 +128,8 @@ typedef struct fw_headers {
  *  compact:           packet split only: 1 = per-warp queues that re-pack
  *                     undecided packets between rule segments, 2 = plain
  *                     lockstep scan; default: 1 for batches of 2^20 packets or
- *                     more, else 2.
+ *                     more, and for partitioned arithmetic scans from 98,304
+ *                     packets; else 2.
  *  predicate:         FW_PRED_CLAMP, FW_PRED_CMP, FW_PRED_ARITH or FW_PRED_RANGE
  *                     (0 = default, the arithmetic form).
  *  segment_rules:     packet split with compaction: rules in the first segment
@@ -142,8 +148,9 @@ typedef struct fw_headers {
  *                     same.
  *  lane_packets:      compacting packet split with the partition: packets each
  *                     lane scans at once (1 = one, 2 = two sharing every rule
- *                     load; 0 = default: two, or one when block_threads <= 768
- *                     and blocks_per_sm >= 2 select the dense form).
+ *                     load; 0 = default: two, or one when an explicit
+ *                     block_threads <= 768 and blocks_per_sm >= 2 select the
+ *                     dense form).
  */
 typedef struct fw_config {
     int32_t mode;

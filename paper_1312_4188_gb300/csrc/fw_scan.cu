@@ -162,6 +162,8 @@ struct SplitParams {
 
 constexpr int kNoMatch = 0x7F7F7F7F;  // byte-fill sentinel, larger than any rule index
 constexpr int64_t kCompactMinPackets = int64_t(1) << 20;  // default packet split compacts from this batch size
+constexpr int64_t kCompactMidPackets = int64_t(3) << 15;  // ... and the partitioned scan, in small blocks, from this
+constexpr int64_t kMidMaxPackets = int64_t(1) << 22;      // largest batch given the small-block shape by default
 
 // BLOCK = true: all warps of the block share one packet group and split its
 // chunks round-robin. BLOCK = false: each warp owns a packet group alone.
@@ -306,7 +308,13 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
     if (cfg.compact < 0 || cfg.compact > 2) return FW_EINVAL;
     // Default: compaction for large batches; small batches need every thread
     // they can get, so they take the lockstep form with smaller blocks.
-    const bool compact = cfg.compact == 1 || (cfg.compact == 0 && n >= kCompactMinPackets);
+    // Default decomposition by batch size (times on the 10K-rule list): the lockstep scan for
+    // small batches; the compacting scan of the protocol partition from 98,304 packets, up to
+    // 2^22 in 128-thread blocks, eight per SM, where it beats both lockstep and the 1,024-thread
+    // form (2^19: 15.0 vs 29.1 and 18.9 us; 2^22: 78.9 vs 148.0 and 82.0 us), and in
+    // 1,024-thread blocks above (2^24: 269 vs 298 us); every compacting form from 2^20.
+    const bool mid_ok = pred == FW_PRED_ARITH && cfg.partition != 2 && n >= kCompactMidPackets;
+    const bool compact = cfg.compact == 1 || (cfg.compact == 0 && (n >= kCompactMinPackets || mid_ok));
     // Protocol partition (stored for the arithmetic form only): default on in
     // the compacting kernel, which sorts each warp's batch by class so that a
     // warp's lanes share one sub-list; in the lockstep kernel lanes of a warp
@@ -344,23 +352,28 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
         p.verdict = rs->d_part_verdict;
     }
     const int need_all = (int)((p.n_scan + kChunkRules - 1) / kChunkRules * kChunkRules);
-    int threads = cfg.block_threads > 0 ? cfg.block_threads : (compact ? 1024 : 512);
+    const bool auto_mid = compact && part && n <= kMidMaxPackets && cfg.block_threads <= 0 &&
+                          cfg.blocks_per_sm <= 0 && cfg.lane_packets != 1;
+    int threads = cfg.block_threads > 0 ? cfg.block_threads : (compact ? (auto_mid ? 128 : 1024) : 512);
     if (cfg.block_threads <= 0 && !compact) {
         // at least two blocks per SM when the batch allows it
         const int64_t nq = (n + 3) / 4;
         const int64_t t = nq / (2 * (int64_t)sm_count(rs->device)) / 32 * 32;
         threads = (int)std::max<int64_t>(64, std::min<int64_t>(512, t));
     }
-    const int per_sm = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : (compact ? 1 : 2);
+    const int per_sm = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : (compact ? (auto_mid ? 8 : 1) : 2);
     if (threads % 32 != 0 || threads > 1024) return FW_EINVAL;
     if (cfg.lane_packets < 0 || cfg.lane_packets > 2) return FW_EINVAL;
-    // Compacting forms: one 1,024-thread block per SM by default; "dense" = two blocks of at
-    // most 768 threads. With the protocol partition the default gives each lane two packets
-    // per group (every rule load feeds two checks); the dense form keeps one.
-    const bool dense = compact && threads <= 768 && per_sm >= 2;
+    // Compacting forms: one 1,024-thread block per SM by default; "dense" = the one-packet
+    // kernel for two or more blocks of at most 768 threads per SM. With the protocol partition
+    // the default gives each lane two packets per group (every rule load feeds two checks),
+    // unless a dense shape was asked for.
+    const bool dense = compact && cfg.lane_packets != 2 && !auto_mid && threads <= 768 && per_sm >= 2;
     const bool lane2 = compact && part && (cfg.lane_packets == 2 || (cfg.lane_packets == 0 && !dense));
-    if (lane2 && dense) return FW_EINVAL;  // the two-packet form is built for one 1,024-thread block per SM
-    int want = cfg.smem_rules > 0 ? cfg.smem_rules : (cfg.smem_rules < 0 ? 0 : (compact ? 2048 : 3072));
+    // the two-packet kernel is built for 64 registers a thread: at most 1,024 threads per SM
+    if (lane2 && (int64_t)threads * per_sm > 1024) return FW_EINVAL;
+    int want = cfg.smem_rules > 0 ? cfg.smem_rules
+                                  : (cfg.smem_rules < 0 ? 0 : (compact ? (auto_mid ? 256 : 2048) : 3072));
     want = (want / kChunkRules) * kChunkRules;
     p.n_smem = std::min(want, need_all);
     p.batch = cfg.packets_per_group > 0 ? cfg.packets_per_group : 256;

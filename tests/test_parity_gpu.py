@@ -211,3 +211,16 @@ def test_scan_10k_x_16m_sampled(torch_cuda, big, mode, kw):
     ga = act.cpu().numpy()
     assert np.array_equal(ga, np.where(gi >= 0, rules["action"][np.maximum(gi, 0)], W.DROP))
     rs.destroy()
+
+
+@pytest.mark.parametrize("n_pkts", [98_303, 98_304, 200_003, 1_048_576, 4_194_304, 4_194_305])
+@pytest.mark.parametrize("catch_all", [True, False], ids=["plain", "no_catch_all"])
+def test_default_shapes_around_size_thresholds(torch_cuda, n_pkts, catch_all):
+    """AUTO switches lockstep -> two-packet scan in 128-thread blocks at 98,304 packets and to
+    1,024-thread blocks above 2^22: every side of both switches against the oracle."""
+    rules = W.gen_rules(1000, 21)
+    if not catch_all:
+        rules = no_catch_all(rules)
+    hdr = W.gen_packets(rules, n_pkts, 23)
+    want = oracle.classify(rules, hdr, threads=THREADS)
+    assert_same(run_gpu(torch_cuda, rules, hdr, "packet_split", {}), want, f"auto {n_pkts}")
