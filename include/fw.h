@@ -254,8 +254,10 @@ typedef struct fw_job {
  * 256; an item carries up to packets_per_item - 8 packets, the rest holds the
  * pads that keep each protocol class region even for the two-packet scan) and
  * segment_rules (first rule segment of the compacting scan, multiple of 4,
- * default 64). block_threads (default 1024) x max packets_per_item x 16 bytes
- * of shared memory per block must fit in 227 KB.
+ * default 64). block_threads (default 512; blocks_per_sm default 2: the
+ * kernel's 64 registers a thread let 1,024 of its threads reside per SM) x
+ * max packets_per_item x 16 bytes of shared memory per block must fit in
+ * 227 KB.
  */
 typedef struct fw_plan_config {
     int32_t block_threads;
