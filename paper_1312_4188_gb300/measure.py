@@ -2,6 +2,7 @@
 
   python -m paper_1312_4188_gb300.measure lindex   # learned index vs scan, 100K rules x 64M packets
   python -m paper_1312_4188_gb300.measure lindex_scan  # the same on 10K rules x 16M packets
+  python -m paper_1312_4188_gb300.measure lindex_deep  # ... and on that list without catch-alls
   python -m paper_1312_4188_gb300.measure batched  # 256 rule sets in one persistent launch
   python -m paper_1312_4188_gb300.measure serving  # continuous batching, Poisson arrivals
   python -m paper_1312_4188_gb300.measure variants # the 10K x 16M scan: permuted Zipf ranks, no catch-all
@@ -255,8 +256,13 @@ def lindex_scan_workload(args):
     return lindex(args, "scan_10k_x_16m_zipf", full=False)
 
 
-COMMANDS = {"lindex": lindex, "lindex_scan": lindex_scan_workload, "batched": batched, "serving": serving,
-            "variants": variants}
+def lindex_deep(args):
+    """The learned index on the 10K-rule x 16M-packet list without catch-alls (deep scans)."""
+    return lindex(args, "scan_10k_x_16m_no_catch_all", full=False)
+
+
+COMMANDS = {"lindex": lindex, "lindex_scan": lindex_scan_workload, "lindex_deep": lindex_deep, "batched": batched,
+            "serving": serving, "variants": variants}
 
 
 def main(argv=None):
