@@ -279,7 +279,9 @@ def main():
     # the default packet split scans the packet's protocol sub-list: its algorithmic work is the
     # rules of that sub-list up to the match, which is what the roofline counts
     partitioned = args.mode in ("auto", "packet_split")
-    scan_sum = partition_depth(rules, out_idx.cpu().numpy(), hdr["proto"]) if partitioned else depth_sum
+    part = rs.partition()
+    scan_sum = (partition_depth(rules, out_idx.cpu().numpy(), hdr, part["key_field"], part["key_bits"])
+                if partitioned else depth_sum)
     scan_checks_per_s = scan_sum / (mean_launch_ms * 1e-3)
     ops_per_s = scan_checks_per_s * OPS_PER_CHECK
     hbm_gbs = BYTES_PER_PACKET * n / (mean_launch_ms * 1e-3) / 1e9

@@ -194,6 +194,15 @@ void fw_ruleset_destroy(fw_ruleset *rs);
 /* Number of rules, and the index of the first rule that matches every packet (-1 if none). */
 int64_t fw_ruleset_size(const fw_ruleset *rs);
 int64_t fw_ruleset_first_catch_all(const fw_ruleset *rs);
+/*
+ * The rule set's partition (arithmetic form; see fw_config.partition): the
+ * number of classes, and the address key that splits each protocol class:
+ * key_field 0 = none, 1 = source, 2 = destination address, key_bits 0..3 top
+ * bits. A packet's class is its protocol class << key_bits | the top key_bits
+ * bits of the keyed address. The key is chosen at create time as the one with
+ * the shortest mean sub-list.
+ */
+int fw_ruleset_partition(const fw_ruleset *rs, int32_t *n_classes, int32_t *key_field, int32_t *key_bits);
 
 /*
  * Synchronise the device and report whether any kernel that used `rs` gave

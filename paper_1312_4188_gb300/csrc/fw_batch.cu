@@ -40,6 +40,8 @@ __global__ void __launch_bounds__(1024) k_batch(BatchParams p) {
         t.n_smem = 0;  // rules come through L1: jobs of one launch use different rule sets
         t.n_scan = 0;
         t.n_classes = J.n_classes;
+        t.key_field = J.key_field;
+        t.key_bits = J.key_bits;
         t.class_off = J.class_off;
         t.class_len = J.class_len;
         t.class_of = J.class_of;
@@ -66,6 +68,8 @@ void fill_batch_job(BatchJobDev &d, const fw_ruleset *rs, const fw_headers &h, i
     d.verdict = rs->d_part_verdict;
     d.class_of = rs->d_class_of;
     d.n_classes = rs->n_classes;
+    d.key_field = rs->key_field;
+    d.key_bits = rs->key_bits;
     for (int c = 0; c < kMaxClasses; ++c) {
         d.class_off[c] = rs->class_off[c];
         d.class_len[c] = rs->class_len[c];

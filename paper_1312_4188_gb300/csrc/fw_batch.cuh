@@ -16,6 +16,7 @@ struct BatchJobDev {
     const uint32_t *verdict;  // original index | action << 31 per stored record
     const uint8_t *class_of;
     int32_t n_classes;
+    int32_t key_field, key_bits;  // address key of the partition (see part_class)
     int32_t vec;  // 1 when the job's buffers allow the vector loads
     int32_t class_off[kMaxClasses];
     int32_t class_len[kMaxClasses];

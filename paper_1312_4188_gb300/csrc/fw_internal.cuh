@@ -25,7 +25,13 @@
 namespace fwk {
 
 constexpr int kChunkRules = 256;          // rules per TMA chunk / padding granule
-constexpr int kMaxClasses = 8;            // protocol classes of the partitioned rule lists
+constexpr int kMaxProtoClasses = 8;       // protocol classes: up to 7 exact protocols + "other"
+// Classes of the partitioned rule lists (protocol class x address key). Eight,
+// not more: on the 10K-rule list (4 protocol classes) one key bit, 8 classes,
+// takes 0.243 ms against 0.273 with no key and 0.262 with two bits, 16 classes
+// (the 100K-rule list: 5.37, 7.26 and 6.39 ms); past 8, more divergent groups
+// and wider sort counters cost more than the shorter sub-lists save.
+constexpr int kMaxClasses = 8;
 constexpr uint32_t kStatusTimeout = 1u;   // a bounded wait gave up
 constexpr uint32_t kStatusBadArgs = 2u;   // device-side sanity check failed
 
@@ -165,6 +171,16 @@ __device__ __forceinline__ bool mismatch_range_c(const PktA &p, const uint4 &a, 
            ((p.x * b.z + b.w) > wtop);
 }
 
+// Partition class of a packet (see fw_ruleset): protocol class, then the top
+// key_bits bits of the keyed address. key_shift = 32 - key_bits; with no key,
+// key_field is 0 and the shift is never taken.
+__device__ __forceinline__ uint32_t part_class(uint32_t pclass, int key_field, int key_bits, uint32_t src,
+                                               uint32_t dst) {
+    if (key_field == 0) return pclass;
+    const uint32_t a = key_field == 1 ? src : dst;
+    return (pclass << key_bits) | (a >> (32 - key_bits));
+}
+
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -241,14 +257,18 @@ struct fw_ruleset {
     uint32_t *d_wtop;         // n_pad words (arithmetic form)
     fwk::RecArith *d_range;   // n_pad records (range form)
     uint32_t *d_range_wtop;   // n_pad words (range form)
-    // Protocol partition (arithmetic form): class c's sub-list holds, in list
-    // order, the reachable rules whose protocol set can contain a packet of
+    // Partition (arithmetic form): a packet's class is its protocol class
+    // (d_class_of) times 2^key_bits plus the top key_bits bits of its source
+    // (key_field 1) or destination (key_field 2) address. Class c's sub-list
+    // holds, in list order, the reachable rules that can contain a packet of
     // class c; the sub-lists are stored one after another.
-    int32_t n_classes;                 // 1..kMaxClasses; the last class is "other"
-    int32_t class_off[8];              // first record of each sub-list (multiple of 4)
-    int32_t class_len[8];              // records in each sub-list (multiple of 4, padding never matches)
+    int32_t n_classes;                 // 1..kMaxClasses (protocol classes << key_bits)
+    int32_t key_field;                 // 0 = no address key, 1 = src, 2 = dst
+    int32_t key_bits;                  // 0..3
+    int32_t class_off[fwk::kMaxClasses];  // first record of each sub-list (multiple of 4)
+    int32_t class_len[fwk::kMaxClasses];  // records in each sub-list (multiple of 4, padding never matches)
     int64_t part_pad;                  // records stored (multiple of kChunkRules)
-    uint8_t *d_class_of;               // 256 entries: protocol -> class
+    uint8_t *d_class_of;               // 256 entries: protocol -> protocol class
     fwk::RecArith *d_part;             // part_pad records
     uint32_t *d_part_wtop;             // part_pad words
     int32_t *d_part_orig;              // part_pad original rule indices (-1 for padding)
@@ -263,7 +283,7 @@ int cuda_status(cudaError_t e);
 uint32_t prefix_mask(unsigned prefix);  // top `prefix` bits set; 0 for prefix 0
 bool is_catch_all(const fw_rule &r);    // all five fields wildcards
 int validate_rule(const fw_rule &r);    // FW_OK or FW_EINVAL
-// Protocol partition of rules [0, n): up to kMaxClasses - 1 classes for the
+// Protocol partition of rules [0, n): up to kMaxProtoClasses - 1 classes for the
 // exact protocols those rules use most, plus "other" for every other protocol
 // value. class_of[p] is protocol p's class; lists[c] holds, in list order, the
 // rules whose protocol set can contain a packet of class c (protocol "any", or

@@ -79,8 +79,8 @@ struct fw_lindex {
     float4 *d_model[fwk::kFields] = {};
     int32_t shift[fwk::kFields] = {};
     int n_classes = 0;
-    uint32_t *d_bits[fwk::kMaxClasses][fwk::kFields] = {};
-    int32_t *d_orig[fwk::kMaxClasses] = {};
+    uint32_t *d_bits[fwk::kMaxProtoClasses][fwk::kFields] = {};
+    int32_t *d_orig[fwk::kMaxProtoClasses] = {};
     fwk::LiClassDev *d_cls = nullptr;
     uint8_t *d_class_of = nullptr;
     uint8_t *d_action = nullptr;
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(512) k_li_classify(LiDev d, const uint32_t *__
                                                      const uint16_t *__restrict__ dport,
                                                      const uint8_t *__restrict__ proto, int64_t n,
                                                      int32_t *__restrict__ out_idx, uint8_t *__restrict__ out_act) {
-    __shared__ LiClassDev scls[kMaxClasses];
+    __shared__ LiClassDev scls[kMaxProtoClasses];
     extern __shared__ __align__(16) uint32_t sbound[];
     if (threadIdx.x < d.n_classes) scls[threadIdx.x] = d.cls[threadIdx.x];
     const uint32_t *bound[kFields];
@@ -335,7 +335,7 @@ extern "C" void fw_lindex_destroy(fw_lindex *li) {
         cudaFree(li->d_bound[f]);
         cudaFree(li->d_model[f]);
     }
-    for (int c = 0; c < kMaxClasses; ++c) {
+    for (int c = 0; c < kMaxProtoClasses; ++c) {
         for (int f = 0; f < kFields; ++f) cudaFree(li->d_bits[c][f]);
         cudaFree(li->d_orig[c]);
     }

@@ -105,7 +105,7 @@ void protocol_classes(const fw_rule *rules, int64_t n, std::vector<uint8_t> &cla
     for (int p = 0; p < 256; ++p)
         if (cnt[p] > 0) order.push_back(p);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cnt[a] > cnt[b]; });
-    if ((int)order.size() > kMaxClasses - 1) order.resize(kMaxClasses - 1);
+    if ((int)order.size() > kMaxProtoClasses - 1) order.resize(kMaxProtoClasses - 1);
     const int n_classes = (int)order.size() + 1;
     class_of.assign(256, (uint8_t)(n_classes - 1));
     for (size_t c = 0; c < order.size(); ++c) class_of[order[c]] = (uint8_t)c;
@@ -167,15 +167,58 @@ extern "C" int fw_ruleset_create_ex(const fw_rule *rules, int64_t n, fw_ruleset 
             hr[k].a = make_uint4(0u, 0xFFFFFFFFu, 0u, 0xFFFFFFFFu);
         }
     }
-    // Protocol partition: up to kMaxClasses - 1 classes for the exact
-    // protocols most used by reachable rules, plus "other" for every other
-    // protocol value. Sub-list c keeps, in list order, the rules with
-    // protocol "any" or with class c's protocol ("other": any, or an exact
-    // protocol without a class of its own).
+    // Partition: protocol classes (up to 7 exact protocols most used by
+    // reachable rules, plus "other"), each split again by the top key_bits
+    // bits of the source or destination address. Sub-list (p, k) keeps, in
+    // list order, the rules whose protocol set can contain class p's packets
+    // (protocol "any" or class p's protocol; for "other": any, or an exact
+    // protocol without a class of its own) and whose address prefix can
+    // contain an address with top bits k (a prefix shorter than key_bits
+    // covers several k; prefix 0 covers all). A packet's sub-list therefore
+    // holds every rule that can match it, in order, and its first match is the
+    // same. The key (field and bits, at most kMaxClasses classes in all) is
+    // the one with the shortest mean sub-list, which is what a packet scans if
+    // its key values are spread evenly; no key when none shortens it (or when
+    // the protocols alone fill the classes).
     {
         std::vector<uint8_t> class_of;
-        std::vector<std::vector<int64_t>> lists;
-        protocol_classes(rules, rs->n_eff, class_of, lists);
+        std::vector<std::vector<int64_t>> plists;
+        protocol_classes(rules, rs->n_eff, class_of, plists);
+        const int np = (int)plists.size();
+        auto covers = [&](const fw_rule &r, int field, int bits, uint32_t k) {
+            const unsigned len = field == 1 ? r.src_prefix : r.dst_prefix;
+            const uint32_t a = field == 1 ? r.src_addr : r.dst_addr;
+            if (len == 0) return true;
+            if (len >= (unsigned)bits) return (a >> (32 - bits)) == k;
+            return (k >> (bits - len)) == (a >> (32 - len));
+        };
+        auto sublists = [&](int field, int bits) {
+            std::vector<std::vector<int64_t>> out((size_t)np << bits);
+            for (int p = 0; p < np; ++p)
+                for (uint32_t k = 0; k < (1u << bits); ++k)
+                    for (int64_t r : plists[p])
+                        if (bits == 0 || covers(rules[r], field, bits, k)) out[((size_t)p << bits) | k].push_back(r);
+            return out;
+        };
+        int best_field = 0, best_bits = 0;
+        double best = 0;
+        for (const auto &L : plists) best += (double)L.size();
+        best /= np;
+        for (int field = 1; field <= 2; ++field)
+            for (int bits = 1; bits <= 3 && (np << bits) <= kMaxClasses; ++bits) {
+                const auto L = sublists(field, bits);
+                double mean = 0;
+                for (const auto &l : L) mean += (double)l.size();
+                mean /= (double)L.size();
+                if (mean < best) {
+                    best = mean;
+                    best_field = field;
+                    best_bits = bits;
+                }
+            }
+        const auto lists = sublists(best_field, best_bits);
+        rs->key_field = best_field;
+        rs->key_bits = best_bits;
         rs->n_classes = (int)lists.size();
         int64_t off = 0;
         for (int c = 0; c < kMaxClasses; ++c) {
@@ -239,6 +282,16 @@ extern "C" int fw_ruleset_create_ex(const fw_rule *rules, int64_t n, fw_ruleset 
         return set_status(cuda_status(e));
     }
     *out = rs;
+    return FW_OK;
+}
+
+extern "C" int fw_ruleset_partition(const fw_ruleset *rs, int32_t *n_classes, int32_t *key_field,
+                                    int32_t *key_bits) {
+    if (rs == nullptr || n_classes == nullptr || key_field == nullptr || key_bits == nullptr)
+        return set_status(FW_EINVAL);
+    *n_classes = rs->n_classes;
+    *key_field = rs->key_field;
+    *key_bits = rs->key_bits;
     return FW_OK;
 }
 

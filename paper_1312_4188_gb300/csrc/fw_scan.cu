@@ -48,8 +48,9 @@ __global__ void __launch_bounds__(1024) k_packet_split(ScanParams p) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if constexpr (PART) {
-                // the packet's protocol class picks its sub-list
-                const int c = __ldg(p.class_of + (pkt_proto<Pol>(pk[j]) & 0xFFu));
+                // the packet's partition class picks its sub-list
+                const int c = (int)part_class(__ldg(p.class_of + (pkt_proto<Pol>(pk[j]) & 0xFFu)), p.key_field,
+                                              p.key_bits, pk[j].src, pk[j].dst);
                 const int off = p.class_off[c];
                 const int r = scan_range<Pol>(pk[j], 0, p.class_len[c], shifted_view<Pol>(sv, off),
                                               max(0, n_smem - off), shifted_view<Pol>(gv, off), p.one);
@@ -101,6 +102,8 @@ __device__ __forceinline__ void compact_body(const ScanParams &p) {
     t.n_smem = staged ? p.n_smem : 0;  // a failed prefix wait leaves every rule to global memory
     t.n_scan = p.n_scan;
     t.n_classes = p.n_classes;
+    t.key_field = p.key_field;
+    t.key_bits = p.key_bits;
     t.class_off = cls_off;
     t.class_len = cls_len;
     t.class_of = class_tab;
@@ -343,6 +346,8 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
     p.n_scan = (int)stored;
     if (part) {
         p.n_classes = rs->n_classes;
+        p.key_field = rs->key_field;
+        p.key_bits = rs->key_bits;
         for (int c = 0; c < kMaxClasses; ++c) {
             p.class_off[c] = rs->class_off[c];
             p.class_len[c] = rs->class_len[c];

@@ -33,9 +33,10 @@ struct ScanParams {
     // protocol partition (used by the PART kernels; records are then the
     // concatenated sub-lists and n_scan / n_smem refer to that array)
     int32_t n_classes;
+    int32_t key_field, key_bits;  // address key of the partition (see part_class)
     int32_t class_off[kMaxClasses];
     int32_t class_len[kMaxClasses];
-    const uint8_t *class_of;  // 256 entries
+    const uint8_t *class_of;  // 256 entries: protocol -> protocol class
     const int32_t *orig;      // original rule index of each stored record
     const uint32_t *verdict;  // the same index | action << 31 (one load per decided packet)
 };
@@ -430,6 +431,32 @@ __device__ __forceinline__ void load_protos(const HdrPtrs &h, int64_t n, int64_t
     }
 }
 
+// Partition classes of quad q (packets 4q..4q+3) for a count pass: the protocol
+// bytes, plus the keyed address words when the partition has an address key;
+// nv = how many of the four exist.
+template <bool VEC, class T>
+__device__ __forceinline__ void load_classes4(const T &t, int64_t q, uint32_t cls[4], int &nv) {
+    uint32_t pr4;
+    load_protos<VEC>(t.h, t.n, q, true, pr4, nv);
+    uint32_t a[4] = {0, 0, 0, 0};
+    if (t.key_field != 0) {
+        const uint32_t *arr = t.key_field == 1 ? t.h.src : t.h.dst;
+        const int64_t b = q * 4;
+        if (VEC && nv == 4) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(arr) + q);
+            a[0] = v.x;
+            a[1] = v.y;
+            a[2] = v.z;
+            a[3] = v.w;
+        } else {
+            for (int j = 0; j < nv; ++j) a[j] = arr[b + j];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        cls[j] = part_class(t.class_of[(pr4 >> (8 * j)) & 0xFFu], t.key_field, t.key_bits, a[j], a[j]);
+}
+
 // Protocol of a packet held in a policy's packet form (the partition key).
 template <class Pol>
 __device__ __forceinline__ uint32_t pkt_proto(const typename Pol::Pk &p);
@@ -460,8 +487,9 @@ struct BatchTarget {
     typename Pol::View sv, gv;        // shared-memory prefix / global records
     int n_smem;                       // records resident in the shared prefix
     int n_scan;                       // records of the whole list (unpartitioned)
-    int n_classes;                    // partition: classes, sub-list offsets and lengths,
-    const int32_t *class_off;         //   protocol -> class table, original rule index
+    int n_classes;                    // partition: classes, address key, sub-list offsets and
+    int key_field, key_bits;          //   lengths, protocol -> protocol class table, original
+    const int32_t *class_off;         //   rule index
     const int32_t *class_len;
     const uint8_t *class_of;
     const int32_t *orig;
@@ -491,10 +519,10 @@ __device__ __forceinline__ void run_batch(const BatchTarget<Pol> &t, int64_t bas
         if (lane < 2 * kMaxClasses) wc[lane] = 0;
         __syncwarp();
         for (int qq = lane; qq * 4 < cnt; qq += 32) {
-            uint32_t pr4;
+            uint32_t cls[4];
             int nv;
-            load_protos<VEC>(t.h, t.n, base / 4 + qq, true, pr4, nv);
-            for (int j = 0; j < nv; ++j) atomicAdd(&wc[t.class_of[(pr4 >> (8 * j)) & 0xFFu]], 1);
+            load_classes4<VEC>(t, base / 4 + qq, cls, nv);
+            for (int j = 0; j < nv; ++j) atomicAdd(&wc[cls[j]], 1);
         }
         __syncwarp();
         if (lane == 0) {
@@ -512,7 +540,9 @@ __device__ __forceinline__ void run_batch(const BatchTarget<Pol> &t, int64_t bas
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 if (j >= nv) continue;
-                const int pos = atomicAdd(&wc[kMaxClasses + t.class_of[pkt_proto<Pol>(pk[j]) & 0xFFu]], 1);
+                const uint32_t c = part_class(t.class_of[pkt_proto<Pol>(pk[j]) & 0xFFu], t.key_field, t.key_bits,
+                                              pk[j].src, pk[j].dst);
+                const int pos = atomicAdd(&wc[kMaxClasses + c], 1);
                 Q[pos] = Pol::pack(pk[j], qq * 4 + j);
             }
         }
@@ -584,14 +614,18 @@ __device__ __forceinline__ int pair_slot(int pos) { return (pos & ~63) + ((pos &
 // below the queue capacity, which shared memory bounds far below 0xFFFF.
 constexpr uint32_t kNoSlot = 0xFFFFu;
 
-// Per-lane class counters: 16-bit fields, classes 0-3 in lo and 4-7 in hi.
-__device__ __forceinline__ uint32_t class_field(uint64_t lo, uint64_t hi, uint32_t c) {
-    return (uint32_t)((c < 4 ? lo : hi) >> (16 * (c & 3))) & 0xFFFFu;
+// Per-lane class counters: 16-bit fields, four classes to a 64-bit word.
+struct ClassCounts {
+    uint64_t w[kMaxClasses / 4];
+};
+static_assert(kMaxClasses == 8, "ClassCounts selects between two words");
+__device__ __forceinline__ uint32_t class_field(const ClassCounts &k, uint32_t c) {
+    return (uint32_t)((c < 4 ? k.w[0] : k.w[1]) >> (16 * (c & 3))) & 0xFFFFu;
 }
-__device__ __forceinline__ void class_bump(uint64_t &lo, uint64_t &hi, uint32_t c) {
+__device__ __forceinline__ void class_bump(ClassCounts &k, uint32_t c) {
     const uint64_t inc = 1ull << (16 * (c & 3));
-    if (c < 4) lo += inc;
-    else hi += inc;
+    if (c < 4) k.w[0] += inc;
+    else k.w[1] += inc;
 }
 
 // Queue entries of the two-packet scan carry their class in bits 28-30 of the
@@ -635,30 +669,32 @@ __device__ __forceinline__ void run_batch_pairs(const BatchTarget<Pol> &t, int64
                                                 int lane) {
     int *cnt_c = wc, *cur_c = wc + kMaxClasses;
     const int nc = t.n_classes;
-    uint64_t lo = 0, hi = 0;
+    ClassCounts own{};
     for (int qq = lane; qq * 4 < cnt; qq += 32) {
-        uint32_t pr4;
+        uint32_t cls[4];
         int nv;
-        load_protos<VEC>(t.h, t.n, base / 4 + qq, true, pr4, nv);
+        load_classes4<VEC>(t, base / 4 + qq, cls, nv);
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            if (j < nv) class_bump(lo, hi, t.class_of[(pr4 >> (8 * j)) & 0xFFu]);
+            if (j < nv) class_bump(own, cls[j]);
     }
-    uint64_t elo = lo, ehi = hi;  // inclusive scan over lanes, then exclusive
+    ClassCounts ex = own, tot;  // inclusive scan over lanes, then exclusive
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        const uint64_t a = __shfl_up_sync(0xFFFFFFFFu, elo, d), b = __shfl_up_sync(0xFFFFFFFFu, ehi, d);
-        if (lane >= d) {
-            elo += a;
-            ehi += b;
+#pragma unroll
+        for (int i = 0; i < kMaxClasses / 4; ++i) {
+            const uint64_t a = __shfl_up_sync(0xFFFFFFFFu, ex.w[i], d);
+            if (lane >= d) ex.w[i] += a;
         }
     }
-    const uint64_t tlo = __shfl_sync(0xFFFFFFFFu, elo, 31), thi = __shfl_sync(0xFFFFFFFFu, ehi, 31);
-    elo -= lo;
-    ehi -= hi;
+#pragma unroll
+    for (int i = 0; i < kMaxClasses / 4; ++i) {
+        tot.w[i] = __shfl_sync(0xFFFFFFFFu, ex.w[i], 31);
+        ex.w[i] -= own.w[i];
+    }
     int m = 0;
     for (int c = 0; c < nc; ++c) {
-        const int tc = (int)class_field(tlo, thi, (uint32_t)c);
+        const int tc = (int)class_field(tot, (uint32_t)c);
         if (lane == 0) {
             cur_c[c] = m;
             cnt_c[c] = tc;
@@ -673,9 +709,10 @@ __device__ __forceinline__ void run_batch_pairs(const BatchTarget<Pol> &t, int64
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (j >= nv) continue;
-            const uint32_t c = t.class_of[pkt_proto<Pol>(pk[j]) & 0xFFu];
-            const int pos = cur_c[c] + (int)class_field(elo, ehi, c);
-            class_bump(elo, ehi, c);
+            const uint32_t c = part_class(t.class_of[pkt_proto<Pol>(pk[j]) & 0xFFu], t.key_field, t.key_bits,
+                                          pk[j].src, pk[j].dst);
+            const int pos = cur_c[c] + (int)class_field(ex, c);
+            class_bump(ex, c);
             uint4 e = Pol::pack(pk[j], qq * 4 + j);
             e.w |= c << 28;
             Q[pair_slot(pos)] = e;

@@ -131,6 +131,7 @@ SIGNATURES = {
     "fw_ruleset_destroy": (None, [P]),
     "fw_ruleset_size": (I64, [P]),
     "fw_ruleset_first_catch_all": (I64, [P]),
+    "fw_ruleset_partition": (ctypes.c_int, [P, P, P, P]),
     "fw_ruleset_check": (ctypes.c_int, [P]),
     "fw_classify": (ctypes.c_int, [P, ctypes.POINTER(fw_headers), I64, P, P, P]),
     "fw_classify_ex": (ctypes.c_int, [P, ctypes.POINTER(fw_headers), I64, P, P, P, ctypes.POINTER(fw_config)]),
@@ -225,6 +226,13 @@ class Ruleset:
     @property
     def first_catch_all(self) -> int:
         return int(lib().fw_ruleset_first_catch_all(self.handle))
+
+    def partition(self) -> dict:
+        """{"classes", "key_field" (0 none, 1 src, 2 dst), "key_bits"} of the partitioned scan."""
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().fw_ruleset_partition(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "fw_ruleset_partition")
+        return {"classes": a.value, "key_field": b.value, "key_bits": c.value}
 
     def size(self) -> int:
         return int(lib().fw_ruleset_size(self.handle))

@@ -239,7 +239,8 @@ def variants(args):
         same = bool(torch.equal(idx, ref_i) and torch.equal(act, ref_a))
         idx_np = idx.cpu().numpy()
         depth = np.where(idx_np >= 0, idx_np.astype(np.int64) + 1, rs.size()).sum()
-        scan = partition_depth(rules, idx_np, hdr["proto"])
+        part = rs.partition()
+        scan = partition_depth(rules, idx_np, hdr, part["key_field"], part["key_bits"])
         checks_s = scan / (t * 1e-3)
         out.append({"form": "scan", "workload": name, "rules": int(len(rules)), "packets": n,
                     "ms": t, "mpackets_s": n / t / 1e3, "mean_depth": float(depth / n),
