@@ -224,3 +224,20 @@ def test_default_shapes_around_size_thresholds(torch_cuda, n_pkts, catch_all):
     hdr = W.gen_packets(rules, n_pkts, 23)
     want = oracle.classify(rules, hdr, threads=THREADS)
     assert_same(run_gpu(torch_cuda, rules, hdr, "packet_split", {}), want, f"auto {n_pkts}")
+
+
+def test_partition_key_on_destination(torch_cuda):
+    """With every source prefix a wildcard the rule set must key its partition on the destination
+    address; every partitioned kernel then agrees with the oracle."""
+    rules = W.gen_rules(2000, 31)
+    rules["src_prefix"] = 0
+    rules = no_catch_all(rules)
+    rs = fw.fw_ruleset_create(rules)
+    part = rs.partition()
+    assert part["key_field"] == 2 and 1 <= part["key_bits"] <= 3 and part["classes"] <= 8
+    hdr = W.gen_packets(rules, 300_000, 32)
+    want = oracle.classify(rules, hdr, threads=THREADS)
+    for kw in ({}, {"compact": 1}, {"compact": 1, "lane_packets": 1}, {"compact": 2, "partition": 1},
+               {"compact": 1, "block_threads": 256, "segment_rules": 8}):
+        assert_same(run_gpu(torch_cuda, rules, hdr, "packet_split", kw, rs=rs), want, f"dst key {kw}")
+    rs.destroy()
