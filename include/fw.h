@@ -137,15 +137,16 @@ typedef struct fw_headers {
  *                     packets per lane 512, or 32 when the longest protocol
  *                     sub-list exceeds 2,048 rules; with one packet per lane 64
  *                     (partitioned) or 16 (whole list).
- *  partition:         packet split, arithmetic form: 1 = scan the protocol
- *                     partition (default with compaction), 2 = scan the whole
- *                     list (default for the lockstep scan). A rule set
- *                     keeps, per protocol class (the exact protocols its rules
- *                     use most, plus "every other protocol"), the sub-list of
- *                     rules whose protocol can match that class, in list order;
- *                     a packet scans only its class's sub-list, which contains
- *                     every rule that can match it, so the first match is the
- *                     same.
+ *  partition:         packet split, arithmetic form: 1 = scan the partition
+ *                     (default with compaction), 2 = scan the whole list
+ *                     (default for the lockstep scan). A rule set keeps, per
+ *                     class (a protocol class: the exact protocols its rules
+ *                     use most, plus "every other protocol"; split again by
+ *                     the top bit(s) of the source or destination address, see
+ *                     fw_ruleset_partition), the sub-list of rules that can
+ *                     match a packet of that class, in list order; a packet
+ *                     scans only its class's sub-list, which contains every
+ *                     rule that can match it, so the first match is the same.
  *  lane_packets:      compacting packet split with the partition: packets each
  *                     lane scans at once (1 = one, 2 = two sharing every rule
  *                     load; 0 = default: two, or one when an explicit
