@@ -397,8 +397,10 @@ int fw_server_replay(fw_server *sv, fw_request *reqs, int64_t n, int64_t timeout
  * fw_classify). Each rule field is an interval of its key space (Sec. IV:
  * prefix = address interval, port range, protocol value or all). Per field
  * the key space is cut at every interval end into elementary intervals. The
- * protocol selects a class as in fw_classify's partition (the up to 7 exact
- * protocols most used, plus "other"); per class, row j of a field's bitmap
+ * protocol and address key select a class as in fw_classify's partition (the
+ * up to 7 exact protocols most used, plus "other", split by the top bits of
+ * one address where that shortens the sub-lists; fw_ruleset_partition
+ * describes it); per class, row j of a field's bitmap
  * (src, dst, sport, dport) has bit b set when the b-th rule of the class's
  * sub-list covers interval j. A packet's first match (Sec. I) is the rule
  * behind the lowest set bit of the AND of its four rows in its class (five
@@ -436,7 +438,9 @@ typedef struct fw_lindex_stats {
     int32_t max_error[5];   /* stored maximum model error per field, in positions */
     int64_t bitmap_bytes;   /* device bytes of all rows */
     int64_t fallbacks;      /* verified windows that failed (0 when the bounds hold) */
-    int64_t classes;        /* protocol classes (one set of rows each) */
+    int64_t classes;        /* partition classes (one set of rows each) */
+    int32_t key_field;      /* address key of the partition: 0 none, 1 src, 2 dst */
+    int32_t key_bits;       /* top address bits in the key */
 } fw_lindex_stats;
 
 typedef struct fw_lindex fw_lindex;

@@ -290,5 +290,20 @@ int validate_rule(const fw_rule &r);    // FW_OK or FW_EINVAL
 // class c's protocol; for "other": any, or an exact protocol without a class).
 void protocol_classes(const fw_rule *rules, int64_t n, std::vector<uint8_t> &class_of,
                       std::vector<std::vector<int64_t>> &lists);
+// Partition of rules [0, n) into the classes the packet-split and learned-index
+// kernels use: protocol classes as above, each split again by the top key_bits
+// bits of the source (key_field 1) or destination (2) address; key_field 0 is
+// no key. Class c = pclass << key_bits | key, and lists[c] keeps, in list
+// order, the rules of pclass's list whose address prefix on that field can
+// contain an address with top bits `key` (a prefix shorter than key_bits covers
+// several keys; prefix 0 covers all). So a packet's list holds every rule that
+// can match it, in order, and its first match is unchanged. The key (at most
+// kMaxClasses classes in all) is the one with the lowest mean list cost, what a
+// packet scans when key values are spread evenly: the length (granule <= 1),
+// else ceil(length / granule) with a minimum of 1, for a reader that takes the
+// list `granule` rules at a time. No key when none lowers it or the protocols
+// alone fill the classes.
+void partition_lists(const fw_rule *rules, int64_t n, int64_t granule, std::vector<uint8_t> &class_of,
+                     std::vector<std::vector<int64_t>> &lists, int &key_field, int &key_bits);
 int sm_count(int dev);                  // SMs of device `dev` (cached)
 }  // namespace fwk

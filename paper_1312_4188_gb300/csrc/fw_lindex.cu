@@ -5,9 +5,10 @@
 // rule model: a prefix is an address interval, a port range an interval, a
 // protocol one value or all of them). Cutting each field's key space at every
 // interval endpoint gives "elementary intervals" inside which no rule's
-// field test changes. The protocol is handled by the same partition as the
-// scan: per protocol class, the sub-list of rules whose protocol can match a
-// packet of that class, in list order. For class c, field f (src, dst, sport,
+// field test changes. Rules are split by the same partition as the scan's
+// (protocol class and, where it shortens the lists, the top bits of one
+// address): per class, the sub-list of rules that can match a packet of that
+// class, in list order. For class c, field f (src, dst, sport,
 // dport) and elementary interval j, the row bits_{c,f}[j] has bit b set
 // exactly when the b-th rule of c's sub-list covers interval j in field f. A
 // packet of class c lies in that rule iff bit b is set in the rows of its four
@@ -15,8 +16,8 @@
 // set bit of the AND of four rows, found by scanning words from the start.
 // The sub-list holds every rule that can match the packet, in order, so the
 // answer is the whole list's first match. When more exact protocols are in use
-// than there are classes, the "other" class holds rules of several protocols
-// and gets protocol rows too, ANDed as a fifth row.
+// than there are protocol classes, the "other" classes hold rules of several
+// protocols and get protocol rows too, ANDed as a fifth row.
 //
 // Locating a key's elementary interval: a piecewise-linear FP32 model per
 // field (the key space cut into `segments` equal parts, one line per part fit
@@ -36,7 +37,7 @@
 namespace fwk {
 
 constexpr int kFields = 5;      // src, dst, sport, dport, proto (intervals and models)
-constexpr int kRowFields = 4;   // fields with bitmap rows; the protocol selects the class
+constexpr int kRowFields = 4;   // fields with bitmap rows; the protocol (and key) select the class
 constexpr int kKeyBits[kFields] = {32, 32, 16, 16, 8};
 
 struct LiFieldDev {
@@ -46,11 +47,11 @@ struct LiFieldDev {
     int32_t shift;          // segment = key >> shift
 };
 
-// One protocol class: its rows (per field, M_f rows of W words) and the
-// original rule index behind each bit (-1 past the sub-list). A class that
-// holds rules of several exact protocols ("other", when more protocols are in
-// use than there are classes) also has protocol rows (bits[4]); for every
-// other class the protocol test is implied by the class.
+// One class: its rows (per field, M_f rows of W words) and the original rule
+// index behind each bit (-1 past the sub-list). A class that holds rules of
+// several exact protocols ("other", when more protocols are in use than there
+// are protocol classes) also has protocol rows (bits[4]); for every other
+// class the protocol test is implied by the class.
 struct LiClassDev {
     const uint32_t *bits[kFields];
     const int32_t *orig;
@@ -61,7 +62,8 @@ struct LiDev {
     LiFieldDev f[kFields];
     const LiClassDev *cls;  // n_classes entries (device memory)
     int32_t n_classes;
-    const uint8_t *class_of;  // protocol -> class (256 entries)
+    int32_t key_field, key_bits;  // address key of the partition (part_class)
+    const uint8_t *class_of;  // protocol -> protocol class (256 entries)
     const uint8_t *action;
     unsigned long long *fallbacks;
 };
@@ -78,9 +80,9 @@ struct fw_lindex {
     uint32_t *d_bound[fwk::kFields] = {};
     float4 *d_model[fwk::kFields] = {};
     int32_t shift[fwk::kFields] = {};
-    int n_classes = 0;
-    uint32_t *d_bits[fwk::kMaxProtoClasses][fwk::kFields] = {};
-    int32_t *d_orig[fwk::kMaxProtoClasses] = {};
+    int n_classes = 0, key_field = 0, key_bits = 0;
+    uint32_t *d_bits[fwk::kMaxClasses][fwk::kFields] = {};
+    int32_t *d_orig[fwk::kMaxClasses] = {};
     fwk::LiClassDev *d_cls = nullptr;
     uint8_t *d_class_of = nullptr;
     uint8_t *d_action = nullptr;
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(512) k_li_classify(LiDev d, const uint32_t *__
                                                      const uint16_t *__restrict__ dport,
                                                      const uint8_t *__restrict__ proto, int64_t n,
                                                      int32_t *__restrict__ out_idx, uint8_t *__restrict__ out_act) {
-    __shared__ LiClassDev scls[kMaxProtoClasses];
+    __shared__ LiClassDev scls[kMaxClasses];
     extern __shared__ __align__(16) uint32_t sbound[];
     if (threadIdx.x < d.n_classes) scls[threadIdx.x] = d.cls[threadIdx.x];
     const uint32_t *bound[kFields];
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(512) k_li_classify(LiDev d, const uint32_t *__
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t pr = proto[i];
         const uint32_t key[kRowFields] = {src[i], dst[i], sport[i], dport[i]};
-        const LiClassDev &c = scls[__ldg(d.class_of + pr)];
+        const LiClassDev &c = scls[part_class(__ldg(d.class_of + pr), d.key_field, d.key_bits, key[0], key[1])];
         const int64_t W = c.W;
         const uint4 *row[kFields];
 #pragma unroll
@@ -335,7 +337,7 @@ extern "C" void fw_lindex_destroy(fw_lindex *li) {
         cudaFree(li->d_bound[f]);
         cudaFree(li->d_model[f]);
     }
-    for (int c = 0; c < kMaxProtoClasses; ++c) {
+    for (int c = 0; c < kMaxClasses; ++c) {
         for (int f = 0; f < kFields; ++f) cudaFree(li->d_bits[c][f]);
         cudaFree(li->d_orig[c]);
     }
@@ -371,8 +373,11 @@ extern "C" int fw_lindex_create(const fw_rule *rules, int64_t n, const fw_lindex
     cudaGetDevice(&li->device);
     std::vector<uint8_t> class_of;
     std::vector<std::vector<int64_t>> lists;
-    protocol_classes(rules, li->n_idx, class_of, lists);
+    // a packet reads whole row words, 128 rules per uint4, at least one: a key
+    // is taken only where it shortens those
+    partition_lists(rules, li->n_idx, 128, class_of, lists, li->key_field, li->key_bits);
     li->n_classes = (int)lists.size();
+    const int n_proto_classes = li->n_classes >> li->key_bits;
     std::vector<char> mixed((size_t)li->n_classes, 0);  // sub-list holds exact protocols of different values
     for (int c = 0; c < li->n_classes; ++c) {
         int first = -1;
@@ -382,7 +387,7 @@ extern "C" int fw_lindex_create(const fw_rule *rules, int64_t n, const fw_lindex
                 else if (rules[k].proto != first) mixed[c] = 1;
             }
         // the "other" class matches every protocol without a class: one exact rule is enough
-        if (c == li->n_classes - 1 && first >= 0) mixed[c] = 1;
+        if ((c >> li->key_bits) == n_proto_classes - 1 && first >= 0) mixed[c] = 1;
     }
     std::vector<LiClassDev> hcls((size_t)li->n_classes);
     for (int c = 0; c < li->n_classes; ++c) {
@@ -506,6 +511,8 @@ extern "C" int fw_lindex_classify(const fw_lindex *li, const fw_headers *hdrs, i
     d.action = li->d_action;
     d.fallbacks = li->d_fallbacks;
     d.n_classes = li->n_classes;
+    d.key_field = li->key_field;
+    d.key_bits = li->key_bits;
     // the fields' interval starts in shared memory when they fit in 48 KB
     int64_t nb = 0;
     for (int f = 0; f < kFields; ++f) nb += li->M[f];
@@ -534,6 +541,8 @@ extern "C" int fw_lindex_get_stats(fw_lindex *li, fw_lindex_stats *st) {
     }
     st->bitmap_bytes = li->bitmap_bytes;
     st->classes = li->n_classes;
+    st->key_field = li->key_field;
+    st->key_bits = li->key_bits;
     cudaError_t e = cudaDeviceSynchronize();
     unsigned long long fb = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&fb, li->d_fallbacks, sizeof(fb), cudaMemcpyDeviceToHost);

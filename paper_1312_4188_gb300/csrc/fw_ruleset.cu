@@ -120,6 +120,50 @@ void protocol_classes(const fw_rule *rules, int64_t n, std::vector<uint8_t> &cla
     }
 }
 
+void partition_lists(const fw_rule *rules, int64_t n, int64_t granule, std::vector<uint8_t> &class_of,
+                     std::vector<std::vector<int64_t>> &lists, int &key_field, int &key_bits) {
+    std::vector<std::vector<int64_t>> plists;
+    protocol_classes(rules, n, class_of, plists);
+    const int np = (int)plists.size();
+    auto covers = [&](const fw_rule &r, int field, int bits, uint32_t k) {
+        const unsigned len = field == 1 ? r.src_prefix : r.dst_prefix;
+        const uint32_t a = field == 1 ? r.src_addr : r.dst_addr;
+        if (len == 0) return true;
+        if (len >= (unsigned)bits) return (a >> (32 - bits)) == k;
+        return (k >> (bits - len)) == (a >> (32 - len));
+    };
+    auto sublists = [&](int field, int bits) {
+        std::vector<std::vector<int64_t>> out((size_t)np << bits);
+        for (int p = 0; p < np; ++p)
+            for (uint32_t k = 0; k < (1u << bits); ++k)
+                for (int64_t r : plists[p])
+                    if (bits == 0 || covers(rules[r], field, bits, k)) out[((size_t)p << bits) | k].push_back(r);
+        return out;
+    };
+    auto cost = [&](size_t len) {
+        return granule <= 1 ? (double)len : (double)std::max<int64_t>(1, ((int64_t)len + granule - 1) / granule);
+    };
+    int best_field = 0, best_bits = 0;
+    double best = 0;
+    for (const auto &L : plists) best += cost(L.size());
+    best /= np;
+    for (int field = 1; field <= 2; ++field)
+        for (int bits = 1; bits <= 3 && (np << bits) <= kMaxClasses; ++bits) {
+            const auto L = sublists(field, bits);
+            double mean = 0;
+            for (const auto &l : L) mean += cost(l.size());
+            mean /= (double)L.size();
+            if (mean < best) {
+                best = mean;
+                best_field = field;
+                best_bits = bits;
+            }
+        }
+    lists = sublists(best_field, best_bits);
+    key_field = best_field;
+    key_bits = best_bits;
+}
+
 }  // namespace fwk
 
 using namespace fwk;
@@ -167,58 +211,15 @@ extern "C" int fw_ruleset_create_ex(const fw_rule *rules, int64_t n, fw_ruleset 
             hr[k].a = make_uint4(0u, 0xFFFFFFFFu, 0u, 0xFFFFFFFFu);
         }
     }
-    // Partition: protocol classes (up to 7 exact protocols most used by
-    // reachable rules, plus "other"), each split again by the top key_bits
-    // bits of the source or destination address. Sub-list (p, k) keeps, in
-    // list order, the rules whose protocol set can contain class p's packets
-    // (protocol "any" or class p's protocol; for "other": any, or an exact
-    // protocol without a class of its own) and whose address prefix can
-    // contain an address with top bits k (a prefix shorter than key_bits
-    // covers several k; prefix 0 covers all). A packet's sub-list therefore
-    // holds every rule that can match it, in order, and its first match is the
-    // same. The key (field and bits, at most kMaxClasses classes in all) is
-    // the one with the shortest mean sub-list, which is what a packet scans if
-    // its key values are spread evenly; no key when none shortens it (or when
-    // the protocols alone fill the classes).
+    // Partition into per-class sub-lists (protocol class and address key; the
+    // key is chosen by partition_lists), packed 4-aligned, one after another.
     {
         std::vector<uint8_t> class_of;
-        std::vector<std::vector<int64_t>> plists;
-        protocol_classes(rules, rs->n_eff, class_of, plists);
-        const int np = (int)plists.size();
-        auto covers = [&](const fw_rule &r, int field, int bits, uint32_t k) {
-            const unsigned len = field == 1 ? r.src_prefix : r.dst_prefix;
-            const uint32_t a = field == 1 ? r.src_addr : r.dst_addr;
-            if (len == 0) return true;
-            if (len >= (unsigned)bits) return (a >> (32 - bits)) == k;
-            return (k >> (bits - len)) == (a >> (32 - len));
-        };
-        auto sublists = [&](int field, int bits) {
-            std::vector<std::vector<int64_t>> out((size_t)np << bits);
-            for (int p = 0; p < np; ++p)
-                for (uint32_t k = 0; k < (1u << bits); ++k)
-                    for (int64_t r : plists[p])
-                        if (bits == 0 || covers(rules[r], field, bits, k)) out[((size_t)p << bits) | k].push_back(r);
-            return out;
-        };
-        int best_field = 0, best_bits = 0;
-        double best = 0;
-        for (const auto &L : plists) best += (double)L.size();
-        best /= np;
-        for (int field = 1; field <= 2; ++field)
-            for (int bits = 1; bits <= 3 && (np << bits) <= kMaxClasses; ++bits) {
-                const auto L = sublists(field, bits);
-                double mean = 0;
-                for (const auto &l : L) mean += (double)l.size();
-                mean /= (double)L.size();
-                if (mean < best) {
-                    best = mean;
-                    best_field = field;
-                    best_bits = bits;
-                }
-            }
-        const auto lists = sublists(best_field, best_bits);
-        rs->key_field = best_field;
-        rs->key_bits = best_bits;
+        std::vector<std::vector<int64_t>> lists;
+        int key_field = 0, key_bits = 0;
+        partition_lists(rules, rs->n_eff, 1, class_of, lists, key_field, key_bits);
+        rs->key_field = key_field;
+        rs->key_bits = key_bits;
         rs->n_classes = (int)lists.size();
         int64_t off = 0;
         for (int c = 0; c < kMaxClasses; ++c) {

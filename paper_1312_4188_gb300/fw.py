@@ -86,7 +86,8 @@ class fw_lindex_config(ctypes.Structure):
 class fw_lindex_stats(ctypes.Structure):
     _fields_ = [("rules", ctypes.c_int64), ("rules_indexed", ctypes.c_int64), ("words_per_row", ctypes.c_int64),
                 ("segments", ctypes.c_int64), ("intervals", ctypes.c_int64 * 5), ("max_error", ctypes.c_int32 * 5),
-                ("bitmap_bytes", ctypes.c_int64), ("fallbacks", ctypes.c_int64), ("classes", ctypes.c_int64)]
+                ("bitmap_bytes", ctypes.c_int64), ("fallbacks", ctypes.c_int64), ("classes", ctypes.c_int64),
+                ("key_field", ctypes.c_int32), ("key_bits", ctypes.c_int32)]
 
 
 class fw_job(ctypes.Structure):
@@ -356,7 +357,8 @@ class LIndex:
         _check(lib().fw_lindex_get_stats(self.handle, ctypes.byref(st)), "fw_lindex_get_stats")
         return {"rules": st.rules, "rules_indexed": st.rules_indexed, "words_per_row": st.words_per_row,
                 "segments": st.segments, "intervals": list(st.intervals), "max_error": list(st.max_error),
-                "bitmap_bytes": st.bitmap_bytes, "fallbacks": st.fallbacks, "classes": st.classes}
+                "bitmap_bytes": st.bitmap_bytes, "fallbacks": st.fallbacks, "classes": st.classes,
+                "key_field": st.key_field, "key_bits": st.key_bits}
 
     def destroy(self):
         if self.handle is not None and self.handle.value:

@@ -122,3 +122,27 @@ def test_classify_rejects_bad_arguments(L):
     assert L.fw_classify_ex(fake, ctypes.byref(hp), 8, fake, fake, None, ctypes.byref(cfg)) == fw.FW_EINVAL
     cfg = fw.make_config(99)
     assert L.fw_classify_ex(fake, ctypes.byref(hp), 8, fake, fake, None, ctypes.byref(cfg)) == fw.FW_EINVAL
+
+
+STRUCTS = ("fw_headers", "fw_config", "fw_lindex_config", "fw_lindex_stats", "fw_job", "fw_plan_config",
+           "fw_server_config", "fw_server_stats", "fw_request")
+
+
+def test_binding_structs_match_header(tmp_path):
+    """Every ctypes struct of the binding has the header's size and field offsets (gcc's view)."""
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "fw.h"', "int main(void) {"]
+    want = []
+    for name in STRUCTS:
+        cls = getattr(fw, name)
+        lines.append(f'printf("%zu\\n", sizeof({name}));')
+        want.append(ctypes.sizeof(cls))
+        for field, _ in cls._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({name}, {field}));')
+            want.append(getattr(cls, field).offset)
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got == want
