@@ -120,9 +120,11 @@ typedef struct fw_headers {
  *  packets_per_group: rule split: packets handled together by one warp group
  *                     (default 64 for warp and grid mode, 256 for block mode);
  *                     packet split with compaction: queue entries per warp
- *                     batch (multiple of 128, default 256; with two packets
- *                     per lane a batch holds up to 4 or 8 fewer packets, room
- *                     for the protocol class pads).
+ *                     batch (multiple of 128, default 256, or 128 when the
+ *                     batch would not give every resident warp a full
+ *                     256-entry queue; with two packets per lane a batch
+ *                     holds up to 4 or 8 fewer packets, room for the class
+ *                     pads).
  *  rule_slices:       number of rule slices across the grid (RULE_SPLIT_GRID,
  *                     default 8).
  *  compact:           packet split only: 1 = per-warp queues that re-pack

@@ -382,6 +382,14 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
     want = (want / kChunkRules) * kChunkRules;
     p.n_smem = std::min(want, need_all);
     p.batch = cfg.packets_per_group > 0 ? cfg.packets_per_group : 256;
+    if (compact && cfg.packets_per_group <= 0) {
+        // a batch too small to fill every resident warp's 256-entry queue takes 128-entry
+        // queues: twice the warps get packets (1K rules x 100K packets: 101 blocks on 152 SMs
+        // with 256 entries, 201 with 128)
+        const int pads = lane2 ? ((rs->n_classes + 3) & ~3) : 0;
+        const int64_t warps = (int64_t)sm_count(rs->device) * per_sm * (threads / 32);
+        if ((n + warps - 1) / warps <= 128 - pads) p.batch = 128;
+    }
     if (compact && (p.batch % 128 != 0 || p.batch > 65536)) return FW_EINVAL;
     // First segment. With two packets per lane a segment boundary (a re-sort of every queued
     // packet) pays only when sub-lists are long enough for a long tail of deep packets: with the
