@@ -207,6 +207,36 @@ int64_t fw_ruleset_first_catch_all(const fw_ruleset *rs);
  */
 int fw_ruleset_partition(const fw_ruleset *rs, int32_t *n_classes, int32_t *key_field, int32_t *key_bits);
 
+#define FW_MAX_CLASSES 8
+
+/*
+ * The partition of rules[0, n) as given, computed on the host (no device
+ * work; usable without a GPU). fw_ruleset_create partitions its rules up to
+ * and including the first catch-all with granule 1; fw_lindex_create the rules
+ * it indexes with granule 128.
+ *  Protocol classes: the up to 7 exact protocols most used by the rules (ties
+ *  to the lower value), then "other" for every remaining protocol value. Each
+ *  is split by the top key_bits bits of the source (key_field 1) or destination
+ *  (2) address, key_bits 1..3, at most FW_MAX_CLASSES classes in all; class =
+ *  protocol class << key_bits | key. A class's sub-list keeps, in list order,
+ *  the rules that can match one of its packets (protocol "any" or the class's
+ *  protocol, or for "other" any protocol without a class of its own; an
+ *  address prefix that can hold the key), so a packet's first match is the
+ *  same in its sub-list as in the whole list.
+ *  granule: the key (or none) with the lowest mean per-class cost is taken,
+ *  the sub-list length for granule 1, else ceil(length / granule) and at least
+ *  1. Candidates go source before destination, fewer bits first; a later one
+ *  must be strictly lower, and none when no key is.
+ *  Outputs: n_classes, key_field, key_bits as fw_ruleset_partition;
+ *  class_len (FW_MAX_CLASSES entries, may be NULL): each class's sub-list
+ *  length, 0 past n_classes; proto_class (256 entries, may be NULL): the
+ *  protocol class of each protocol value.
+ * FW_EINVAL for rules NULL with n > 0, n < 0 or n > 2^30, granule < 1, an
+ * invalid rule (as fw_ruleset_create), or a NULL n_classes/key_field/key_bits.
+ */
+int fw_partition_plan(const fw_rule *rules, int64_t n, int32_t granule, int32_t *n_classes, int32_t *key_field,
+                      int32_t *key_bits, int64_t *class_len, uint8_t *proto_class);
+
 /*
  * Synchronise the device and report whether any kernel that used `rs` gave
  * up on a bounded wait since the last check (FW_ETIMEOUT; the flag is then

@@ -296,6 +296,30 @@ extern "C" int fw_ruleset_partition(const fw_ruleset *rs, int32_t *n_classes, in
     return FW_OK;
 }
 
+extern "C" int fw_partition_plan(const fw_rule *rules, int64_t n, int32_t granule, int32_t *n_classes,
+                                 int32_t *key_field, int32_t *key_bits, int64_t *class_len, uint8_t *proto_class) {
+    static_assert(FW_MAX_CLASSES == kMaxClasses, "public class bound");
+    if (n < 0 || (n > 0 && rules == nullptr) || n > (int64_t(1) << 30) || granule < 1 || n_classes == nullptr ||
+        key_field == nullptr || key_bits == nullptr)
+        return set_status(FW_EINVAL);
+    for (int64_t k = 0; k < n; ++k) {
+        const int s = validate_rule(rules[k]);
+        if (s != FW_OK) return set_status(s);
+    }
+    std::vector<uint8_t> class_of;
+    std::vector<std::vector<int64_t>> lists;
+    int kf = 0, kb = 0;
+    partition_lists(rules, n, granule, class_of, lists, kf, kb);
+    *n_classes = (int32_t)lists.size();
+    *key_field = kf;
+    *key_bits = kb;
+    if (class_len != nullptr)
+        for (int c = 0; c < kMaxClasses; ++c) class_len[c] = c < (int)lists.size() ? (int64_t)lists[c].size() : 0;
+    if (proto_class != nullptr)
+        for (int p = 0; p < 256; ++p) proto_class[p] = class_of[p];
+    return FW_OK;
+}
+
 extern "C" fw_ruleset *fw_ruleset_create(const fw_rule *rules, int64_t n) {
     fw_ruleset *rs = nullptr;
     fw_ruleset_create_ex(rules, n, &rs);

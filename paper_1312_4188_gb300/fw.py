@@ -133,6 +133,7 @@ SIGNATURES = {
     "fw_ruleset_size": (I64, [P]),
     "fw_ruleset_first_catch_all": (I64, [P]),
     "fw_ruleset_partition": (ctypes.c_int, [P, P, P, P]),
+    "fw_partition_plan": (ctypes.c_int, [P, I64, ctypes.c_int32, P, P, P, P, P]),
     "fw_ruleset_check": (ctypes.c_int, [P]),
     "fw_classify": (ctypes.c_int, [P, ctypes.POINTER(fw_headers), I64, P, P, P]),
     "fw_classify_ex": (ctypes.c_int, [P, ctypes.POINTER(fw_headers), I64, P, P, P, ctypes.POINTER(fw_config)]),
@@ -251,6 +252,21 @@ class Ruleset:
             self.destroy()
         except Exception:
             pass
+
+
+def fw_partition_plan(rules, granule: int = 1) -> dict:
+    """The partition of ``rules`` as given (host only): {"classes", "key_field", "key_bits",
+    "class_len" (per class), "proto_class" (256 protocol classes)}."""
+    r = _as_rules(rules)
+    a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    lens = np.zeros(8, dtype=np.int64)
+    pc = np.zeros(256, dtype=np.uint8)
+    s = lib().fw_partition_plan(r.ctypes.data_as(P) if r.size else None, int(r.shape[0]), int(granule),
+                                ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), lens.ctypes.data_as(P),
+                                pc.ctypes.data_as(P))
+    _check(s, "fw_partition_plan")
+    return {"classes": a.value, "key_field": b.value, "key_bits": c.value, "class_len": lens[:a.value].tolist(),
+            "proto_class": pc}
 
 
 def fw_ruleset_create(rules) -> Ruleset:

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
+import partition_ref as R
 from paper_1312_4188_gb300 import fw, workload as W
 
 pytestmark = pytest.mark.gpu
@@ -70,33 +71,6 @@ def test_golden_and_tiny_domain(torch_cuda):
         assert st["fallbacks"] == 0
 
 
-def class_sublists(rules, key_field, key_bits):
-    """Per class, the rules that can match one of its packets, in list order: the 7 exact
-    protocols most used then "other", each split by the top key_bits bits of one address
-    (a prefix shorter than the key covers every key it contains)."""
-    exact = rules["proto_any"] == 0
-    cnt = np.bincount(rules["proto"][exact].astype(np.int64), minlength=256)
-    order = sorted(np.nonzero(cnt)[0].tolist(), key=lambda p: (-cnt[p], p))[:7]
-    lists = []
-    for c in range(len(order) + 1):
-        if c < len(order):
-            pm = ~exact | (rules["proto"] == order[c])
-        else:
-            pm = ~exact | ~np.isin(rules["proto"], order)
-        keys = range(1 << key_bits) if key_field else [None]
-        for k in keys:
-            m = pm.copy()
-            if k is not None:
-                fld = "src" if key_field == 1 else "dst"
-                for j in np.nonzero(m)[0]:
-                    ln, a = int(rules[fld + "_prefix"][j]), int(rules[fld + "_addr"][j])
-                    lo = a & ((0xFFFFFFFF << (32 - ln)) & 0xFFFFFFFF) if ln else 0
-                    hi = lo | ((1 << (32 - ln)) - 1)
-                    m[j] = (lo >> (32 - key_bits)) <= k <= (hi >> (32 - key_bits))
-            lists.append(np.nonzero(m)[0])
-    return lists
-
-
 def test_stats_shape(torch_cuda):
     rules = no_catch_all(W.gen_rules(2000, 8))
     li = fw.fw_lindex_create(rules, truncate=2)
@@ -105,24 +79,18 @@ def test_stats_shape(torch_cuda):
     assert all(1 <= m <= 2 * len(rules) + 1 for m in st["intervals"])
     assert st["intervals"][4] <= 257
     # the scan's partition, keyed by what a packet here reads: whole 128-rule row words (at least
-    # one); the key (field 1..2, bits 1..3, at most 8 classes) with the lowest mean, none on a tie
-    def best_key(cost):
-        n_p = len(class_sublists(rules, 0, 0))
-        key, best = (0, 0), cost(class_sublists(rules, 0, 0))
-        for f in (1, 2):
-            for b in (1, 2, 3):
-                if n_p << b <= 8 and cost(class_sublists(rules, f, b)) < best:
-                    key, best = (f, b), cost(class_sublists(rules, f, b))
-        return key
-    words = best_key(lambda ls: np.mean([max(1, -(-len(x) // 128)) for x in ls]))
+    # one), the key with the lowest mean (partition_ref's definition; fw_partition_plan agrees)
+    words = R.best_key(rules, 128)
     assert (st["key_field"], st["key_bits"]) == words
+    plan = fw.fw_partition_plan(rules, 128)
+    assert (plan["key_field"], plan["key_bits"], plan["classes"]) == (*words, st["classes"])
     # the scan reads rules one at a time: its key minimises the mean length (here another key)
     rs = fw.fw_ruleset_create(rules)
     part = rs.partition()
     rs.destroy()
-    length = best_key(lambda ls: np.mean([len(x) for x in ls]))
+    length = R.best_key(rules, 1)
     assert (part["key_field"], part["key_bits"]) == length != words
-    lists = class_sublists(rules, st["key_field"], st["key_bits"])
+    lists = R.class_sublists(rules, *words)
     assert len(lists) == st["classes"]
     wpr = [max(4, -(-len(x) // 128) * 4) for x in lists]
     assert st["words_per_row"] == max(wpr)

@@ -235,9 +235,26 @@ def test_partition_key_on_destination(torch_cuda):
     rs = fw.fw_ruleset_create(rules)
     part = rs.partition()
     assert part["key_field"] == 2 and 1 <= part["key_bits"] <= 3 and part["classes"] <= 8
+    plan = fw.fw_partition_plan(rules, 1)  # the host-only plan of the same rules
+    assert (plan["classes"], plan["key_field"], plan["key_bits"]) == (part["classes"], part["key_field"],
+                                                                      part["key_bits"])
     hdr = W.gen_packets(rules, 300_000, 32)
     want = oracle.classify(rules, hdr, threads=THREADS)
     for kw in ({}, {"compact": 1}, {"compact": 1, "lane_packets": 1}, {"compact": 2, "partition": 1},
                {"compact": 1, "block_threads": 256, "segment_rules": 8}):
         assert_same(run_gpu(torch_cuda, rules, hdr, "packet_split", kw, rs=rs), want, f"dst key {kw}")
     rs.destroy()
+
+
+def test_partition_matches_host_plan_up_to_first_catch_all(torch_cuda):
+    """A rule set partitions its rules up to and including the first catch-all (no packet gets
+    past it): the plan of exactly those rules."""
+    rules = W.gen_rules(10_000, 3)
+    rs = fw.fw_ruleset_create(rules)
+    part = rs.partition()
+    ca = rs.first_catch_all
+    assert ca >= 0
+    plan = fw.fw_partition_plan(rules[:ca + 1], 1)
+    rs.destroy()
+    assert (plan["classes"], plan["key_field"], plan["key_bits"]) == (part["classes"], part["key_field"],
+                                                                      part["key_bits"])
