@@ -146,3 +146,102 @@ def test_binding_structs_match_header(tmp_path):
     subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     assert got == want
+
+
+def _cfg(cls, **kw):
+    c = cls()
+    for k, v in kw.items():
+        if isinstance(v, tuple):
+            getattr(c, k)[0] = v[0]
+        else:
+            setattr(c, k, v)
+    return c
+
+
+def test_plan_rejects_bad_arguments(L):
+    out = ctypes.c_void_p()
+    assert L.fw_plan_create(None, 0, None, None) == fw.FW_EINVAL
+    assert L.fw_plan_create(None, -1, None, ctypes.byref(out)) == fw.FW_EINVAL
+    assert L.fw_plan_create(None, 2, None, ctypes.byref(out)) == fw.FW_EINVAL
+    # shared memory: 32 warps x 4,096 queue entries x 16 B is past the 227 KB a block may hold
+    for kw in ({"n_classes": 5}, {"packets_per_item": (100,)}, {"packets_per_item": (8192,)},
+               {"segment_rules": (6,)}, {"block_threads": 48}, {"block_threads": 2048},
+               {"block_threads": 1024, "packets_per_item": (4096,)}):
+        cfg = _cfg(fw.fw_plan_config, **kw)
+        assert L.fw_plan_create(None, 0, ctypes.byref(cfg), ctypes.byref(out)) == fw.FW_EINVAL, kw
+        assert out.value is None
+    jobs = (fw.fw_job * 1)()
+    jobs[0].n = 10  # no rule set
+    assert L.fw_plan_create(jobs, 1, None, ctypes.byref(out)) == fw.FW_EINVAL
+    assert L.fw_plan_launch(None, None) == fw.FW_EINVAL
+    assert L.fw_plan_launch_graph(None, None) == fw.FW_EINVAL
+    assert L.fw_plan_items(None) == -1
+    L.fw_plan_destroy(None)
+
+
+def test_lindex_rejects_bad_arguments(L):
+    out = ctypes.c_void_p()
+    r = np.ascontiguousarray(W.gen_rules(10, 1))
+    ptr = r.ctypes.data_as(ctypes.c_void_p)
+    assert L.fw_lindex_create(ptr, 10, None, None) == fw.FW_EINVAL
+    assert L.fw_lindex_create(None, 5, None, ctypes.byref(out)) == fw.FW_EINVAL
+    assert L.fw_lindex_create(ptr, -1, None, ctypes.byref(out)) == fw.FW_EINVAL
+    for kw in ({"segments": 3}, {"segments": 1 << 17}, {"truncate": 3}, {"truncate": -1}):
+        cfg = _cfg(fw.fw_lindex_config, **kw)
+        assert L.fw_lindex_create(ptr, 10, ctypes.byref(cfg), ctypes.byref(out)) == fw.FW_EINVAL, kw
+    bad = r.copy()
+    bad["sport_lo"][2], bad["sport_hi"][2] = 9, 3
+    assert L.fw_lindex_create(bad.ctypes.data_as(ctypes.c_void_p), 10, None, ctypes.byref(out)) == fw.FW_EINVAL
+    assert out.value is None
+    fake = ctypes.c_void_p(1)  # never dereferenced: argument checks come first
+    h = fw.fw_headers()
+    assert L.fw_lindex_classify(None, ctypes.byref(h), 10, None, None, None) == fw.FW_EINVAL
+    assert L.fw_lindex_classify(fake, ctypes.byref(h), -1, None, None, None) == fw.FW_EINVAL
+    assert L.fw_lindex_classify(fake, ctypes.byref(h), 0, None, None, None) == fw.FW_OK
+    assert L.fw_lindex_classify(fake, ctypes.byref(h), 10, None, None, None) == fw.FW_EINVAL
+    assert L.fw_lindex_get_stats(None, None) == fw.FW_EINVAL
+    L.fw_lindex_destroy(None)
+
+
+def test_server_rejects_bad_arguments(L):
+    out = ctypes.c_void_p()
+    sets = (ctypes.c_void_p * 2)(1, 1)  # never dereferenced: configuration checks come first
+    nulls = (ctypes.c_void_p * 2)(None, None)
+    assert L.fw_server_create(sets, 2, None, None) == fw.FW_EINVAL
+    assert L.fw_server_create(sets, 0, None, ctypes.byref(out)) == fw.FW_EINVAL
+    assert L.fw_server_create(None, 2, None, ctypes.byref(out)) == fw.FW_EINVAL
+    assert L.fw_server_create(nulls, 2, None, ctypes.byref(out)) == fw.FW_EINVAL
+    for kw in ({"mode": 3}, {"slots": 17}, {"slots": -1}, {"max_group_requests": -1}, {"max_pending": -1},
+               {"max_group_packets": -1}, {"arena_bytes": 1000}, {"packets_per_item": 100},
+               {"packets_per_item": 8192}, {"segment_rules": 6}, {"block_threads": 33}, {"block_threads": 2048},
+               {"block_threads": 1024, "packets_per_item": 4096}):
+        cfg = _cfg(fw.fw_server_config, **kw)
+        assert L.fw_server_create(sets, 2, ctypes.byref(cfg), ctypes.byref(out)) == fw.FW_EINVAL, kw
+        assert out.value is None
+    ticket = ctypes.c_uint64()
+    h = fw.fw_headers()
+    assert L.fw_server_submit(None, 0, ctypes.byref(h), 10, None, None, ctypes.byref(ticket)) == fw.FW_EINVAL
+    assert L.fw_server_wait(None, 1, 0, None) == fw.FW_EINVAL
+    assert L.fw_server_drain(None, 0) == fw.FW_EINVAL
+    assert L.fw_server_get_stats(None, None) == fw.FW_EINVAL
+    assert L.fw_server_register_buffer(None, None, 0) == fw.FW_EINVAL
+    assert L.fw_server_unregister_buffer(None, None) == fw.FW_EINVAL
+    assert L.fw_server_replay(None, None, 0, 0) == fw.FW_EINVAL
+    L.fw_server_destroy(None)
+
+
+def test_host_pipeline_rejects_bad_arguments(L):
+    out = ctypes.c_void_p()
+    assert L.fw_host_pipeline_create(0, 0, None) == fw.FW_EINVAL
+    assert L.fw_host_pipeline_create(-1, 0, ctypes.byref(out)) == fw.FW_EINVAL
+    assert L.fw_host_pipeline_create(0, 9, ctypes.byref(out)) == fw.FW_EINVAL
+    assert L.fw_host_pipeline_create(0, -1, ctypes.byref(out)) == fw.FW_EINVAL
+    fake = ctypes.c_void_p(1)  # never dereferenced: argument checks come first
+    h = fw.fw_headers()
+    copy = fw.FW_HOST_COPY
+    assert L.fw_classify_host(None, fake, ctypes.byref(h), 10, None, None, copy, None) == fw.FW_EINVAL
+    assert L.fw_classify_host(fake, None, ctypes.byref(h), 10, None, None, copy, None) == fw.FW_EINVAL
+    assert L.fw_classify_host(fake, fake, ctypes.byref(h), -1, None, None, copy, None) == fw.FW_EINVAL
+    assert L.fw_classify_host(fake, fake, ctypes.byref(h), 0, None, None, copy, None) == fw.FW_OK
+    assert L.fw_classify_host(fake, fake, ctypes.byref(h), 10, None, None, copy, None) == fw.FW_EINVAL
+    L.fw_host_pipeline_destroy(None)
