@@ -46,7 +46,7 @@ FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "sms": 152}
 KERNEL_SOURCES = ["paper_1312_4188_gb300/csrc/fw_scan.cu", "paper_1312_4188_gb300/csrc/fw_scan.cuh",
                   "paper_1312_4188_gb300/csrc/fw_internal.cuh"]
 # the kernel the default (auto) configuration launches for this workload: the compacting scan of
-# the protocol-partitioned lists with two packets per lane
+# the partitioned lists (protocol class and address key) with two packets per lane
 KERNEL_NAME = "k_packet_split_compact_x2"
 TRAFFIC_RECORD = "profiles/k_packet_split_compact_x2_scan_10k_x_16m.md"
 TRAFFIC_WORKLOAD = "scan_10k_x_16m_zipf"  # the workload and mode (auto) the record was captured on
@@ -290,8 +290,8 @@ def main():
 
     value = ws * n * args.steps / (total_ms * 1e-3) / 1e6
     checks_per_s = depth_sum / (mean_launch_ms * 1e-3)
-    # the default packet split scans the packet's protocol sub-list: its algorithmic work is the
-    # rules of that sub-list up to the match, which is what the roofline counts
+    # the default packet split scans the sub-list of the packet's partition class: its algorithmic
+    # work is the rules of that sub-list up to the match, which is what the roofline counts
     partitioned = args.mode in ("auto", "packet_split")
     part = rs.partition()
     scan_sum = (partition_depth(rules, out_idx.cpu().numpy(), hdr, part["key_field"], part["key_bits"])
@@ -322,8 +322,8 @@ def main():
         "rule_checks_per_s": checks_per_s,
         "scan_checks_per_s": scan_checks_per_s,
         "rule_checks_note": ("rule_checks_per_s counts first-match index + 1 (N if unmatched) per packet over "
-                             "the whole list; scan_checks_per_s counts the rules of the packet's protocol "
-                             "sub-list that the partitioned scan examines (the roofline numerator)"),
+                             "the whole list; scan_checks_per_s counts the rules of the sub-list of the packet's "
+                             "partition class that the partitioned scan examines (the roofline numerator)"),
         "latency_ms": {"launch_p50": per[len(per) // 2], "launch_p99": per[min(len(per) - 1, int(0.99 * len(per)))],
                        "launch_mean": mean_launch_ms, "packets_per_launch": n},
         "workload_stats": {"first_catch_all": rs.first_catch_all, "mean_depth": depth_sum / n,

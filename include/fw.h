@@ -136,7 +136,7 @@ typedef struct fw_headers {
  *                     (0 = default, the arithmetic form).
  *  segment_rules:     packet split with compaction: rules in the first segment
  *                     (multiple of 4; later segments double). Default: with two
- *                     packets per lane 512, or 32 when the longest protocol
+ *                     packets per lane 512, or 32 when the longest class
  *                     sub-list exceeds 2,048 rules; with one packet per lane 64
  *                     (partitioned) or 16 (whole list).
  *  partition:         packet split, arithmetic form: 1 = scan the partition

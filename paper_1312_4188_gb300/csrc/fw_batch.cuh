@@ -6,8 +6,9 @@
 
 namespace fwk {
 
-// One job of a batched launch: its rule set's protocol partition (the
-// concatenated sub-lists in the arithmetic form), its headers and outputs.
+// One job of a batched launch: its rule set's partition (protocol classes and
+// address key; the concatenated sub-lists in the arithmetic form), its headers
+// and outputs.
 struct BatchJobDev {
     const RecArith *rec;
     const uint32_t *wtop;
