@@ -245,3 +245,14 @@ def test_host_pipeline_rejects_bad_arguments(L):
     assert L.fw_classify_host(fake, fake, ctypes.byref(h), 0, None, None, copy, None) == fw.FW_OK
     assert L.fw_classify_host(fake, fake, ctypes.byref(h), 10, None, None, copy, None) == fw.FW_EINVAL
     L.fw_host_pipeline_destroy(None)
+
+
+@pytest.mark.parametrize("lang", ["c", "c++"])
+def test_header_compiles_alone_without_warnings(tmp_path, lang):
+    """include/fw.h is self-contained and warning-free as strict C11 and C++17."""
+    src = tmp_path / ("h.c" if lang == "c" else "h.cpp")
+    src.write_text('#include "fw.h"\nint main(void) { return (int)sizeof(fw_rule) - 24; }\n')
+    cc, std = ("gcc", "-std=c11") if lang == "c" else ("g++", "-std=c++17")
+    subprocess.run([cc, std, "-Wall", "-Wextra", "-Wpedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-o", str(tmp_path / "h")], check=True)
+    assert subprocess.run([str(tmp_path / "h")]).returncode == 0
