@@ -72,3 +72,32 @@ def test_sample_positions():
     assert len(np.unique(pos)) == 100 and pos.min() >= 0 and pos.max() < 1000
     assert np.array_equal(pos, W.sample_positions(1000, 100, 3))
     assert np.array_equal(W.sample_positions(10, 100, 3), np.arange(10))
+
+
+def test_permuted_zipf_ranks_name_the_permuted_rules():
+    """With rank_perm the Zipf rank r draws rule rank_perm[r]. On pairwise non-overlapping rules a
+    packet drawn inside a rule matches that rule alone, so the oracle's index recovers the draw."""
+    import oracle
+    rules = P.non_overlapping_rules(40, 12)
+    n = len(rules)
+    perm = np.random.default_rng(5).permutation(n)
+    hdr = W.gen_packets(rules, 200_000, 6, in_rule_frac=1.0, zipf_s=1.1, rank_perm=perm)
+    idx, _, _ = oracle.classify(rules, hdr)
+    assert (idx >= 0).all()
+    by_rank = np.bincount(idx, minlength=n)[perm]  # matches per Zipf rank
+    p = np.arange(1, n + 1, dtype=float) ** -1.1
+    p /= p.sum()
+    # every rank's share within 5 standard deviations of its Zipf probability
+    sd = np.sqrt(p * (1 - p) / len(idx))
+    assert np.all(np.abs(by_rank / len(idx) - p) < 5 * sd + 1e-9)
+    assert by_rank[0] == by_rank.max() and perm[0] != 0  # the top rank is not the first rule here
+
+
+def test_without_catch_alls_removes_exactly_the_catch_alls():
+    rules = W.gen_rules(5000, 3)
+    ca = np.array([P.rule_sets(r) == P.rule_sets(P.catch_all()[0]) for r in rules])
+    kept = W.without_catch_alls(rules)
+    assert ca.sum() > 0 and len(kept) == len(rules) - ca.sum()
+    assert np.array_equal(kept, rules[~ca])  # list order kept
+    r2, _ = W.make_workload("scan_10k_x_16m_no_catch_all", 1000)
+    assert not any(P.rule_sets(r) == P.rule_sets(P.catch_all()[0]) for r in r2)
