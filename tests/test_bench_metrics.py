@@ -55,3 +55,35 @@ def test_partition_depth_matches_explicit_sublists(key_field, key_bits):
         idx, _, _ = oracle.classify(rules, h)
         assert bench.partition_depth(rules, idx, h, key_field, key_bits) == \
             explicit_partition_depth(rules, idx, h, key_field, key_bits)
+
+
+def test_partition_depth_follows_the_library_plan():
+    """For an unmatched packet the metric counts its whole sub-list: that length equals the class
+    length in the library's own plan (fw_partition_plan) of the rules up to the first catch-all,
+    for the key the library picks."""
+    import partition_ref as R
+    from paper_1312_4188_gb300 import fw
+    keys = set()
+    # five protocol classes leave no room for a key; four (the generator's protocols) leave one bit
+    for seed, n_rules, extra_proto in ((1, 300, True), (4, 2000, False), (5, 1000, False)):
+        rules = W.gen_rules(n_rules, seed)
+        if extra_proto:
+            rules["proto"][::7] = 47
+            rules["proto_any"][::7] = 0
+        ca = np.nonzero((rules["src_prefix"] == 0) & (rules["dst_prefix"] == 0) & (rules["sport_lo"] == 0)
+                        & (rules["sport_hi"] == 65535) & (rules["dport_lo"] == 0) & (rules["dport_hi"] == 65535)
+                        & (rules["proto_any"] != 0))[0]
+        n_eff = int(ca[0]) + 1 if len(ca) else len(rules)
+        plan = fw.fw_partition_plan(rules[:n_eff], 1)
+        kf, kb = plan["key_field"], plan["key_bits"]
+        keys.add((kf, kb))
+        for proto in (0, 1, 6, 17, 47, 99, 255):
+            for top in range(8):
+                h = W.empty_headers(1)
+                h["proto"][0] = proto
+                h["src"][0] = (top << 29) | 12345
+                h["dst"][0] = ((7 - top) << 29) | 678
+                c = int(R.packet_class(h, plan["proto_class"], kf, kb)[0])
+                got = bench.partition_depth(rules, np.array([-1], dtype=np.int32), h, kf, kb)
+                assert got == plan["class_len"][c], (seed, proto, top)
+    assert (0, 0) in keys and any(k != (0, 0) for k in keys)
