@@ -190,7 +190,9 @@ def run_reference(args, ws, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": args.workload, "rules": w["n_rules"], "packets": w["n_packets"]},
+        "config": {"workload": args.workload, "rules": w["n_rules"], "packets": w["n_packets"],
+                   "zipf_s": w["zipf_s"], "rules_seed": w["rules_seed"], "packets_seed": w["packets_seed"],
+                   "parallelism": f"CPU oracle on {cores} host threads"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{m} packets at fixed seeded positions of the {w['n_packets']}-packet batch per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
