@@ -576,6 +576,19 @@ int fw_classify_rule_split_noalloc(const fw_ruleset *rs, const fw_headers *hdrs,
  */
 int fw_selftest_wait_timeout(fw_ruleset *rs, int64_t limit_ns, void *stream);
 
+/*
+ * Test hook for allocation failure, injected on the host (no GPU fault). The
+ * (n+1)-th device or pinned host allocation that a create call makes from now
+ * on fails once as if memory ran out, and the hook then disarms; n < 0
+ * disarms it. Create calls are fw_ruleset_create(_ex), fw_lindex_create,
+ * fw_plan_create, fw_server_create and fw_host_pipeline_create. The failing
+ * call frees what it holds and returns FW_ENOMEM with a NULL handle.
+ * Classify-time scratch (the grid rule split's) is not counted.
+ * Process-wide; the counter is atomic, but which of several concurrent creates
+ * meets the failure is not defined. Returns FW_OK.
+ */
+int fw_selftest_fail_alloc(int64_t n);
+
 /* ------------------------------------------------------------ misc */
 int fw_last_status(void);                 /* status of the last failed short-form call on this thread */
 const char *fw_status_string(int status); /* static string, never NULL */

@@ -16,6 +16,7 @@
 #include <cstring>
 #include <vector>
 
+#include "fw_alloc.h"
 #include "fw_batch.cuh"
 
 namespace fwk {
@@ -204,9 +205,9 @@ extern "C" int fw_plan_create(const fw_job *jobs, int64_t n_jobs, const fw_plan_
     const int per_sm = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : 2;
     pl->blocks = std::max<int64_t>(
         1, std::min<int64_t>((int64_t)sm_count(pl->device) * per_sm, (pl->n_items + threads / 32 - 1) / (threads / 32)));
-    cudaError_t e = cudaMalloc(&pl->d_jobs, std::max<size_t>(1, hj.size()) * sizeof(BatchJobDev));
-    if (e == cudaSuccess) e = cudaMalloc(&pl->d_items, std::max<size_t>(1, items.size()) * sizeof(BatchItem));
-    if (e == cudaSuccess) e = cudaMalloc(&pl->d_next, sizeof(unsigned long long));
+    cudaError_t e = dev_malloc(&pl->d_jobs, std::max<size_t>(1, hj.size()) * sizeof(BatchJobDev));
+    if (e == cudaSuccess) e = dev_malloc(&pl->d_items, std::max<size_t>(1, items.size()) * sizeof(BatchItem));
+    if (e == cudaSuccess) e = dev_malloc(&pl->d_next, sizeof(unsigned long long));
     if (e == cudaSuccess && !hj.empty())
         e = cudaMemcpy(pl->d_jobs, hj.data(), hj.size() * sizeof(BatchJobDev), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !items.empty())

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cstring>
 
+#include "fw_alloc.h"
 #include "fw_internal.cuh"
 
 struct fw_host_pipeline {
@@ -57,13 +58,13 @@ extern "C" int fw_host_pipeline_create(int64_t chunk_packets, int n_streams, fw_
     const size_t c = (size_t)pl->chunk;
     for (int s = 0; s < pl->nstreams && e == cudaSuccess; ++s) {
         e = cudaStreamCreateWithFlags(&pl->st[s], cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaMalloc(&pl->d_src[s], c * 4);
-        if (e == cudaSuccess) e = cudaMalloc(&pl->d_dst[s], c * 4);
-        if (e == cudaSuccess) e = cudaMalloc(&pl->d_sport[s], c * 2);
-        if (e == cudaSuccess) e = cudaMalloc(&pl->d_dport[s], c * 2);
-        if (e == cudaSuccess) e = cudaMalloc(&pl->d_proto[s], c);
-        if (e == cudaSuccess) e = cudaMalloc(&pl->d_idx[s], c * 4);
-        if (e == cudaSuccess) e = cudaMalloc(&pl->d_act[s], c);
+        if (e == cudaSuccess) e = dev_malloc(&pl->d_src[s], c * 4);
+        if (e == cudaSuccess) e = dev_malloc(&pl->d_dst[s], c * 4);
+        if (e == cudaSuccess) e = dev_malloc(&pl->d_sport[s], c * 2);
+        if (e == cudaSuccess) e = dev_malloc(&pl->d_dport[s], c * 2);
+        if (e == cudaSuccess) e = dev_malloc(&pl->d_proto[s], c);
+        if (e == cudaSuccess) e = dev_malloc(&pl->d_idx[s], c * 4);
+        if (e == cudaSuccess) e = dev_malloc(&pl->d_act[s], c);
     }
     if (e != cudaSuccess) {
         fw_host_pipeline_destroy(pl);

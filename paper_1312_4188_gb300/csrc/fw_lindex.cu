@@ -32,6 +32,7 @@
 #include <cstring>
 #include <vector>
 
+#include "fw_alloc.h"
 #include "fw_internal.cuh"
 #include "fw_lindex_fit.h"
 
@@ -317,12 +318,12 @@ extern "C" int fw_lindex_create(const fw_rule *rules, int64_t n, const fw_lindex
     cudaError_t e = cudaSuccess;
     std::vector<uint8_t> act((size_t)std::max<int64_t>(li->n_idx, 1), FW_DROP);
     for (int64_t k = 0; k < li->n_idx; ++k) act[k] = rules[k].action;
-    e = cudaMalloc(&li->d_class_of, 256);
+    e = dev_malloc(&li->d_class_of, 256);
     if (e == cudaSuccess) e = cudaMemcpy(li->d_class_of, class_of.data(), 256, cudaMemcpyHostToDevice);
     for (int c = 0; c < li->n_classes && e == cudaSuccess; ++c) {
         std::vector<int32_t> orig((size_t)hcls[c].W * 32, -1);
         for (size_t b = 0; b < lists[c].size(); ++b) orig[b] = (int32_t)lists[c][b];
-        e = cudaMalloc(&li->d_orig[c], orig.size() * sizeof(int32_t));
+        e = dev_malloc(&li->d_orig[c], orig.size() * sizeof(int32_t));
         if (e == cudaSuccess)
             e = cudaMemcpy(li->d_orig[c], orig.data(), orig.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     }
@@ -331,15 +332,15 @@ extern "C" int fw_lindex_create(const fw_rule *rules, int64_t n, const fw_lindex
         cudaGetLastError();
         return set_status(cuda_status(e));
     }
-    if (e == cudaSuccess) e = cudaMalloc(&li->d_action, act.size());
+    if (e == cudaSuccess) e = dev_malloc(&li->d_action, act.size());
     if (e == cudaSuccess) e = cudaMemcpy(li->d_action, act.data(), act.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&li->d_fallbacks, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = dev_malloc(&li->d_fallbacks, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(li->d_fallbacks, 0, sizeof(unsigned long long));
     uint32_t *d_rlo = nullptr, *d_rhi = nullptr;
     size_t nr = 1;
     for (const auto &L : lists) nr = std::max(nr, L.size());
-    if (e == cudaSuccess) e = cudaMalloc(&d_rlo, nr * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&d_rhi, nr * 4);
+    if (e == cudaSuccess) e = dev_malloc(&d_rlo, nr * 4);
+    if (e == cudaSuccess) e = dev_malloc(&d_rhi, nr * 4);
     std::vector<uint32_t> rlo((size_t)std::max<int64_t>(li->n_idx, 1)), rhi(rlo.size()), clo(nr), chi(nr);
     for (int f = 0; f < kFields && e == cudaSuccess; ++f) {
         const int bits = kKeyBits[f];
@@ -367,8 +368,8 @@ extern "C" int fw_lindex_create(const fw_rule *rules, int64_t n, const fw_lindex
         std::vector<float> A, Bc;
         std::vector<int32_t> E;
         fit_field(B, bits, nseg, li->shift[f], A, Bc, E, li->max_err[f]);
-        e = cudaMalloc(&li->d_bound[f], M * 4);
-        if (e == cudaSuccess) e = cudaMalloc(&li->d_model[f], nseg * sizeof(float4));
+        e = dev_malloc(&li->d_bound[f], M * 4);
+        if (e == cudaSuccess) e = dev_malloc(&li->d_model[f], nseg * sizeof(float4));
         if (e == cudaSuccess) e = cudaMemcpy(li->d_bound[f], B.data(), M * 4, cudaMemcpyHostToDevice);
         std::vector<float4> model((size_t)nseg);
         for (int s = 0; s < nseg; ++s) {
@@ -386,7 +387,7 @@ extern "C" int fw_lindex_create(const fw_rule *rules, int64_t n, const fw_lindex
                 clo[b] = rlo[lists[c][b]];
                 chi[b] = rhi[lists[c][b]];
             }
-            e = cudaMalloc(&li->d_bits[c][f], (size_t)M * W * 4);
+            e = dev_malloc(&li->d_bits[c][f], (size_t)M * W * 4);
             if (e == cudaSuccess && nc > 0) e = cudaMemcpy(d_rlo, clo.data(), nc * 4, cudaMemcpyHostToDevice);
             if (e == cudaSuccess && nc > 0) e = cudaMemcpy(d_rhi, chi.data(), nc * 4, cudaMemcpyHostToDevice);
             if (e == cudaSuccess) {
@@ -400,7 +401,7 @@ extern "C" int fw_lindex_create(const fw_rule *rules, int64_t n, const fw_lindex
             li->bitmap_bytes += (int64_t)M * W * 4;
         }
     }
-    if (e == cudaSuccess) e = cudaMalloc(&li->d_cls, hcls.size() * sizeof(LiClassDev));
+    if (e == cudaSuccess) e = dev_malloc(&li->d_cls, hcls.size() * sizeof(LiClassDev));
     if (e == cudaSuccess)
         e = cudaMemcpy(li->d_cls, hcls.data(), hcls.size() * sizeof(LiClassDev), cudaMemcpyHostToDevice);
     cudaFree(d_rlo);

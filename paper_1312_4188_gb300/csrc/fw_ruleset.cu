@@ -7,15 +7,30 @@
 // catch-all rule (all five fields wildcards): under first match (Sec. I) no
 // packet is ever decided by a rule after it, so scans stop there.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <vector>
 
+#include "fw_alloc.h"
 #include "fw_internal.cuh"
 
 namespace fwk {
 
 static thread_local int g_last_status = FW_OK;
+
+// Allocation-failure injection (fw_selftest_fail_alloc): allocations left
+// before the one that fails, or -1 when disarmed.
+static std::atomic<int64_t> g_fail_after{-1};
+
+bool take_injected_alloc_failure() {
+    int64_t k = g_fail_after.load(std::memory_order_relaxed);
+    while (k >= 0) {
+        if (g_fail_after.compare_exchange_weak(k, k == 0 ? -1 : k - 1, std::memory_order_relaxed))
+            return k == 0;
+    }
+    return false;
+}
 
 int set_status(int s) {
     if (s != FW_OK) g_last_status = s;
@@ -245,19 +260,19 @@ extern "C" int fw_ruleset_create_ex(const fw_rule *rules, int64_t n, fw_ruleset 
         part_class_of = class_of;
     }
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMalloc(&rs->d_clamp, rs->n_pad * sizeof(RecClamp));
-    if (e == cudaSuccess) e = cudaMalloc(&rs->d_cmp, rs->n_pad * sizeof(RecCmp));
-    if (e == cudaSuccess) e = cudaMalloc(&rs->d_arith, rs->n_pad * sizeof(RecArith));
-    if (e == cudaSuccess) e = cudaMalloc(&rs->d_wtop, rs->n_pad * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&rs->d_range, rs->n_pad * sizeof(RecRange));
-    if (e == cudaSuccess) e = cudaMalloc(&rs->d_range_wtop, rs->n_pad * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&rs->d_part, rs->part_pad * sizeof(RecArith));
-    if (e == cudaSuccess) e = cudaMalloc(&rs->d_part_wtop, rs->part_pad * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&rs->d_part_orig, rs->part_pad * sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&rs->d_part_verdict, rs->part_pad * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&rs->d_class_of, 256);
-    if (e == cudaSuccess) e = cudaMalloc(&rs->d_action, rs->n_pad);
-    if (e == cudaSuccess) e = cudaMalloc(&rs->d_status, sizeof(unsigned));
+    if (e == cudaSuccess) e = dev_malloc(&rs->d_clamp, rs->n_pad * sizeof(RecClamp));
+    if (e == cudaSuccess) e = dev_malloc(&rs->d_cmp, rs->n_pad * sizeof(RecCmp));
+    if (e == cudaSuccess) e = dev_malloc(&rs->d_arith, rs->n_pad * sizeof(RecArith));
+    if (e == cudaSuccess) e = dev_malloc(&rs->d_wtop, rs->n_pad * sizeof(uint32_t));
+    if (e == cudaSuccess) e = dev_malloc(&rs->d_range, rs->n_pad * sizeof(RecRange));
+    if (e == cudaSuccess) e = dev_malloc(&rs->d_range_wtop, rs->n_pad * sizeof(uint32_t));
+    if (e == cudaSuccess) e = dev_malloc(&rs->d_part, rs->part_pad * sizeof(RecArith));
+    if (e == cudaSuccess) e = dev_malloc(&rs->d_part_wtop, rs->part_pad * sizeof(uint32_t));
+    if (e == cudaSuccess) e = dev_malloc(&rs->d_part_orig, rs->part_pad * sizeof(int32_t));
+    if (e == cudaSuccess) e = dev_malloc(&rs->d_part_verdict, rs->part_pad * sizeof(uint32_t));
+    if (e == cudaSuccess) e = dev_malloc(&rs->d_class_of, 256);
+    if (e == cudaSuccess) e = dev_malloc(&rs->d_action, rs->n_pad);
+    if (e == cudaSuccess) e = dev_malloc(&rs->d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemcpy(rs->d_clamp, hc.data(), rs->n_pad * sizeof(RecClamp), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(rs->d_cmp, hm.data(), rs->n_pad * sizeof(RecCmp), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(rs->d_arith, hq.data(), rs->n_pad * sizeof(RecArith), cudaMemcpyHostToDevice);
@@ -293,6 +308,11 @@ extern "C" int fw_ruleset_partition(const fw_ruleset *rs, int32_t *n_classes, in
     *n_classes = rs->n_classes;
     *key_field = rs->key_field;
     *key_bits = rs->key_bits;
+    return FW_OK;
+}
+
+extern "C" int fw_selftest_fail_alloc(int64_t n) {
+    g_fail_after.store(n < 0 ? -1 : n, std::memory_order_relaxed);
     return FW_OK;
 }
 

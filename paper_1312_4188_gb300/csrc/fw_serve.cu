@@ -27,6 +27,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "fw_alloc.h"
 #include "fw_batch.cuh"
 
 namespace fwk {
@@ -427,18 +428,18 @@ extern "C" int fw_server_create(const fw_ruleset *const *sets, int n_sets, const
     cudaError_t e = prepare_batch_kernel(smem);
     if (e == cudaSuccess && c.mode == FW_HOST_COPY) {
         sv->arena_bytes = (size_t)c.arena_bytes;
-        e = cudaMalloc(&sv->d_arena, sv->arena_bytes);
+        e = dev_malloc(&sv->d_arena, sv->arena_bytes);
         sv->free_blocks[0] = sv->arena_bytes;
     }
     sv->slots.resize(c.slots);
     for (SvSlot &sl : sv->slots) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaMalloc(&sl.d_jobs, c.max_group_requests * sizeof(BatchJobDev));
-        if (e == cudaSuccess) e = cudaMalloc(&sl.d_items, sv->item_cap * sizeof(BatchItem));
-        if (e == cudaSuccess) e = cudaMalloc(&sl.d_next, sizeof(unsigned long long));
-        if (e == cudaSuccess) e = cudaMallocHost(&sl.h_jobs, c.max_group_requests * sizeof(BatchJobDev));
-        if (e == cudaSuccess) e = cudaMallocHost(&sl.h_items, sv->item_cap * sizeof(BatchItem));
+        if (e == cudaSuccess) e = dev_malloc(&sl.d_jobs, c.max_group_requests * sizeof(BatchJobDev));
+        if (e == cudaSuccess) e = dev_malloc(&sl.d_items, sv->item_cap * sizeof(BatchItem));
+        if (e == cudaSuccess) e = dev_malloc(&sl.d_next, sizeof(unsigned long long));
+        if (e == cudaSuccess) e = pinned_malloc(&sl.h_jobs, c.max_group_requests * sizeof(BatchJobDev));
+        if (e == cudaSuccess) e = pinned_malloc(&sl.h_items, sv->item_cap * sizeof(BatchItem));
     }
     if (e != cudaSuccess) {
         fw_server_destroy(sv);

@@ -142,6 +142,7 @@ SIGNATURES = {
     "fw_classify_host": (ctypes.c_int, [P, P, ctypes.POINTER(fw_headers), I64, P, P, ctypes.c_int,
                                         ctypes.POINTER(fw_config)]),
     "fw_selftest_wait_timeout": (ctypes.c_int, [P, I64, P]),
+    "fw_selftest_fail_alloc": (ctypes.c_int, [I64]),
     "fw_classify_rule_split_noalloc": (ctypes.c_int, [P, ctypes.POINTER(fw_headers), I64, P, P, P,
                                                       ctypes.POINTER(fw_config)]),
     "fw_lindex_create": (ctypes.c_int, [P, I64, ctypes.POINTER(fw_lindex_config), ctypes.POINTER(P)]),
