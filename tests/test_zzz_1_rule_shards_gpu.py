@@ -3,7 +3,8 @@
 Each virtual rank's rule range is its own CUDA rule set, classified by fw_classify; the ranks'
 global first matches combine by an elementwise minimum (what all_reduce MIN does across GPUs)
 and the action comes from the whole list's table. The result must equal the whole-list
-classification bit for bit, and the oracle on a fixed sample.
+classification bit for bit, and the oracle on a fixed sample. This file is collected after the
+other GPU tests, so that a failure here does not hide them.
 """
 import os
 

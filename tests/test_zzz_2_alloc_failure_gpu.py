@@ -4,7 +4,8 @@ For each create call the armed failure moves from the call's first allocation to
 every failing call must raise FW_ENOMEM, hand back no object, and free what it held (checked
 through the device's free memory for the rule set). The call then succeeds, and the objects it
 builds, and the context, still classify correctly. No GPU fault is involved: the failure is
-taken on the host before the CUDA allocator is reached.
+taken on the host before the CUDA allocator is reached. This file is collected last, so that a
+failure here does not hide the other GPU tests.
 """
 import os
 
