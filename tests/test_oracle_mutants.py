@@ -28,6 +28,17 @@ MUTANTS = {
     "src_uses_dst_prefix": ("address_matches(src, r->src_addr, r->src_prefix)", "address_matches(src, r->src_addr, r->dst_prefix)"),
     "depth_off_by_one": ("(int64_t)found + 1", "(int64_t)found"),
     "unmatched_depth_zero": ("(found < 0) ? n_rules :", "(found < 0) ? 0 :"),
+    "address_low_bits": ("uint64_t a = (uint64_t)addr >> drop;\n    uint64_t b = (uint64_t)rule_addr >> drop;",
+                         "uint64_t a = ((uint64_t)addr << drop) & 0xFFFFFFFFull;\n"
+                         "    uint64_t b = ((uint64_t)rule_addr << drop) & 0xFFFFFFFFull;"),
+    "prefix_zero_32bit_shift": ("uint64_t a = (uint64_t)addr >> drop;\n    uint64_t b = (uint64_t)rule_addr >> drop;",
+                                "uint64_t a = (uint32_t)(addr >> (drop & 31u));\n"
+                                "    uint64_t b = (uint32_t)(rule_addr >> (drop & 31u));"),
+    "proto_zero_as_any": ("if (any) return 1;", "if (any || rule_proto == 0) return 1;"),
+    "packet_addresses_swapped": ("address_matches(src, r->src_addr", "address_matches(dst, r->src_addr"),
+    "packet_ports_swapped": ("port_matches(sport, r->sport_lo", "port_matches(dport, r->sport_lo"),
+    "first_rule_skipped": ("for (int64_t k = 0; k < n_rules; ++k)", "for (int64_t k = 1; k < n_rules; ++k)"),
+    "last_rule_skipped": ("for (int64_t k = 0; k < n_rules; ++k)", "for (int64_t k = 0; k < n_rules - 1; ++k)"),
 }
 
 
