@@ -96,6 +96,17 @@ def sweep(rs, dh, n, candidates, reps=20, warmup=3):
     return out
 
 
+def pick_best(results):
+    """The fastest candidate of a ``sweep`` whose verdicts equal the first candidate's (None when
+    every candidate was rejected). Every candidate computes the same function, so a candidate
+    whose verdicts differ is a bug: that raises instead of being ranked."""
+    differ = [c for c, _, same in results if same is False]
+    if differ:
+        raise RuntimeError(f"{len(differ)} candidate(s) returned different verdicts, e.g. {differ[0]}")
+    ok = [(ms, i) for i, (_, ms, same) in enumerate(results) if same is True and ms != float("inf")]
+    return results[min(ok)[1]][0] if ok else None
+
+
 PLAN_CANDIDATES = [(ppi, seg) for ppi in (128, 256) for seg in (16, 64, 256, 1024)]
 CLASS_LIMITS = (256, 4096)  # reachable rules: <= 256, <= 4096, larger
 
@@ -190,8 +201,14 @@ def main(argv=None):
     for c, ms, same in res:
         print(json.dumps({"workload": a.workload, "device": name, "config": c, "ms": ms,
                           "mpackets_s": n / (ms * 1e-3) / 1e6 if ms != float("inf") else 0.0, "same": same}))
-    if res and res[0][1] != float("inf"):
-        store(f"{name}|{a.workload}|{a.set}", res[0][0])
+    try:
+        best = pick_best(res)
+    except RuntimeError as e:
+        print(json.dumps({"workload": a.workload, "device": name, "error": str(e)}))
+        rs.destroy()
+        return 1
+    if best is not None:
+        store(f"{name}|{a.workload}|{a.set}", best)
     rs.destroy()
     return 0
 
