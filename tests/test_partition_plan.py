@@ -152,3 +152,42 @@ def test_plan_rejects_bad_arguments(L):
     bad = r.copy()
     bad["src_prefix"][3] = 33
     assert L.fw_partition_plan(bad.ctypes.data_as(ctypes.c_void_p), 10, 1, *refs, None, None) == fw.FW_EINVAL
+
+
+def random_rule_set(rng):
+    """Small random lists that stress the partition's choices: 0 to 12 exact protocols (ties in
+    their counts included), prefixes of 0 to 4 bits as often as long ones (shorter than a key
+    of up to 3 bits), and sizes from empty up."""
+    n = int(rng.integers(0, 60))
+    r = W.empty_rules(n)
+    protos = rng.choice(256, size=int(rng.integers(0, 13)), replace=False)
+    for i in range(n):
+        for f in ("src", "dst"):
+            r[f + "_addr"][i] = rng.integers(0, 1 << 32, dtype=np.uint64)
+            r[f + "_prefix"][i] = rng.integers(0, 5) if rng.random() < 0.5 else rng.integers(5, 33)
+        for f in ("sport", "dport"):
+            a, b = sorted(rng.integers(0, 65536, size=2))
+            r[f + "_lo"][i], r[f + "_hi"][i] = a, b
+        if len(protos) == 0 or rng.random() < 0.3:
+            r["proto_any"][i] = 1
+        else:
+            r["proto"][i] = protos[rng.integers(len(protos))]
+        r["action"][i] = rng.integers(2)
+    return r
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_plan_matches_definition_on_random_lists(L, seed):
+    rng = np.random.default_rng(500 + seed)
+    keyed = 0
+    for _ in range(60):
+        rules = random_rule_set(rng)
+        for granule in (1, 4, 128):
+            plan = fw.fw_partition_plan(rules, granule)
+            key = R.best_key(rules, granule)
+            assert (plan["key_field"], plan["key_bits"]) == key
+            lists = R.class_sublists(rules, *key)
+            assert plan["class_len"] == [len(x) for x in lists]
+            assert np.array_equal(plan["proto_class"], R.protocol_classes(rules)[1])
+            keyed += key != (0, 0)
+    assert keyed > 0  # the search reaches keyed partitions
