@@ -2,7 +2,7 @@
 
 Each ``csrc/*.cu`` translation unit is compiled in parallel with nvcc and the
 objects are linked into ``paper_1312_4188_gb300/libfw.so`` (CUDA runtime linked
-statically, so the library only needs the driver at run time).
+statically, so the library only needs the NVIDIA driver (libcuda) at run time).
 """
 from __future__ import annotations
 
