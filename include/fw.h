@@ -221,8 +221,9 @@ int fw_ruleset_partition(const fw_ruleset *rs, int32_t *n_classes, int32_t *key_
  *  protocol class << key_bits | key. A class's sub-list keeps, in list order,
  *  the rules that can match one of its packets (protocol "any" or the class's
  *  protocol, or for "other" any protocol without a class of its own; an
- *  address prefix that can hold the key), so a packet's first match is the
- *  same in its sub-list as in the whole list.
+ *  address prefix that can hold the key), so a packet's first match (Sec. I)
+ *  is the same in its sub-list as in the whole list. The partition itself is
+ *  not in the paper: it is this library's way to shorten the scan.
  *  granule: the key (or none) with the lowest mean per-class cost is taken,
  *  the sub-list length for granule 1, else ceil(length / granule) and at least
  *  1. Candidates go source before destination, fewer bits first; a later one
