@@ -154,6 +154,22 @@ typedef struct fw_headers {
  *                     load; 0 = default: two, or one when an explicit
  *                     block_threads <= 768 and blocks_per_sm >= 2 select the
  *                     dense form).
+ *  filter:            packet split through the bucket filter of the partition:
+ *                     per class, bitmaps over its sub-list indexed by the top 8
+ *                     bits of the source address, of the destination address
+ *                     and the top 4 bits of both ports; a packet tests exactly,
+ *                     in list order, only the rules whose three bits are all
+ *                     set, which include every rule that contains it, so its
+ *                     first match is the same. A rule set has the filter when
+ *                     every class sub-list holds at most 64 rules and the
+ *                     "every other protocol" class holds no exact-protocol
+ *                     rule. 0 = default: the filter kernel whenever the rule
+ *                     set has one and no other field of this struct except
+ *                     mode (AUTO or PACKET_SPLIT), block_threads and
+ *                     blocks_per_sm is set; 1 = the filter kernel
+ *                     (FW_EINVAL if the rule set has none); 2 = never.
+ *                     block_threads (<= 512, default 512) and blocks_per_sm
+ *                     (default 3) shape its launch.
  */
 typedef struct fw_config {
     int32_t mode;
@@ -167,7 +183,8 @@ typedef struct fw_config {
     int32_t segment_rules;
     int32_t partition;
     int32_t lane_packets;
-    int32_t reserved[5];           /* must be zero */
+    int32_t filter;
+    int32_t reserved[4];           /* must be zero */
 } fw_config;
 
 typedef struct fw_ruleset fw_ruleset;
@@ -237,6 +254,16 @@ int fw_ruleset_partition(const fw_ruleset *rs, int32_t *n_classes, int32_t *key_
  */
 int fw_partition_plan(const fw_rule *rules, int64_t n, int32_t granule, int32_t *n_classes, int32_t *key_field,
                       int32_t *key_bits, int64_t *class_len, uint8_t *proto_class);
+
+/*
+ * Bucket filter of the rule set's partition (see fw_config.filter): *words
+ * receives the 32-bit words per bitmap row (1 or 2; 0 when the rule set has
+ * no filter: a class sub-list longer than 64 rules, or the "every other
+ * protocol" class holding exact-protocol rules), *bytes the size of the
+ * filter block each block of the filter kernel stages into shared memory.
+ * Host only. FW_EINVAL for NULL arguments.
+ */
+int fw_ruleset_filter(const fw_ruleset *rs, int32_t *words, int64_t *bytes);
 
 /*
  * Synchronise the device and report whether any kernel that used `rs` gave
@@ -541,18 +568,22 @@ int fw_classify_host(fw_host_pipeline *pl, const fw_ruleset *rs, const fw_header
  * tenants), or code that runs where the stream-ordered allocator has been
  * disabled.
  *
- * Same result as fw_classify_ex with FW_MODE_RULE_SPLIT_GRID, but the
- * per-packet partial minima live in a file-scope device array of
- * FW_NOALLOC_MAX_PACKETS int32 values instead of a per-call allocation. No
- * cudaMalloc, cudaFree or other allocating routine is called. The caller
- * still passes the device headers and the two device output arrays.
+ * Same result as fw_classify_ex with FW_MODE_RULE_SPLIT_GRID (same cfg
+ * fields, same launch shape, same kernels), but the per-packet partial minima
+ * live in a file-scope device array of FW_NOALLOC_MAX_PACKETS int32 values
+ * instead of a per-call allocation. No cudaMalloc, cudaFree or other
+ * allocating routine is called. The caller still passes the device headers
+ * and the two device output arrays.
  *  - n > FW_NOALLOC_MAX_PACKETS: FW_ERANGE, nothing is launched.
- *  - Other argument errors as fw_classify (FW_EINVAL); cfg may be NULL, and
- *    only its rule_slices, packets_per_group and block_threads fields are
- *    read (mode must be 0 or FW_MODE_RULE_SPLIT_GRID).
+ *  - Other argument errors as fw_classify_ex (FW_EINVAL: also for non-zero
+ *    reserved fields, and when the current device is not the rule set's);
+ *    cfg may be NULL; mode must be 0 or FW_MODE_RULE_SPLIT_GRID.
  *  - The first call on a device looks up that device's address of the array
- *    (cudaGetSymbolAddress) with the device current and caches it; make that
- *    first call before any stream capture.
+ *    (cudaGetSymbolAddress) with the device current and caches it. With the
+ *    CUDA runtime's lazy module loading, that first call may also load the
+ *    library's kernels and the array itself onto the device, which takes
+ *    device memory once. So make one warm-up call per device at start-up,
+ *    before any stream capture; later calls allocate nothing.
  *  - Every call on a device shares the one array, and each call re-fills the
  *    part it uses before use, so stale contents from an earlier call never
  *    leak into a result. Two calls whose work overlaps on the GPU (different
@@ -564,6 +595,27 @@ int fw_classify_host(fw_host_pipeline *pl, const fw_ruleset *rs, const fw_header
 int fw_classify_rule_split_noalloc(const fw_ruleset *rs, const fw_headers *hdrs, int64_t n,
                                    int32_t *out_rule_idx, uint8_t *out_action, void *stream,
                                    const fw_config *cfg);
+
+/* ------------------------------------------------------------ measurement */
+/*
+ * Integer throughput microbenchmark (the paper has no counterpart: it measures
+ * the INT32 peak that rule-check rates are reported against, on the GPU the
+ * library runs on). Enqueues one kernel on `stream`: `blocks` x `threads`
+ * threads, each running `iters` loop trips of 128 independent-chain 32-bit
+ * integer instructions with no memory traffic, then one uint32 store per
+ * thread into `sink` (device memory, at least blocks*threads uint32, caller
+ * owned). kind 0: lop3 only (the integer ALU pipe); kind 1: mad.lo.u32 only
+ * (integer multiply-add, issued on the FMA pipe); kind 2: both alternated 1:1
+ * (the issue limit when both pipes are fed). *ops_per_launch receives the
+ * instruction count of one launch (blocks*threads*iters*128, per-thread ops,
+ * i.e. lanes x instructions); the caller times the launch (CUDA events on
+ * `stream`) and divides.
+ *  - FW_EINVAL: kind outside 0..2, iters outside 1..2^24, blocks outside
+ *    1..2^20, threads not a multiple of 32 in 32..512, NULL sink or
+ *    ops_per_launch. FW_ECUDA: launch failure.
+ */
+int fw_int32_peak_launch(int kind, int32_t iters, int32_t blocks, int32_t threads, uint32_t *sink,
+                         void *stream, int64_t *ops_per_launch);
 
 /* ------------------------------------------------------------ self test */
 /*

@@ -44,10 +44,19 @@ PACKET_SPLIT_CANDIDATES = (
             smem_rules=3072, packets_per_group=256, segment_rules=16)]
 )
 
+# the bucket-filter packet split (rejected, and skipped, for a rule set without a filter)
+PACKET_SPLIT_CANDIDATES += [dict(mode="packet_split", filter=1, block_threads=bt, blocks_per_sm=bps)
+                            for (bt, bps) in ((512, 3), (512, 2), (256, 6), (384, 4), (128, 12))]
+
 RULE_SPLIT_CANDIDATES = (
-    [dict(mode="rule_split_warp", block_threads=bt, packets_per_group=g) for bt in (128, 256) for g in (32, 64, 128)]
-    + [dict(mode="rule_split_block", block_threads=bt, packets_per_group=g) for bt in (128, 256) for g in (128, 256)]
-    + [dict(mode="rule_split_grid", rule_slices=s, packets_per_group=g) for s in (2, 4, 8) for g in (32, 64)]
+    [dict(mode="rule_split_warp", block_threads=bt, blocks_per_sm=bps) for bt in (128, 256) for bps in (4, 8)]
+    + [dict(mode="rule_split_block", block_threads=bt) for bt in (128, 256, 512)]
+    + [dict(mode="rule_split_grid", rule_slices=s) for s in (1, 2, 4, 8)]
+    + [dict(mode="rule_split_warp", partition=2, block_threads=bt, packets_per_group=g)
+       for bt in (128, 256) for g in (32, 64, 128)]
+    + [dict(mode="rule_split_block", partition=2, block_threads=bt, packets_per_group=g)
+       for bt in (128, 256) for g in (128, 256)]
+    + [dict(mode="rule_split_grid", partition=2, rule_slices=s, packets_per_group=g) for s in (2, 4, 8) for g in (32, 64)]
 )
 
 

@@ -1,0 +1,325 @@
+// Packet split through a bucket filter (Sec. IV.A data-parallel: every thread
+// holds the whole rule list and takes its own packets; first match, default
+// deny, Sec. I).
+//
+// The rule list is partitioned as for the other packet-split kernels: a packet
+// of class c (its protocol class and address key) can only be matched by the
+// rules of class c's sub-list, kept in list order. For short sub-lists (at most
+// 64 records) each class also gets three bitmaps per bucket value, one bit per
+// sub-list record:
+//   table 0, bucket = top 8 bits of the source address: bit j set when rule j's
+//            source prefix contains some address with those top bits;
+//   table 1, the same for the destination address;
+//   table 2, bucket = (sport >> 12) << 4 | (dport >> 12): bit j set when rule
+//            j's source port range meets [sb*4096, sb*4096+4095] and its
+//            destination port range meets [db*4096, db*4096+4095].
+// A rule that contains the packet passes all three (each of its field sets
+// holds the packet's value, so it meets the bucket of that value), so the AND
+// of the packet's three rows is a superset of the sub-list rules that match
+// it. Testing the candidates in increasing bit order, exactly, and stopping at
+// the first that passes therefore returns the first match of the sub-list,
+// which is the packet's first match in the whole list. A candidate whose
+// fields are unions of whole buckets (prefixes of at most 8 bits, port ranges
+// aligned to 4,096) passes exactly when its bits are set, so it needs no test
+// (the exact mask; the catch-all is one such rule).
+//
+// The exact test reads one 16-byte record per candidate:
+//   x: source address bits 23..0 (pre-masked) | shift << 24,
+//      shift = min(32 - prefix, 24): the address test is
+//      ((src ^ x) & 0xFFFFFF) >> shift == 0 (bits 31..24 are decided by the
+//      bucket, exactly, for every prefix);
+//   y: the same for the destination;
+//   z: sport_lo | (sport_hi - sport_lo) << 16: (sport - lo) <= width, unsigned;
+//   w: the same for the destination port.
+// The protocol needs no test: every rule of an exact-protocol class has that
+// protocol or "any", and the filter is built only when the "every other
+// protocol" class holds no exact-protocol rule.
+//
+// One filter block (tables, exact masks, records, verdict words, the protocol
+// class table and the class offsets) is staged into each block's shared memory
+// by 1-D TMA bulk copies (no multicast) with a bounded mbarrier wait; a thread
+// takes four consecutive packets per step (16-byte header loads), so a warp
+// streams 832 contiguous header bytes per step and writes its verdicts with
+// 16-byte and 4-byte stores.
+#include <algorithm>
+#include <cstring>
+#include <type_traits>
+
+#include "fw_alloc.h"
+#include "fw_scan.cuh"
+
+namespace fwk {
+
+constexpr int kFilterMaxRecords = 64;  // bits of the widest bitmap row
+
+// Byte offsets of the filter block's parts (32-bit: the block fits in shared memory).
+struct FilterOffsets {
+    int32_t tables, exact, recs, verdicts, class_of, class_off;
+};
+
+struct FilterParams {
+    const unsigned char *blk;  // the filter block in global memory
+    FilterOffsets L;
+    int32_t blk_bytes;
+    int32_t n_classes, key_field, key_bits;
+    HdrPtrs h;
+    int64_t n;
+    int32_t *out_idx;
+    uint8_t *out_act;
+    unsigned *status;
+};
+
+// The exact test of one candidate (see the record layout above).
+__device__ __forceinline__ bool filter_verify(const uint4 &v, uint32_t s, uint32_t d, uint32_t sp, uint32_t dp) {
+    const bool s_ok = (((s ^ v.x) & 0xFFFFFFu) >> (v.x >> 24)) == 0u;
+    const bool d_ok = (((d ^ v.y) & 0xFFFFFFu) >> (v.y >> 24)) == 0u;
+    const bool sp_ok = (sp - (v.z & 0xFFFFu)) <= (v.z >> 16);
+    const bool dp_ok = (dp - (v.w & 0xFFFFu)) <= (v.w >> 16);
+    return s_ok & d_ok & sp_ok & dp_ok;
+}
+
+template <int W>
+using FilterMask = typename std::conditional<W == 1, uint32_t, uint64_t>::type;
+
+// Candidate mask of one packet and its class's first stored record.
+template <int W>
+__device__ __forceinline__ FilterMask<W> filter_candidates(const unsigned char *base, const FilterParams &p,
+                                                           uint32_t s, uint32_t d, uint32_t sp, uint32_t dp,
+                                                           uint32_t pr, int &cls) {
+    using M = FilterMask<W>;
+    uint32_t c = base[p.L.class_of + pr];
+    if (p.key_field != 0) c = (c << p.key_bits) | ((p.key_field == 1 ? s : d) >> (32 - p.key_bits));
+    cls = (int)c;
+    const M *T = reinterpret_cast<const M *>(base + p.L.tables);
+    const uint32_t row = c * 256u, step = (uint32_t)p.n_classes * 256u;
+    return T[row + (s >> 24)] & T[step + row + (d >> 24)] & T[2u * step + row + (((sp >> 12) << 4) | (dp >> 12))];
+}
+
+// First candidate that passes its exact test: its verdict word, or ~0u.
+template <int W>
+__device__ __forceinline__ uint32_t filter_first(const unsigned char *base, const FilterParams &p, FilterMask<W> m,
+                                                 int cls, uint32_t s, uint32_t d, uint32_t sp, uint32_t dp) {
+    using M = FilterMask<W>;
+    if (m == 0) return 0xFFFFFFFFu;
+    const int off = reinterpret_cast<const int32_t *>(base + p.L.class_off)[cls];
+    const M ex = reinterpret_cast<const M *>(base + p.L.exact)[cls];
+    const uint4 *V = reinterpret_cast<const uint4 *>(base + p.L.recs) + off;
+    while (m != 0) {
+        const int k = W == 1 ? __ffs((unsigned)m) - 1 : __ffsll((unsigned long long)m) - 1;
+        if (((ex >> k) & 1u) || filter_verify(V[k], s, d, sp, dp))
+            return reinterpret_cast<const uint32_t *>(base + p.L.verdicts)[off + k];
+        m &= m - 1;
+    }
+    return 0xFFFFFFFFu;
+}
+
+// The grid-stride loop over packet quads, with the filter block at `base`
+// (shared memory, or global memory after a failed staging wait).
+template <int W, bool VEC>
+__device__ __forceinline__ void filter_loop(const FilterParams &p, const unsigned char *base) {
+    const int64_t nq = (p.n + 3) / 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += stride) {
+        uint32_t s[4], d[4], sp[4], dp[4], pr[4];
+        int cnt = 4;
+        const int64_t b = q * 4;
+        if (VEC && b + 3 < p.n) {
+            const uint4 sv = __ldcs(reinterpret_cast<const uint4 *>(p.h.src) + q);
+            const uint4 dv = __ldcs(reinterpret_cast<const uint4 *>(p.h.dst) + q);
+            const uint2 spv = __ldcs(reinterpret_cast<const uint2 *>(p.h.sport) + q);
+            const uint2 dpv = __ldcs(reinterpret_cast<const uint2 *>(p.h.dport) + q);
+            const uint32_t prv = __ldcs(reinterpret_cast<const unsigned int *>(p.h.proto) + q);
+            s[0] = sv.x, s[1] = sv.y, s[2] = sv.z, s[3] = sv.w;
+            d[0] = dv.x, d[1] = dv.y, d[2] = dv.z, d[3] = dv.w;
+            sp[0] = spv.x & 0xFFFFu, sp[1] = spv.x >> 16, sp[2] = spv.y & 0xFFFFu, sp[3] = spv.y >> 16;
+            dp[0] = dpv.x & 0xFFFFu, dp[1] = dpv.x >> 16, dp[2] = dpv.y & 0xFFFFu, dp[3] = dpv.y >> 16;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) pr[j] = (prv >> (8 * j)) & 0xFFu;
+        } else {
+            cnt = p.n - b < 4 ? (int)(p.n - b) : 4;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const bool in = j < cnt;
+                s[j] = in ? p.h.src[b + j] : 0u;
+                d[j] = in ? p.h.dst[b + j] : 0u;
+                sp[j] = in ? p.h.sport[b + j] : 0u;
+                dp[j] = in ? p.h.dport[b + j] : 0u;
+                pr[j] = in ? p.h.proto[b + j] : 0u;
+            }
+        }
+        int32_t idx[4];
+        uint32_t acts = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int cls;
+            const FilterMask<W> m = filter_candidates<W>(base, p, s[j], d[j], sp[j], dp[j], pr[j], cls);
+            const uint32_t vw = filter_first<W>(base, p, m, cls, s[j], d[j], sp[j], dp[j]);
+            idx[j] = vw == 0xFFFFFFFFu ? -1 : (int32_t)(vw & 0x7FFFFFFFu);
+            acts |= (vw == 0xFFFFFFFFu ? (uint32_t)FW_DROP : vw >> 31) << (8 * j);
+        }
+        if (VEC && cnt == 4) {
+            __stcs(reinterpret_cast<int4 *>(p.out_idx) + q, make_int4(idx[0], idx[1], idx[2], idx[3]));
+            __stcs(reinterpret_cast<unsigned int *>(p.out_act) + q, acts);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (j < cnt) {
+                    p.out_idx[b + j] = idx[j];
+                    p.out_act[b + j] = (uint8_t)(acts >> (8 * j));
+                }
+            }
+        }
+    }
+}
+
+template <int W, bool VEC>
+__global__ void __launch_bounds__(512, 3) k_packet_split_filter(FilterParams p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&bar, (uint32_t)p.blk_bytes);
+        for (int32_t o = 0; o < p.blk_bytes; o += 32768)
+            bulk_load(smem + o, p.blk + o, (uint32_t)min(32768, p.blk_bytes - o), &bar);
+    }
+    const bool ok = mbar_wait_bounded(&bar, 0, p.status);
+    if (__syncthreads_and(ok) != 0) {
+        filter_loop<W, VEC>(p, smem);
+    } else {
+        // a failed wait leaves the block reading the filter from global memory; before it exits,
+        // the copies that may still be in flight into its shared memory get a second bounded wait
+        filter_loop<W, VEC>(p, p.blk);
+        if (threadIdx.x == 0) mbar_wait_bounded(&bar, 0, p.status);
+    }
+}
+
+// ------------------------------------------------------------ host side
+// Exact-test record of a rule (layout above).
+static uint4 verify_record(const fw_rule &r) {
+    const uint32_t ss = std::min(32u - r.src_prefix, 24u), ds = std::min(32u - r.dst_prefix, 24u);
+    const uint32_t sa = r.src_addr & prefix_mask(r.src_prefix) & 0xFFFFFFu;
+    const uint32_t da = r.dst_addr & prefix_mask(r.dst_prefix) & 0xFFFFFFu;
+    return make_uint4(sa | (ss << 24), da | (ds << 24), r.sport_lo | ((uint32_t)(r.sport_hi - r.sport_lo) << 16),
+                      r.dport_lo | ((uint32_t)(r.dport_hi - r.dport_lo) << 16));
+}
+
+// Does the prefix (addr, len) contain an address whose top 8 bits are b?
+static bool prefix_meets_bucket(uint32_t addr, unsigned len, uint32_t b) {
+    if (len == 0) return true;
+    if (len >= 8) return (addr >> 24) == b;
+    return (b >> (8 - len)) == (addr >> (32 - len));
+}
+
+cudaError_t build_filter(const fw_rule *rules, const std::vector<std::vector<int64_t>> &lists,
+                         const std::vector<uint8_t> &class_of, int n_proto_classes, fw_ruleset *rs) {
+    rs->filter_words = 0;
+    rs->filter_bytes = 0;
+    rs->d_filter = nullptr;
+    const int nc = rs->n_classes;
+    int longest = 0;
+    for (int c = 0; c < nc; ++c) longest = std::max(longest, rs->class_len[c]);
+    if (nc < 1 || longest > kFilterMaxRecords) return cudaSuccess;
+    // the "every other protocol" classes must hold protocol-"any" rules only
+    for (int c = 0; c < nc; ++c) {
+        if ((c >> rs->key_bits) != n_proto_classes - 1) continue;
+        for (int64_t k : lists[c])
+            if (!rules[k].proto_any) return cudaSuccess;
+    }
+    const int W = longest <= 32 ? 1 : 2;
+    const int64_t records = rs->class_off[kMaxClasses - 1] + rs->class_len[kMaxClasses - 1];
+    const FilterLayout L = filter_layout(nc, W, records);
+    if (L.total > 227 * 1024 - 64) return cudaSuccess;  // must fit one block's shared memory
+    const int64_t bytes = L.total;
+    std::vector<unsigned char> blk((size_t)bytes, 0);
+    uint32_t *tab = reinterpret_cast<uint32_t *>(blk.data() + L.tables);
+    uint32_t *exact = reinterpret_cast<uint32_t *>(blk.data() + L.exact);
+    uint4 *recs = reinterpret_cast<uint4 *>(blk.data() + L.recs);
+    uint32_t *vw = reinterpret_cast<uint32_t *>(blk.data() + L.verdicts);
+    auto set_bit = [&](uint32_t *row, int j) { row[j >> 5] |= 1u << (j & 31); };
+    for (int c = 0; c < nc; ++c) {
+        for (size_t j = 0; j < lists[c].size(); ++j) {
+            const fw_rule &r = rules[lists[c][j]];
+            const int64_t at = rs->class_off[c] + (int64_t)j;
+            recs[at] = verify_record(r);
+            vw[at] = (uint32_t)lists[c][j] | ((uint32_t)(r.action & 1u) << 31);
+            for (uint32_t b = 0; b < 256; ++b) {
+                if (prefix_meets_bucket(r.src_addr, r.src_prefix, b))
+                    set_bit(tab + ((size_t)(0 * nc + c) * 256 + b) * W, (int)j);
+                if (prefix_meets_bucket(r.dst_addr, r.dst_prefix, b))
+                    set_bit(tab + ((size_t)(1 * nc + c) * 256 + b) * W, (int)j);
+            }
+            for (uint32_t sb = (uint32_t)r.sport_lo >> 12; sb <= (uint32_t)r.sport_hi >> 12; ++sb)
+                for (uint32_t db = (uint32_t)r.dport_lo >> 12; db <= (uint32_t)r.dport_hi >> 12; ++db)
+                    set_bit(tab + ((size_t)(2 * nc + c) * 256 + ((sb << 4) | db)) * W, (int)j);
+            const bool whole = r.src_prefix <= 8 && r.dst_prefix <= 8 && (r.sport_lo & 0xFFFu) == 0 &&
+                               (r.sport_hi & 0xFFFu) == 0xFFFu && (r.dport_lo & 0xFFFu) == 0 &&
+                               (r.dport_hi & 0xFFFu) == 0xFFFu;
+            if (whole) set_bit(exact + (size_t)c * W, (int)j);
+        }
+    }
+    std::memcpy(blk.data() + L.class_of, class_of.data(), 256);
+    std::memcpy(blk.data() + L.class_off, rs->class_off, sizeof(int32_t) * kMaxClasses);
+    cudaError_t e = dev_malloc(&rs->d_filter, (size_t)bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(rs->d_filter, blk.data(), (size_t)bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    rs->filter_words = W;
+    rs->filter_bytes = bytes;
+    return cudaSuccess;
+}
+
+int launch_filter(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *out_idx, uint8_t *out_act,
+                  cudaStream_t st, int threads, int blocks_per_sm) {
+    if (rs->filter_words == 0) return FW_EINVAL;
+    FilterParams p;
+    std::memset(&p, 0, sizeof(p));
+    const int64_t records = rs->class_off[kMaxClasses - 1] + rs->class_len[kMaxClasses - 1];
+    p.blk = rs->d_filter;
+    const FilterLayout L = filter_layout(rs->n_classes, rs->filter_words, records);
+    p.L = FilterOffsets{(int32_t)L.tables, (int32_t)L.exact, (int32_t)L.recs, (int32_t)L.verdicts,
+                        (int32_t)L.class_of, (int32_t)L.class_off};
+    p.blk_bytes = (int32_t)rs->filter_bytes;
+    p.n_classes = rs->n_classes;
+    p.key_field = rs->key_field;
+    p.key_bits = rs->key_bits;
+    p.h = h;
+    p.n = n;
+    p.out_idx = out_idx;
+    p.out_act = out_act;
+    p.status = rs->d_status;
+    threads = threads > 0 ? threads : 512;
+    const int per_sm = blocks_per_sm > 0 ? blocks_per_sm : 3;
+    if (threads % 32 != 0 || threads > 512) return FW_EINVAL;
+    const size_t smem = (size_t)rs->filter_bytes;
+    if ((size_t)per_sm * (smem + 1024) > 228 * 1024) return FW_EINVAL;
+    const int64_t nq = (n + 3) / 4;
+    int64_t blocks = std::min<int64_t>((int64_t)sm_count(rs->device) * per_sm, (nq + threads - 1) / threads);
+    blocks = std::max<int64_t>(1, blocks);
+    const bool vec = (reinterpret_cast<uintptr_t>(h.src) % 16 == 0) && (reinterpret_cast<uintptr_t>(h.dst) % 16 == 0) &&
+                     (reinterpret_cast<uintptr_t>(h.sport) % 8 == 0) && (reinterpret_cast<uintptr_t>(h.dport) % 8 == 0) &&
+                     (reinterpret_cast<uintptr_t>(h.proto) % 4 == 0) && (reinterpret_cast<uintptr_t>(out_idx) % 16 == 0) &&
+                     (reinterpret_cast<uintptr_t>(out_act) % 4 == 0);
+    cudaError_t e = cudaSuccess;
+#define FW_LAUNCH_F(WW, V)                                                                                  \
+    do {                                                                                                    \
+        if (smem > 48 * 1024)                                                                               \
+            e = cudaFuncSetAttribute(k_packet_split_filter<WW, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                     (int)smem);                                                            \
+        if (e == cudaSuccess) k_packet_split_filter<WW, V><<<(unsigned)blocks, threads, smem, st>>>(p);    \
+    } while (0)
+    if (rs->filter_words == 1) {
+        if (vec) FW_LAUNCH_F(1, true);
+        else FW_LAUNCH_F(1, false);
+    } else {
+        if (vec) FW_LAUNCH_F(2, true);
+        else FW_LAUNCH_F(2, false);
+    }
+#undef FW_LAUNCH_F
+    if (e != cudaSuccess) return cuda_status(e);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace fwk

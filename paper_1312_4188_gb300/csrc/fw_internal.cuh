@@ -273,12 +273,22 @@ struct fw_ruleset {
     uint32_t *d_part_wtop;             // part_pad words
     int32_t *d_part_orig;              // part_pad original rule indices (-1 for padding)
     uint32_t *d_part_verdict;          // part_pad words: original index | action << 31
+    // Bucket filter over the partition (fw_filter.cu): per class, bitmaps over
+    // the class sub-list indexed by a packet's address and port buckets, plus a
+    // compact exact-test record per stored record. Built when every sub-list
+    // holds at most 64 records and no class mixes exact protocols.
+    int32_t filter_words;              // 0 = no filter, else 1 or 2 (32-bit words per bitmap row)
+    int64_t filter_bytes;              // bytes of d_filter (staged whole into shared memory)
+    unsigned char *d_filter;           // the filter block (layout: FilterLayout)
     uint8_t *d_action;        // n_pad actions
     unsigned *d_status;       // device error flags (kStatus*)
 };
 
 namespace fwk {
 int set_status(int s);  // records s as this thread's last status; returns s
+// FW_OK when the current device is the one the rule set was created on, FW_EINVAL
+// when it is another, FW_ECUDA when the current device cannot be read.
+int check_device(const fw_ruleset *rs);
 int cuda_status(cudaError_t e);
 uint32_t prefix_mask(unsigned prefix);  // top `prefix` bits set; 0 for prefix 0
 bool is_catch_all(const fw_rule &r);    // all five fields wildcards
@@ -306,4 +316,42 @@ void protocol_classes(const fw_rule *rules, int64_t n, std::vector<uint8_t> &cla
 void partition_lists(const fw_rule *rules, int64_t n, int64_t granule, std::vector<uint8_t> &class_of,
                      std::vector<std::vector<int64_t>> &lists, int &key_field, int &key_bits);
 int sm_count(int dev);                  // SMs of device `dev` (cached)
+
+// Bucket filter (fw_filter.cu). Byte offsets of the parts of the filter block
+// for n_classes classes, `words` 32-bit words per bitmap row and `records`
+// stored sub-list records (every part starts on a 16-byte boundary).
+struct FilterLayout {
+    int64_t tables, exact, recs, verdicts, class_of, class_off, total;
+};
+constexpr int kFilterTables = 3;  // source top 8 bits, destination top 8 bits, (sport, dport) top 4 bits each
+__host__ __device__ inline FilterLayout filter_layout(int n_classes, int words, int64_t records) {
+    FilterLayout L;
+    auto up16 = [](int64_t b) { return (b + 15) / 16 * 16; };
+    L.tables = 0;
+    L.exact = up16(L.tables + (int64_t)kFilterTables * n_classes * 256 * words * 4);
+    L.recs = up16(L.exact + (int64_t)n_classes * words * 4);
+    L.verdicts = up16(L.recs + records * 16);
+    L.class_of = up16(L.verdicts + records * 4);
+    L.class_off = L.class_of + 256;
+    L.total = up16(L.class_off + 4 * kMaxClasses);
+    return L;
+}
+// Builds rs->d_filter from the partition (lists[c] = original rule indices of
+// class c's sub-list, class_of = protocol -> protocol class) when it applies;
+// leaves filter_words 0 otherwise. Returns a CUDA error only for a failed
+// allocation or copy.
+cudaError_t build_filter(const fw_rule *rules, const std::vector<std::vector<int64_t>> &lists,
+                         const std::vector<uint8_t> &class_of, int n_proto_classes, fw_ruleset *rs);
+struct HdrPtrs;
+// Rule split (fw_rule_split.cu): warp, block or grid mode over the partition or the whole
+// list; grid mode combines through `scratch` (n int32 of device memory) when it is given, else
+// through a stream-ordered allocation.
+int rule_split_run(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *out_idx, uint8_t *out_act,
+                   cudaStream_t st, const fw_config &cfg, int32_t *scratch);
+int launch_rule_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *out_idx, uint8_t *out_act,
+                      cudaStream_t st, const fw_config &cfg);
+// Packet split through the bucket filter (FW_OK, or a status for a bad
+// configuration / launch failure). threads, blocks_per_sm: launch shape (0 = default).
+int launch_filter(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *out_idx, uint8_t *out_act,
+                  cudaStream_t st, int threads, int blocks_per_sm);
 }  // namespace fwk

@@ -43,6 +43,16 @@ int cuda_status(cudaError_t e) {
     return FW_ECUDA;
 }
 
+int check_device(const fw_ruleset *rs) {
+    int dev = -1;
+    const cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_status(e);
+    }
+    return dev == rs->device ? FW_OK : FW_EINVAL;
+}
+
 uint32_t prefix_mask(unsigned prefix) {
     return prefix == 0 ? 0u : (0xFFFFFFFFu << (32u - prefix));
 }
@@ -209,6 +219,7 @@ extern "C" int fw_ruleset_create_ex(const fw_rule *rules, int64_t n, fw_ruleset 
     std::vector<int32_t> part_orig;
     std::vector<uint32_t> part_verdict;
     std::vector<uint8_t> part_class_of;
+    std::vector<std::vector<int64_t>> part_lists;
     std::vector<uint32_t> hw(rs->n_pad);
     std::vector<RecRange> hr(rs->n_pad);
     std::vector<uint32_t> hrw(rs->n_pad);
@@ -258,6 +269,7 @@ extern "C" int fw_ruleset_create_ex(const fw_rule *rules, int64_t n, fw_ruleset 
                 part_verdict[at] = (uint32_t)k | ((uint32_t)(ha[k] & 1u) << 31);
             }
         part_class_of = class_of;
+        part_lists = std::move(lists);
     }
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = dev_malloc(&rs->d_clamp, rs->n_pad * sizeof(RecClamp));
@@ -292,6 +304,7 @@ extern "C" int fw_ruleset_create_ex(const fw_rule *rules, int64_t n, fw_ruleset 
     if (e == cudaSuccess) e = cudaMemcpy(rs->d_class_of, part_class_of.data(), 256, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(rs->d_action, ha.data(), rs->n_pad, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(rs->d_status, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = build_filter(rules, part_lists, part_class_of, rs->n_classes >> rs->key_bits, rs);
     if (e != cudaSuccess) {
         fw_ruleset_destroy(rs);
         cudaGetLastError();
@@ -308,6 +321,13 @@ extern "C" int fw_ruleset_partition(const fw_ruleset *rs, int32_t *n_classes, in
     *n_classes = rs->n_classes;
     *key_field = rs->key_field;
     *key_bits = rs->key_bits;
+    return FW_OK;
+}
+
+extern "C" int fw_ruleset_filter(const fw_ruleset *rs, int32_t *words, int64_t *bytes) {
+    if (rs == nullptr || words == nullptr || bytes == nullptr) return set_status(FW_EINVAL);
+    *words = rs->filter_words;
+    *bytes = rs->filter_bytes;
     return FW_OK;
 }
 
@@ -361,6 +381,7 @@ extern "C" void fw_ruleset_destroy(fw_ruleset *rs) {
     if (rs->d_class_of) cudaFree(rs->d_class_of);
     if (rs->d_action) cudaFree(rs->d_action);
     if (rs->d_status) cudaFree(rs->d_status);
+    if (rs->d_filter) cudaFree(rs->d_filter);
     delete rs;
 }
 

@@ -21,7 +21,6 @@
 #include <algorithm>
 #include <climits>
 #include <cstring>
-#include <mutex>
 
 #include "fw_scan.cuh"
 
@@ -148,138 +147,9 @@ __global__ void __launch_bounds__(1024) k_packet_split_compact_x2(ScanParams p) 
     compact_body<Pol, VEC, PART, 2>(p);
 }
 
-// ------------------------------------------------------------ rule split kernel
-struct SplitParams {
-    const RecClamp *clamp;
-    const uint8_t *action;
-    int n_scan;        // rules scanned (multiple of 4; padded records never match)
-    int slice_rules;   // rules per slice along gridDim.y (multiple of 32)
-    int group;         // packets per group (multiple of 32)
-    int gw;            // block mode: warps sharing one packet group (<= warps per block)
-    HdrPtrs h;
-    int64_t n;
-    int32_t *out_idx;
-    uint8_t *out_act;
-    int32_t *partial;  // grid mode: per-packet minimum across slices (pre-set to kNoMatch)
-};
-
-constexpr int kNoMatch = 0x7F7F7F7F;  // byte-fill sentinel, larger than any rule index
 constexpr int64_t kCompactMinPackets = int64_t(1) << 20;  // default packet split compacts from this batch size
 constexpr int64_t kCompactMidPackets = int64_t(3) << 15;  // ... and the partitioned scan, in small blocks, from this
 constexpr int64_t kMidMaxPackets = int64_t(1) << 22;      // largest batch given the small-block shape by default
-
-// BLOCK = true: all warps of the block share one packet group and split its
-// chunks round-robin. BLOCK = false: each warp owns a packet group alone.
-// Barrier over the gw warps of packet group g: the warp itself when gw is 1,
-// otherwise named barrier 1 + g (barrier 0 is __syncthreads'; at most 8 groups
-// share a block when gw >= 2).
-__device__ __forceinline__ void group_sync(int gw, int g) {
-    if (gw == 1) __syncwarp();
-    else asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(gw * 32) : "memory");
-}
-
-template <bool BLOCK>
-__global__ void __launch_bounds__(512) k_rule_split(SplitParams p) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nwarps = blockDim.x >> 5;
-    const int G = p.group;
-    // Block mode (the paper's hybrid): gw warps share a packet group and split its rule
-    // chunks; a block holds nwarps / gw such groups, each synchronised by its own named
-    // barrier (gw is the chunk count when the list is short, so no warp sits idle).
-    const int gw = BLOCK ? p.gw : 1;
-    const int groups_per_block = nwarps / gw;
-    const int my_group = warp / gw;
-    if (my_group >= groups_per_block) return;  // warps left over when gw does not divide nwarps
-    const int w_in_group = warp % gw;
-    const int gt = w_in_group * 32 + lane;  // thread index within the group
-    const int gthreads = gw * 32;
-    Pkt *stage = reinterpret_cast<Pkt *>(smem) + (size_t)my_group * G;
-    int *best = reinterpret_cast<int *>(smem + (size_t)groups_per_block * G * sizeof(Pkt)) + (size_t)my_group * G;
-
-    const int r0 = blockIdx.y * p.slice_rules;
-    const int r1 = min(p.n_scan, r0 + p.slice_rules);
-    const int64_t n_groups = (p.n + G - 1) / G;
-    for (int64_t g = (int64_t)blockIdx.x * groups_per_block + my_group; g < n_groups;
-         g += (int64_t)gridDim.x * groups_per_block) {
-        const int64_t base = g * G;
-        for (int t = gt; t < G; t += gthreads) {
-            const int64_t i = base + t;
-            if (i < p.n) {
-                stage[t] = {p.h.src[i], p.h.dst[i], ports_of(p.h.sport[i], p.h.dport[i]), p.h.proto[i]};
-                best[t] = INT_MAX;
-            } else {
-                stage[t] = {0, 0, 0, 0};
-                best[t] = -1;  // no packet: never pending
-            }
-        }
-        group_sync(gw, my_group);
-        for (int c0 = r0 + w_in_group * 32; c0 < r1; c0 += gw * 32) {
-            const int k = c0 + lane;
-            uint4 a = make_uint4(0, 0, 0, 0), b = make_uint4(0, 0xFFFFFFFFu, kNeverProto, 0xFFFFFFFFu);
-            if (k < r1) {
-                a = __ldg(&p.clamp[k].a);
-                b = __ldg(&p.clamp[k].b);
-            }
-            // Packets already decided by an earlier (or this) chunk are skipped. The
-            // pending set is taken by ballot so that the loop stays warp-uniform;
-            // a stale read only costs a redundant check (atomicMin keeps the minimum).
-            bool pending = false;
-            for (int t0 = 0; t0 < G; t0 += 32) {
-                unsigned pend = __ballot_sync(0xFFFFFFFFu, *reinterpret_cast<volatile int *>(&best[t0 + lane]) > c0);
-                pending |= pend != 0u;
-                // up to four pending packets per pass: four independent test chains and
-                // ballots in flight instead of one load-test-vote chain at a time
-                while (pend != 0u) {
-                    int t[4];
-                    bool has[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        has[j] = pend != 0u;
-                        t[j] = has[j] ? t0 + __ffs(pend) - 1 : t0;
-                        pend &= pend - 1u;  // no-op once empty
-                    }
-                    unsigned bal[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const Pkt pk = stage[t[j]];
-                        bal[j] = __ballot_sync(0xFFFFFFFFu, has[j] && mismatch_clamp(pk, a, b) == 0u);
-                    }
-                    if (lane == 0) {
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            if (bal[j] != 0u) atomicMin(&best[t[j]], c0 + __ffs(bal[j]) - 1);
-                    }
-                }
-            }
-            if (!pending) break;
-        }
-        group_sync(gw, my_group);
-        for (int t = gt; t < G; t += gthreads) {
-            const int64_t i = base + t;
-            if (i >= p.n) break;
-            const int bt = best[t];
-            if (p.partial != nullptr) {
-                if (bt != INT_MAX) atomicMin(&p.partial[i], bt);
-            } else {
-                const int r = bt == INT_MAX ? -1 : bt;
-                p.out_idx[i] = r;
-                p.out_act[i] = r >= 0 ? __ldg(p.action + r) : (uint8_t)FW_DROP;
-            }
-        }
-        group_sync(gw, my_group);
-    }
-}
-
-__global__ void k_rule_split_finalize(const int32_t *__restrict__ partial, const uint8_t *__restrict__ action,
-                                      int64_t n, int32_t *__restrict__ out_idx, uint8_t *__restrict__ out_act) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int v = partial[i];
-        const int r = v == kNoMatch ? -1 : v;
-        out_idx[i] = r;
-        out_act[i] = r >= 0 ? __ldg(action + r) : (uint8_t)FW_DROP;
-    }
-}
 
 // ------------------------------------------------------------ host side
 int sm_count(int dev) {
@@ -303,6 +173,14 @@ static cudaError_t ensure_smem(K kernel, size_t bytes) {
 
 int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *out_idx, uint8_t *out_act,
                         cudaStream_t st, const fw_config &cfg) {
+    if (cfg.filter < 0 || cfg.filter > 2) return FW_EINVAL;
+    // The bucket filter (fw_filter.cu): on request, or by default when the rule set has one and
+    // nothing but the launch shape is configured.
+    const bool shape_only = cfg.smem_rules == 0 && cfg.packets_per_group == 0 && cfg.rule_slices == 0 &&
+                            cfg.compact == 0 && (cfg.predicate == 0 || cfg.predicate == FW_PRED_ARITH) &&
+                            cfg.segment_rules == 0 && cfg.partition == 0 && cfg.lane_packets == 0;
+    if (cfg.filter == 1 || (cfg.filter == 0 && shape_only && rs->filter_words > 0))
+        return launch_filter(rs, h, n, out_idx, out_act, st, cfg.block_threads, cfg.blocks_per_sm);
     ScanParams p;
     std::memset(&p, 0, sizeof(p));
     const int pred = cfg.predicate == 0 ? FW_PRED_ARITH : cfg.predicate;
@@ -478,72 +356,6 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
     return cuda_status(cudaGetLastError());
 }
 
-int launch_rule_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *out_idx, uint8_t *out_act,
-                      cudaStream_t st, const fw_config &cfg) {
-    SplitParams p;
-    p.clamp = rs->d_clamp;
-    p.action = rs->d_action;
-    p.n_scan = (int)((rs->n_eff + 3) / 4 * 4);
-    p.h = h;
-    p.n = n;
-    p.out_idx = out_idx;
-    p.out_act = out_act;
-    p.partial = nullptr;
-    const bool block_mode = cfg.mode == FW_MODE_RULE_SPLIT_BLOCK;
-    const bool grid_mode = cfg.mode == FW_MODE_RULE_SPLIT_GRID;
-    const int threads = cfg.block_threads > 0 ? cfg.block_threads : (block_mode ? 512 : 256);
-    if (threads % 32 != 0 || threads > 512) return FW_EINVAL;
-    int G = cfg.packets_per_group > 0 ? cfg.packets_per_group : (block_mode ? 256 : 64);
-    if (G % 32 != 0 || G > 4096) return FW_EINVAL;
-    p.group = G;
-    const int nwarps = threads / 32;
-    // block mode: as many warps per group as the list has 32-rule chunks, up to the block
-    p.gw = block_mode ? std::max(1, std::min(nwarps, (p.n_scan + 31) / 32)) : 1;
-    const int groups_per_block = nwarps / p.gw;
-    const size_t smem = (size_t)groups_per_block * G * (sizeof(Pkt) + sizeof(int));
-    if (smem > 227 * 1024) return FW_EINVAL;
-    int slices = 1;
-    if (grid_mode) {
-        slices = cfg.rule_slices > 0 ? cfg.rule_slices : 8;
-        slices = std::max(1, std::min(std::min(slices, 65535), (p.n_scan + 31) / 32));
-    }
-    p.slice_rules = ((p.n_scan + slices - 1) / slices + 31) / 32 * 32;
-    if (p.slice_rules == 0) p.slice_rules = 32;
-    slices = (p.n_scan + p.slice_rules - 1) / p.slice_rules;
-    if (slices < 1) slices = 1;
-    const int per_sm = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : 4;
-    const int64_t n_groups = (n + G - 1) / G;
-    int64_t bx = std::max<int64_t>(1, (int64_t)sm_count(rs->device) * per_sm / (grid_mode ? slices : 1));
-    bx = std::min<int64_t>(bx, (n_groups + groups_per_block - 1) / groups_per_block);
-    bx = std::max<int64_t>(bx, 1);
-    cudaError_t e = cudaSuccess;
-    if (grid_mode) {
-        e = cudaMallocAsync(reinterpret_cast<void **>(&p.partial), (size_t)n * sizeof(int32_t), st);
-        if (e != cudaSuccess) return cuda_status(e);
-        e = cudaMemsetAsync(p.partial, 0x7F, (size_t)n * sizeof(int32_t), st);
-    }
-    dim3 grid((unsigned)bx, (unsigned)slices);
-    if (e == cudaSuccess) {
-        if (block_mode) {
-            e = ensure_smem(k_rule_split<true>, smem);
-            if (e == cudaSuccess) k_rule_split<true><<<grid, threads, smem, st>>>(p);
-        } else {
-            e = ensure_smem(k_rule_split<false>, smem);
-            if (e == cudaSuccess) k_rule_split<false><<<grid, threads, smem, st>>>(p);
-        }
-    }
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (grid_mode) {
-        if (e == cudaSuccess) {
-            const int fb = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count(rs->device) * 8);
-            k_rule_split_finalize<<<std::max(fb, 1), 256, 0, st>>>(p.partial, p.action, n, out_idx, out_act);
-            e = cudaGetLastError();
-        }
-        cudaFreeAsync(p.partial, st);
-    }
-    return cuda_status(e);
-}
-
 }  // namespace fwk
 
 using namespace fwk;
@@ -558,8 +370,12 @@ static int classify_impl(const fw_ruleset *rs, const fw_headers *hdrs, int64_t n
     fw_config cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     if (cfg_in != nullptr) cfg = *cfg_in;
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 4; ++i)
         if (cfg.reserved[i] != 0) return FW_EINVAL;
+    if (cfg.mode < FW_MODE_AUTO || cfg.mode > FW_MODE_RULE_SPLIT_GRID) return FW_EINVAL;
+    if (cfg.filter < 0 || cfg.filter > 2) return FW_EINVAL;
+    const int dev_ok = check_device(rs);
+    if (dev_ok != FW_OK) return dev_ok;
     HdrPtrs h{hdrs->src, hdrs->dst, hdrs->sport, hdrs->dport, hdrs->proto};
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     switch (cfg.mode) {
@@ -602,90 +418,3 @@ extern "C" int fw_selftest_wait_timeout(fw_ruleset *rs, int64_t limit_ns, void *
     return set_status(cuda_status(cudaGetLastError()));
 }
 
-// ------------------------------------------------------------ allocation-free grid rule split
-// Scratch for fw_classify_rule_split_noalloc: the per-packet partial minima of
-// the grid rule split, at a fixed address on every device that loads this
-// library. Host code must not use the symbol itself as a device address; the
-// address is looked up per device with cudaGetSymbolAddress.
-static __device__ __align__(256) int32_t g_noalloc_partial[FW_NOALLOC_MAX_PACKETS];
-
-static std::mutex g_noalloc_mu;
-static int32_t *g_noalloc_ptr[64] = {};
-
-// Device address of g_noalloc_partial on the current device (looked up once per device).
-static int noalloc_scratch(int32_t **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_status(e);
-    if (dev < 0 || dev >= 64) return FW_EINVAL;
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (g_noalloc_ptr[dev] == nullptr) {
-        void *ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_noalloc_partial);
-        if (e != cudaSuccess || ptr == nullptr) {
-            cudaGetLastError();
-            return e != cudaSuccess ? cuda_status(e) : FW_ECUDA;
-        }
-        g_noalloc_ptr[dev] = static_cast<int32_t *>(ptr);
-    }
-    *out = g_noalloc_ptr[dev];
-    return FW_OK;
-}
-
-extern "C" int fw_classify_rule_split_noalloc(const fw_ruleset *rs, const fw_headers *hdrs, int64_t n,
-                                              int32_t *out_idx, uint8_t *out_act, void *stream,
-                                              const fw_config *cfg_in) {
-    if (rs == nullptr || n < 0) return set_status(FW_EINVAL);
-    if (n > FW_NOALLOC_MAX_PACKETS) return set_status(FW_ERANGE);
-    if (n == 0) return FW_OK;
-    if (hdrs == nullptr || hdrs->src == nullptr || hdrs->dst == nullptr || hdrs->sport == nullptr ||
-        hdrs->dport == nullptr || hdrs->proto == nullptr || out_idx == nullptr || out_act == nullptr)
-        return set_status(FW_EINVAL);
-    fw_config cfg;
-    std::memset(&cfg, 0, sizeof(cfg));
-    if (cfg_in != nullptr) cfg = *cfg_in;
-    if (cfg.mode != FW_MODE_AUTO && cfg.mode != FW_MODE_RULE_SPLIT_GRID) return set_status(FW_EINVAL);
-    int32_t *partial = nullptr;
-    int s = noalloc_scratch(&partial);
-    if (s != FW_OK) return set_status(s);
-
-    SplitParams p;
-    p.clamp = rs->d_clamp;
-    p.action = rs->d_action;
-    p.n_scan = (int)((rs->n_eff + 3) / 4 * 4);
-    p.h = HdrPtrs{hdrs->src, hdrs->dst, hdrs->sport, hdrs->dport, hdrs->proto};
-    p.n = n;
-    p.out_idx = out_idx;
-    p.out_act = out_act;
-    p.partial = partial;
-    p.gw = 1;
-    const int threads = cfg.block_threads > 0 ? cfg.block_threads : 256;
-    if (threads % 32 != 0 || threads > 512) return set_status(FW_EINVAL);
-    const int G = cfg.packets_per_group > 0 ? cfg.packets_per_group : 64;
-    if (G % 32 != 0 || G > 4096) return set_status(FW_EINVAL);
-    p.group = G;
-    const int groups_per_block = threads / 32;
-    const size_t smem = (size_t)groups_per_block * G * (sizeof(Pkt) + sizeof(int));
-    if (smem > 227 * 1024) return set_status(FW_EINVAL);
-    int slices = cfg.rule_slices > 0 ? cfg.rule_slices : 8;
-    slices = std::max(1, std::min(std::min(slices, 65535), (p.n_scan + 31) / 32));
-    p.slice_rules = std::max(32, ((p.n_scan + slices - 1) / slices + 31) / 32 * 32);
-    slices = std::max(1, (p.n_scan + p.slice_rules - 1) / p.slice_rules);
-    const int64_t n_groups = (n + G - 1) / G;
-    int64_t bx = std::max<int64_t>(1, (int64_t)sm_count(rs->device) * 4 / slices);
-    bx = std::max<int64_t>(1, std::min<int64_t>(bx, (n_groups + groups_per_block - 1) / groups_per_block));
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    // every packet's partial minimum starts at the no-match sentinel
-    cudaError_t e = cudaMemsetAsync(partial, 0x7F, (size_t)n * sizeof(int32_t), st);
-    if (e == cudaSuccess) e = ensure_smem(k_rule_split<false>, smem);
-    if (e == cudaSuccess) {
-        k_rule_split<false><<<dim3((unsigned)bx, (unsigned)slices), threads, smem, st>>>(p);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) {
-        const int fb = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count(rs->device) * 8);
-        k_rule_split_finalize<<<std::max(fb, 1), 256, 0, st>>>(partial, p.action, n, out_idx, out_act);
-        e = cudaGetLastError();
-    }
-    return set_status(cuda_status(e));
-}

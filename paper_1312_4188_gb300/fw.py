@@ -66,7 +66,7 @@ class fw_config(ctypes.Structure):
                 ("smem_rules", ctypes.c_int32), ("packets_per_group", ctypes.c_int32),
                 ("rule_slices", ctypes.c_int32), ("compact", ctypes.c_int32), ("predicate", ctypes.c_int32),
                 ("segment_rules", ctypes.c_int32), ("partition", ctypes.c_int32), ("lane_packets", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("filter", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 def make_config(mode=FW_MODE_AUTO, **kw) -> fw_config:
@@ -135,6 +135,7 @@ SIGNATURES = {
     "fw_ruleset_partition": (ctypes.c_int, [P, P, P, P]),
     "fw_partition_plan": (ctypes.c_int, [P, I64, ctypes.c_int32, P, P, P, P, P]),
     "fw_ruleset_check": (ctypes.c_int, [P]),
+    "fw_ruleset_filter": (ctypes.c_int, [P, P, P]),
     "fw_classify": (ctypes.c_int, [P, ctypes.POINTER(fw_headers), I64, P, P, P]),
     "fw_classify_ex": (ctypes.c_int, [P, ctypes.POINTER(fw_headers), I64, P, P, P, ctypes.POINTER(fw_config)]),
     "fw_host_pipeline_create": (ctypes.c_int, [I64, ctypes.c_int, ctypes.POINTER(P)]),
@@ -166,6 +167,8 @@ SIGNATURES = {
     "fw_server_unregister_buffer": (ctypes.c_int, [P, P]),
     "fw_server_get_stats": (ctypes.c_int, [P, ctypes.POINTER(fw_server_stats)]),
     "fw_server_replay": (ctypes.c_int, [P, ctypes.POINTER(fw_request), I64, I64]),
+    "fw_int32_peak_launch": (ctypes.c_int, [ctypes.c_int, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P,
+                                            ctypes.POINTER(I64)]),
     "fw_last_status": (ctypes.c_int, []),
     "fw_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "fw_abi_version": (ctypes.c_int, []),
@@ -236,6 +239,12 @@ class Ruleset:
         _check(lib().fw_ruleset_partition(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
                "fw_ruleset_partition")
         return {"classes": a.value, "key_field": b.value, "key_bits": c.value}
+
+    def filter(self) -> dict:
+        """{"words" (0 = no bucket filter), "bytes"} of the rule set's bucket filter."""
+        w, b = ctypes.c_int32(), ctypes.c_int64()
+        _check(lib().fw_ruleset_filter(self.handle, ctypes.byref(w), ctypes.byref(b)), "fw_ruleset_filter")
+        return {"words": w.value, "bytes": b.value}
 
     def size(self) -> int:
         return int(lib().fw_ruleset_size(self.handle))
@@ -537,3 +546,16 @@ def pinned_headers(h: dict) -> dict:
     import torch
     views = {"src": np.int32, "dst": np.int32, "sport": np.int16, "dport": np.int16, "proto": np.uint8}
     return {f: torch.from_numpy(np.ascontiguousarray(h[f]).view(views[f])).pin_memory() for f in HEADER_FIELDS}
+
+
+INT32_PEAK_KINDS = {"alu_lop3": 0, "fma_imad": 1, "mixed": 2}
+
+
+def fw_int32_peak_launch(kind: int, iters: int, blocks: int, threads: int, sink, stream=None) -> int:
+    """Enqueue the integer-throughput microbenchmark (``sink``: device tensor of at least
+    blocks*threads uint32); returns the instruction count of the launch (lanes x instructions)."""
+    ops = ctypes.c_int64()
+    s = lib().fw_int32_peak_launch(int(kind), int(iters), int(blocks), int(threads),
+                                   ctypes.c_void_p(sink.data_ptr()), _stream_handle(stream), ctypes.byref(ops))
+    _check(s, "fw_int32_peak_launch")
+    return int(ops.value)

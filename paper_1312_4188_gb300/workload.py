@@ -181,13 +181,16 @@ def _gen_block(rules, n_rules, m, seed, block, in_rule_frac, cdf, rank_perm=None
 
 
 def gen_packets(rules: np.ndarray, n: int, seed: int, in_rule_frac: float = 0.6,
-                zipf_s: float | None = None, start: int = 0, rank_perm: np.ndarray | None = None) -> dict:
+                zipf_s: float | None = None, start: int = 0, rank_perm: np.ndarray | None = None,
+                workers: int = 1) -> dict:
     """Draw packets ``start .. start+n-1`` of the batch defined by (rules, seed, ...).
 
     Returns SoA numpy arrays keyed by ``HEADER_FIELDS``. ``zipf_s=None`` picks the
     rule of an in-rule packet uniformly; otherwise Zipf(zipf_s) over the index, or,
     with ``rank_perm`` (a permutation of the rule indices), over the ranks, rank r
     naming rule ``rank_perm[r]`` (popular rules no longer sit at the top of the list).
+    ``workers`` > 1 draws the blocks on that many threads (each block has its own
+    generator, so the result does not depend on it).
     """
     n_rules = int(rules.shape[0])
     cdf = zipf_cdf(n_rules, zipf_s) if (zipf_s is not None and n_rules > 0) else None
@@ -196,13 +199,22 @@ def gen_packets(rules: np.ndarray, n: int, seed: int, in_rule_frac: float = 0.6,
         return out
     end = start + n
     b0, b1 = start // BLOCK, (end - 1) // BLOCK
-    for b in range(b0, b1 + 1):
+
+    def one(b):
         bs = b * BLOCK
         blk = _gen_block(rules, n_rules, BLOCK, seed, b, in_rule_frac, cdf, rank_perm)
         lo = max(start, bs)
         hi = min(end, bs + BLOCK)
         for f in HEADER_FIELDS:
             out[f][lo - start:hi - start] = blk[f][lo - bs:hi - bs]
+
+    if workers > 1 and b1 > b0:
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(min(int(workers), b1 - b0 + 1)) as ex:
+            list(ex.map(one, range(b0, b1 + 1)))
+    else:
+        for b in range(b0, b1 + 1):
+            one(b)
     return out
 
 
@@ -243,7 +255,7 @@ WORKLOADS = {
 }
 
 
-def make_workload(name: str, n_packets: int | None = None):
+def make_workload(name: str, n_packets: int | None = None, workers: int = 1):
     w = WORKLOADS[name]
     rules = gen_rules(w["n_rules"], w["rules_seed"])
     if w.get("drop_catch_alls"):
@@ -253,7 +265,7 @@ def make_workload(name: str, n_packets: int | None = None):
         rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence((w["rules_seed"], w["rank_perm_seed"]))))
         perm = rng.permutation(len(rules))
     n = w["n_packets"] if n_packets is None else n_packets
-    hdr = gen_packets(rules, n, w["packets_seed"], zipf_s=w["zipf_s"], rank_perm=perm)
+    hdr = gen_packets(rules, n, w["packets_seed"], zipf_s=w["zipf_s"], rank_perm=perm, workers=workers)
     return rules, hdr
 
 
@@ -263,18 +275,24 @@ def log_uniform_int(rng: np.random.Generator, lo: int, hi: int, size: int) -> np
 
 
 def gen_batched(n_sets: int = 256, seed: int = 7, rules_range=(64, 65536), packets_range=(1024, 1 << 20),
-                zipf_s: float | None = None):
+                zipf_s: float | None = None, workers: int = 1):
     """``n_sets`` independent (rules, headers) jobs with log-uniform rule and packet counts.
 
     Every set is drawn with the rule generator above from its own seed, and its
     batch with the packet generator (same 60/40 in-rule / uniform mix).
+    ``workers`` > 1 draws the sets on that many threads (same result).
     """
     rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence((int(seed), 0x42415443))))
     nr = log_uniform_int(rng, rules_range[0], rules_range[1], n_sets)
     npk = log_uniform_int(rng, packets_range[0], packets_range[1], n_sets)
-    jobs = []
-    for i in range(n_sets):
+
+    def one(i):
         rules = gen_rules(int(nr[i]), 1_000_000 + 1000 * int(seed) + i)
         hdr = gen_packets(rules, int(npk[i]), 2_000_000 + 1000 * int(seed) + i, zipf_s=zipf_s)
-        jobs.append((rules, hdr))
-    return jobs
+        return rules, hdr
+
+    if workers > 1 and n_sets > 1:
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(min(int(workers), n_sets)) as ex:
+            return list(ex.map(one, range(n_sets)))
+    return [one(i) for i in range(n_sets)]

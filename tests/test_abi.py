@@ -124,6 +124,33 @@ def test_classify_rejects_bad_arguments(L):
     assert L.fw_classify_ex(fake, ctypes.byref(hp), 8, fake, fake, None, ctypes.byref(cfg)) == fw.FW_EINVAL
 
 
+def test_ruleset_filter_rejects_null(L):
+    w, b = ctypes.c_int32(), ctypes.c_int64()
+    assert L.fw_ruleset_filter(None, ctypes.byref(w), ctypes.byref(b)) == fw.FW_EINVAL
+    fake = ctypes.c_void_p(64)  # never dereferenced: argument checks come first
+    assert L.fw_ruleset_filter(fake, None, ctypes.byref(b)) == fw.FW_EINVAL
+    assert L.fw_ruleset_filter(fake, ctypes.byref(w), None) == fw.FW_EINVAL
+
+
+def test_filter_field_out_of_range_is_rejected(L):
+    fake = ctypes.c_void_p(1)  # never dereferenced: argument checks come first
+    hp = fw.fw_headers(*([ctypes.c_void_p(16)] * 5))
+    for v in (-1, 3):
+        cfg = fw.make_config(fw.FW_MODE_PACKET_SPLIT, filter=v)
+        assert L.fw_classify_ex(fake, ctypes.byref(hp), 8, fake, fake, None, ctypes.byref(cfg)) == fw.FW_EINVAL
+
+
+def test_int32_peak_rejects_bad_arguments(L):
+    ops = ctypes.c_int64()
+    fake = ctypes.c_void_p(256)  # never dereferenced: argument checks come first
+    for kind, iters, blocks, threads, sink, out in ((3, 1, 1, 32, fake, ops), (-1, 1, 1, 32, fake, ops),
+                                                    (0, 0, 1, 32, fake, ops), (0, 1 << 25, 1, 32, fake, ops),
+                                                    (0, 1, 0, 32, fake, ops), (0, 1, 1, 48, fake, ops),
+                                                    (0, 1, 1, 1024, fake, ops), (0, 1, 1, 32, None, ops)):
+        assert L.fw_int32_peak_launch(kind, iters, blocks, threads, sink, None, ctypes.byref(out)) == fw.FW_EINVAL
+    assert L.fw_int32_peak_launch(0, 1, 1, 32, fake, None, None) == fw.FW_EINVAL
+
+
 STRUCTS = ("fw_headers", "fw_config", "fw_lindex_config", "fw_lindex_stats", "fw_job", "fw_plan_config",
            "fw_server_config", "fw_server_stats", "fw_request")
 

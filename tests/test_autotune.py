@@ -45,6 +45,12 @@ def test_candidates_are_valid_launch_shapes(c):
         assert c.get("segment_rules", 0) % 4 == 0
         if c.get("lane_packets") == 2:  # the two-packet kernel: at most 1,024 threads per SM
             assert bt * c.get("blocks_per_sm", 1) <= 1024
+    if c.get("filter") == 1:  # the bucket-filter kernel: at most 512 threads, at most 3 blocks of 512
+        assert bt <= 512 and bt * c.get("blocks_per_sm", 3) <= 1536
+    if c["mode"].startswith("rule_split") and c.get("partition", 0) != 2:
+        # partitioned rule split: fixed groups, warp and grid mode in blocks of at most 256 threads
+        assert c.get("packets_per_group", 0) == 0
+        assert c["mode"] == "rule_split_block" or bt <= 256
 
 
 def test_plan_candidates():

@@ -38,15 +38,24 @@ CONFIGS = [
     ("packet_split", {"compact": 2, "predicate": fw.FW_PRED_CLAMP}),
     ("packet_split", {"compact": 2, "smem_rules": -1, "predicate": fw.FW_PRED_CMP}),
     ("packet_split", {"compact": 2, "block_threads": 96, "blocks_per_sm": 1, "smem_rules": 512}),
+    ("packet_split", {"filter": 2}),
     ("rule_split_warp", {}),
-    ("rule_split_warp", {"packets_per_group": 32, "block_threads": 64}),
+    ("rule_split_warp", {"block_threads": 64, "blocks_per_sm": 8}),
+    ("rule_split_warp", {"partition": 2}),
+    ("rule_split_warp", {"partition": 2, "packets_per_group": 32, "block_threads": 64}),
     ("rule_split_block", {}),
-    ("rule_split_block", {"block_threads": 64, "packets_per_group": 96}),
     ("rule_split_block", {"block_threads": 160}),
-    ("rule_split_block", {"block_threads": 512, "packets_per_group": 128}),
+    ("rule_split_block", {"block_threads": 32}),
+    ("rule_split_block", {"partition": 2}),
+    ("rule_split_block", {"partition": 2, "block_threads": 64, "packets_per_group": 96}),
+    ("rule_split_block", {"partition": 2, "block_threads": 160}),
+    ("rule_split_block", {"partition": 2, "block_threads": 512, "packets_per_group": 128}),
     ("rule_split_grid", {}),
     ("rule_split_grid", {"rule_slices": 3}),
-    ("rule_split_grid", {"rule_slices": 64, "packets_per_group": 32}),
+    ("rule_split_grid", {"rule_slices": 2, "block_threads": 96}),
+    ("rule_split_grid", {"partition": 2}),
+    ("rule_split_grid", {"partition": 2, "rule_slices": 3}),
+    ("rule_split_grid", {"partition": 2, "rule_slices": 64, "packets_per_group": 32}),
 ]
 CFG_IDS = [f"{m}-{'-'.join(f'{k}{v}' for k, v in kw.items()) or 'default'}" for m, kw in CONFIGS]
 

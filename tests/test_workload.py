@@ -101,3 +101,18 @@ def test_without_catch_alls_removes_exactly_the_catch_alls():
     assert np.array_equal(kept, rules[~ca])  # list order kept
     r2, _ = W.make_workload("scan_10k_x_16m_no_catch_all", 1000)
     assert not any(P.rule_sets(r) == P.rule_sets(P.catch_all()[0]) for r in r2)
+
+
+def test_threaded_generation_gives_the_same_inputs():
+    rules = W.gen_rules(300, 11)
+    n = 3 * W.BLOCK + 12345
+    a = W.gen_packets(rules, n, 12, zipf_s=1.1, start=777)
+    b = W.gen_packets(rules, n, 12, zipf_s=1.1, start=777, workers=4)
+    for f in W.HEADER_FIELDS:
+        assert np.array_equal(a[f], b[f])
+    s1 = W.gen_batched(6, seed=3, rules_range=(64, 512), packets_range=(1024, 4096))
+    s4 = W.gen_batched(6, seed=3, rules_range=(64, 512), packets_range=(1024, 4096), workers=4)
+    for (r1, h1), (r4, h4) in zip(s1, s4):
+        assert np.array_equal(r1, r4)
+        for f in W.HEADER_FIELDS:
+            assert np.array_equal(h1[f], h4[f])

@@ -41,20 +41,41 @@ def _noalloc(torch, rs, dh, n, cfg=None):
     return s, idx[:n], act[:n]
 
 
-def test_two_calls_match_the_allocating_entry_point(torch_cuda):
+def _call(torch, rs, dh, n, idx, act, cfg=None):
+    hs = fw.headers_struct(dh)
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return fw.lib().fw_classify_rule_split_noalloc(rs.handle, ctypes.byref(hs), n, ctypes.c_void_p(idx.data_ptr()),
+                                                   ctypes.c_void_p(act.data_ptr()), st,
+                                                   ctypes.byref(cfg) if cfg is not None else None)
+
+
+@pytest.mark.parametrize("partition", [0, 2], ids=["partition", "whole_list"])
+def test_two_calls_match_the_allocating_entry_point(torch_cuda, partition):
     torch = torch_cuda
     rules = W.gen_rules(3000, 17)
     keep = ~((rules["src_prefix"] == 0) & (rules["dst_prefix"] == 0))  # deep scans, many unmatched
     rules = rules[keep]
     rs = fw.fw_ruleset_create(rules)
+    cfg = fw.make_config("rule_split_grid", partition=partition)
     batches = [W.gen_packets(rules, 300_001, 18), W.gen_packets(rules, 77_777, 19, zipf_s=1.1)]
+    dhs = [fw.headers_to_device(h) for h in batches]
+    outs = [(torch.full((len(h["src"]),), -7, dtype=torch.int32, device="cuda"),
+             torch.full((len(h["src"]),), 9, dtype=torch.uint8, device="cuda")) for h in batches]
+    wants = [fw.fw_classify(rs, dh, len(h["src"]), config=cfg) for dh, h in zip(dhs, batches)]
+    # warm-up: the first call on a device may load the library's module (and its scratch array)
+    assert _call(torch, rs, dhs[1], len(batches[1]["src"]), *outs[1], cfg) == fw.FW_OK
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    alloc0, reserved0 = torch.cuda.memory_allocated(), torch.cuda.memory_reserved()
     for call, hdr in enumerate(batches):
         n = len(hdr["src"])
-        dh = fw.headers_to_device(hdr)
-        want_idx, want_act = fw.fw_classify(rs, dh, n, config=fw.make_config("rule_split_grid"))
-        s, idx, act = _noalloc(torch, rs, dh, n)
+        idx, act = outs[call]
+        s = _call(torch, rs, dhs[call], n, idx, act, cfg)
         torch.cuda.synchronize()
         assert s == fw.FW_OK, f"call {call}: status {s}"
+        assert torch.cuda.mem_get_info()[0] == free0, f"call {call}: device memory was allocated"
+        assert torch.cuda.memory_allocated() == alloc0 and torch.cuda.memory_reserved() == reserved0
+        want_idx, want_act = wants[call]
         assert torch.equal(idx, want_idx), f"call {call}: rule index differs from fw_classify_ex"
         assert torch.equal(act, want_act), f"call {call}: action differs from fw_classify_ex"
         assert int((idx >= 0).sum()) > 0 and int((idx < 0).sum()) > 0
@@ -77,6 +98,17 @@ def test_limits_and_arguments(torch_cuda):
     bad = fw.make_config("packet_split")
     s, _, _ = _noalloc(torch, rs, dh, 64, bad)
     assert s == fw.FW_EINVAL
+    bad = fw.make_config("rule_split_grid")
+    bad.reserved[1] = 3  # reserved fields must be zero, as for fw_classify_ex
+    s, _, _ = _noalloc(torch, rs, dh, 64, bad)
+    assert s == fw.FW_EINVAL
+    ex = fw.lib().fw_classify_ex(rs.handle, ctypes.byref(hs), 64, None, None, None, ctypes.byref(bad))
+    assert ex == fw.FW_EINVAL
+    # an empty batch is a no-op for all three calls, and none of them clears the last failure
+    assert L.fw_last_status() == fw.FW_EINVAL
+    assert L.fw_classify_rule_split_noalloc(rs.handle, ctypes.byref(hs), 0, None, None, None, None) == fw.FW_OK
+    assert L.fw_classify(rs.handle, ctypes.byref(hs), 0, None, None, None) == fw.FW_OK
+    assert L.fw_last_status() == fw.FW_EINVAL
     # the largest accepted batch, with explicit slices
     n = fw.FW_NOALLOC_MAX_PACKETS
     hdr = W.gen_packets(rules, n, 7)
