@@ -266,6 +266,34 @@ int fw_partition_plan(const fw_rule *rules, int64_t n, int32_t granule, int32_t 
 int fw_ruleset_filter(const fw_ruleset *rs, int32_t *words, int64_t *bytes);
 
 /*
+ * The bucket filter a rule set built from these rules would hold (host only,
+ * no device memory): the rules up to the first catch-all are partitioned as by
+ * fw_partition_plan (granule 1) and, when the partition admits a filter (see
+ * fw_ruleset_filter), its filter block is built and copied to `block`.
+ * The paper has no counterpart: this exposes the host-side construction so
+ * that it can be checked without a GPU.
+ *  Outputs: *words (0 = no filter, else 1 or 2 32-bit words per bitmap row),
+ *  *bytes (the block size, 0 without a filter), class_off / class_len
+ *  (FW_MAX_CLASSES entries each, may be NULL): first stored record and record
+ *  count (a multiple of 4, padding included) of every class sub-list.
+ *  Block layout, every part starting on a 16-byte boundary, nc classes,
+ *  W words per row, R stored records: three bitmap tables of nc x 256 rows of
+ *  W uint32 words each (table 0 indexed by the source address's top 8 bits,
+ *  table 1 by the destination's, table 2 by (sport >> 12) << 4 | (dport >> 12);
+ *  row bit j = record j of the class sub-list); nc exact masks of W words
+ *  (bit j: the record needs no exact test); R exact-test records of four
+ *  uint32 (source address bits 23..0 | min(32 - prefix, 24) << 24; the same
+ *  for the destination; sport_lo | (sport_hi - sport_lo) << 16; the same for
+ *  dport); R verdict words (original rule index | action << 31); the 256-byte
+ *  protocol -> protocol class table; the FW_MAX_CLASSES int32 class offsets.
+ * FW_EINVAL as fw_partition_plan, or for NULL bytes/words, capacity < 0, or a
+ * NULL block with capacity > 0; FW_ERANGE when 0 < capacity < the block size.
+ * With capacity 0 only the sizes are returned.
+ */
+int fw_filter_plan(const fw_rule *rules, int64_t n, void *block, int64_t capacity, int64_t *bytes,
+                   int32_t *words, int32_t *class_off, int32_t *class_len);
+
+/*
  * Synchronise the device and report whether any kernel that used `rs` gave
  * up on a bounded wait since the last check (FW_ETIMEOUT; the flag is then
  * cleared) or a CUDA error is pending (FW_ECUDA).

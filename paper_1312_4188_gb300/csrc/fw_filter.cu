@@ -214,27 +214,26 @@ static bool prefix_meets_bucket(uint32_t addr, unsigned len, uint32_t b) {
     return (b >> (8 - len)) == (addr >> (32 - len));
 }
 
-cudaError_t build_filter(const fw_rule *rules, const std::vector<std::vector<int64_t>> &lists,
-                         const std::vector<uint8_t> &class_of, int n_proto_classes, fw_ruleset *rs) {
-    rs->filter_words = 0;
-    rs->filter_bytes = 0;
-    rs->d_filter = nullptr;
-    const int nc = rs->n_classes;
+int filter_block(const fw_rule *rules, const std::vector<std::vector<int64_t>> &lists,
+                 const std::vector<uint8_t> &class_of, int key_bits, const int32_t *class_off,
+                 const int32_t *class_len, std::vector<unsigned char> &blk) {
+    blk.clear();
+    const int nc = (int)lists.size();
+    const int n_proto_classes = nc >> key_bits;
     int longest = 0;
-    for (int c = 0; c < nc; ++c) longest = std::max(longest, rs->class_len[c]);
-    if (nc < 1 || longest > kFilterMaxRecords) return cudaSuccess;
+    for (int c = 0; c < nc; ++c) longest = std::max(longest, class_len[c]);
+    if (nc < 1 || longest > kFilterMaxRecords) return 0;
     // the "every other protocol" classes must hold protocol-"any" rules only
     for (int c = 0; c < nc; ++c) {
-        if ((c >> rs->key_bits) != n_proto_classes - 1) continue;
+        if ((c >> key_bits) != n_proto_classes - 1) continue;
         for (int64_t k : lists[c])
-            if (!rules[k].proto_any) return cudaSuccess;
+            if (!rules[k].proto_any) return 0;
     }
     const int W = longest <= 32 ? 1 : 2;
-    const int64_t records = rs->class_off[kMaxClasses - 1] + rs->class_len[kMaxClasses - 1];
+    const int64_t records = class_off[kMaxClasses - 1] + class_len[kMaxClasses - 1];
     const FilterLayout L = filter_layout(nc, W, records);
-    if (L.total > 227 * 1024 - 64) return cudaSuccess;  // must fit one block's shared memory
-    const int64_t bytes = L.total;
-    std::vector<unsigned char> blk((size_t)bytes, 0);
+    if (L.total > 227 * 1024 - 64) return 0;  // must fit one block's shared memory
+    blk.assign((size_t)L.total, 0);
     uint32_t *tab = reinterpret_cast<uint32_t *>(blk.data() + L.tables);
     uint32_t *exact = reinterpret_cast<uint32_t *>(blk.data() + L.exact);
     uint4 *recs = reinterpret_cast<uint4 *>(blk.data() + L.recs);
@@ -243,7 +242,7 @@ cudaError_t build_filter(const fw_rule *rules, const std::vector<std::vector<int
     for (int c = 0; c < nc; ++c) {
         for (size_t j = 0; j < lists[c].size(); ++j) {
             const fw_rule &r = rules[lists[c][j]];
-            const int64_t at = rs->class_off[c] + (int64_t)j;
+            const int64_t at = class_off[c] + (int64_t)j;
             recs[at] = verify_record(r);
             vw[at] = (uint32_t)lists[c][j] | ((uint32_t)(r.action & 1u) << 31);
             for (uint32_t b = 0; b < 256; ++b) {
@@ -262,12 +261,23 @@ cudaError_t build_filter(const fw_rule *rules, const std::vector<std::vector<int
         }
     }
     std::memcpy(blk.data() + L.class_of, class_of.data(), 256);
-    std::memcpy(blk.data() + L.class_off, rs->class_off, sizeof(int32_t) * kMaxClasses);
-    cudaError_t e = dev_malloc(&rs->d_filter, (size_t)bytes);
-    if (e == cudaSuccess) e = cudaMemcpy(rs->d_filter, blk.data(), (size_t)bytes, cudaMemcpyHostToDevice);
+    std::memcpy(blk.data() + L.class_off, class_off, sizeof(int32_t) * kMaxClasses);
+    return W;
+}
+
+cudaError_t build_filter(const fw_rule *rules, const std::vector<std::vector<int64_t>> &lists,
+                         const std::vector<uint8_t> &class_of, fw_ruleset *rs) {
+    rs->filter_words = 0;
+    rs->filter_bytes = 0;
+    rs->d_filter = nullptr;
+    std::vector<unsigned char> blk;
+    const int W = filter_block(rules, lists, class_of, rs->key_bits, rs->class_off, rs->class_len, blk);
+    if (W == 0) return cudaSuccess;
+    cudaError_t e = dev_malloc(&rs->d_filter, blk.size());
+    if (e == cudaSuccess) e = cudaMemcpy(rs->d_filter, blk.data(), blk.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
     rs->filter_words = W;
-    rs->filter_bytes = bytes;
+    rs->filter_bytes = (int64_t)blk.size();
     return cudaSuccess;
 }
 
@@ -323,3 +333,34 @@ int launch_filter(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *ou
 }
 
 }  // namespace fwk
+
+using namespace fwk;
+
+extern "C" int fw_filter_plan(const fw_rule *rules, int64_t n, void *block, int64_t capacity, int64_t *bytes,
+                              int32_t *words, int32_t *class_off, int32_t *class_len) {
+    if (n < 0 || (n > 0 && rules == nullptr) || n > (int64_t(1) << 30) || capacity < 0 ||
+        (capacity > 0 && block == nullptr) || bytes == nullptr || words == nullptr)
+        return set_status(FW_EINVAL);
+    int64_t n_eff = n;
+    for (int64_t k = 0; k < n; ++k) {
+        const int s = validate_rule(rules[k]);
+        if (s != FW_OK) return set_status(s);
+        if (n_eff == n && is_catch_all(rules[k])) n_eff = k + 1;
+    }
+    std::vector<uint8_t> class_of;
+    std::vector<std::vector<int64_t>> lists;
+    int key_field = 0, key_bits = 0;
+    partition_lists(rules, n_eff, 1, class_of, lists, key_field, key_bits);
+    int32_t off[kMaxClasses], len[kMaxClasses];
+    pack_sublists(lists, off, len);
+    std::vector<unsigned char> blk;
+    *words = filter_block(rules, lists, class_of, key_bits, off, len, blk);
+    *bytes = (int64_t)blk.size();
+    if (class_off != nullptr) std::memcpy(class_off, off, sizeof(off));
+    if (class_len != nullptr) std::memcpy(class_len, len, sizeof(len));
+    if (!blk.empty() && capacity > 0) {
+        if (capacity < (int64_t)blk.size()) return set_status(FW_ERANGE);
+        std::memcpy(block, blk.data(), blk.size());
+    }
+    return FW_OK;
+}

@@ -341,7 +341,15 @@ __host__ __device__ inline FilterLayout filter_layout(int n_classes, int words, 
 // leaves filter_words 0 otherwise. Returns a CUDA error only for a failed
 // allocation or copy.
 cudaError_t build_filter(const fw_rule *rules, const std::vector<std::vector<int64_t>> &lists,
-                         const std::vector<uint8_t> &class_of, int n_proto_classes, fw_ruleset *rs);
+                         const std::vector<uint8_t> &class_of, fw_ruleset *rs);
+// The filter block itself (host only): fills `blk` and returns the words per bitmap row, or
+// returns 0 (and leaves `blk` empty) when the partition does not admit a filter.
+int filter_block(const fw_rule *rules, const std::vector<std::vector<int64_t>> &lists,
+                 const std::vector<uint8_t> &class_of, int key_bits, const int32_t *class_off,
+                 const int32_t *class_len, std::vector<unsigned char> &blk);
+// Offsets and lengths of the stored sub-lists: each list padded to a multiple of 4 records,
+// stored one after another (kMaxClasses entries; classes past lists.size() are empty).
+void pack_sublists(const std::vector<std::vector<int64_t>> &lists, int32_t *class_off, int32_t *class_len);
 struct HdrPtrs;
 // Rule split (fw_rule_split.cu): warp, block or grid mode over the partition or the whole
 // list; grid mode combines through `scratch` (n int32 of device memory) when it is given, else

@@ -145,6 +145,16 @@ void protocol_classes(const fw_rule *rules, int64_t n, std::vector<uint8_t> &cla
     }
 }
 
+void pack_sublists(const std::vector<std::vector<int64_t>> &lists, int32_t *class_off, int32_t *class_len) {
+    int64_t off = 0;
+    for (int c = 0; c < kMaxClasses; ++c) {
+        const int64_t len = c < (int)lists.size() ? (int64_t)(lists[c].size() + 3) / 4 * 4 : 0;
+        class_off[c] = (int32_t)off;
+        class_len[c] = (int32_t)len;
+        off += len;
+    }
+}
+
 void partition_lists(const fw_rule *rules, int64_t n, int64_t granule, std::vector<uint8_t> &class_of,
                      std::vector<std::vector<int64_t>> &lists, int &key_field, int &key_bits) {
     std::vector<std::vector<int64_t>> plists;
@@ -247,13 +257,8 @@ extern "C" int fw_ruleset_create_ex(const fw_rule *rules, int64_t n, fw_ruleset 
         rs->key_field = key_field;
         rs->key_bits = key_bits;
         rs->n_classes = (int)lists.size();
-        int64_t off = 0;
-        for (int c = 0; c < kMaxClasses; ++c) {
-            const int64_t len = c < rs->n_classes ? (int64_t)(lists[c].size() + 3) / 4 * 4 : 0;
-            rs->class_off[c] = (int32_t)off;
-            rs->class_len[c] = (int32_t)len;
-            off += len;
-        }
+        pack_sublists(lists, rs->class_off, rs->class_len);
+        const int64_t off = rs->class_off[kMaxClasses - 1] + rs->class_len[kMaxClasses - 1];
         rs->part_pad = std::max<int64_t>(kChunkRules, (off + kChunkRules - 1) / kChunkRules * kChunkRules);
         part_rec.resize(rs->part_pad);
         part_wtop.resize(rs->part_pad);
@@ -304,7 +309,7 @@ extern "C" int fw_ruleset_create_ex(const fw_rule *rules, int64_t n, fw_ruleset 
     if (e == cudaSuccess) e = cudaMemcpy(rs->d_class_of, part_class_of.data(), 256, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(rs->d_action, ha.data(), rs->n_pad, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(rs->d_status, 0, sizeof(unsigned));
-    if (e == cudaSuccess) e = build_filter(rules, part_lists, part_class_of, rs->n_classes >> rs->key_bits, rs);
+    if (e == cudaSuccess) e = build_filter(rules, part_lists, part_class_of, rs);
     if (e != cudaSuccess) {
         fw_ruleset_destroy(rs);
         cudaGetLastError();

@@ -136,6 +136,7 @@ SIGNATURES = {
     "fw_partition_plan": (ctypes.c_int, [P, I64, ctypes.c_int32, P, P, P, P, P]),
     "fw_ruleset_check": (ctypes.c_int, [P]),
     "fw_ruleset_filter": (ctypes.c_int, [P, P, P]),
+    "fw_filter_plan": (ctypes.c_int, [P, I64, P, I64, P, P, P, P]),
     "fw_classify": (ctypes.c_int, [P, ctypes.POINTER(fw_headers), I64, P, P, P]),
     "fw_classify_ex": (ctypes.c_int, [P, ctypes.POINTER(fw_headers), I64, P, P, P, ctypes.POINTER(fw_config)]),
     "fw_host_pipeline_create": (ctypes.c_int, [I64, ctypes.c_int, ctypes.POINTER(P)]),
@@ -277,6 +278,23 @@ def fw_partition_plan(rules, granule: int = 1) -> dict:
     _check(s, "fw_partition_plan")
     return {"classes": a.value, "key_field": b.value, "key_bits": c.value, "class_len": lens[:a.value].tolist(),
             "proto_class": pc}
+
+
+def fw_filter_plan(rules) -> dict:
+    """The bucket filter a rule set of ``rules`` would hold, built on the host: {"words", "block"
+    (uint8 array, empty without a filter), "class_off", "class_len"}."""
+    r = _as_rules(rules)
+    nb, w = ctypes.c_int64(), ctypes.c_int32()
+    off = np.zeros(8, dtype=np.int32)
+    ln = np.zeros(8, dtype=np.int32)
+    rp = r.ctypes.data_as(P) if r.size else None
+    _check(lib().fw_filter_plan(rp, int(r.shape[0]), None, 0, ctypes.byref(nb), ctypes.byref(w), None, None),
+           "fw_filter_plan")
+    blk = np.zeros(max(nb.value, 0), dtype=np.uint8)
+    _check(lib().fw_filter_plan(rp, int(r.shape[0]), blk.ctypes.data_as(P) if blk.size else None, int(blk.size),
+                                ctypes.byref(nb), ctypes.byref(w), off.ctypes.data_as(P), ln.ctypes.data_as(P)),
+           "fw_filter_plan")
+    return {"words": w.value, "block": blk, "class_off": off, "class_len": ln}
 
 
 def fw_ruleset_create(rules) -> Ruleset:

@@ -48,14 +48,25 @@ def edge_rules(n, seed, whole_share=0.15):
         hi_v = np.where(kind == 0, 65535, np.where(kind == 1, lo_v, np.where(kind == 5, np.minimum(lo_v + 4095, 65535), np.minimum(lo_v + width, 65535))))
         r[lo_f] = lo_v
         r[hi_f] = hi_v
-    whole = rng.random(n) < whole_share
-    r["src_prefix"][whole] = rng.integers(0, 9, whole.sum())
-    r["dst_prefix"][whole] = rng.integers(0, 9, whole.sum())
+    u = rng.random(n)
+    whole = u < whole_share
+    # nearly whole: every field on bucket edges but one port end a little inside its bucket
+    near = (u >= whole_share) & (u < 2 * whole_share)
+    wn = whole | near
+    r["src_prefix"][wn] = rng.integers(0, 9, wn.sum())
+    r["dst_prefix"][wn] = rng.integers(0, 9, wn.sum())
     for lo_f, hi_f in (("sport_lo", "sport_hi"), ("dport_lo", "dport_hi")):
-        a = rng.integers(0, 16, whole.sum())
-        b = np.minimum(a + rng.integers(0, 4, whole.sum()), 15)
-        r[lo_f][whole] = a * 4096
-        r[hi_f][whole] = b * 4096 + 4095
+        a = rng.integers(0, 16, wn.sum())
+        b = np.minimum(a + rng.integers(0, 4, wn.sum()), 15)
+        r[lo_f][wn] = a * 4096
+        r[hi_f][wn] = b * 4096 + 4095
+    k = np.nonzero(near)[0]
+    which = rng.integers(0, 4, k.size)  # sport lo / sport hi / dport lo / dport hi moved inside
+    step = rng.integers(1, 200, k.size)
+    for f, w in (("sport_lo", 0), ("sport_hi", 1), ("dport_lo", 2), ("dport_hi", 3)):
+        sel = k[which == w]
+        v = r[f][sel].astype(np.int64) + (step[which == w] if w % 2 == 0 else -step[which == w])
+        r[f][sel] = v
     return r
 
 

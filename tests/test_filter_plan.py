@@ -1,0 +1,168 @@
+"""The bucket filter's host-built tables and exact-test records against the oracle (CPU only).
+
+fw_filter_plan returns the filter block a rule set would stage into shared
+memory. Here the block is decoded by its documented layout and used to
+classify packets the way the filter kernel does: AND the packet's three bucket
+rows in its class, take the candidates in increasing record order, and accept
+the first one whose exact-mask bit is set or whose exact-test record accepts
+the packet. The verdict word of that record must equal the oracle's first
+match and action for every packet (random and edge packets, many rule sets).
+Two properties are checked on their own as well: the oracle's first match
+always has all three bucket bits set (the rows never drop a matching rule),
+and a record marked exact contains every packet whose bucket bits it has.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import partition_ref as R
+from paper_1312_4188_gb300 import fw, workload as W
+from test_filter_gpu import edge_packets, edge_rules
+
+
+def up16(b):
+    return (b + 15) // 16 * 16
+
+
+def decode(plan, n_classes):
+    """Arrays of the filter block (documented layout)."""
+    blk, w = plan["block"], plan["words"]
+    recs_n = int(plan["class_off"][-1] + plan["class_len"][-1])
+    tab_bytes = 3 * n_classes * 256 * w * 4
+    exact_off = up16(tab_bytes)
+    recs_off = up16(exact_off + n_classes * w * 4)
+    vw_off = up16(recs_off + recs_n * 16)
+    cls_off = up16(vw_off + recs_n * 4)
+    words = blk[:tab_bytes].view(np.uint32).reshape(3, n_classes, 256, w).astype(np.uint64)
+    rows = words[..., 0] | (words[..., 1] << np.uint64(32) if w == 2 else np.uint64(0))
+    ex = blk[exact_off:exact_off + n_classes * w * 4].view(np.uint32).reshape(n_classes, w).astype(np.uint64)
+    exact = ex[:, 0] | (ex[:, 1] << np.uint64(32) if w == 2 else np.uint64(0))
+    recs = blk[recs_off:recs_off + recs_n * 16].view(np.uint32).reshape(recs_n, 4)
+    vw = blk[vw_off:vw_off + recs_n * 4].view(np.uint32)
+    proto_class = blk[cls_off:cls_off + 256]
+    class_off = blk[cls_off + 256:cls_off + 256 + 32].view(np.int32)
+    return rows, exact, recs, vw, proto_class, class_off
+
+
+def reachable(rules):
+    ca = np.nonzero((rules["src_prefix"] == 0) & (rules["dst_prefix"] == 0) & (rules["sport_lo"] == 0) &
+                    (rules["sport_hi"] == 65535) & (rules["dport_lo"] == 0) & (rules["dport_hi"] == 65535) &
+                    (rules["proto_any"] != 0))[0]
+    return rules[:int(ca[0]) + 1] if len(ca) else rules
+
+
+def exact_test(rec, h):
+    """The record's exact test (source/destination address bits below the bucket, port ranges)."""
+    x, y, z, w = (rec[:, i].astype(np.int64) for i in range(4))
+    s, d = h["src"].astype(np.int64), h["dst"].astype(np.int64)
+    sp, dp = h["sport"].astype(np.int64), h["dport"].astype(np.int64)
+    ok = (((s ^ x) & 0xFFFFFF) >> (x >> 24)) == 0
+    ok &= (((d ^ y) & 0xFFFFFF) >> (y >> 24)) == 0
+    ok &= (sp - (z & 0xFFFF) >= 0) & (sp - (z & 0xFFFF) <= (z >> 16))
+    ok &= (dp - (w & 0xFFFF) >= 0) & (dp - (w & 0xFFFF) <= (w >> 16))
+    return ok
+
+
+def filter_classify(rules, hdr):
+    """Verdicts of the filter built for `rules`, decoded and applied as the kernel applies it."""
+    plan = fw.fw_filter_plan(rules)
+    if plan["words"] == 0:
+        return None
+    part = fw.fw_partition_plan(reachable(rules))
+    nc, kf, kb = part["classes"], part["key_field"], part["key_bits"]
+    rows, exact, recs, vw, proto_class, class_off = decode(plan, nc)
+    assert np.array_equal(proto_class, part["proto_class"])
+    assert np.array_equal(class_off, plan["class_off"])
+    c = R.packet_class(hdr, part["proto_class"], kf, kb).astype(np.int64)
+    s8 = hdr["src"].astype(np.int64) >> 24
+    d8 = hdr["dst"].astype(np.int64) >> 24
+    pb = ((hdr["sport"].astype(np.int64) >> 12) << 4) | (hdr["dport"].astype(np.int64) >> 12)
+    m = rows[0, c, s8] & rows[1, c, d8] & rows[2, c, pb]
+    off = class_off[c].astype(np.int64)
+    n = len(c)
+    idx = np.full(n, -1, dtype=np.int64)
+    act = np.zeros(n, dtype=np.uint8)
+    done = np.zeros(n, dtype=bool)
+    for j in range(32 * plan["words"]):
+        bit = ((m >> np.uint64(j)) & np.uint64(1)).astype(bool) & ~done
+        if not bit.any():
+            continue
+        at = off + j
+        sel = np.nonzero(bit)[0]
+        ex = ((exact[c[sel]] >> np.uint64(j)) & np.uint64(1)).astype(bool)
+        ok = ex | exact_test(recs[at[sel]], {f: hdr[f][sel] for f in W.HEADER_FIELDS})
+        hit = sel[ok]
+        v = vw[at[hit]]
+        idx[hit] = v & 0x7FFFFFFF
+        act[hit] = v >> 31
+        done[hit] = True
+    return plan, (c, m, off, rows, exact, recs, vw), idx.astype(np.int32), act
+
+
+RULE_SETS = [("edge", 12, 1), ("edge", 30, 2), ("edge", 45, 3), ("edge", 70, 4), ("edge", 100, 5), ("edge", 160, 6),
+             ("gen", 3, 7), ("gen", 40, 8), ("gen", 10_000, 3), ("gen", 1000, 1)]
+
+
+def rule_set(kind, n, seed):
+    return edge_rules(n, 900 + seed) if kind == "edge" else W.gen_rules(n, seed)
+
+
+@pytest.mark.parametrize("kind,n,seed", RULE_SETS)
+def test_filter_block_classifies_like_the_oracle(kind, n, seed):
+    rules = rule_set(kind, n, seed)
+    a = W.gen_packets(rules, 20_000, 60 + seed)
+    b = edge_packets(reachable(rules), 61 + seed)
+    hdr = {f: np.concatenate([a[f], b[f]]) for f in W.HEADER_FIELDS}
+    got = filter_classify(rules, hdr)
+    if got is None:
+        pytest.skip("no filter for this rule set")
+    _, (c, m, off, rows, exact, recs, vw), idx, act = got
+    o_idx, o_act, _ = oracle.classify(rules, hdr)
+    bad = np.nonzero((idx != o_idx) | (act != o_act))[0]
+    assert bad.size == 0, f"{bad.size} packets differ from the oracle, first {bad[0]}"
+    # the first match always survives the bucket rows
+    matched = np.nonzero(o_idx >= 0)[0]
+    orig = (vw & 0x7FFFFFFF).astype(np.int64)
+    for i in matched[:3000]:
+        pos = np.nonzero(orig[off[i]:off[i] + 64] == o_idx[i])[0]
+        assert pos.size >= 1 and (int(m[i]) >> int(pos[0])) & 1, f"packet {i}: its first match is not a candidate"
+
+
+def test_exact_records_contain_every_packet_of_their_buckets():
+    for kind, n, seed in RULE_SETS:
+        rules = rule_set(kind, n, seed)
+        plan = fw.fw_filter_plan(rules)
+        if plan["words"] == 0:
+            continue
+        part = fw.fw_partition_plan(reachable(rules))
+        rows, exact, recs, vw, _, class_off = decode(plan, part["classes"])
+        hdr = W.gen_packets(rules, 20_000, 70 + seed)
+        c = R.packet_class(hdr, part["proto_class"], part["key_field"], part["key_bits"]).astype(np.int64)
+        s8, d8 = hdr["src"].astype(np.int64) >> 24, hdr["dst"].astype(np.int64) >> 24
+        pb = ((hdr["sport"].astype(np.int64) >> 12) << 4) | (hdr["dport"].astype(np.int64) >> 12)
+        m = rows[0, c, s8] & rows[1, c, d8] & rows[2, c, pb] & exact[c]
+        for j in range(32 * plan["words"]):
+            sel = np.nonzero(((m >> np.uint64(j)) & np.uint64(1)).astype(bool))[0]
+            if sel.size == 0:
+                continue
+            rule = int(vw[class_off[c[sel[0]]] + j] & 0x7FFFFFFF)
+            same = sel[(vw[class_off[c[sel]] + j] & 0x7FFFFFFF) == rule]
+            one = rules[rule:rule + 1]
+            o_idx, _, _ = oracle.classify(one, {f: hdr[f][same] for f in W.HEADER_FIELDS})
+            assert np.all(o_idx == 0), f"exact record {j} (rule {rule}) misses packets of its buckets"
+
+
+def test_no_filter_cases_and_arguments():
+    long_list = W.gen_rules(400, 12)
+    long_list = long_list[~((long_list["src_prefix"] == 0) & (long_list["dst_prefix"] == 0))]
+    assert fw.fw_filter_plan(long_list)["words"] == 0
+    many = W.gen_rules(60, 13)
+    many["proto_any"] = 0
+    many["proto"] = np.arange(60) % 12
+    assert fw.fw_filter_plan(many)["words"] == 0
+    empty = fw.fw_filter_plan(W.empty_rules(0))
+    assert empty["words"] == 1 and empty["block"].size > 0
+    bad = W.gen_rules(5, 1)
+    bad["src_prefix"][2] = 40
+    with pytest.raises(fw.FwError):
+        fw.fw_filter_plan(bad)

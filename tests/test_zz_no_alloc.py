@@ -65,16 +65,20 @@ def test_two_calls_match_the_allocating_entry_point(torch_cuda, partition):
     # warm-up: the first call on a device may load the library's module (and its scratch array)
     assert _call(torch, rs, dhs[1], len(batches[1]["src"]), *outs[1], cfg) == fw.FW_OK
     torch.cuda.synchronize()
+    # no torch work between the two measured calls, so that any change in free device memory is
+    # the entry point's own
     free0 = torch.cuda.mem_get_info()[0]
     alloc0, reserved0 = torch.cuda.memory_allocated(), torch.cuda.memory_reserved()
+    status, free_after = [], []
     for call, hdr in enumerate(batches):
-        n = len(hdr["src"])
-        idx, act = outs[call]
-        s = _call(torch, rs, dhs[call], n, idx, act, cfg)
+        status.append(_call(torch, rs, dhs[call], len(hdr["src"]), *outs[call], cfg))
         torch.cuda.synchronize()
-        assert s == fw.FW_OK, f"call {call}: status {s}"
-        assert torch.cuda.mem_get_info()[0] == free0, f"call {call}: device memory was allocated"
-        assert torch.cuda.memory_allocated() == alloc0 and torch.cuda.memory_reserved() == reserved0
+        free_after.append(torch.cuda.mem_get_info()[0])
+    assert status == [fw.FW_OK, fw.FW_OK], status
+    assert free_after == [free0, free0], f"device memory was allocated: free {free0} -> {free_after}"
+    assert torch.cuda.memory_allocated() == alloc0 and torch.cuda.memory_reserved() == reserved0
+    for call in range(2):
+        idx, act = outs[call]
         want_idx, want_act = wants[call]
         assert torch.equal(idx, want_idx), f"call {call}: rule index differs from fw_classify_ex"
         assert torch.equal(act, want_act), f"call {call}: action differs from fw_classify_ex"
