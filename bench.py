@@ -783,12 +783,16 @@ def main():
 
     if rank == 0 and args.modes:
         modes = {}
-        variants = {"packet_split_one_lane": ("packet_split", {"lane_packets": 1}),
+        variants = {"packet_split_scan_x2": ("packet_split", {"filter": 2}),
+                    "packet_split_one_lane": ("packet_split", {"lane_packets": 1}),
                     "packet_split_dense": ("packet_split", {"block_threads": 768, "blocks_per_sm": 2, "smem_rules": 1024}),
                     "packet_split_whole_list": ("packet_split", {"partition": 2}),
                     "packet_split_lockstep": ("packet_split", {"compact": 2}),
                     "packet_split_lockstep_whole_list": ("packet_split", {"compact": 2, "partition": 2}),
-                    "packet_split_lockstep_clamp": ("packet_split", {"compact": 2, "predicate": fw.FW_PRED_CLAMP})}
+                    "packet_split_lockstep_clamp": ("packet_split", {"compact": 2, "predicate": fw.FW_PRED_CLAMP}),
+                    "rule_split_warp_whole_list": ("rule_split_warp", {"partition": 2}),
+                    "rule_split_block_whole_list": ("rule_split_block", {"partition": 2}),
+                    "rule_split_grid_whole_list": ("rule_split_grid", {"partition": 2})}
         tmp_i, tmp_a = torch.empty_like(out_idx), torch.empty_like(out_act)
         for name, (mname, kw) in variants.items():
             c = fw.make_config(mname, **kw)

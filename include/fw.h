@@ -277,15 +277,16 @@ int fw_ruleset_filter(const fw_ruleset *rs, int32_t *words, int64_t *bytes);
  *  (FW_MAX_CLASSES entries each, may be NULL): first stored record and record
  *  count (a multiple of 4, padding included) of every class sub-list.
  *  Block layout, every part starting on a 16-byte boundary, nc classes,
- *  W words per row, R stored records: three bitmap tables of nc x 256 rows of
- *  W uint32 words each (table 0 indexed by the source address's top 8 bits,
- *  table 1 by the destination's, table 2 by (sport >> 12) << 4 | (dport >> 12);
- *  row bit j = record j of the class sub-list); nc exact masks of W words
- *  (bit j: the record needs no exact test); R exact-test records of four
- *  uint32 (source address bits 23..0 | min(32 - prefix, 24) << 24; the same
- *  for the destination; sport_lo | (sport_hi - sport_lo) << 16; the same for
- *  dport); R verdict words (original rule index | action << 31); the 256-byte
- *  protocol -> protocol class table; the FW_MAX_CLASSES int32 class offsets.
+ *  W words per row, R stored records: the bitmap rows, [class][table][256]
+ *  rows of W uint32 words (table 0 indexed by the source address's top 8
+ *  bits, table 1 by the destination's, table 2 by (sport >> 12) << 4 |
+ *  (dport >> 12); row bit j = record j of the class sub-list); one uint4 per
+ *  class (first stored record, exact mask low and high word, 0; exact bit j:
+ *  the record needs no exact test); R exact-test records of two uint4
+ *  ({saddr & smask, smask, daddr & dmask, dmask} and {-sport_lo,
+ *  sport_hi - sport_lo, -dport_lo, dport_hi - dport_lo}, mod 2^32); R verdict
+ *  words (original rule index | action << 31); the 256-byte protocol ->
+ *  protocol class table.
  * FW_EINVAL as fw_partition_plan, or for NULL bytes/words, capacity < 0, or a
  * NULL block with capacity > 0; FW_ERANGE when 0 < capacity < the block size.
  * With capacity 0 only the sizes are returned.

@@ -23,14 +23,13 @@
 // aligned to 4,096) passes exactly when its bits are set, so it needs no test
 // (the exact mask; the catch-all is one such rule).
 //
-// The exact test reads one 16-byte record per candidate:
-//   x: source address bits 23..0 (pre-masked) | shift << 24,
-//      shift = min(32 - prefix, 24): the address test is
-//      ((src ^ x) & 0xFFFFFF) >> shift == 0 (bits 31..24 are decided by the
-//      bucket, exactly, for every prefix);
-//   y: the same for the destination;
-//   z: sport_lo | (sport_hi - sport_lo) << 16: (sport - lo) <= width, unsigned;
-//   w: the same for the destination port.
+// The exact test reads one 32-byte record per candidate, the arithmetic form
+// of the address and port tests: {saddr & smask, smask, daddr & dmask,
+// dmask} and {-sport_lo, sport_hi - sport_lo, -dport_lo, dport_hi - dport_lo}
+// (mod 2^32); the addresses are tested as ((a ^ addr) & mask) == 0 with one
+// 3-input logic op each, the ports as (port - lo) <= width with one
+// multiply-add (FMA pipe) and one unsigned compare each, all four chained into
+// one predicate.
 // The protocol needs no test: every rule of an exact-protocol class has that
 // protocol or "any", and the filter is built only when the "every other
 // protocol" class holds no exact-protocol rule.
@@ -54,14 +53,15 @@ constexpr int kFilterMaxRecords = 64;  // bits of the widest bitmap row
 
 // Byte offsets of the filter block's parts (32-bit: the block fits in shared memory).
 struct FilterOffsets {
-    int32_t tables, exact, recs, verdicts, class_of, class_off;
+    int32_t tables, classes, recs, verdicts, class_of;
 };
 
 struct FilterParams {
     const unsigned char *blk;  // the filter block in global memory
     FilterOffsets L;
     int32_t blk_bytes;
-    int32_t n_classes, key_field, key_bits;
+    int32_t n_classes, key_bits;
+    uint32_t one;  // the constant 1, opaque to the compiler (the port offsets become multiply-adds)
     HdrPtrs h;
     int64_t n;
     int32_t *out_idx;
@@ -69,45 +69,57 @@ struct FilterParams {
     unsigned *status;
 };
 
-// The exact test of one candidate (see the record layout above).
-__device__ __forceinline__ bool filter_verify(const uint4 &v, uint32_t s, uint32_t d, uint32_t sp, uint32_t dp) {
-    const bool s_ok = (((s ^ v.x) & 0xFFFFFFu) >> (v.x >> 24)) == 0u;
-    const bool d_ok = (((d ^ v.y) & 0xFFFFFFu) >> (v.y >> 24)) == 0u;
-    const bool sp_ok = (sp - (v.z & 0xFFFFu)) <= (v.z >> 16);
-    const bool dp_ok = (dp - (v.w & 0xFFFFu)) <= (v.w >> 16);
-    return s_ok & d_ok & sp_ok & dp_ok;
+// Non-zero exactly when the packet is outside the record's rule (see the record layout above).
+__device__ __forceinline__ uint32_t filter_mismatch(uint32_t s, uint32_t d, uint32_t sp, uint32_t dp, const uint4 &a,
+                                                    const uint4 &b, uint32_t one) {
+    const uint32_t ts = sp * one + b.x;
+    const uint32_t td = dp * one + b.z;
+    uint32_t r;
+    asm("{\n\t"
+        ".reg .pred q;\n\t"
+        ".reg .b32 t;\n\t"
+        "setp.gt.u32 q, %1, %2;\n\t"
+        "lop3.or.b32 t|q, %3, %4, %5, 0x28, q;\n\t"
+        "lop3.or.b32 t|q, %6, %7, %8, 0x28, q;\n\t"
+        "setp.gt.or.u32 q, %9, %10, q;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t"
+        "}"
+        : "=r"(r)
+        : "r"(ts), "r"(b.y), "r"(s), "r"(a.x), "r"(a.y), "r"(d), "r"(a.z), "r"(a.w), "r"(td), "r"(b.w));
+    return r;
 }
 
 template <int W>
 using FilterMask = typename std::conditional<W == 1, uint32_t, uint64_t>::type;
 
-// Candidate mask of one packet and its class's first stored record.
-template <int W>
+// The packet's class (KEY: 0 no address key, 1 source, 2 destination) and the AND of its three
+// bucket rows in that class.
+template <int W, int KEY>
 __device__ __forceinline__ FilterMask<W> filter_candidates(const unsigned char *base, const FilterParams &p,
                                                            uint32_t s, uint32_t d, uint32_t sp, uint32_t dp,
-                                                           uint32_t pr, int &cls) {
+                                                           uint32_t pr, uint32_t &cls) {
     using M = FilterMask<W>;
     uint32_t c = base[p.L.class_of + pr];
-    if (p.key_field != 0) c = (c << p.key_bits) | ((p.key_field == 1 ? s : d) >> (32 - p.key_bits));
-    cls = (int)c;
-    const M *T = reinterpret_cast<const M *>(base + p.L.tables);
-    const uint32_t row = c * 256u, step = (uint32_t)p.n_classes * 256u;
-    return T[row + (s >> 24)] & T[step + row + (d >> 24)] & T[2u * step + row + (((sp >> 12) << 4) | (dp >> 12))];
+    if (KEY != 0) c = (c << p.key_bits) | ((KEY == 1 ? s : d) >> (32 - p.key_bits));
+    cls = c;
+    const M *T = reinterpret_cast<const M *>(base + p.L.tables) + c * 768u;
+    return T[s >> 24] & T[256u + (d >> 24)] & T[512u + (((sp >> 12) << 4) | (dp >> 12))];
 }
 
 // First candidate that passes its exact test: its verdict word, or ~0u.
 template <int W>
 __device__ __forceinline__ uint32_t filter_first(const unsigned char *base, const FilterParams &p, FilterMask<W> m,
-                                                 int cls, uint32_t s, uint32_t d, uint32_t sp, uint32_t dp) {
+                                                 uint32_t cls, uint32_t s, uint32_t d, uint32_t sp, uint32_t dp) {
     using M = FilterMask<W>;
     if (m == 0) return 0xFFFFFFFFu;
-    const int off = reinterpret_cast<const int32_t *>(base + p.L.class_off)[cls];
-    const M ex = reinterpret_cast<const M *>(base + p.L.exact)[cls];
-    const uint4 *V = reinterpret_cast<const uint4 *>(base + p.L.recs) + off;
+    // class info: first stored record, exact mask (low, high word)
+    const uint4 ci = reinterpret_cast<const uint4 *>(base + p.L.classes)[cls];
+    const M ex = W == 1 ? (M)ci.y : (M)(((uint64_t)ci.z << 32) | ci.y);
+    const uint4 *V = reinterpret_cast<const uint4 *>(base + p.L.recs) + 2 * ci.x;
     while (m != 0) {
         const int k = W == 1 ? __ffs((unsigned)m) - 1 : __ffsll((unsigned long long)m) - 1;
-        if (((ex >> k) & 1u) || filter_verify(V[k], s, d, sp, dp))
-            return reinterpret_cast<const uint32_t *>(base + p.L.verdicts)[off + k];
+        if (((ex >> k) & 1u) || filter_mismatch(s, d, sp, dp, V[2 * k], V[2 * k + 1], p.one) == 0u)
+            return reinterpret_cast<const uint32_t *>(base + p.L.verdicts)[ci.x + k];
         m &= m - 1;
     }
     return 0xFFFFFFFFu;
@@ -115,7 +127,7 @@ __device__ __forceinline__ uint32_t filter_first(const unsigned char *base, cons
 
 // The grid-stride loop over packet quads, with the filter block at `base`
 // (shared memory, or global memory after a failed staging wait).
-template <int W, bool VEC>
+template <int W, int KEY, bool VEC>
 __device__ __forceinline__ void filter_loop(const FilterParams &p, const unsigned char *base) {
     const int64_t nq = (p.n + 3) / 4;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -151,8 +163,8 @@ __device__ __forceinline__ void filter_loop(const FilterParams &p, const unsigne
         uint32_t acts = 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            int cls;
-            const FilterMask<W> m = filter_candidates<W>(base, p, s[j], d[j], sp[j], dp[j], pr[j], cls);
+            uint32_t cls;
+            const FilterMask<W> m = filter_candidates<W, KEY>(base, p, s[j], d[j], sp[j], dp[j], pr[j], cls);
             const uint32_t vw = filter_first<W>(base, p, m, cls, s[j], d[j], sp[j], dp[j]);
             idx[j] = vw == 0xFFFFFFFFu ? -1 : (int32_t)(vw & 0x7FFFFFFFu);
             acts |= (vw == 0xFFFFFFFFu ? (uint32_t)FW_DROP : vw >> 31) << (8 * j);
@@ -172,7 +184,7 @@ __device__ __forceinline__ void filter_loop(const FilterParams &p, const unsigne
     }
 }
 
-template <int W, bool VEC>
+template <int W, int KEY, bool VEC>
 __global__ void __launch_bounds__(512, 3) k_packet_split_filter(FilterParams p) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bar;
@@ -188,23 +200,22 @@ __global__ void __launch_bounds__(512, 3) k_packet_split_filter(FilterParams p) 
     }
     const bool ok = mbar_wait_bounded(&bar, 0, p.status);
     if (__syncthreads_and(ok) != 0) {
-        filter_loop<W, VEC>(p, smem);
+        filter_loop<W, KEY, VEC>(p, smem);
     } else {
         // a failed wait leaves the block reading the filter from global memory; before it exits,
         // the copies that may still be in flight into its shared memory get a second bounded wait
-        filter_loop<W, VEC>(p, p.blk);
+        filter_loop<W, KEY, VEC>(p, p.blk);
         if (threadIdx.x == 0) mbar_wait_bounded(&bar, 0, p.status);
     }
 }
 
 // ------------------------------------------------------------ host side
 // Exact-test record of a rule (layout above).
-static uint4 verify_record(const fw_rule &r) {
-    const uint32_t ss = std::min(32u - r.src_prefix, 24u), ds = std::min(32u - r.dst_prefix, 24u);
-    const uint32_t sa = r.src_addr & prefix_mask(r.src_prefix) & 0xFFFFFFu;
-    const uint32_t da = r.dst_addr & prefix_mask(r.dst_prefix) & 0xFFFFFFu;
-    return make_uint4(sa | (ss << 24), da | (ds << 24), r.sport_lo | ((uint32_t)(r.sport_hi - r.sport_lo) << 16),
-                      r.dport_lo | ((uint32_t)(r.dport_hi - r.dport_lo) << 16));
+static void verify_record(const fw_rule &r, uint4 *rec) {
+    const uint32_t sm = prefix_mask(r.src_prefix), dm = prefix_mask(r.dst_prefix);
+    rec[0] = make_uint4(r.src_addr & sm, sm, r.dst_addr & dm, dm);
+    rec[1] = make_uint4(0u - (uint32_t)r.sport_lo, (uint32_t)(r.sport_hi - r.sport_lo), 0u - (uint32_t)r.dport_lo,
+                        (uint32_t)(r.dport_hi - r.dport_lo));
 }
 
 // Does the prefix (addr, len) contain an address whose top 8 bits are b?
@@ -235,33 +246,33 @@ int filter_block(const fw_rule *rules, const std::vector<std::vector<int64_t>> &
     if (L.total > 227 * 1024 - 64) return 0;  // must fit one block's shared memory
     blk.assign((size_t)L.total, 0);
     uint32_t *tab = reinterpret_cast<uint32_t *>(blk.data() + L.tables);
-    uint32_t *exact = reinterpret_cast<uint32_t *>(blk.data() + L.exact);
+    uint4 *cinfo = reinterpret_cast<uint4 *>(blk.data() + L.classes);
     uint4 *recs = reinterpret_cast<uint4 *>(blk.data() + L.recs);
     uint32_t *vw = reinterpret_cast<uint32_t *>(blk.data() + L.verdicts);
     auto set_bit = [&](uint32_t *row, int j) { row[j >> 5] |= 1u << (j & 31); };
+    auto row = [&](int c, int t, uint32_t b) { return tab + (((size_t)c * kFilterTables + t) * 256 + b) * W; };
     for (int c = 0; c < nc; ++c) {
+        uint32_t exact[2] = {0u, 0u};
         for (size_t j = 0; j < lists[c].size(); ++j) {
             const fw_rule &r = rules[lists[c][j]];
             const int64_t at = class_off[c] + (int64_t)j;
-            recs[at] = verify_record(r);
+            verify_record(r, recs + 2 * at);
             vw[at] = (uint32_t)lists[c][j] | ((uint32_t)(r.action & 1u) << 31);
             for (uint32_t b = 0; b < 256; ++b) {
-                if (prefix_meets_bucket(r.src_addr, r.src_prefix, b))
-                    set_bit(tab + ((size_t)(0 * nc + c) * 256 + b) * W, (int)j);
-                if (prefix_meets_bucket(r.dst_addr, r.dst_prefix, b))
-                    set_bit(tab + ((size_t)(1 * nc + c) * 256 + b) * W, (int)j);
+                if (prefix_meets_bucket(r.src_addr, r.src_prefix, b)) set_bit(row(c, 0, b), (int)j);
+                if (prefix_meets_bucket(r.dst_addr, r.dst_prefix, b)) set_bit(row(c, 1, b), (int)j);
             }
             for (uint32_t sb = (uint32_t)r.sport_lo >> 12; sb <= (uint32_t)r.sport_hi >> 12; ++sb)
                 for (uint32_t db = (uint32_t)r.dport_lo >> 12; db <= (uint32_t)r.dport_hi >> 12; ++db)
-                    set_bit(tab + ((size_t)(2 * nc + c) * 256 + ((sb << 4) | db)) * W, (int)j);
+                    set_bit(row(c, 2, (sb << 4) | db), (int)j);
             const bool whole = r.src_prefix <= 8 && r.dst_prefix <= 8 && (r.sport_lo & 0xFFFu) == 0 &&
                                (r.sport_hi & 0xFFFu) == 0xFFFu && (r.dport_lo & 0xFFFu) == 0 &&
                                (r.dport_hi & 0xFFFu) == 0xFFFu;
-            if (whole) set_bit(exact + (size_t)c * W, (int)j);
+            if (whole) exact[j >> 5] |= 1u << (j & 31);
         }
+        cinfo[c] = make_uint4((uint32_t)class_off[c], exact[0], exact[1], 0u);
     }
     std::memcpy(blk.data() + L.class_of, class_of.data(), 256);
-    std::memcpy(blk.data() + L.class_off, class_off, sizeof(int32_t) * kMaxClasses);
     return W;
 }
 
@@ -289,12 +300,12 @@ int launch_filter(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *ou
     const int64_t records = rs->class_off[kMaxClasses - 1] + rs->class_len[kMaxClasses - 1];
     p.blk = rs->d_filter;
     const FilterLayout L = filter_layout(rs->n_classes, rs->filter_words, records);
-    p.L = FilterOffsets{(int32_t)L.tables, (int32_t)L.exact, (int32_t)L.recs, (int32_t)L.verdicts,
-                        (int32_t)L.class_of, (int32_t)L.class_off};
+    p.L = FilterOffsets{(int32_t)L.tables, (int32_t)L.classes, (int32_t)L.recs, (int32_t)L.verdicts,
+                        (int32_t)L.class_of};
     p.blk_bytes = (int32_t)rs->filter_bytes;
     p.n_classes = rs->n_classes;
-    p.key_field = rs->key_field;
     p.key_bits = rs->key_bits;
+    p.one = 1u;
     p.h = h;
     p.n = n;
     p.out_idx = out_idx;
@@ -312,21 +323,29 @@ int launch_filter(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *ou
                      (reinterpret_cast<uintptr_t>(h.sport) % 8 == 0) && (reinterpret_cast<uintptr_t>(h.dport) % 8 == 0) &&
                      (reinterpret_cast<uintptr_t>(h.proto) % 4 == 0) && (reinterpret_cast<uintptr_t>(out_idx) % 16 == 0) &&
                      (reinterpret_cast<uintptr_t>(out_act) % 4 == 0);
+    const int key = rs->key_bits == 0 ? 0 : rs->key_field;
     cudaError_t e = cudaSuccess;
-#define FW_LAUNCH_F(WW, V)                                                                                  \
+#define FW_LAUNCH_F(WW, KK, V)                                                                              \
     do {                                                                                                    \
         if (smem > 48 * 1024)                                                                               \
-            e = cudaFuncSetAttribute(k_packet_split_filter<WW, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                     (int)smem);                                                            \
-        if (e == cudaSuccess) k_packet_split_filter<WW, V><<<(unsigned)blocks, threads, smem, st>>>(p);    \
+            e = cudaFuncSetAttribute(k_packet_split_filter<WW, KK, V>,                                      \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);               \
+        if (e == cudaSuccess) k_packet_split_filter<WW, KK, V><<<(unsigned)blocks, threads, smem, st>>>(p); \
+    } while (0)
+#define FW_LAUNCH_FK(WW, V)                                                                                 \
+    do {                                                                                                    \
+        if (key == 1) FW_LAUNCH_F(WW, 1, V);                                                                \
+        else if (key == 2) FW_LAUNCH_F(WW, 2, V);                                                           \
+        else FW_LAUNCH_F(WW, 0, V);                                                                         \
     } while (0)
     if (rs->filter_words == 1) {
-        if (vec) FW_LAUNCH_F(1, true);
-        else FW_LAUNCH_F(1, false);
+        if (vec) FW_LAUNCH_FK(1, true);
+        else FW_LAUNCH_FK(1, false);
     } else {
-        if (vec) FW_LAUNCH_F(2, true);
-        else FW_LAUNCH_F(2, false);
+        if (vec) FW_LAUNCH_FK(2, true);
+        else FW_LAUNCH_FK(2, false);
     }
+#undef FW_LAUNCH_FK
 #undef FW_LAUNCH_F
     if (e != cudaSuccess) return cuda_status(e);
     return cuda_status(cudaGetLastError());

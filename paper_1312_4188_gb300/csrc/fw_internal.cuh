@@ -321,19 +321,18 @@ int sm_count(int dev);                  // SMs of device `dev` (cached)
 // for n_classes classes, `words` 32-bit words per bitmap row and `records`
 // stored sub-list records (every part starts on a 16-byte boundary).
 struct FilterLayout {
-    int64_t tables, exact, recs, verdicts, class_of, class_off, total;
+    int64_t tables, classes, recs, verdicts, class_of, total;
 };
 constexpr int kFilterTables = 3;  // source top 8 bits, destination top 8 bits, (sport, dport) top 4 bits each
 __host__ __device__ inline FilterLayout filter_layout(int n_classes, int words, int64_t records) {
     FilterLayout L;
     auto up16 = [](int64_t b) { return (b + 15) / 16 * 16; };
-    L.tables = 0;
-    L.exact = up16(L.tables + (int64_t)kFilterTables * n_classes * 256 * words * 4);
-    L.recs = up16(L.exact + (int64_t)n_classes * words * 4);
-    L.verdicts = up16(L.recs + records * 16);
-    L.class_of = up16(L.verdicts + records * 4);
-    L.class_off = L.class_of + 256;
-    L.total = up16(L.class_off + 4 * kMaxClasses);
+    L.tables = 0;                                                          // [class][table][256][words] uint32
+    L.classes = up16(L.tables + (int64_t)kFilterTables * n_classes * 256 * words * 4);  // [class] uint4
+    L.recs = L.classes + (int64_t)n_classes * 16;                          // [record] 2 x uint4
+    L.verdicts = L.recs + records * 32;                                    // [record] uint32
+    L.class_of = up16(L.verdicts + records * 4);                           // [256] uint8
+    L.total = up16(L.class_of + 256);
     return L;
 }
 // Builds rs->d_filter from the partition (lists[c] = original rule indices of

@@ -295,6 +295,89 @@ __global__ void __launch_bounds__(256) k_rule_split_part(PartSplitParams p) {
     }
 }
 
+// Warp mode for short sub-lists: k packets x 32/k rules per warp step. The warp's lanes form
+// 32 / SEG segments of SEG lanes; each segment works on one packet of the group at a time, lane
+// j of the segment testing record k + j of the packet's class sub-list, and the segment's bits of
+// the warp vote give that packet's first match among those SEG records (the segment-level
+// minimum). A segment whose packet is decided (or whose sub-list ends) takes the next packet of
+// the group, so the warp's lanes stay busy across packets of different depths and classes.
+template <int SEG>
+__global__ void __launch_bounds__(256) k_rule_split_seg(PartSplitParams p) {
+    __shared__ PktA stage_all[8][kWarpGroup];
+    __shared__ uint8_t cls_all[8][kWarpGroup];
+    __shared__ int res_all[8][kWarpGroup];
+    constexpr int NS = 32 / SEG;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    PktA *stage = stage_all[warp];
+    uint8_t *scls = cls_all[warp];
+    int *res = res_all[warp];
+    const int seg = lane / SEG, sl = lane % SEG;
+    const unsigned seg_mask = (SEG == 32 ? 0xFFFFFFFFu : ((1u << SEG) - 1u)) << (seg * SEG);
+    const int nwarps = blockDim.x >> 5;
+    const int64_t n_groups = (p.n + kWarpGroup - 1) / kWarpGroup;
+    for (int64_t g = (int64_t)blockIdx.x * nwarps + warp; g < n_groups; g += (int64_t)gridDim.x * nwarps) {
+        const int64_t base = g * kWarpGroup;
+        const int cnt = (int)min((int64_t)kWarpGroup, p.n - base);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int t = lane + 32 * u;
+            const int64_t i = base + t;
+            uint32_t s = 0, d = 0, sp = 0, dp = 0, pr = 0;
+            if (t < cnt) {
+                s = p.h.src[i];
+                d = p.h.dst[i];
+                sp = p.h.sport[i];
+                dp = p.h.dport[i];
+                pr = p.h.proto[i];
+            }
+            stage[t] = PktA{s, d, sp, x_of(pr, dp)};
+            scls[t] = (uint8_t)part_class(__ldg(p.class_of + pr), p.key_field, p.key_bits, s, d);
+        }
+        __syncwarp();
+        int cur = seg, k = 0, next = NS;
+        while (true) {
+            const bool active = cur < cnt;
+            if (__ballot_sync(0xFFFFFFFFu, active) == 0u) break;
+            int len = 0, off = 0;
+            bool m = false;
+            if (active) {
+                const PktA pk = stage[cur];
+                const int c = scls[cur];
+                off = p.class_off[c];
+                len = p.class_len[c];
+                const int pos = k + sl;
+                if (pos < len) {
+                    const uint4 a = __ldg(&p.rec[off + pos].a), b = __ldg(&p.rec[off + pos].b);
+                    m = !mismatch_arith(pk, a, b, __ldg(p.wtop + off + pos), p.one);
+                }
+            }
+            const unsigned bits = __ballot_sync(0xFFFFFFFFu, m) & seg_mask;
+            const bool done = active && (bits != 0u || k + SEG >= len);
+            if (done && sl == 0) res[cur] = bits != 0u ? k + (__ffs(bits) - 1 - seg * SEG) : INT_MAX;
+            // decided segments take the next packets of the group, in segment order
+            const unsigned dn = __ballot_sync(0xFFFFFFFFu, done && sl == 0);
+            if (done) {
+                cur = next + __popc(dn & ((1u << (seg * SEG)) - 1u));
+                k = 0;
+            } else {
+                k += SEG;
+            }
+            next += __popc(dn);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int t = lane + 32 * u;
+            if (t >= cnt) continue;
+            const int r = res[t];
+            const uint32_t vw = r != INT_MAX ? __ldg(p.verdict + p.class_off[scls[t]] + r) : 0xFFFFFFFFu;
+            p.out_idx[base + t] = r != INT_MAX ? (int32_t)(vw & 0x7FFFFFFFu) : -1;
+            p.out_act[base + t] = r != INT_MAX ? (uint8_t)(vw >> 31) : (uint8_t)FW_DROP;
+        }
+        __syncwarp();
+    }
+}
+
 // Block mode (the paper's hybrid, Sec. IV.C): the block's warps share a group of 32 packets per
 // warp and split the (class, chunk) work items of that group round-robin; each item tests the
 // class's packets not yet decided at an earlier chunk and combines matches by shared atomicMin.
@@ -412,6 +495,8 @@ int rule_split_run(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *o
         // grid mode: no more slices than the longest sub-list has chunks
         p.slices = grid_mode ? std::max(1, std::min(cfg.rule_slices > 0 ? cfg.rule_slices : 8, max_chunks)) : 1;
         if (p.slices > 65535) return FW_EINVAL;
+        // warp mode over short sub-lists: four packets of 8 records per warp step (k_rule_split_seg)
+        const bool seg = !block_mode && !grid_mode && max_chunks <= 2;
         const int G = block_mode ? threads : kWarpGroup * (threads / 32);
         const int64_t groups = (n + G - 1) / G;
         int64_t bx = std::max<int64_t>(1, (int64_t)sm_count(rs->device) * per_sm / p.slices);
@@ -421,6 +506,7 @@ int rule_split_run(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *o
         if (e == cudaSuccess) {
             if (block_mode) k_rule_split_part_block<<<(unsigned)bx, threads, 0, st>>>(p);
             else if (grid_mode) k_rule_split_part<true><<<dim3((unsigned)bx, (unsigned)p.slices), threads, 0, st>>>(p);
+            else if (seg) k_rule_split_seg<8><<<(unsigned)bx, threads, 0, st>>>(p);
             else k_rule_split_part<false><<<(unsigned)bx, threads, 0, st>>>(p);
             e = cudaGetLastError();
         }

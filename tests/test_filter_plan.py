@@ -28,19 +28,20 @@ def decode(plan, n_classes):
     """Arrays of the filter block (documented layout)."""
     blk, w = plan["block"], plan["words"]
     recs_n = int(plan["class_off"][-1] + plan["class_len"][-1])
-    tab_bytes = 3 * n_classes * 256 * w * 4
-    exact_off = up16(tab_bytes)
-    recs_off = up16(exact_off + n_classes * w * 4)
-    vw_off = up16(recs_off + recs_n * 16)
-    cls_off = up16(vw_off + recs_n * 4)
-    words = blk[:tab_bytes].view(np.uint32).reshape(3, n_classes, 256, w).astype(np.uint64)
+    tab_bytes = n_classes * 3 * 256 * w * 4
+    cls_off = up16(tab_bytes)
+    recs_off = cls_off + n_classes * 16
+    vw_off = recs_off + recs_n * 32
+    pc_off = up16(vw_off + recs_n * 4)
+    words = blk[:tab_bytes].view(np.uint32).reshape(n_classes, 3, 256, w).astype(np.uint64)
     rows = words[..., 0] | (words[..., 1] << np.uint64(32) if w == 2 else np.uint64(0))
-    ex = blk[exact_off:exact_off + n_classes * w * 4].view(np.uint32).reshape(n_classes, w).astype(np.uint64)
-    exact = ex[:, 0] | (ex[:, 1] << np.uint64(32) if w == 2 else np.uint64(0))
-    recs = blk[recs_off:recs_off + recs_n * 16].view(np.uint32).reshape(recs_n, 4)
+    rows = rows.transpose(1, 0, 2)  # [table][class][bucket]
+    ci = blk[cls_off:cls_off + n_classes * 16].view(np.uint32).reshape(n_classes, 4)
+    exact = ci[:, 1].astype(np.uint64) | (ci[:, 2].astype(np.uint64) << np.uint64(32))
+    class_off = ci[:, 0].astype(np.int32)
+    recs = blk[recs_off:recs_off + recs_n * 32].view(np.uint32).reshape(recs_n, 8)
     vw = blk[vw_off:vw_off + recs_n * 4].view(np.uint32)
-    proto_class = blk[cls_off:cls_off + 256]
-    class_off = blk[cls_off + 256:cls_off + 256 + 32].view(np.int32)
+    proto_class = blk[pc_off:pc_off + 256]
     return rows, exact, recs, vw, proto_class, class_off
 
 
@@ -52,14 +53,15 @@ def reachable(rules):
 
 
 def exact_test(rec, h):
-    """The record's exact test (source/destination address bits below the bucket, port ranges)."""
-    x, y, z, w = (rec[:, i].astype(np.int64) for i in range(4))
+    """The record's exact test: masked address equality, port offsets within their widths (mod 2^32)."""
+    r = rec.astype(np.int64)
     s, d = h["src"].astype(np.int64), h["dst"].astype(np.int64)
     sp, dp = h["sport"].astype(np.int64), h["dport"].astype(np.int64)
-    ok = (((s ^ x) & 0xFFFFFF) >> (x >> 24)) == 0
-    ok &= (((d ^ y) & 0xFFFFFF) >> (y >> 24)) == 0
-    ok &= (sp - (z & 0xFFFF) >= 0) & (sp - (z & 0xFFFF) <= (z >> 16))
-    ok &= (dp - (w & 0xFFFF) >= 0) & (dp - (w & 0xFFFF) <= (w >> 16))
+    m32 = 0xFFFFFFFF
+    ok = ((s ^ r[:, 0]) & r[:, 1]) == 0
+    ok &= ((d ^ r[:, 2]) & r[:, 3]) == 0
+    ok &= ((sp + r[:, 4]) & m32) <= r[:, 5]
+    ok &= ((dp + r[:, 6]) & m32) <= r[:, 7]
     return ok
 
 
@@ -72,7 +74,7 @@ def filter_classify(rules, hdr):
     nc, kf, kb = part["classes"], part["key_field"], part["key_bits"]
     rows, exact, recs, vw, proto_class, class_off = decode(plan, nc)
     assert np.array_equal(proto_class, part["proto_class"])
-    assert np.array_equal(class_off, plan["class_off"])
+    assert np.array_equal(class_off, plan["class_off"][:nc])
     c = R.packet_class(hdr, part["proto_class"], kf, kb).astype(np.int64)
     s8 = hdr["src"].astype(np.int64) >> 24
     d8 = hdr["dst"].astype(np.int64) >> 24
