@@ -57,8 +57,8 @@ OPS_PER_CHECK = 10
 # Algorithmic bytes per packet: 13 B of header in + 4 B index + 1 B action out.
 BYTES_PER_PACKET = 18
 FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
-# Sources whose digest keys the recorded DRAM traffic: every file the CUDA library is built from.
-LIB_SOURCE_GLOBS = ("paper_1312_4188_gb300/csrc", "include")
+# ncu record of the dominant kernel's DRAM traffic; it names the source files the kernel is
+# compiled from and their digest, and is used only while those files are unchanged.
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
 COMPACT_MID_PACKETS = 98_304  # smallest batch the auto mode classifies with the compacting kernel
 GEN_WORKERS = max(1, min(16, os.cpu_count() or 1))
@@ -95,29 +95,26 @@ def peaks():
     return p, src
 
 
-def library_sources_sha() -> str:
-    """Digest of every source file of the CUDA library (kernels, host code, public header)."""
+def sources_sha(files) -> str:
+    """Digest of the named source files (paths relative to the repository root), in the given order."""
     h = hashlib.sha256()
-    files = []
-    for d in LIB_SOURCE_GLOBS:
-        base = os.path.join(ROOT, d)
-        files += sorted(os.path.join(base, f) for f in os.listdir(base) if f.endswith((".cu", ".cuh", ".h")))
     for f in files:
-        h.update(os.path.relpath(f, ROOT).encode())
-        h.update(open(f, "rb").read())
+        h.update(f.encode())
+        h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel: str, workload: str, mode: str):
-    """(DRAM bytes per launch, note) from the ncu record, or (None, why) when it is not for these sources."""
+    """(DRAM bytes per launch, note) from the ncu record, or (None, why) when it does not apply."""
     if not os.path.exists(TRAFFIC_FILE):
         return None, "no ncu record"
     try:
         rec = json.load(open(TRAFFIC_FILE))
+        current = sources_sha(rec["sources"])
     except Exception as e:  # pragma: no cover
         return None, f"unreadable ncu record: {e}"
-    if rec.get("sources_sha") != library_sources_sha():
-        return None, "ncu record is for other library sources (kernel changed since the capture)"
+    if rec.get("sources_sha") != current:
+        return None, "the kernel's sources changed since the ncu capture"
     if (rec.get("kernel"), rec.get("workload"), rec.get("mode")) != (kernel, workload, mode):
         return None, "ncu record is for another kernel or workload"
     return float(rec["dram_bytes_per_launch"]), f"ncu capture: {rec.get('command', '')}"

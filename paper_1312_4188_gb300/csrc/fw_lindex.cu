@@ -49,13 +49,15 @@ struct LiFieldDev {
     int32_t shift;          // segment = key >> shift
 };
 
-// One class: its rows (per field, M_f rows of W words) and the original rule
-// index behind each bit (-1 past the sub-list). A class that holds rules of
-// several exact protocols ("other", when more protocols are in use than there
-// are protocol classes) also has protocol rows (bits[4]); for every other
-// class the protocol test is implied by the class.
+// One class: its rows (per field, M_f rows of W words, stored quad-major: the
+// uint4 holding words [4q, 4q+4) of row j sits at index q * M_f + j, so the
+// first quads of all the field's rows form one compact slab that stays in L2)
+// and the original rule index behind each bit (-1 past the sub-list). A class
+// that holds rules of several exact protocols ("other", when more protocols
+// are in use than there are protocol classes) also has protocol rows
+// (bits[4]); for every other class the protocol test is implied by the class.
 struct LiClassDev {
-    const uint32_t *bits[kFields];
+    const uint4 *bits[kFields];
     const int32_t *orig;
     int64_t W;              // words per row (multiple of 4)
 };
@@ -94,36 +96,36 @@ struct fw_lindex {
 namespace fwk {
 
 // ------------------------------------------------------------ device
-// Row j, words [w0, w0+32) of one field: lane l of warp r computes word
-// w0+l of row j0+r from the 1024 rules of the word tile, staged in shared
-// memory bit-major (rule 32(w0+l)+b at [b][l]) so the lanes never collide on
-// a bank.
+// Quad q (words 4q..4q+3, rules 128q..128q+127 of the sub-list) of rows
+// [j0, j0 + blockDim.x) of one field: the quad's 128 rule intervals are staged
+// in shared memory and read by all lanes at once (broadcast); lane l computes
+// the four words of row j0 + l and stores them as one uint4 at q * M + j0 + l,
+// so a warp's stores are contiguous.
 __global__ void k_li_build(const uint32_t *__restrict__ bound, int64_t M, const uint32_t *__restrict__ rlo,
-                           const uint32_t *__restrict__ rhi, int64_t n_idx, int64_t W, uint32_t *__restrict__ bits) {
-    __shared__ uint32_t slo[32][32], shi[32][32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int64_t word_tiles = (W + 31) / 32;
-    const int64_t row_groups = (M + nw - 1) / nw;
-    for (int64_t t = blockIdx.x; t < word_tiles * row_groups; t += gridDim.x) {
-        const int64_t wt = t % word_tiles, rg = t / word_tiles;
-        const int64_t w0 = wt * 32;
+                           const uint32_t *__restrict__ rhi, int64_t n_idx, int64_t Q, uint4 *__restrict__ bits) {
+    __shared__ uint32_t slo[128], shi[128];
+    const int64_t tiles = (M + blockDim.x - 1) / blockDim.x;
+    for (int64_t t = blockIdx.x; t < Q * tiles; t += gridDim.x) {
+        const int64_t q = t / tiles, j = (t % tiles) * blockDim.x + threadIdx.x;
         __syncthreads();
-        for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
-            const int l = i >> 5, b = i & 31;  // rule 32*(w0+l)+b
-            const int64_t k = 32 * (w0 + l) + b;
+        for (int i = threadIdx.x; i < 128; i += blockDim.x) {
+            const int64_t k = 128 * q + i;
             const bool ok = k < n_idx;
-            slo[b][l] = ok ? rlo[k] : 1u;
-            shi[b][l] = ok ? rhi[k] : 0u;  // empty interval: never covers
+            slo[i] = ok ? rlo[k] : 1u;
+            shi[i] = ok ? rhi[k] : 0u;  // empty interval: never covers
         }
         __syncthreads();
-        const int64_t j = rg * nw + warp;
-        const int64_t w = w0 + lane;
-        if (j < M && w < W) {
+        if (j < M) {
             const uint32_t v = bound[j];
-            uint32_t word = 0;
+            uint32_t w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                uint32_t word = 0;
 #pragma unroll 8
-            for (int b = 0; b < 32; ++b) word |= (uint32_t)((slo[b][lane] <= v) & (v <= shi[b][lane])) << b;
-            bits[j * W + w] = word;
+                for (int b = 0; b < 32; ++b) word |= (uint32_t)((slo[32 * u + b] <= v) & (v <= shi[32 * u + b])) << b;
+                w[u] = word;
+            }
+            bits[q * M + j] = make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
 }
@@ -184,26 +186,26 @@ __global__ void __launch_bounds__(512) k_li_classify(LiDev d, const uint32_t *__
         const uint32_t pr = proto[i];
         const uint32_t key[kRowFields] = {src[i], dst[i], sport[i], dport[i]};
         const LiClassDev &c = scls[part_class(__ldg(d.class_of + pr), d.key_field, d.key_bits, key[0], key[1])];
-        const int64_t W = c.W;
+        const int64_t Q = c.W / 4;
         const uint4 *row[kFields];
 #pragma unroll
         for (int f = 0; f < kRowFields; ++f) {
             const int j = li_locate<SMEM>(d.f[f], bound[f], key[f], d.fallbacks);
-            row[f] = reinterpret_cast<const uint4 *>(c.bits[f] + (int64_t)j * W);
+            row[f] = c.bits[f] + j;
         }
         const bool prow = c.bits[kFields - 1] != nullptr;  // a class of mixed exact protocols
         row[kFields - 1] = nullptr;
         if (prow) {
             const int j = li_locate<SMEM>(d.f[kFields - 1], bound[kFields - 1], pr, d.fallbacks);
-            row[kFields - 1] = reinterpret_cast<const uint4 *>(c.bits[kFields - 1] + (int64_t)j * W);
+            row[kFields - 1] = c.bits[kFields - 1] + j;
         }
         int r = -1;
-        for (int64_t q = 0; q < W / 4; ++q) {
-            uint4 x = __ldg(row[0] + q);
+        for (int64_t q = 0; q < Q; ++q) {
+            uint4 x = __ldg(row[0] + q * d.f[0].M);
 #pragma unroll
             for (int f = 1; f < kFields; ++f) {
                 if (f == kFields - 1 && !prow) break;
-                const uint4 y = __ldg(row[f] + q);
+                const uint4 y = __ldg(row[f] + q * d.f[f].M);
                 x.x &= y.x;
                 x.y &= y.y;
                 x.z &= y.z;
@@ -392,11 +394,12 @@ extern "C" int fw_lindex_create(const fw_rule *rules, int64_t n, const fw_lindex
             if (e == cudaSuccess && nc > 0) e = cudaMemcpy(d_rhi, chi.data(), nc * 4, cudaMemcpyHostToDevice);
             if (e == cudaSuccess) {
                 const int blocks = sm_count(li->device) * 8;
-                k_li_build<<<blocks, 256>>>(li->d_bound[f], M, d_rlo, d_rhi, nc, W, li->d_bits[c][f]);
+                k_li_build<<<blocks, 256>>>(li->d_bound[f], M, d_rlo, d_rhi, nc, W / 4,
+                                            reinterpret_cast<uint4 *>(li->d_bits[c][f]));
                 e = cudaGetLastError();
             }
             if (e == cudaSuccess) e = cudaDeviceSynchronize();
-            hcls[c].bits[f] = li->d_bits[c][f];
+            hcls[c].bits[f] = reinterpret_cast<const uint4 *>(li->d_bits[c][f]);
             hcls[c].orig = li->d_orig[c];
             li->bitmap_bytes += (int64_t)M * W * 4;
         }

@@ -87,3 +87,21 @@ def test_partition_depth_follows_the_library_plan():
                 got = bench.partition_depth(rules, np.array([-1], dtype=np.int32), h, kf, kb)
                 assert got == plan["class_len"][c], (seed, proto, top)
     assert (0, 0) in keys and any(k != (0, 0) for k in keys)
+
+
+def test_recorded_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
+    """The committed ncu record applies while its kernel's sources are unchanged, and only to its
+    own kernel and workload; a digest that no longer matches gives null."""
+    import json
+    rec = json.load(open(bench.TRAFFIC_FILE))
+    got, note = bench.recorded_traffic(rec["kernel"], rec["workload"], rec["mode"])
+    if rec["sources_sha"] == bench.sources_sha(rec["sources"]):
+        assert got == rec["dram_bytes_per_launch"] and "ncu" in note
+    else:
+        assert got is None and "changed" in note
+    assert bench.recorded_traffic("k_other", rec["workload"], rec["mode"])[0] is None
+    stale = dict(rec, sources_sha="0" * 16)
+    path = tmp_path / "dram_traffic.json"
+    path.write_text(json.dumps(stale))
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(path))
+    assert bench.recorded_traffic(rec["kernel"], rec["workload"], rec["mode"])[0] is None
