@@ -787,6 +787,9 @@ def main():
                     "packet_split_lockstep": ("packet_split", {"compact": 2}),
                     "packet_split_lockstep_whole_list": ("packet_split", {"compact": 2, "partition": 2}),
                     "packet_split_lockstep_clamp": ("packet_split", {"compact": 2, "predicate": fw.FW_PRED_CLAMP}),
+                    "rule_split_warp_seg2": ("rule_split_warp", {"segment_rules": 2}),
+                    "rule_split_warp_seg8": ("rule_split_warp", {"segment_rules": 8}),
+                    "rule_split_warp_seg16": ("rule_split_warp", {"segment_rules": 16}),
                     "rule_split_warp_whole_list": ("rule_split_warp", {"partition": 2}),
                     "rule_split_block_whole_list": ("rule_split_block", {"partition": 2}),
                     "rule_split_grid_whole_list": ("rule_split_grid", {"partition": 2})}

@@ -138,7 +138,11 @@ typedef struct fw_headers {
  *                     (multiple of 4; later segments double). Default: with two
  *                     packets per lane 512, or 32 when the longest class
  *                     sub-list exceeds 2,048 rules; with one packet per lane 64
- *                     (partitioned) or 16 (whole list).
+ *                     (partitioned) or 16 (whole list). Rule split, warp mode
+ *                     over the partition when every class sub-list holds at
+ *                     most 64 rules: lanes per packet (2, 4, 8 or 16; a warp
+ *                     step tests 32 / segment_rules packets against that many
+ *                     consecutive rules each; default 4).
  *  partition:         packet split, arithmetic form: 1 = scan the partition
  *                     (default with compaction), 2 = scan the whole list
  *                     (default for the lockstep scan). A rule set keeps, per

@@ -49,7 +49,8 @@ PACKET_SPLIT_CANDIDATES += [dict(mode="packet_split", filter=1, block_threads=bt
                             for (bt, bps) in ((512, 3), (512, 2), (256, 6), (384, 4), (128, 12))]
 
 RULE_SPLIT_CANDIDATES = (
-    [dict(mode="rule_split_warp", block_threads=bt, blocks_per_sm=bps) for bt in (128, 256) for bps in (4, 8)]
+    [dict(mode="rule_split_warp", block_threads=bt, blocks_per_sm=bps, segment_rules=sr)
+     for bt in (128, 256) for bps in (4, 8) for sr in (2, 4, 8, 16)]
     + [dict(mode="rule_split_block", block_threads=bt) for bt in (128, 256, 512)]
     + [dict(mode="rule_split_grid", rule_slices=s) for s in (1, 2, 4, 8)]
     + [dict(mode="rule_split_warp", partition=2, block_threads=bt, packets_per_group=g)

@@ -7,8 +7,10 @@
 // list of jobs into a device work list of items, each a run of up to
 // `packets_per_item` packets of one job. A persistent grid of warps takes
 // items from a global counter (dynamic scheduling, so cheap and expensive
-// items balance), and each warp runs the two-packets-per-lane first-match scan
-// of fw_scan.cuh on its item against the item's own rule set, read through L1.
+// items balance), and each warp classifies its item against the item's own rule
+// set, read through L1: through the rule set's bucket filter when it has one
+// (fw_filter.cuh), else with the two-packets-per-lane first-match scan of
+// fw_scan.cuh.
 // Items are ordered by decreasing rule-set size so the long scans start
 // first. Per size class of rule set (by reachable rules) the plan carries its
 // own item size and first rule segment, chosen by the autotuner.
@@ -20,6 +22,19 @@
 #include "fw_batch.cuh"
 
 namespace fwk {
+
+// One item of a job with a bucket filter: the job's filter block read through L1, one packet per
+// lane at a time. Kept out of line so that its registers do not add to the scan path's.
+__device__ __noinline__ void batch_filter_item(const BatchJobDev &J, const BatchItem &item, int lane, uint32_t one) {
+    const FilterView fv = J.fv;
+    for (int k = lane; k < item.count; k += 32) {
+        const int64_t i = item.start + k;
+        const uint32_t vw = filter_packet_wide<-1>(J.filter, fv, J.h.src[i], J.h.dst[i], J.h.sport[i], J.h.dport[i],
+                                                   J.h.proto[i], one);
+        J.out_idx[i] = vw == 0xFFFFFFFFu ? -1 : (int32_t)(vw & 0x7FFFFFFFu);
+        J.out_act[i] = vw == 0xFFFFFFFFu ? (uint8_t)FW_DROP : (uint8_t)(vw >> 31);
+    }
+}
 
 __global__ void __launch_bounds__(1024) k_batch(BatchParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -33,6 +48,10 @@ __global__ void __launch_bounds__(1024) k_batch(BatchParams p) {
         if (it >= (unsigned long long)p.n_items) break;
         const BatchItem item = p.items[it];
         const BatchJobDev &J = p.jobs[item.job];
+        if (J.filter != nullptr) {
+            batch_filter_item(J, item, lane, p.one);
+            continue;
+        }
         BatchTarget<PolArith> t;
         t.h = J.h;
         t.n = J.n;
@@ -80,6 +99,8 @@ void fill_batch_job(BatchJobDev &d, const fw_ruleset *rs, const fw_headers &h, i
     d.n = n;
     d.out_idx = out_idx;
     d.out_act = out_act;
+    d.filter = rs->filter_words > 0 ? rs->d_filter : nullptr;
+    d.fv = filter_view(rs);
 }
 
 size_t batch_smem_bytes(int threads, int32_t qcap) {

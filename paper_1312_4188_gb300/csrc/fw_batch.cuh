@@ -2,7 +2,7 @@
 // the serving scheduler (fw_serve.cu).
 #pragma once
 
-#include "fw_scan.cuh"
+#include "fw_filter.cuh"
 
 namespace fwk {
 
@@ -25,6 +25,9 @@ struct BatchJobDev {
     int64_t n;
     int32_t *out_idx;
     uint8_t *out_act;
+    // the rule set's bucket filter (null when it has none): its items are classified through it
+    const unsigned char *filter;
+    FilterView fv;
 };
 
 struct BatchItem {

@@ -4,8 +4,8 @@
 //
 // The rule list is partitioned as for the other packet-split kernels: a packet
 // of class c (its protocol class and address key) can only be matched by the
-// rules of class c's sub-list, kept in list order. For short sub-lists (at most
-// 64 records) each class also gets three bitmaps per bucket value, one bit per
+// rules of class c's sub-list, kept in list order. For sub-lists of at most
+// 512 records each class also gets three bitmaps per bucket value, one bit per
 // sub-list record:
 //   table 0, bucket = top 8 bits of the source address: bit j set when rule j's
 //            source prefix contains some address with those top bits;
@@ -34,9 +34,12 @@
 // protocol or "any", and the filter is built only when the "every other
 // protocol" class holds no exact-protocol rule.
 //
-// One filter block (tables, exact masks, records, verdict words, the protocol
-// class table and the class offsets) is staged into each block's shared memory
-// by 1-D TMA bulk copies (no multicast) with a bounded mbarrier wait; a thread
+// One filter block (tables, class info, exact masks, records, verdict words,
+// the protocol class table). Rows of one or two words: every block stages the
+// filter block into its shared memory by 1-D TMA bulk copies (no multicast)
+// with a bounded mbarrier wait, and a row is one integer. Wider rows (sub-lists
+// of 65..512 records): the block stays in global memory, read through L1, and
+// the rows are ANDed a word at a time up to the first match. In both, a thread
 // takes four consecutive packets per step (16-byte header loads), so a warp
 // streams 832 contiguous header bytes per step and writes its verdicts with
 // 16-byte and 4-byte stores.
@@ -45,22 +48,14 @@
 #include <type_traits>
 
 #include "fw_alloc.h"
-#include "fw_scan.cuh"
+#include "fw_filter.cuh"
 
 namespace fwk {
 
-constexpr int kFilterMaxRecords = 64;  // bits of the widest bitmap row
-
-// Byte offsets of the filter block's parts (32-bit: the block fits in shared memory).
-struct FilterOffsets {
-    int32_t tables, classes, recs, verdicts, class_of;
-};
-
 struct FilterParams {
     const unsigned char *blk;  // the filter block in global memory
-    FilterOffsets L;
+    FilterView v;
     int32_t blk_bytes;
-    int32_t n_classes, key_bits;
     uint32_t one;  // the constant 1, opaque to the compiler (the port offsets become multiply-adds)
     HdrPtrs h;
     int64_t n;
@@ -69,60 +64,18 @@ struct FilterParams {
     unsigned *status;
 };
 
-// Non-zero exactly when the packet is outside the record's rule (see the record layout above).
-__device__ __forceinline__ uint32_t filter_mismatch(uint32_t s, uint32_t d, uint32_t sp, uint32_t dp, const uint4 &a,
-                                                    const uint4 &b, uint32_t one) {
-    const uint32_t ts = sp * one + b.x;
-    const uint32_t td = dp * one + b.z;
-    uint32_t r;
-    asm("{\n\t"
-        ".reg .pred q;\n\t"
-        ".reg .b32 t;\n\t"
-        "setp.gt.u32 q, %1, %2;\n\t"
-        "lop3.or.b32 t|q, %3, %4, %5, 0x28, q;\n\t"
-        "lop3.or.b32 t|q, %6, %7, %8, 0x28, q;\n\t"
-        "setp.gt.or.u32 q, %9, %10, q;\n\t"
-        "selp.u32 %0, 1, 0, q;\n\t"
-        "}"
-        : "=r"(r)
-        : "r"(ts), "r"(b.y), "r"(s), "r"(a.x), "r"(a.y), "r"(d), "r"(a.z), "r"(a.w), "r"(td), "r"(b.w));
-    return r;
-}
-
-template <int W>
-using FilterMask = typename std::conditional<W == 1, uint32_t, uint64_t>::type;
-
-// The packet's class (KEY: 0 no address key, 1 source, 2 destination) and the AND of its three
-// bucket rows in that class.
+// Verdict word of one packet (~0u when no rule matches). W = 1, 2: one-integer
+// rows from `base` (shared memory); W = 0: rows of any width from global memory.
 template <int W, int KEY>
-__device__ __forceinline__ FilterMask<W> filter_candidates(const unsigned char *base, const FilterParams &p,
-                                                           uint32_t s, uint32_t d, uint32_t sp, uint32_t dp,
-                                                           uint32_t pr, uint32_t &cls) {
-    using M = FilterMask<W>;
-    uint32_t c = base[p.L.class_of + pr];
-    if (KEY != 0) c = (c << p.key_bits) | ((KEY == 1 ? s : d) >> (32 - p.key_bits));
-    cls = c;
-    const M *T = reinterpret_cast<const M *>(base + p.L.tables) + c * 768u;
-    return T[s >> 24] & T[256u + (d >> 24)] & T[512u + (((sp >> 12) << 4) | (dp >> 12))];
-}
-
-// First candidate that passes its exact test: its verdict word, or ~0u.
-template <int W>
-__device__ __forceinline__ uint32_t filter_first(const unsigned char *base, const FilterParams &p, FilterMask<W> m,
-                                                 uint32_t cls, uint32_t s, uint32_t d, uint32_t sp, uint32_t dp) {
-    using M = FilterMask<W>;
-    if (m == 0) return 0xFFFFFFFFu;
-    // class info: first stored record, exact mask (low, high word)
-    const uint4 ci = reinterpret_cast<const uint4 *>(base + p.L.classes)[cls];
-    const M ex = W == 1 ? (M)ci.y : (M)(((uint64_t)ci.z << 32) | ci.y);
-    const uint4 *V = reinterpret_cast<const uint4 *>(base + p.L.recs) + 2 * ci.x;
-    while (m != 0) {
-        const int k = W == 1 ? __ffs((unsigned)m) - 1 : __ffsll((unsigned long long)m) - 1;
-        if (((ex >> k) & 1u) || filter_mismatch(s, d, sp, dp, V[2 * k], V[2 * k + 1], p.one) == 0u)
-            return reinterpret_cast<const uint32_t *>(base + p.L.verdicts)[ci.x + k];
-        m &= m - 1;
+__device__ __forceinline__ uint32_t filter_verdict(const unsigned char *base, const FilterParams &p, uint32_t s,
+                                                   uint32_t d, uint32_t sp, uint32_t dp, uint32_t pr) {
+    if constexpr (W == 0) {
+        return filter_packet_wide<KEY>(base, p.v, s, d, sp, dp, pr, p.one);
+    } else {
+        uint32_t cls;
+        const FilterMask<W> m = filter_candidates<W, KEY>(base, p.v, s, d, sp, dp, pr, cls);
+        return filter_first<W>(base, p.v, m, cls, s, d, sp, dp, p.one);
     }
-    return 0xFFFFFFFFu;
 }
 
 // The grid-stride loop over packet quads, with the filter block at `base`
@@ -163,9 +116,7 @@ __device__ __forceinline__ void filter_loop(const FilterParams &p, const unsigne
         uint32_t acts = 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            uint32_t cls;
-            const FilterMask<W> m = filter_candidates<W, KEY>(base, p, s[j], d[j], sp[j], dp[j], pr[j], cls);
-            const uint32_t vw = filter_first<W>(base, p, m, cls, s[j], d[j], sp[j], dp[j]);
+            const uint32_t vw = filter_verdict<W, KEY>(base, p, s[j], d[j], sp[j], dp[j], pr[j]);
             idx[j] = vw == 0xFFFFFFFFu ? -1 : (int32_t)(vw & 0x7FFFFFFFu);
             acts |= (vw == 0xFFFFFFFFu ? (uint32_t)FW_DROP : vw >> 31) << (8 * j);
         }
@@ -209,6 +160,12 @@ __global__ void __launch_bounds__(512, 3) k_packet_split_filter(FilterParams p) 
     }
 }
 
+// Rows wider than two words: the filter block is read from global memory (L1).
+template <int KEY, bool VEC>
+__global__ void __launch_bounds__(512, 3) k_packet_split_filter_wide(FilterParams p) {
+    filter_loop<0, KEY, VEC>(p, p.blk);
+}
+
 // ------------------------------------------------------------ host side
 // Exact-test record of a rule (layout above).
 static void verify_record(const fw_rule &r, uint4 *rec) {
@@ -240,19 +197,19 @@ int filter_block(const fw_rule *rules, const std::vector<std::vector<int64_t>> &
         for (int64_t k : lists[c])
             if (!rules[k].proto_any) return 0;
     }
-    const int W = longest <= 32 ? 1 : 2;
+    const int W = (longest + 31) / 32 > 0 ? (longest + 31) / 32 : 1;
     const int64_t records = class_off[kMaxClasses - 1] + class_len[kMaxClasses - 1];
     const FilterLayout L = filter_layout(nc, W, records);
-    if (L.total > 227 * 1024 - 64) return 0;  // must fit one block's shared memory
     blk.assign((size_t)L.total, 0);
     uint32_t *tab = reinterpret_cast<uint32_t *>(blk.data() + L.tables);
     uint4 *cinfo = reinterpret_cast<uint4 *>(blk.data() + L.classes);
+    uint32_t *exact_all = reinterpret_cast<uint32_t *>(blk.data() + L.exact);
     uint4 *recs = reinterpret_cast<uint4 *>(blk.data() + L.recs);
     uint32_t *vw = reinterpret_cast<uint32_t *>(blk.data() + L.verdicts);
     auto set_bit = [&](uint32_t *row, int j) { row[j >> 5] |= 1u << (j & 31); };
     auto row = [&](int c, int t, uint32_t b) { return tab + (((size_t)c * kFilterTables + t) * 256 + b) * W; };
     for (int c = 0; c < nc; ++c) {
-        uint32_t exact[2] = {0u, 0u};
+        uint32_t *exact = exact_all + (size_t)c * W;
         for (size_t j = 0; j < lists[c].size(); ++j) {
             const fw_rule &r = rules[lists[c][j]];
             const int64_t at = class_off[c] + (int64_t)j;
@@ -270,7 +227,7 @@ int filter_block(const fw_rule *rules, const std::vector<std::vector<int64_t>> &
                                (r.dport_hi & 0xFFFu) == 0xFFFu;
             if (whole) exact[j >> 5] |= 1u << (j & 31);
         }
-        cinfo[c] = make_uint4((uint32_t)class_off[c], exact[0], exact[1], 0u);
+        cinfo[c] = make_uint4((uint32_t)class_off[c], exact[0], W > 1 ? exact[1] : 0u, 0u);
     }
     std::memcpy(blk.data() + L.class_of, class_of.data(), 256);
     return W;
@@ -292,30 +249,29 @@ cudaError_t build_filter(const fw_rule *rules, const std::vector<std::vector<int
     return cudaSuccess;
 }
 
+// Shared-memory staging applies to rows of one or two words whose block fits three blocks per SM.
+bool filter_staged(const fw_ruleset *rs) { return rs->filter_words <= 2 && rs->filter_bytes <= 72 * 1024; }
+
 int launch_filter(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *out_idx, uint8_t *out_act,
                   cudaStream_t st, int threads, int blocks_per_sm) {
     if (rs->filter_words == 0) return FW_EINVAL;
     FilterParams p;
     std::memset(&p, 0, sizeof(p));
-    const int64_t records = rs->class_off[kMaxClasses - 1] + rs->class_len[kMaxClasses - 1];
     p.blk = rs->d_filter;
-    const FilterLayout L = filter_layout(rs->n_classes, rs->filter_words, records);
-    p.L = FilterOffsets{(int32_t)L.tables, (int32_t)L.classes, (int32_t)L.recs, (int32_t)L.verdicts,
-                        (int32_t)L.class_of};
+    p.v = filter_view(rs);
     p.blk_bytes = (int32_t)rs->filter_bytes;
-    p.n_classes = rs->n_classes;
-    p.key_bits = rs->key_bits;
     p.one = 1u;
     p.h = h;
     p.n = n;
     p.out_idx = out_idx;
     p.out_act = out_act;
     p.status = rs->d_status;
+    const bool staged = filter_staged(rs);
     threads = threads > 0 ? threads : 512;
     const int per_sm = blocks_per_sm > 0 ? blocks_per_sm : 3;
-    if (threads % 32 != 0 || threads > 512) return FW_EINVAL;
-    const size_t smem = (size_t)rs->filter_bytes;
-    if ((size_t)per_sm * (smem + 1024) > 228 * 1024) return FW_EINVAL;
+    if (threads % 32 != 0 || threads > 512 || per_sm > 64) return FW_EINVAL;
+    const size_t smem = staged ? (size_t)rs->filter_bytes : 0;
+    if (staged && (size_t)per_sm * (smem + 1024) > 228 * 1024) return FW_EINVAL;
     const int64_t nq = (n + 3) / 4;
     int64_t blocks = std::min<int64_t>((int64_t)sm_count(rs->device) * per_sm, (nq + threads - 1) / threads);
     blocks = std::max<int64_t>(1, blocks);
@@ -323,7 +279,7 @@ int launch_filter(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *ou
                      (reinterpret_cast<uintptr_t>(h.sport) % 8 == 0) && (reinterpret_cast<uintptr_t>(h.dport) % 8 == 0) &&
                      (reinterpret_cast<uintptr_t>(h.proto) % 4 == 0) && (reinterpret_cast<uintptr_t>(out_idx) % 16 == 0) &&
                      (reinterpret_cast<uintptr_t>(out_act) % 4 == 0);
-    const int key = rs->key_bits == 0 ? 0 : rs->key_field;
+    const int key = p.v.key_field;
     cudaError_t e = cudaSuccess;
 #define FW_LAUNCH_F(WW, KK, V)                                                                              \
     do {                                                                                                    \
@@ -332,9 +288,15 @@ int launch_filter(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *ou
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);               \
         if (e == cudaSuccess) k_packet_split_filter<WW, KK, V><<<(unsigned)blocks, threads, smem, st>>>(p); \
     } while (0)
+#define FW_LAUNCH_G(KK, V)                                                                                  \
+    k_packet_split_filter_wide<KK, V><<<(unsigned)blocks, threads, 0, st>>>(p)
 #define FW_LAUNCH_FK(WW, V)                                                                                 \
     do {                                                                                                    \
-        if (key == 1) FW_LAUNCH_F(WW, 1, V);                                                                \
+        if (!staged) {                                                                                      \
+            if (key == 1) FW_LAUNCH_G(1, V);                                                                \
+            else if (key == 2) FW_LAUNCH_G(2, V);                                                           \
+            else FW_LAUNCH_G(0, V);                                                                         \
+        } else if (key == 1) FW_LAUNCH_F(WW, 1, V);                                                         \
         else if (key == 2) FW_LAUNCH_F(WW, 2, V);                                                           \
         else FW_LAUNCH_F(WW, 0, V);                                                                         \
     } while (0)
@@ -346,6 +308,7 @@ int launch_filter(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *ou
         else FW_LAUNCH_FK(2, false);
     }
 #undef FW_LAUNCH_FK
+#undef FW_LAUNCH_G
 #undef FW_LAUNCH_F
     if (e != cudaSuccess) return cuda_status(e);
     return cuda_status(cudaGetLastError());

@@ -1,0 +1,153 @@
+// Bucket filter: the per-packet first-match routine shared by the packet-split
+// filter kernel (fw_filter.cu) and the batched persistent kernel (fw_batch.cu).
+//
+// A rule set whose partition class sub-lists hold at most kFilterMaxRecords
+// records carries a filter block (layout: filter_layout in fw_internal.cuh):
+//  - per class c and bucket table t, 256 rows of W 32-bit words, bit j of a row
+//    set when record j of c's sub-list can hold a packet of that bucket:
+//      t = 0: top 8 bits of the source address,
+//      t = 1: top 8 bits of the destination address,
+//      t = 2: (sport >> 12) << 4 | (dport >> 12);
+//  - per class {first stored record, exact mask words 0 and 1, 0}, and the
+//    exact mask of every word (bit j set when record j's fields are unions of
+//    whole buckets, so that its bits alone decide it);
+//  - per record an exact-test record (two uint4) and a verdict word
+//    (original rule index | action << 31);
+//  - the protocol -> protocol class table.
+// A rule that contains the packet has its bit set in all three of the
+// packet's rows (each of its field sets holds the packet's value, so it meets
+// that value's bucket): the AND of the rows is a superset of the matching
+// records. Candidates are tested in increasing record order, and the first that
+// passes is the packet's first match in its class sub-list, i.e. in the list.
+#pragma once
+
+#include "fw_scan.cuh"
+
+namespace fwk {
+
+// What a kernel needs to read a filter block: 32-bit byte offsets of its parts,
+// the partition's class count and address key, and the row width.
+struct FilterView {
+    int32_t tables, classes, exact, recs, verdicts, class_of;
+    int32_t n_classes, key_field, key_bits, words;
+};
+
+inline FilterView filter_view(const fw_ruleset *rs) {
+    const int64_t records = rs->class_off[kMaxClasses - 1] + rs->class_len[kMaxClasses - 1];
+    const FilterLayout L = filter_layout(rs->n_classes, rs->filter_words, records);
+    FilterView v;
+    v.tables = (int32_t)L.tables;
+    v.classes = (int32_t)L.classes;
+    v.exact = (int32_t)L.exact;
+    v.recs = (int32_t)L.recs;
+    v.verdicts = (int32_t)L.verdicts;
+    v.class_of = (int32_t)L.class_of;
+    v.n_classes = rs->n_classes;
+    v.key_field = rs->key_bits == 0 ? 0 : rs->key_field;
+    v.key_bits = rs->key_bits;
+    v.words = rs->filter_words;
+    return v;
+}
+
+// Non-zero exactly when the packet is outside the record's rule. The record is
+// {saddr & smask, smask, daddr & dmask, dmask} and {-sport_lo, sport_hi -
+// sport_lo, -dport_lo, dport_hi - dport_lo} (mod 2^32): two 3-input logic ops
+// for the addresses, a multiply-add (`one` = 1 at run time, so it is issued on
+// the FMA pipe) and an unsigned compare per port, chained into one predicate.
+__device__ __forceinline__ uint32_t filter_mismatch(uint32_t s, uint32_t d, uint32_t sp, uint32_t dp, const uint4 &a,
+                                                    const uint4 &b, uint32_t one) {
+    const uint32_t ts = sp * one + b.x;
+    const uint32_t td = dp * one + b.z;
+    uint32_t r;
+    asm("{\n\t"
+        ".reg .pred q;\n\t"
+        ".reg .b32 t;\n\t"
+        "setp.gt.u32 q, %1, %2;\n\t"
+        "lop3.or.b32 t|q, %3, %4, %5, 0x28, q;\n\t"
+        "lop3.or.b32 t|q, %6, %7, %8, 0x28, q;\n\t"
+        "setp.gt.or.u32 q, %9, %10, q;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t"
+        "}"
+        : "=r"(r)
+        : "r"(ts), "r"(b.y), "r"(s), "r"(a.x), "r"(a.y), "r"(d), "r"(a.z), "r"(a.w), "r"(td), "r"(b.w));
+    return r;
+}
+
+// The packet's partition class (KEY: 0 no address key, 1 source, 2 destination, -1 read from v).
+template <int KEY>
+__device__ __forceinline__ uint32_t filter_class(const unsigned char *base, const FilterView &v, uint32_t s,
+                                                 uint32_t d, uint32_t pr) {
+    uint32_t c = base[v.class_of + pr];
+    const int key = KEY >= 0 ? KEY : v.key_field;
+    if (key != 0) c = (c << v.key_bits) | ((key == 1 ? s : d) >> (32 - v.key_bits));
+    return c;
+}
+
+template <int W>
+using FilterMask = typename std::conditional<W == 1, uint32_t, uint64_t>::type;
+
+// Rows of one or two words (W = 1, 2): the three rows' AND as one integer.
+template <int W, int KEY>
+__device__ __forceinline__ FilterMask<W> filter_candidates(const unsigned char *base, const FilterView &v,
+                                                           uint32_t s, uint32_t d, uint32_t sp, uint32_t dp,
+                                                           uint32_t pr, uint32_t &cls) {
+    using M = FilterMask<W>;
+    const uint32_t c = filter_class<KEY>(base, v, s, d, pr);
+    cls = c;
+    const M *T = reinterpret_cast<const M *>(base + v.tables) + c * 768u;
+    return T[s >> 24] & T[256u + (d >> 24)] & T[512u + (((sp >> 12) << 4) | (dp >> 12))];
+}
+
+// First candidate of m (W = 1, 2) that passes its exact test: its verdict word, or ~0u.
+template <int W>
+__device__ __forceinline__ uint32_t filter_first(const unsigned char *base, const FilterView &v, FilterMask<W> m,
+                                                 uint32_t cls, uint32_t s, uint32_t d, uint32_t sp, uint32_t dp,
+                                                 uint32_t one) {
+    using M = FilterMask<W>;
+    if (m == 0) return 0xFFFFFFFFu;
+    // class info: first stored record, exact mask (low, high word)
+    const uint4 ci = reinterpret_cast<const uint4 *>(base + v.classes)[cls];
+    const M ex = W == 1 ? (M)ci.y : (M)(((uint64_t)ci.z << 32) | ci.y);
+    const uint4 *V = reinterpret_cast<const uint4 *>(base + v.recs) + 2 * ci.x;
+    while (m != 0) {
+        const int k = W == 1 ? __ffs((unsigned)m) - 1 : __ffsll((unsigned long long)m) - 1;
+        if (((ex >> k) & 1u) || filter_mismatch(s, d, sp, dp, V[2 * k], V[2 * k + 1], one) == 0u)
+            return reinterpret_cast<const uint32_t *>(base + v.verdicts)[ci.x + k];
+        m &= m - 1;
+    }
+    return 0xFFFFFFFFu;
+}
+
+// Any row width (v.words 32-bit words): the rows are ANDed one word at a time
+// from word 0, and the candidates of each word are tested before the next word
+// is read, so a packet reads its rows only up to its first match. The block is
+// read through the L1 cache (global memory).
+template <int KEY>
+__device__ __forceinline__ uint32_t filter_packet_wide(const unsigned char *__restrict__ base, const FilterView &v,
+                                                       uint32_t s, uint32_t d, uint32_t sp, uint32_t dp, uint32_t pr,
+                                                       uint32_t one) {
+    const uint32_t c = filter_class<KEY>(base, v, s, d, pr);
+    const int W = v.words;
+    const uint32_t *T = reinterpret_cast<const uint32_t *>(base + v.tables) + (size_t)c * 768u * W;
+    const uint32_t *r0 = T + (s >> 24) * W;
+    const uint32_t *r1 = T + (256u + (d >> 24)) * W;
+    const uint32_t *r2 = T + (512u + (((sp >> 12) << 4) | (dp >> 12))) * W;
+    const uint32_t *ex = reinterpret_cast<const uint32_t *>(base + v.exact) + (size_t)c * W;
+    const int first = (int)__ldg(reinterpret_cast<const uint32_t *>(base + v.classes) + 4 * c);
+    const uint4 *V = reinterpret_cast<const uint4 *>(base + v.recs) + 2 * first;
+    for (int w = 0; w < W; ++w) {
+        uint32_t m = __ldg(r0 + w) & __ldg(r1 + w) & __ldg(r2 + w);
+        if (m == 0u) continue;
+        const uint32_t e = __ldg(ex + w);
+        while (m != 0u) {
+            const int k = 32 * w + __ffs(m) - 1;
+            if (((e >> (k & 31)) & 1u) ||
+                filter_mismatch(s, d, sp, dp, __ldg(V + 2 * k), __ldg(V + 2 * k + 1), one) == 0u)
+                return __ldg(reinterpret_cast<const uint32_t *>(base + v.verdicts) + first + k);
+            m &= m - 1u;
+        }
+    }
+    return 0xFFFFFFFFu;
+}
+
+}  // namespace fwk

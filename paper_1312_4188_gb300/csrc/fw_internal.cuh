@@ -273,12 +273,12 @@ struct fw_ruleset {
     uint32_t *d_part_wtop;             // part_pad words
     int32_t *d_part_orig;              // part_pad original rule indices (-1 for padding)
     uint32_t *d_part_verdict;          // part_pad words: original index | action << 31
-    // Bucket filter over the partition (fw_filter.cu): per class, bitmaps over
-    // the class sub-list indexed by a packet's address and port buckets, plus a
-    // compact exact-test record per stored record. Built when every sub-list
-    // holds at most 64 records and no class mixes exact protocols.
-    int32_t filter_words;              // 0 = no filter, else 1 or 2 (32-bit words per bitmap row)
-    int64_t filter_bytes;              // bytes of d_filter (staged whole into shared memory)
+    // Bucket filter over the partition (fw_filter.cuh): per class, bitmaps over
+    // the class sub-list indexed by a packet's address and port buckets, plus an
+    // exact-test record per stored record. Built when every sub-list holds at
+    // most kFilterMaxRecords records and no class mixes exact protocols.
+    int32_t filter_words;              // 0 = no filter, else 1..16 (32-bit words per bitmap row)
+    int64_t filter_bytes;              // bytes of d_filter
     unsigned char *d_filter;           // the filter block (layout: FilterLayout)
     uint8_t *d_action;        // n_pad actions
     unsigned *d_status;       // device error flags (kStatus*)
@@ -321,15 +321,17 @@ int sm_count(int dev);                  // SMs of device `dev` (cached)
 // for n_classes classes, `words` 32-bit words per bitmap row and `records`
 // stored sub-list records (every part starts on a 16-byte boundary).
 struct FilterLayout {
-    int64_t tables, classes, recs, verdicts, class_of, total;
+    int64_t tables, classes, exact, recs, verdicts, class_of, total;
 };
 constexpr int kFilterTables = 3;  // source top 8 bits, destination top 8 bits, (sport, dport) top 4 bits each
+constexpr int kFilterMaxRecords = 512;  // longest class sub-list a filter covers (16-word rows)
 __host__ __device__ inline FilterLayout filter_layout(int n_classes, int words, int64_t records) {
     FilterLayout L;
     auto up16 = [](int64_t b) { return (b + 15) / 16 * 16; };
     L.tables = 0;                                                          // [class][table][256][words] uint32
     L.classes = up16(L.tables + (int64_t)kFilterTables * n_classes * 256 * words * 4);  // [class] uint4
-    L.recs = L.classes + (int64_t)n_classes * 16;                          // [record] 2 x uint4
+    L.exact = L.classes + (int64_t)n_classes * 16;                         // [class][words] uint32
+    L.recs = up16(L.exact + (int64_t)n_classes * words * 4);               // [record] 2 x uint4
     L.verdicts = L.recs + records * 32;                                    // [record] uint32
     L.class_of = up16(L.verdicts + records * 4);                           // [256] uint8
     L.total = up16(L.class_of + 256);

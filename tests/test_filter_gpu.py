@@ -126,7 +126,7 @@ def assert_same(got, want, what=""):
                            f"want ({wi[bad[0]]},{wa[bad[0]]})")
 
 
-CASES = [(12, 1), (30, 2), (45, 3), (70, 4), (100, 5), (160, 6)]
+CASES = [(12, 1), (30, 2), (45, 3), (70, 4), (100, 5), (160, 6), (400, 7), (900, 8)]
 
 
 @pytest.mark.parametrize("n_rules,seed", CASES)
@@ -144,13 +144,14 @@ def test_edges_against_oracle(torch_cuda, n_rules, seed, cfg):
     rs.destroy()
 
 
-def test_both_bitmap_widths_are_exercised(torch_cuda):
+def test_all_bitmap_widths_are_exercised(torch_cuda):
+    """One- and two-word rows (staged in shared memory) and wider rows (read from global memory)."""
     widths = set()
     for n_rules, seed in CASES:
         rs = fw.fw_ruleset_create(edge_rules(n_rules, 900 + seed))
         widths.add(rs.filter()["words"])
         rs.destroy()
-    assert {1, 2} <= widths, widths
+    assert {1, 2} <= widths and max(widths) > 2, widths
 
 
 @pytest.mark.parametrize("n_pkts", [1, 3, 4, 5, 63, 1023, 4097, 100_003])
@@ -198,7 +199,7 @@ def test_default_deny_and_empty_rule_set(torch_cuda):
 
 
 def test_filter_refused_when_the_rule_set_has_none(torch_cuda):
-    long_list = W.gen_rules(400, 12)
+    long_list = W.gen_rules(4000, 12)
     long_list = long_list[~((long_list["src_prefix"] == 0) & (long_list["dst_prefix"] == 0))]
     many_protos = W.gen_rules(60, 13)
     many_protos["proto_any"] = 0

@@ -25,24 +25,37 @@ def up16(b):
 
 
 def decode(plan, n_classes):
-    """Arrays of the filter block (documented layout)."""
+    """Arrays of the filter block (documented layout): rows [table][class][bucket][word] (uint32),
+    exact masks [class][word], records [record][8], verdict words, protocol classes, class offsets."""
     blk, w = plan["block"], plan["words"]
     recs_n = int(plan["class_off"][-1] + plan["class_len"][-1])
     tab_bytes = n_classes * 3 * 256 * w * 4
     cls_off = up16(tab_bytes)
-    recs_off = cls_off + n_classes * 16
+    ex_off = cls_off + n_classes * 16
+    recs_off = up16(ex_off + n_classes * w * 4)
     vw_off = recs_off + recs_n * 32
     pc_off = up16(vw_off + recs_n * 4)
-    words = blk[:tab_bytes].view(np.uint32).reshape(n_classes, 3, 256, w).astype(np.uint64)
-    rows = words[..., 0] | (words[..., 1] << np.uint64(32) if w == 2 else np.uint64(0))
-    rows = rows.transpose(1, 0, 2)  # [table][class][bucket]
+    rows = blk[:tab_bytes].view(np.uint32).reshape(n_classes, 3, 256, w).transpose(1, 0, 2, 3)
     ci = blk[cls_off:cls_off + n_classes * 16].view(np.uint32).reshape(n_classes, 4)
-    exact = ci[:, 1].astype(np.uint64) | (ci[:, 2].astype(np.uint64) << np.uint64(32))
+    exact = blk[ex_off:ex_off + n_classes * w * 4].view(np.uint32).reshape(n_classes, w)
+    assert np.array_equal(ci[:, 1], exact[:, 0]) and (w == 1 or np.array_equal(ci[:, 2], exact[:, 1]))
     class_off = ci[:, 0].astype(np.int32)
     recs = blk[recs_off:recs_off + recs_n * 32].view(np.uint32).reshape(recs_n, 8)
     vw = blk[vw_off:vw_off + recs_n * 4].view(np.uint32)
     proto_class = blk[pc_off:pc_off + 256]
     return rows, exact, recs, vw, proto_class, class_off
+
+
+def candidates(rows, c, hdr):
+    """[packet][word] AND of the packet's three bucket rows."""
+    s8 = hdr["src"].astype(np.int64) >> 24
+    d8 = hdr["dst"].astype(np.int64) >> 24
+    pb = ((hdr["sport"].astype(np.int64) >> 12) << 4) | (hdr["dport"].astype(np.int64) >> 12)
+    return rows[0, c, s8] & rows[1, c, d8] & rows[2, c, pb]
+
+
+def bit(words, j):
+    return ((words[:, j // 32] >> np.uint32(j % 32)) & np.uint32(1)).astype(bool)
 
 
 def reachable(rules):
@@ -76,22 +89,19 @@ def filter_classify(rules, hdr):
     assert np.array_equal(proto_class, part["proto_class"])
     assert np.array_equal(class_off, plan["class_off"][:nc])
     c = R.packet_class(hdr, part["proto_class"], kf, kb).astype(np.int64)
-    s8 = hdr["src"].astype(np.int64) >> 24
-    d8 = hdr["dst"].astype(np.int64) >> 24
-    pb = ((hdr["sport"].astype(np.int64) >> 12) << 4) | (hdr["dport"].astype(np.int64) >> 12)
-    m = rows[0, c, s8] & rows[1, c, d8] & rows[2, c, pb]
+    m = candidates(rows, c, hdr)
     off = class_off[c].astype(np.int64)
     n = len(c)
     idx = np.full(n, -1, dtype=np.int64)
     act = np.zeros(n, dtype=np.uint8)
     done = np.zeros(n, dtype=bool)
     for j in range(32 * plan["words"]):
-        bit = ((m >> np.uint64(j)) & np.uint64(1)).astype(bool) & ~done
-        if not bit.any():
+        cand = bit(m, j) & ~done
+        if not cand.any():
             continue
         at = off + j
-        sel = np.nonzero(bit)[0]
-        ex = ((exact[c[sel]] >> np.uint64(j)) & np.uint64(1)).astype(bool)
+        sel = np.nonzero(cand)[0]
+        ex = bit(exact[c[sel]], j)
         ok = ex | exact_test(recs[at[sel]], {f: hdr[f][sel] for f in W.HEADER_FIELDS})
         hit = sel[ok]
         v = vw[at[hit]]
@@ -102,7 +112,8 @@ def filter_classify(rules, hdr):
 
 
 RULE_SETS = [("edge", 12, 1), ("edge", 30, 2), ("edge", 45, 3), ("edge", 70, 4), ("edge", 100, 5), ("edge", 160, 6),
-             ("gen", 3, 7), ("gen", 40, 8), ("gen", 10_000, 3), ("gen", 1000, 1)]
+             ("edge", 400, 7), ("edge", 900, 8), ("gen", 3, 7), ("gen", 40, 8), ("gen", 10_000, 3),
+             ("gen", 1000, 1), ("gen", 10_000, 40), ("gen", 1000, 41)]
 
 
 def rule_set(kind, n, seed):
@@ -125,9 +136,12 @@ def test_filter_block_classifies_like_the_oracle(kind, n, seed):
     # the first match always survives the bucket rows
     matched = np.nonzero(o_idx >= 0)[0]
     orig = (vw & 0x7FFFFFFF).astype(np.int64)
+    width = 32 * got[0]["words"]
     for i in matched[:3000]:
-        pos = np.nonzero(orig[off[i]:off[i] + 64] == o_idx[i])[0]
-        assert pos.size >= 1 and (int(m[i]) >> int(pos[0])) & 1, f"packet {i}: its first match is not a candidate"
+        pos = np.nonzero(orig[off[i]:off[i] + width] == o_idx[i])[0]
+        assert pos.size >= 1, f"packet {i}: its first match is not in its class sub-list"
+        j = int(pos[0])
+        assert (int(m[i, j // 32]) >> (j % 32)) & 1, f"packet {i}: its first match is not a candidate"
 
 
 def test_exact_records_contain_every_packet_of_their_buckets():
@@ -140,11 +154,9 @@ def test_exact_records_contain_every_packet_of_their_buckets():
         rows, exact, recs, vw, _, class_off = decode(plan, part["classes"])
         hdr = W.gen_packets(rules, 20_000, 70 + seed)
         c = R.packet_class(hdr, part["proto_class"], part["key_field"], part["key_bits"]).astype(np.int64)
-        s8, d8 = hdr["src"].astype(np.int64) >> 24, hdr["dst"].astype(np.int64) >> 24
-        pb = ((hdr["sport"].astype(np.int64) >> 12) << 4) | (hdr["dport"].astype(np.int64) >> 12)
-        m = rows[0, c, s8] & rows[1, c, d8] & rows[2, c, pb] & exact[c]
+        m = candidates(rows, c, hdr) & exact[c]
         for j in range(32 * plan["words"]):
-            sel = np.nonzero(((m >> np.uint64(j)) & np.uint64(1)).astype(bool))[0]
+            sel = np.nonzero(bit(m, j))[0]
             if sel.size == 0:
                 continue
             rule = int(vw[class_off[c[sel[0]]] + j] & 0x7FFFFFFF)
@@ -155,9 +167,11 @@ def test_exact_records_contain_every_packet_of_their_buckets():
 
 
 def test_no_filter_cases_and_arguments():
-    long_list = W.gen_rules(400, 12)
+    long_list = W.gen_rules(4000, 12)
     long_list = long_list[~((long_list["src_prefix"] == 0) & (long_list["dst_prefix"] == 0))]
-    assert fw.fw_filter_plan(long_list)["words"] == 0
+    assert fw.fw_filter_plan(long_list)["words"] == 0  # class sub-lists over 512 rules
+    widths = {fw.fw_filter_plan(rule_set(k, n, s))["words"] for k, n, s in RULE_SETS}
+    assert {1, 2} <= widths and max(widths) > 2, widths
     many = W.gen_rules(60, 13)
     many["proto_any"] = 0
     many["proto"] = np.arange(60) % 12

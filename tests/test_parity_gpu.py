@@ -41,6 +41,9 @@ CONFIGS = [
     ("packet_split", {"filter": 2}),
     ("rule_split_warp", {}),
     ("rule_split_warp", {"block_threads": 64, "blocks_per_sm": 8}),
+    ("rule_split_warp", {"segment_rules": 2}),
+    ("rule_split_warp", {"segment_rules": 8}),
+    ("rule_split_warp", {"segment_rules": 16, "block_threads": 96}),
     ("rule_split_warp", {"partition": 2}),
     ("rule_split_warp", {"partition": 2, "packets_per_group": 32, "block_threads": 64}),
     ("rule_split_block", {}),

@@ -115,3 +115,21 @@ def test_two_gloo_ranks_combine_by_minimum():
     for _, _, _, idx_b, act_b in out:  # every rank ends with the whole-list answer
         assert np.array_equal(np.frombuffer(idx_b, dtype=np.int32), want_idx)
         assert np.array_equal(np.frombuffer(act_b, dtype=np.uint8), want_act)
+
+
+@pytest.mark.parametrize("world", [4, 9])
+def test_more_ranks_than_rules(world):
+    """Ranks beyond the rule count hold empty ranges: they report no match for every packet, and
+    the minimum over ranks is still the whole list's first match (DROP where no rule matches)."""
+    for rules in (rule_set(4, 3), W.without_catch_alls(rule_set(5, 2)), W.empty_rules(0)):
+        src = rules if len(rules) else rule_set(6, 40)
+        hdr = W.gen_packets(src, 4000, 26)
+        want_idx, want_act, _ = oracle.classify(rules, hdr)
+        g = None
+        for r in range(world):
+            lo, hi = S.shard_range(len(rules), world, r)
+            part = S.to_global(local_first_match(rules, lo, hi, hdr), lo)
+            g = part if g is None else torch.minimum(g, part)
+        idx, act = S.finalize(g, torch.from_numpy(rules["action"].astype(np.uint8)))
+        assert np.array_equal(idx.numpy(), want_idx) and np.array_equal(act.numpy(), want_act)
+        assert np.all(act.numpy()[want_idx < 0] == 0)

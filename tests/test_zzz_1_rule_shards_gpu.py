@@ -78,3 +78,30 @@ def test_rule_shard_alone_is_the_whole_list(torch_cuda):
     sh.destroy()
     want = oracle.classify(rules, hdr, threads=THREADS)
     assert np.array_equal(idx.cpu().numpy(), want[0]) and np.array_equal(act.cpu().numpy(), want[1])
+
+
+@pytest.mark.parametrize("world", [4, 9])
+def test_more_ranks_than_rules(torch_cuda, world):
+    """RuleShard on ranks whose range is empty (more ranks than rules): an empty CUDA rule set
+    answers no match for every packet, and the minimum over ranks equals the oracle, DROP for
+    every packet that no rule matches."""
+    torch = torch_cuda
+    for seed, rules in ((21, W.gen_rules(3, 21)), (22, W.without_catch_alls(W.gen_rules(2, 22))),
+                        (23, W.empty_rules(0))):
+        src = rules if len(rules) else W.gen_rules(40, 24)
+        hdr = W.gen_packets(src, 20_000, seed + 5)
+        dh = fw.headers_to_device(hdr)
+        g = None
+        for r in range(world):
+            sh = S.RuleShard(rules, world, r)
+            local, _ = fw.fw_classify(sh.rs, dh)
+            part = S.to_global(local, sh.lo)
+            g = part if g is None else torch.minimum(g, part)
+            torch.cuda.synchronize()
+            sh.destroy()
+        actions = torch.as_tensor(rules["action"].astype(np.uint8), device="cuda")
+        idx, act = S.finalize(g, actions)
+        want = oracle.classify(rules, hdr, threads=THREADS)
+        got_i, got_a = idx.cpu().numpy(), act.cpu().numpy()
+        assert np.array_equal(got_i, want[0]) and np.array_equal(got_a, want[1]), f"{len(rules)} rules"
+        assert np.all(got_a[want[0] < 0] == fw.FW_DROP)
