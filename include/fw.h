@@ -172,8 +172,11 @@ typedef struct fw_headers {
  *                     mode (AUTO or PACKET_SPLIT), block_threads and
  *                     blocks_per_sm is set; 1 = the filter kernel
  *                     (FW_EINVAL if the rule set has none); 2 = never.
- *                     block_threads (<= 512, default 512) and blocks_per_sm
- *                     (default 3) shape its launch.
+ *                     block_threads (<= 512, default 512), blocks_per_sm
+ *                     (default 3, or 4 with two packets per thread) and
+ *                     lane_packets (packets a thread takes per step: 4 by
+ *                     default, 2 with filter = 1 and one- or two-word rows)
+ *                     shape its launch.
  */
 typedef struct fw_config {
     int32_t mode;

@@ -3,17 +3,18 @@
 //
 // The paper's data-parallel firewall accumulates a set of packets and checks
 // them in parallel against one rule set (Sec. IV.A); its conclusions point to
-// asynchronous launches to cut per-batch delay (Sec. V). Here a plan turns a
-// list of jobs into a device work list of items, each a run of up to
-// `packets_per_item` packets of one job. A persistent grid of warps takes
-// items from a global counter (dynamic scheduling, so cheap and expensive
-// items balance), and each warp classifies its item against the item's own rule
-// set, read through L1: through the rule set's bucket filter when it has one
+// asynchronous launches to cut per-batch delay (Sec. V). Here a plan splits
+// every job into items, runs of up to `packets_per_item` packets. Items are
+// not stored: the plan keeps, per job, the offset of its first item (the
+// exclusive prefix of the jobs' item counts), and a persistent grid of warps
+// claims item indices from a global counter (dynamic scheduling, so cheap and
+// expensive items balance) and finds each item's job by a search of that
+// prefix. Each warp classifies its item against the item's own rule set, read
+// through L1: through the rule set's bucket filter when it has one
 // (fw_filter.cuh), else with the two-packets-per-lane first-match scan of
-// fw_scan.cuh.
-// Items are ordered by decreasing rule-set size so the long scans start
-// first. Per size class of rule set (by reachable rules) the plan carries its
-// own item size and first rule segment, chosen by the autotuner.
+// fw_scan.cuh. Jobs are ordered by decreasing rule-set size so the long scans
+// start first. Per size class of rule set (by reachable rules) the plan
+// carries its own item size and first rule segment, chosen by the autotuner.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -46,8 +47,23 @@ __global__ void __launch_bounds__(1024) k_batch(BatchParams p) {
         if (lane == 0) it = atomicAdd(p.next, 1ull);
         it = __shfl_sync(0xFFFFFFFFu, it, 0);
         if (it >= (unsigned long long)p.n_items) break;
-        const BatchItem item = p.items[it];
-        const BatchJobDev &J = p.jobs[item.job];
+        // the claimed item's job: the last j with prefix[j] <= it (lane 0 searches, all take it)
+        int job = 0;
+        if (lane == 0) {
+            int lo = 0, hi = p.n_jobs - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(p.prefix + mid) <= (int64_t)it) lo = mid;
+                else hi = mid - 1;
+            }
+            job = lo;
+        }
+        job = __shfl_sync(0xFFFFFFFFu, job, 0);
+        const BatchJobDev &J = p.jobs[job];
+        BatchItem item;
+        item.job = job;
+        item.start = ((int64_t)it - __ldg(p.prefix + job)) * J.item_packets;
+        item.count = (int32_t)min((int64_t)J.item_packets, J.n - item.start);
         if (J.filter != nullptr) {
             batch_filter_item(J, item, lane, p.one);
             continue;
@@ -70,7 +86,7 @@ __global__ void __launch_bounds__(1024) k_batch(BatchParams p) {
         t.action = J.action;
         t.out_idx = J.out_idx;
         t.out_act = J.out_act;
-        t.seg0 = item.seg0;
+        t.seg0 = J.seg0;
         t.one = p.one;
         if (J.vec) run_batch_pairs<PolArith, true>(t, item.start, item.count, Q, wc, lane);
         else run_batch_pairs<PolArith, false>(t, item.start, item.count, Q, wc, lane);
@@ -80,7 +96,7 @@ __global__ void __launch_bounds__(1024) k_batch(BatchParams p) {
 static bool al(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 void fill_batch_job(BatchJobDev &d, const fw_ruleset *rs, const fw_headers &h, int64_t n, int32_t *out_idx,
-                    uint8_t *out_act) {
+                    uint8_t *out_act, int32_t item_packets, int32_t seg0) {
     d.rec = rs->d_part;
     d.wtop = rs->d_part_wtop;
     d.action = rs->d_action;
@@ -101,6 +117,8 @@ void fill_batch_job(BatchJobDev &d, const fw_ruleset *rs, const fw_headers &h, i
     d.out_act = out_act;
     d.filter = rs->filter_words > 0 ? rs->d_filter : nullptr;
     d.fv = filter_view(rs);
+    d.item_packets = item_packets;
+    d.seg0 = seg0;
 }
 
 size_t batch_smem_bytes(int threads, int32_t qcap) {
@@ -111,13 +129,14 @@ cudaError_t prepare_batch_kernel(size_t smem_bytes) {
     return cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
 
-cudaError_t launch_batch(const BatchJobDev *d_jobs, const BatchItem *d_items, int64_t n_items,
+cudaError_t launch_batch(const BatchJobDev *d_jobs, const int64_t *d_prefix, int32_t n_jobs, int64_t n_items,
                          unsigned long long *d_next, int32_t qcap, int threads, int64_t blocks, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(d_next, 0, sizeof(unsigned long long), st);
-    if (e != cudaSuccess || n_items == 0) return e;
+    if (e != cudaSuccess || n_items == 0 || n_jobs == 0) return e;
     BatchParams p;
     p.jobs = d_jobs;
-    p.items = d_items;
+    p.prefix = d_prefix;
+    p.n_jobs = n_jobs;
     p.n_items = n_items;
     p.next = d_next;
     p.qcap = qcap;
@@ -137,7 +156,7 @@ struct fw_plan {
     int64_t n_jobs = 0;
     int64_t packets = 0;
     fwk::BatchJobDev *d_jobs = nullptr;
-    fwk::BatchItem *d_items = nullptr;
+    int64_t *d_prefix = nullptr;  // n_jobs + 1 item offsets
     unsigned long long *d_next = nullptr;
     int32_t qcap = 256;
     cudaStream_t cap_stream = nullptr;
@@ -153,7 +172,7 @@ extern "C" void fw_plan_destroy(fw_plan *pl) {
     if (pl->graph) cudaGraphDestroy(pl->graph);
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
     cudaFree(pl->d_jobs);
-    cudaFree(pl->d_items);
+    cudaFree(pl->d_prefix);
     cudaFree(pl->d_next);
     delete pl;
 }
@@ -183,36 +202,27 @@ extern "C" int fw_plan_create(const fw_job *jobs, int64_t n_jobs, const fw_plan_
     if (smem > 227 * 1024) return set_status(FW_EINVAL);
 
     std::vector<BatchJobDev> hj((size_t)n_jobs);
-    std::vector<int> cls((size_t)n_jobs);
     int64_t packets = 0;
+    // jobs (and so their items) longest scans first
+    std::vector<int64_t> order((size_t)n_jobs);
+    for (int64_t j = 0; j < n_jobs; ++j) order[j] = j;
     for (int64_t j = 0; j < n_jobs; ++j) {
         const fw_job &J = jobs[j];
         if (J.rs == nullptr || J.n < 0 || J.n > INT32_MAX) return set_status(FW_EINVAL);
         if (J.n > 0 && (!J.hdrs.src || !J.hdrs.dst || !J.hdrs.sport || !J.hdrs.dport || !J.hdrs.proto ||
                         !J.out_rule_idx || !J.out_action))
             return set_status(FW_EINVAL);
-        fill_batch_job(hj[j], J.rs, J.hdrs, J.n, J.out_rule_idx, J.out_action);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return jobs[a].rs->n_eff > jobs[b].rs->n_eff; });
+    std::vector<int64_t> prefix((size_t)n_jobs + 1, 0);
+    for (int64_t k = 0; k < n_jobs; ++k) {
+        const fw_job &J = jobs[order[k]];
         int c = 0;
         while (c < n_classes - 1 && J.rs->n_eff > cfg.class_max_rules[c]) ++c;
-        cls[j] = c;
+        const int32_t B = item_packets(per_item[c]);
+        fill_batch_job(hj[k], J.rs, J.hdrs, J.n, J.out_rule_idx, J.out_action, B, seg0[c]);
+        prefix[k + 1] = prefix[k] + (J.n + B - 1) / B;
         packets += J.n;
-    }
-    // items, longest scans first
-    std::vector<int64_t> order((size_t)n_jobs);
-    for (int64_t j = 0; j < n_jobs; ++j) order[j] = j;
-    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return jobs[a].rs->n_eff > jobs[b].rs->n_eff; });
-    std::vector<BatchItem> items;
-    for (int64_t j : order) {
-        const int B = item_packets(per_item[cls[j]]);
-        for (int64_t s = 0; s < hj[j].n; s += B) {
-            BatchItem it;
-            it.start = s;
-            it.job = (int32_t)j;
-            it.count = (int32_t)std::min<int64_t>(B, hj[j].n - s);
-            it.seg0 = seg0[cls[j]];
-            it.pad = 0;
-            items.push_back(it);
-        }
     }
     fw_plan *pl = new (std::nothrow) fw_plan();
     if (pl == nullptr) return set_status(FW_ENOMEM);
@@ -220,19 +230,18 @@ extern "C" int fw_plan_create(const fw_job *jobs, int64_t n_jobs, const fw_plan_
     pl->threads = threads;
     pl->smem = smem;
     pl->qcap = qcap;
-    pl->n_items = (int64_t)items.size();
+    pl->n_items = prefix[(size_t)n_jobs];
     pl->n_jobs = n_jobs;
     pl->packets = packets;
     const int per_sm = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : 2;
     pl->blocks = std::max<int64_t>(
         1, std::min<int64_t>((int64_t)sm_count(pl->device) * per_sm, (pl->n_items + threads / 32 - 1) / (threads / 32)));
     cudaError_t e = dev_malloc(&pl->d_jobs, std::max<size_t>(1, hj.size()) * sizeof(BatchJobDev));
-    if (e == cudaSuccess) e = dev_malloc(&pl->d_items, std::max<size_t>(1, items.size()) * sizeof(BatchItem));
+    if (e == cudaSuccess) e = dev_malloc(&pl->d_prefix, prefix.size() * sizeof(int64_t));
     if (e == cudaSuccess) e = dev_malloc(&pl->d_next, sizeof(unsigned long long));
     if (e == cudaSuccess && !hj.empty())
         e = cudaMemcpy(pl->d_jobs, hj.data(), hj.size() * sizeof(BatchJobDev), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !items.empty())
-        e = cudaMemcpy(pl->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pl->d_prefix, prefix.data(), prefix.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = prepare_batch_kernel(smem);
     if (e != cudaSuccess) {
         fw_plan_destroy(pl);
@@ -244,7 +253,8 @@ extern "C" int fw_plan_create(const fw_job *jobs, int64_t n_jobs, const fw_plan_
 }
 
 static cudaError_t enqueue_plan(fw_plan *pl, cudaStream_t st) {
-    return launch_batch(pl->d_jobs, pl->d_items, pl->n_items, pl->d_next, pl->qcap, pl->threads, pl->blocks, st);
+    return launch_batch(pl->d_jobs, pl->d_prefix, (int32_t)pl->n_jobs, pl->n_items, pl->d_next, pl->qcap, pl->threads,
+                        pl->blocks, st);
 }
 
 extern "C" int fw_plan_launch(fw_plan *pl, void *stream) {

@@ -28,19 +28,23 @@ struct BatchJobDev {
     // the rule set's bucket filter (null when it has none): its items are classified through it
     const unsigned char *filter;
     FilterView fv;
+    int32_t item_packets;  // packets per work item of this job
+    int32_t seg0;          // first rule segment of its scan
 };
 
+// One work item: a run of up to item_packets packets of one job. Items are not stored: job j
+// owns items [prefix[j], prefix[j+1]) of the launch (the exclusive prefix of its item counts),
+// and a warp that claims item `it` finds its job by a search of the prefix.
 struct BatchItem {
     int64_t start;
     int32_t job;
-    int32_t count;  // <= packets_per_item of its class
-    int32_t seg0;   // first rule segment of its class
-    int32_t pad;
+    int32_t count;
 };
 
 struct BatchParams {
     const BatchJobDev *jobs;
-    const BatchItem *items;
+    const int64_t *prefix;     // n_jobs + 1 entries: first item of each job, then the item total
+    int32_t n_jobs;
     int64_t n_items;
     unsigned long long *next;  // item counter, zeroed before each launch
     int32_t qcap;              // queue capacity per warp (packets)
@@ -52,14 +56,15 @@ struct BatchParams {
 // one pad for each of up to kMaxClasses classes.
 inline int32_t item_packets(int32_t qcap) { return qcap - kMaxClasses; }
 
-// Fill a job entry from a rule set and device-accessible buffers.
+// Fill a job entry from a rule set and device-accessible buffers (item size and first segment
+// of its work items included).
 void fill_batch_job(BatchJobDev &d, const fw_ruleset *rs, const fw_headers &h, int64_t n, int32_t *out_idx,
-                    uint8_t *out_act);
+                    uint8_t *out_act, int32_t item_packets, int32_t seg0);
 
 // Zero the item counter and launch the persistent kernel on `st` (nothing but
-// the counter reset when n_items is 0). The kernel's shared-memory limit must
+// the counter reset when n_items is 0); d_prefix holds n_jobs + 1 item offsets. The kernel's shared-memory limit must
 // have been raised with prepare_batch_kernel for `qcap` and `threads`.
-cudaError_t launch_batch(const BatchJobDev *d_jobs, const BatchItem *d_items, int64_t n_items,
+cudaError_t launch_batch(const BatchJobDev *d_jobs, const int64_t *d_prefix, int32_t n_jobs, int64_t n_items,
                          unsigned long long *d_next, int32_t qcap, int threads, int64_t blocks, cudaStream_t st);
 cudaError_t prepare_batch_kernel(size_t smem_bytes);
 size_t batch_smem_bytes(int threads, int32_t qcap);  // dynamic shared memory of k_batch

@@ -135,22 +135,92 @@ __device__ __forceinline__ void filter_loop(const FilterParams &p, const unsigne
     }
 }
 
+// The same loop over packet pairs (8-byte, 4-byte and 2-byte header loads): half the header
+// registers of the quad loop, so four 512-thread blocks fit on an SM.
 template <int W, int KEY, bool VEC>
-__global__ void __launch_bounds__(512, 3) k_packet_split_filter(FilterParams p) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ uint64_t bar;
+__device__ __forceinline__ void filter_loop_pairs(const FilterParams &p, const unsigned char *base) {
+    const int64_t np = (p.n + 1) / 2;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < np; q += stride) {
+        uint32_t s[2], d[2], sp[2], dp[2], pr[2];
+        const int64_t b = q * 2;
+        const bool full = b + 1 < p.n;
+        if (VEC && full) {
+            const uint2 sv = __ldcs(reinterpret_cast<const uint2 *>(p.h.src) + q);
+            const uint2 dv = __ldcs(reinterpret_cast<const uint2 *>(p.h.dst) + q);
+            const uint32_t spv = __ldcs(reinterpret_cast<const unsigned int *>(p.h.sport) + q);
+            const uint32_t dpv = __ldcs(reinterpret_cast<const unsigned int *>(p.h.dport) + q);
+            const uint32_t prv = __ldcs(reinterpret_cast<const unsigned short *>(p.h.proto) + q);
+            s[0] = sv.x, s[1] = sv.y, d[0] = dv.x, d[1] = dv.y;
+            sp[0] = spv & 0xFFFFu, sp[1] = spv >> 16, dp[0] = dpv & 0xFFFFu, dp[1] = dpv >> 16;
+            pr[0] = prv & 0xFFu, pr[1] = prv >> 8;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const bool in = b + j < p.n;
+                s[j] = in ? p.h.src[b + j] : 0u;
+                d[j] = in ? p.h.dst[b + j] : 0u;
+                sp[j] = in ? p.h.sport[b + j] : 0u;
+                dp[j] = in ? p.h.dport[b + j] : 0u;
+                pr[j] = in ? p.h.proto[b + j] : 0u;
+            }
+        }
+        int32_t idx[2];
+        uint32_t acts = 0;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const uint32_t vw = filter_verdict<W, KEY>(base, p, s[j], d[j], sp[j], dp[j], pr[j]);
+            idx[j] = vw == 0xFFFFFFFFu ? -1 : (int32_t)(vw & 0x7FFFFFFFu);
+            acts |= (vw == 0xFFFFFFFFu ? (uint32_t)FW_DROP : vw >> 31) << (8 * j);
+        }
+        if (VEC && full) {
+            __stcs(reinterpret_cast<int2 *>(p.out_idx) + q, make_int2(idx[0], idx[1]));
+            __stcs(reinterpret_cast<unsigned short *>(p.out_act) + q, (unsigned short)acts);
+        } else {
+            for (int j = 0; j < 2; ++j) {
+                if (b + j < p.n) {
+                    p.out_idx[b + j] = idx[j];
+                    p.out_act[b + j] = (uint8_t)(acts >> (8 * j));
+                }
+            }
+        }
+    }
+}
+
+// Stage the filter block into shared memory (1-D TMA bulk copies, one bounded mbarrier wait);
+// false when the wait gave up.
+__device__ __forceinline__ bool filter_stage(const FilterParams &p, unsigned char *smem, uint64_t *bar) {
     if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
+        mbar_init(bar, 1);
         fence_mbar_init();
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        mbar_arrive_expect_tx(&bar, (uint32_t)p.blk_bytes);
+        mbar_arrive_expect_tx(bar, (uint32_t)p.blk_bytes);
         for (int32_t o = 0; o < p.blk_bytes; o += 32768)
-            bulk_load(smem + o, p.blk + o, (uint32_t)min(32768, p.blk_bytes - o), &bar);
+            bulk_load(smem + o, p.blk + o, (uint32_t)min(32768, p.blk_bytes - o), bar);
     }
-    const bool ok = mbar_wait_bounded(&bar, 0, p.status);
-    if (__syncthreads_and(ok) != 0) {
+    const bool ok = mbar_wait_bounded(bar, 0, p.status);
+    return __syncthreads_and(ok) != 0;
+}
+
+template <int W, int KEY, bool VEC>
+__global__ void __launch_bounds__(512, 4) k_packet_split_filter_pairs(FilterParams p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar;
+    if (filter_stage(p, smem, &bar)) {
+        filter_loop_pairs<W, KEY, VEC>(p, smem);
+    } else {
+        filter_loop_pairs<W, KEY, VEC>(p, p.blk);
+        if (threadIdx.x == 0) mbar_wait_bounded(&bar, 0, p.status);
+    }
+}
+
+template <int W, int KEY, bool VEC>
+__global__ void __launch_bounds__(512, 3) k_packet_split_filter(FilterParams p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar;
+    if (filter_stage(p, smem, &bar)) {
         filter_loop<W, KEY, VEC>(p, smem);
     } else {
         // a failed wait leaves the block reading the filter from global memory; before it exits,
@@ -253,7 +323,7 @@ cudaError_t build_filter(const fw_rule *rules, const std::vector<std::vector<int
 bool filter_staged(const fw_ruleset *rs) { return rs->filter_words <= 2 && rs->filter_bytes <= 72 * 1024; }
 
 int launch_filter(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *out_idx, uint8_t *out_act,
-                  cudaStream_t st, int threads, int blocks_per_sm) {
+                  cudaStream_t st, int threads, int blocks_per_sm, int lane_packets) {
     if (rs->filter_words == 0) return FW_EINVAL;
     FilterParams p;
     std::memset(&p, 0, sizeof(p));
@@ -267,26 +337,37 @@ int launch_filter(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *ou
     p.out_act = out_act;
     p.status = rs->d_status;
     const bool staged = filter_staged(rs);
+    if (lane_packets != 0 && lane_packets != 2 && lane_packets != 4) return FW_EINVAL;
+    const bool pairs = staged && lane_packets == 2;  // two packets per thread, four blocks per SM
     threads = threads > 0 ? threads : 512;
-    const int per_sm = blocks_per_sm > 0 ? blocks_per_sm : 3;
+    const int per_sm = blocks_per_sm > 0 ? blocks_per_sm : (pairs ? 4 : 3);
     if (threads % 32 != 0 || threads > 512 || per_sm > 64) return FW_EINVAL;
     const size_t smem = staged ? (size_t)rs->filter_bytes : 0;
     if (staged && (size_t)per_sm * (smem + 1024) > 228 * 1024) return FW_EINVAL;
-    const int64_t nq = (n + 3) / 4;
+    const int64_t nq = pairs ? (n + 1) / 2 : (n + 3) / 4;
     int64_t blocks = std::min<int64_t>((int64_t)sm_count(rs->device) * per_sm, (nq + threads - 1) / threads);
     blocks = std::max<int64_t>(1, blocks);
-    const bool vec = (reinterpret_cast<uintptr_t>(h.src) % 16 == 0) && (reinterpret_cast<uintptr_t>(h.dst) % 16 == 0) &&
-                     (reinterpret_cast<uintptr_t>(h.sport) % 8 == 0) && (reinterpret_cast<uintptr_t>(h.dport) % 8 == 0) &&
-                     (reinterpret_cast<uintptr_t>(h.proto) % 4 == 0) && (reinterpret_cast<uintptr_t>(out_idx) % 16 == 0) &&
-                     (reinterpret_cast<uintptr_t>(out_act) % 4 == 0);
+    // vector loads: a quad's (or pair's) header fields and verdicts each in one aligned access
+    const int u = pairs ? 2 : 4;
+    auto al = [](const void *q, size_t a) { return reinterpret_cast<uintptr_t>(q) % a == 0; };
+    const bool vec = al(h.src, 4 * u) && al(h.dst, 4 * u) && al(h.sport, 2 * u) && al(h.dport, 2 * u) &&
+                     al(h.proto, u) && al(out_idx, 4 * u) && al(out_act, u);
     const int key = p.v.key_field;
     cudaError_t e = cudaSuccess;
 #define FW_LAUNCH_F(WW, KK, V)                                                                              \
     do {                                                                                                    \
-        if (smem > 48 * 1024)                                                                               \
-            e = cudaFuncSetAttribute(k_packet_split_filter<WW, KK, V>,                                      \
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);               \
-        if (e == cudaSuccess) k_packet_split_filter<WW, KK, V><<<(unsigned)blocks, threads, smem, st>>>(p); \
+        if (pairs) {                                                                                        \
+            if (smem > 48 * 1024)                                                                           \
+                e = cudaFuncSetAttribute(k_packet_split_filter_pairs<WW, KK, V>,                            \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);           \
+            if (e == cudaSuccess)                                                                           \
+                k_packet_split_filter_pairs<WW, KK, V><<<(unsigned)blocks, threads, smem, st>>>(p);         \
+        } else {                                                                                            \
+            if (smem > 48 * 1024)                                                                           \
+                e = cudaFuncSetAttribute(k_packet_split_filter<WW, KK, V>,                                  \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);           \
+            if (e == cudaSuccess) k_packet_split_filter<WW, KK, V><<<(unsigned)blocks, threads, smem, st>>>(p); \
+        }                                                                                                   \
     } while (0)
 #define FW_LAUNCH_G(KK, V)                                                                                  \
     k_packet_split_filter_wide<KK, V><<<(unsigned)blocks, threads, 0, st>>>(p)

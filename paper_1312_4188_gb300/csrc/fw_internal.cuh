@@ -360,7 +360,8 @@ int rule_split_run(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *o
 int launch_rule_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *out_idx, uint8_t *out_act,
                       cudaStream_t st, const fw_config &cfg);
 // Packet split through the bucket filter (FW_OK, or a status for a bad
-// configuration / launch failure). threads, blocks_per_sm: launch shape (0 = default).
+// configuration / launch failure). threads, blocks_per_sm, lane_packets (packets per
+// thread per step, 2 or 4): launch shape (0 = default).
 int launch_filter(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *out_idx, uint8_t *out_act,
-                  cudaStream_t st, int threads, int blocks_per_sm);
+                  cudaStream_t st, int threads, int blocks_per_sm, int lane_packets);
 }  // namespace fwk

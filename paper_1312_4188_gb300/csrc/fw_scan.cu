@@ -180,7 +180,7 @@ int launch_packet_split(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32
                             cfg.compact == 0 && (cfg.predicate == 0 || cfg.predicate == FW_PRED_ARITH) &&
                             cfg.segment_rules == 0 && cfg.partition == 0 && cfg.lane_packets == 0;
     if (cfg.filter == 1 || (cfg.filter == 0 && shape_only && rs->filter_words > 0))
-        return launch_filter(rs, h, n, out_idx, out_act, st, cfg.block_threads, cfg.blocks_per_sm);
+        return launch_filter(rs, h, n, out_idx, out_act, st, cfg.block_threads, cfg.blocks_per_sm, cfg.lane_packets);
     ScanParams p;
     std::memset(&p, 0, sizeof(p));
     const int pred = cfg.predicate == 0 ? FW_PRED_ARITH : cfg.predicate;

@@ -63,10 +63,10 @@ struct SvSlot {
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
     BatchJobDev *d_jobs = nullptr;
-    BatchItem *d_items = nullptr;
+    int64_t *d_prefix = nullptr;   // first item of every job, then the item total
     unsigned long long *d_next = nullptr;
     BatchJobDev *h_jobs = nullptr;  // pinned staging of the work list
-    BatchItem *h_items = nullptr;
+    int64_t *h_prefix = nullptr;
     bool busy = false;
     bool failed = false;  // the group's launch failed: it completes with FW_ECUDA
     std::vector<SvRequest *> group;
@@ -90,7 +90,6 @@ struct fw_server {
     int device = 0;
     int threads = 512;
     int32_t qcap = 256;
-    int64_t item_cap = 0;
     uint8_t *d_arena = nullptr;
     size_t arena_bytes = 0;
     std::map<size_t, size_t> free_blocks;  // offset -> length
@@ -172,25 +171,20 @@ static cudaError_t launch_group(fw_server *sv, SvSlot &sl) {
             if (e == cudaSuccess) e = cudaMemcpyAsync(pr, r->h.proto, m, cudaMemcpyHostToDevice, sl.st);
             dh = fw_headers{s, d, sp, dp, pr};
         }
-        fill_batch_job(sl.h_jobs[i], sv->sets[r->set], dh, r->n, di, da);
-        for (int64_t s0 = 0; s0 < r->n; s0 += B) {
-            BatchItem &it = sl.h_items[n_items++];
-            it.start = s0;
-            it.job = (int32_t)i;
-            it.count = (int32_t)std::min<int64_t>(B, r->n - s0);
-            it.seg0 = sv->cfg.segment_rules;
-            it.pad = 0;
-        }
+        fill_batch_job(sl.h_jobs[i], sv->sets[r->set], dh, r->n, di, da, B, sv->cfg.segment_rules);
+        sl.h_prefix[i] = n_items;
+        n_items += (r->n + B - 1) / B;
     }
+    sl.h_prefix[sl.group.size()] = n_items;
     const size_t nj = sl.group.size();
     if (e == cudaSuccess) e = cudaMemcpyAsync(sl.d_jobs, sl.h_jobs, nj * sizeof(BatchJobDev), cudaMemcpyHostToDevice, sl.st);
-    if (e == cudaSuccess && n_items > 0)
-        e = cudaMemcpyAsync(sl.d_items, sl.h_items, n_items * sizeof(BatchItem), cudaMemcpyHostToDevice, sl.st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sl.d_prefix, sl.h_prefix, (nj + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, sl.st);
     if (e == cudaSuccess) {
         const int wpb = sv->threads / 32;
         const int64_t blocks =
             std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count(sv->device) * 2, (n_items + wpb - 1) / wpb));
-        e = launch_batch(sl.d_jobs, sl.d_items, n_items, sl.d_next, sv->qcap, sv->threads, blocks, sl.st);
+        e = launch_batch(sl.d_jobs, sl.d_prefix, (int32_t)nj, n_items, sl.d_next, sv->qcap, sv->threads, blocks, sl.st);
     }
     if (copy) {
         for (size_t i = 0; i < nj && e == cudaSuccess; ++i) {
@@ -325,18 +319,6 @@ static const void *device_alias(const void *p) {
     return nullptr;
 }
 
-// Device alias of [p, p + bytes): from a registered range when one covers it,
-// else looked up now.
-static const void *resolve(fw_server *sv, const void *p, size_t bytes) {
-    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
-    {
-        std::lock_guard<std::mutex> lk(sv->reg_mu);
-        for (const SvRange &r : sv->ranges)
-            if (a >= r.lo && a + bytes <= r.hi) return reinterpret_cast<const void *>(a + r.delta);
-    }
-    return device_alias(p);
-}
-
 }  // namespace fwk
 
 using namespace fwk;
@@ -379,10 +361,10 @@ extern "C" void fw_server_destroy(fw_server *sv) {
         if (sl.ev) cudaEventDestroy(sl.ev);
         if (sl.st) cudaStreamDestroy(sl.st);
         cudaFree(sl.d_jobs);
-        cudaFree(sl.d_items);
+        cudaFree(sl.d_prefix);
         cudaFree(sl.d_next);
         cudaFreeHost(sl.h_jobs);
-        cudaFreeHost(sl.h_items);
+        cudaFreeHost(sl.h_prefix);
     }
     cudaFree(sv->d_arena);
     for (auto &kv : sv->live) delete kv.second;
@@ -424,7 +406,6 @@ extern "C" int fw_server_create(const fw_ruleset *const *sets, int n_sets, const
     sv->qcap = c.packets_per_item;
     // a request of n packets needs ceil(n / item_packets) items; a group holds
     // at most max_group_packets packets plus one partial item per request
-    sv->item_cap = c.max_group_packets / item_packets(c.packets_per_item) + c.max_group_requests + 1;
     cudaError_t e = prepare_batch_kernel(smem);
     if (e == cudaSuccess && c.mode == FW_HOST_COPY) {
         sv->arena_bytes = (size_t)c.arena_bytes;
@@ -436,10 +417,10 @@ extern "C" int fw_server_create(const fw_ruleset *const *sets, int n_sets, const
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
         if (e == cudaSuccess) e = dev_malloc(&sl.d_jobs, c.max_group_requests * sizeof(BatchJobDev));
-        if (e == cudaSuccess) e = dev_malloc(&sl.d_items, sv->item_cap * sizeof(BatchItem));
+        if (e == cudaSuccess) e = dev_malloc(&sl.d_prefix, (c.max_group_requests + 1) * sizeof(int64_t));
         if (e == cudaSuccess) e = dev_malloc(&sl.d_next, sizeof(unsigned long long));
         if (e == cudaSuccess) e = pinned_malloc(&sl.h_jobs, c.max_group_requests * sizeof(BatchJobDev));
-        if (e == cudaSuccess) e = pinned_malloc(&sl.h_items, sv->item_cap * sizeof(BatchItem));
+        if (e == cudaSuccess) e = pinned_malloc(&sl.h_prefix, (c.max_group_requests + 1) * sizeof(int64_t));
     }
     if (e != cudaSuccess) {
         fw_server_destroy(sv);
@@ -451,14 +432,18 @@ extern "C" int fw_server_create(const fw_ruleset *const *sets, int n_sets, const
     return FW_OK;
 }
 
-extern "C" int fw_server_submit(fw_server *sv, int set, const fw_headers *h, int64_t n, int32_t *out_idx,
-                                uint8_t *out_act, uint64_t *ticket) {
-    if (sv == nullptr || ticket == nullptr || h == nullptr || n < 1 || n > INT32_MAX) return set_status(FW_EINVAL);
-    if (set < 0 || set >= (int)sv->sets.size()) return set_status(FW_EINVAL);
-    if (!h->src || !h->dst || !h->sport || !h->dport || !h->proto || !out_idx || !out_act) return set_status(FW_EINVAL);
-    if (n > sv->cfg.max_group_packets) return set_status(FW_ERANGE);
+namespace fwk {
+
+// A request checked and, in zero-copy mode, its buffers resolved to device-accessible aliases
+// (one pass over the registered ranges under one lock), without touching the queue.
+static int prepare_request(fw_server *sv, int set, const fw_headers *h, int64_t n, int32_t *out_idx,
+                           uint8_t *out_act, SvRequest **out) {
+    if (h == nullptr || n < 1 || n > INT32_MAX) return FW_EINVAL;
+    if (set < 0 || set >= (int)sv->sets.size()) return FW_EINVAL;
+    if (!h->src || !h->dst || !h->sport || !h->dport || !h->proto || !out_idx || !out_act) return FW_EINVAL;
+    if (n > sv->cfg.max_group_packets) return FW_ERANGE;
     SvRequest *r = new (std::nothrow) SvRequest();
-    if (r == nullptr) return set_status(FW_ENOMEM);
+    if (r == nullptr) return FW_ENOMEM;
     r->set = set;
     r->h = *h;
     r->n = n;
@@ -466,38 +451,79 @@ extern "C" int fw_server_submit(fw_server *sv, int set, const fw_headers *h, int
     r->out_act = out_act;
     if (sv->cfg.mode == FW_HOST_ZEROCOPY) {
         const size_t m = (size_t)n;
-        r->dh.src = static_cast<const uint32_t *>(resolve(sv, h->src, 4 * m));
-        r->dh.dst = static_cast<const uint32_t *>(resolve(sv, h->dst, 4 * m));
-        r->dh.sport = static_cast<const uint16_t *>(resolve(sv, h->sport, 2 * m));
-        r->dh.dport = static_cast<const uint16_t *>(resolve(sv, h->dport, 2 * m));
-        r->dh.proto = static_cast<const uint8_t *>(resolve(sv, h->proto, m));
-        r->d_idx = static_cast<int32_t *>(const_cast<void *>(resolve(sv, out_idx, 4 * m)));
-        r->d_act = static_cast<uint8_t *>(const_cast<void *>(resolve(sv, out_act, m)));
-        if (!r->dh.src || !r->dh.dst || !r->dh.sport || !r->dh.dport || !r->dh.proto || !r->d_idx || !r->d_act) {
-            delete r;
-            return set_status(FW_EINVAL);
+        const void *p[7] = {h->src, h->dst, h->sport, h->dport, h->proto, out_idx, out_act};
+        const size_t len[7] = {4 * m, 4 * m, 2 * m, 2 * m, m, 4 * m, m};
+        const void *d[7] = {};
+        int found = 0;
+        {
+            std::lock_guard<std::mutex> lk(sv->reg_mu);
+            for (int k = 0; k < 7; ++k) {
+                const uintptr_t a = reinterpret_cast<uintptr_t>(p[k]);
+                for (const SvRange &rg : sv->ranges)
+                    if (a >= rg.lo && a + len[k] <= rg.hi) {
+                        d[k] = reinterpret_cast<const void *>(a + rg.delta);
+                        ++found;
+                        break;
+                    }
+            }
         }
+        if (found < 7)
+            for (int k = 0; k < 7; ++k)
+                if (d[k] == nullptr) d[k] = device_alias(p[k]);  // not registered: looked up now
+        r->dh = fw_headers{static_cast<const uint32_t *>(d[0]), static_cast<const uint32_t *>(d[1]),
+                           static_cast<const uint16_t *>(d[2]), static_cast<const uint16_t *>(d[3]),
+                           static_cast<const uint8_t *>(d[4])};
+        r->d_idx = static_cast<int32_t *>(const_cast<void *>(d[5]));
+        r->d_act = static_cast<uint8_t *>(const_cast<void *>(d[6]));
+        for (int k = 0; k < 7; ++k)
+            if (d[k] == nullptr) {
+                delete r;
+                return FW_EINVAL;
+            }
     } else {
         r->bytes = request_bytes(n);
         if (r->bytes > sv->arena_bytes) {
             delete r;
-            return set_status(FW_ERANGE);
+            return FW_ERANGE;
         }
     }
+    *out = r;
+    return FW_OK;
+}
+
+// Queue prepared requests, in order, under one lock; returns how many were queued (the rest do
+// not fit under max_pending and stay with the caller).
+static int64_t enqueue_requests(fw_server *sv, SvRequest *const *rs, int64_t count, uint64_t *tickets) {
+    int64_t k = 0;
     {
         std::lock_guard<std::mutex> lk(sv->mu);
-        if ((int64_t)sv->pending.size() >= sv->cfg.max_pending) {
-            delete r;
-            return set_status(FW_EBUSY);
+        const double t = now_us();
+        for (; k < count && (int64_t)sv->pending.size() < sv->cfg.max_pending; ++k) {
+            SvRequest *r = rs[k];
+            r->ticket = sv->next_ticket++;
+            r->t_submit = t;
+            sv->pending.push_back(r);
+            sv->live[r->ticket] = r;
+            sv->stats.submitted += 1;
+            tickets[k] = r->ticket;
         }
-        r->ticket = sv->next_ticket++;
-        r->t_submit = now_us();
-        sv->pending.push_back(r);
-        sv->live[r->ticket] = r;
-        sv->stats.submitted += 1;
-        *ticket = r->ticket;
     }
-    sv->cv_work.notify_one();
+    if (k > 0) sv->cv_work.notify_one();
+    return k;
+}
+
+}  // namespace fwk
+
+extern "C" int fw_server_submit(fw_server *sv, int set, const fw_headers *h, int64_t n, int32_t *out_idx,
+                                uint8_t *out_act, uint64_t *ticket) {
+    if (sv == nullptr || ticket == nullptr) return set_status(FW_EINVAL);
+    SvRequest *r = nullptr;
+    const int s = prepare_request(sv, set, h, n, out_idx, out_act, &r);
+    if (s != FW_OK) return set_status(s);
+    if (enqueue_requests(sv, &r, 1, ticket) == 0) {
+        delete r;
+        return set_status(FW_EBUSY);
+    }
     return FW_OK;
 }
 
@@ -551,36 +577,60 @@ extern "C" int fw_server_get_stats(fw_server *sv, fw_server_stats *st) {
 extern "C" int fw_server_replay(fw_server *sv, fw_request *reqs, int64_t n, int64_t timeout_us) {
     if (sv == nullptr || n < 0 || (n > 0 && reqs == nullptr)) return set_status(FW_EINVAL);
     std::vector<uint64_t> tickets((size_t)n, 0);
+    std::vector<SvRequest *> batch;
     const double t0 = now_us();
-    for (int64_t i = 0; i < n; ++i) {
-        fw_request &q = reqs[i];
-        const double due = t0 + q.arrival_us;
-        while (now_us() < due) {
-        }
-        for (;;) {
-            const int s = fw_server_submit(sv, q.set, &q.hdrs, q.n, q.out_rule_idx, q.out_action, &tickets[i]);
-            if (s == FW_OK) break;
-            if (s != FW_EBUSY) {
+    // Open loop: every request is submitted at its arrival time; when the submitting thread is
+    // behind, all requests already due are prepared and queued together (one queue lock).
+    int64_t i = 0;
+    while (i < n) {
+        const double now = now_us();
+        if (now < t0 + reqs[i].arrival_us) continue;
+        int64_t j = i;
+        batch.clear();
+        while (j < n && (j == i || now >= t0 + reqs[j].arrival_us) && j - i < 1024) {
+            fw_request &q = reqs[j];
+            SvRequest *r = nullptr;
+            const int s = prepare_request(sv, q.set, &q.hdrs, q.n, q.out_rule_idx, q.out_action, &r);
+            if (s != FW_OK) {
                 q.status = s;
-                tickets[i] = 0;
-                break;
+                tickets[j] = 0;
+                r = nullptr;
             }
-            std::this_thread::yield();
+            batch.push_back(r);
+            ++j;
         }
+        // queue the prepared ones in order (a refused request keeps its status and no ticket)
+        int64_t k = 0;
+        while (k < (int64_t)batch.size()) {
+            if (batch[k] == nullptr) {
+                ++k;
+                continue;
+            }
+            int64_t e = k;
+            while (e < (int64_t)batch.size() && batch[e] != nullptr) ++e;
+            int64_t done = 0;
+            while (done < e - k) {
+                const int64_t got = enqueue_requests(sv, batch.data() + k + done, e - k - done, &tickets[i + k + done]);
+                done += got;
+                if (got == 0) std::this_thread::yield();  // the queue is full: wait for room
+            }
+            k = e;
+        }
+        i = j;
     }
     int worst = FW_OK;
-    for (int64_t i = 0; i < n; ++i) {
-        fw_request &q = reqs[i];
-        if (tickets[i] == 0) {
+    for (int64_t i2 = 0; i2 < n; ++i2) {
+        fw_request &q = reqs[i2];
+        if (tickets[i2] == 0) {
             worst = q.status;
             continue;
         }
         std::unique_lock<std::mutex> lk(sv->mu);
-        SvRequest *r = sv->live[tickets[i]];
+        SvRequest *r = sv->live[tickets[i2]];
         lk.unlock();
         const double t_submit = r->t_submit;
         double lat = 0;
-        const int s = fw_server_wait(sv, tickets[i], timeout_us, &lat);
+        const int s = fw_server_wait(sv, tickets[i2], timeout_us, &lat);
         q.status = s;
         // open-loop latency: from the scheduled arrival, not from the submit call
         q.latency_us = (t_submit + lat) - (t0 + q.arrival_us);

@@ -130,8 +130,9 @@ CASES = [(12, 1), (30, 2), (45, 3), (70, 4), (100, 5), (160, 6), (400, 7), (900,
 
 
 @pytest.mark.parametrize("n_rules,seed", CASES)
-@pytest.mark.parametrize("cfg", [{"filter": 1}, {}, {"filter": 1, "block_threads": 64, "blocks_per_sm": 1}],
-                         ids=["forced", "auto", "small_blocks"])
+@pytest.mark.parametrize("cfg", [{"filter": 1}, {}, {"filter": 1, "block_threads": 64, "blocks_per_sm": 1},
+                                 {"filter": 1, "lane_packets": 2}],
+                         ids=["forced", "auto", "small_blocks", "pairs"])
 def test_edges_against_oracle(torch_cuda, n_rules, seed, cfg):
     rules = edge_rules(n_rules, 900 + seed)
     rs = fw.fw_ruleset_create(rules)
@@ -156,15 +157,16 @@ def test_all_bitmap_widths_are_exercised(torch_cuda):
 
 @pytest.mark.parametrize("n_pkts", [1, 3, 4, 5, 63, 1023, 4097, 100_003])
 @pytest.mark.parametrize("offset", [0, 1, 3])
-def test_sizes_and_misaligned_views(torch_cuda, n_pkts, offset):
+@pytest.mark.parametrize("lane_packets", [0, 2])
+def test_sizes_and_misaligned_views(torch_cuda, n_pkts, offset, lane_packets):
     rules = edge_rules(40, 77)
     rs = fw.fw_ruleset_create(rules)
     assert rs.filter()["words"] > 0
     full = mixed_packets(rules, max(n_pkts, 16), 5)
     hdr = {f: full[f][-n_pkts:] for f in W.HEADER_FIELDS}
     want = oracle.classify(rules, hdr, threads=THREADS)
-    assert_same(classify(torch_cuda, rs, hdr, fw.make_config("packet_split", filter=1), offset), want,
-                f"n={n_pkts} offset={offset}")
+    assert_same(classify(torch_cuda, rs, hdr, fw.make_config("packet_split", filter=1, lane_packets=lane_packets),
+                         offset), want, f"n={n_pkts} offset={offset} lane_packets={lane_packets}")
     rs.destroy()
 
 
