@@ -11,7 +11,8 @@ Besides the headline step, a single-GPU run measures in the same process:
   - the integer throughput of this GPU (the INT32 roofline denominator);
   - the other workloads of the method, each as a record under "configs": the
     plain 1,000-rule x 100,000-packet case, the rule split (warp, block and
-    grid minimum) beside the packet split on the headline batch, 256 batched
+    grid minimum) beside the packet split on the headline batch, two labelled
+    variants of the headline traffic (permuted Zipf ranks; no catch-all), 256 batched
     rule sets in one graph-replayed persistent launch, the learned index at
     100,000 rules x 67,108,864 packets, and serving (Poisson arrivals against
     four device-resident rule sets) at three offered loads.
@@ -424,6 +425,52 @@ def side_rule_split(ctx):
     return rec
 
 
+def side_variants(ctx):
+    """Labelled variants of the headline traffic: Zipf ranks permuted over the rule list, and every
+    all-wildcard rule removed (deep scans, a third of the packets default deny). AUTO beside the
+    two-packet scan (filter = 2); both checked against the oracle on a 1M-packet sample."""
+    import torch
+
+    from paper_1312_4188_gb300 import fw
+    st = ctx["stream"]
+    out = {}
+    for name in ("scan_10k_x_16m_zipf_permuted", "scan_10k_x_16m_no_catch_all"):
+        rules, hdr = W.make_workload(name, workers=GEN_WORKERS)
+        n = len(hdr["src"])
+        dh = fw.headers_to_device(hdr)
+        rs = fw.fw_ruleset_create(rules)
+        idx = torch.empty(n, dtype=torch.int32, device="cuda")
+        act = torch.empty(n, dtype=torch.uint8, device="cuda")
+        rec = {"config": workload_config(name), "filter_words": rs.filter()["words"]}
+        forms = {}
+        ref = None
+        with ClockSampler(ctx["gpu_id"]) as clk:
+            for form, cfg in (("auto", None), ("scan_x2", fw.make_config("packet_split", filter=2))):
+                ts = events_ms(lambda: fw.fw_classify(rs, dh, n, idx, act, stream=st, config=cfg), st, 5, 2)
+                t = statistics.median(ts)
+                forms[form] = {"ms": t, "mpackets_s": n / (1e-3 * t) / 1e6}
+                if ref is None:
+                    ref = (idx.clone(), act.clone())
+                else:
+                    forms[form]["same_as_auto"] = bool(torch.equal(idx, ref[0]) and torch.equal(act, ref[1]))
+        rec["clocks"] = clk.summary()
+        depth = depth_sum_of(ref[0], len(rules))
+        rec.update({"forms": forms, "mpackets_s": forms["auto"]["mpackets_s"],
+                    "workload_stats": {"first_catch_all": rs.first_catch_all, "mean_depth": depth / n,
+                                       "unmatched_frac": float((ref[0] < 0).float().mean().item())},
+                    "roofline": fractions(n, depth, depth, forms["auto"]["ms"], ctx["int_peak"], ctx["alu_peak"],
+                                          ctx["hbm_gbs"])})
+        rec["roofline"].pop("int32_executed")
+        if ctx["cpu"]:
+            pos = W.sample_positions(n, 1 << 20, seed=99)
+            pt = torch.from_numpy(pos).cuda()
+            rec["cpu_baseline"] = oracle_leg(rules, W.take(hdr, pos), ref[0][pt].cpu().numpy(), ref[1][pt].cpu().numpy())
+            rec["cpu_baseline"]["sample"] = f"{len(pos)} packets at fixed seeded positions of the {n}-packet batch"
+        rs.destroy()
+        out[name] = rec
+    return {"variants": out, "mpackets_s": {k: v["mpackets_s"] for k, v in out.items()}}
+
+
 def side_batched(ctx):
     """256 rule sets (64..65,536 rules) with their own batches (1K..1M packets): one graph-replayed launch."""
     import torch
@@ -595,9 +642,11 @@ def side_serving(ctx):
     mean_n = float(req_n.mean())
     rec = {"config": {"workload": "serving_4_sets", "sets_rules": sizes, "requests": n_req,
                       "request_packets": [64, 65536], "packets": total, "arrivals": "Poisson",
-                      "buffers": "device-resident request headers and verdicts", "slots": 8}}
+                      "buffers": "device-resident request headers and verdicts", "slots": 8,
+                      "max_group_requests": 1024, "max_group_packets": 1 << 22}}
     loads = {}
-    sv = fw.Server(sets, mode=fw.FW_HOST_ZEROCOPY, slots=8, max_group_requests=256, arena_bytes=1 << 30)
+    sv = fw.Server(sets, mode=fw.FW_HOST_ZEROCOPY, slots=8, max_group_requests=1024, max_group_packets=1 << 22,
+                   arena_bytes=1 << 30)
     for pool in dpools:
         for t in pool.values():
             sv.register(t)
@@ -654,7 +703,8 @@ def side_serving(ctx):
     return rec
 
 
-SIDE = {"plain_1k_x_100k": side_plain, "rule_split_10k_x_16m": side_rule_split, "batched_256_sets": side_batched,
+SIDE = {"plain_1k_x_100k": side_plain, "rule_split_10k_x_16m": side_rule_split,
+        "variants_10k_x_16m": side_variants, "batched_256_sets": side_batched,
         "lindex_100k_x_64m": side_lindex, "serving_4_sets": side_serving}
 
 
@@ -721,6 +771,8 @@ def main():
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
+    # The timed region: K steps back to back between two events (inputs larger than L2), or, for
+    # inputs that fit in L2, each step between its own events after an L2 flush outside them.
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with ClockSampler(gpu_id) as clk:
         torch.cuda.synchronize()
@@ -733,16 +785,20 @@ def main():
             for i in range(args.steps):
                 if flush:
                     scrub.zero_()
-                ev[i][0].record(stream)
+                    ev[i][0].record(stream)
                 step()
-                ev[i][1].record(stream)
+                if flush:
+                    ev[i][1].record(stream)
             g1.record(stream)
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
     total_ms = sum(a.elapsed_time(b) for a, b in ev) if flush else g0.elapsed_time(g1)
     total_ms = replica.max_over_ranks(total_ms, device="cuda")
-    per = sorted(a.elapsed_time(b) for a, b in ev)
+    # per-launch latency (the roofline's launch duration): each launch between its own events,
+    # after the timed region
+    per = sorted(events_ms(step, stream, max(args.steps, 20), 0, flush=(lambda: scrub.zero_()) if flush else None)) \
+        if not flush else sorted(a.elapsed_time(b) for a, b in ev)
     mean_launch_ms = sum(per) / len(per)
     assert rs.check() == fw.FW_OK, "a bounded device wait timed out"
 
@@ -785,7 +841,9 @@ def main():
         "rule_checks_per_s": depth_sum / (mean_launch_ms * 1e-3),
         "executed_checks_per_s": scan_sum / (mean_launch_ms * 1e-3),
         "latency_ms": {"launch_p50": pct(per, 0.5), "launch_p99": pct(per, 0.99),
-                       "launch_mean": mean_launch_ms, "packets_per_launch": n},
+                       "launch_mean": mean_launch_ms, "packets_per_launch": n,
+                       "how": ("each launch between its own CUDA events, after the timed region" if not flush else
+                               "the timed launches, each between its own CUDA events")},
         "workload_stats": {"first_catch_all": rs.first_catch_all, "mean_depth": depth_sum / n,
                            "mean_scan_depth": scan_sum / n, "unmatched_frac": unmatched,
                            "partition": part},
@@ -796,11 +854,13 @@ def main():
 
     if rank == 0 and args.modes:
         modes = {}
-        variants = {"packet_split_filter_pairs": ("packet_split", {"filter": 1, "lane_packets": 2}),
-                    "packet_split_filter_pairs_3bps": ("packet_split", {"filter": 1, "lane_packets": 2,
-                                                                        "blocks_per_sm": 3}),
-                    "packet_split_filter_256t_6bps": ("packet_split", {"filter": 1, "block_threads": 256,
-                                                                       "blocks_per_sm": 6}),
+        variants = {"packet_split_filter_512t_3bps": ("packet_split", {"filter": 1, "block_threads": 512,
+                                                                       "blocks_per_sm": 3}),
+                    "packet_split_filter_384t_4bps": ("packet_split", {"filter": 1, "block_threads": 384,
+                                                                       "blocks_per_sm": 4}),
+                    "packet_split_filter_pairs": ("packet_split", {"filter": 1, "lane_packets": 2}),
+                    "packet_split_filter_pairs_256t_8bps": ("packet_split", {"filter": 1, "lane_packets": 2,
+                                                                             "block_threads": 256, "blocks_per_sm": 7}),
                     "packet_split_scan_x2": ("packet_split", {"filter": 2}),
                     "packet_split_one_lane": ("packet_split", {"lane_packets": 1}),
                     "packet_split_dense": ("packet_split", {"block_threads": 768, "blocks_per_sm": 2, "smem_rules": 1024}),

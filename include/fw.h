@@ -165,15 +165,20 @@ typedef struct fw_headers {
  *                     in list order, only the rules whose three bits are all
  *                     set, which include every rule that contains it, so its
  *                     first match is the same. A rule set has the filter when
- *                     every class sub-list holds at most 64 rules and the
- *                     "every other protocol" class holds no exact-protocol
- *                     rule. 0 = default: the filter kernel whenever the rule
+ *                     every class sub-list holds at most FW_FILTER_MAX_RULES
+ *                     rules and the "every other protocol" class holds no
+ *                     exact-protocol rule. Rows of one or two words (sub-lists
+ *                     of at most 64 rules) are staged in each block's shared
+ *                     memory; wider rows are read from global memory (L1), a
+ *                     word at a time up to the packet's first match.
+ *                     0 = default: the filter kernel whenever the rule
  *                     set has one and no other field of this struct except
  *                     mode (AUTO or PACKET_SPLIT), block_threads and
  *                     blocks_per_sm is set; 1 = the filter kernel
  *                     (FW_EINVAL if the rule set has none); 2 = never.
  *                     block_threads (<= 512, default 512), blocks_per_sm
- *                     (default 3, or 4 with two packets per thread) and
+ *                     (default 3, or 4 with two packets per thread; fewer
+ *                     when the staged filter's shared memory does not fit) and
  *                     lane_packets (packets a thread takes per step: 4 by
  *                     default, 2 with filter = 1 and one- or two-word rows)
  *                     shape its launch.
@@ -262,10 +267,14 @@ int fw_ruleset_partition(const fw_ruleset *rs, int32_t *n_classes, int32_t *key_
 int fw_partition_plan(const fw_rule *rules, int64_t n, int32_t granule, int32_t *n_classes, int32_t *key_field,
                       int32_t *key_bits, int64_t *class_len, uint8_t *proto_class);
 
+/* Longest class sub-list a bucket filter covers (rows of up to 256 words). */
+#define FW_FILTER_MAX_RULES 8192
+
 /*
  * Bucket filter of the rule set's partition (see fw_config.filter): *words
- * receives the 32-bit words per bitmap row (1 or 2; 0 when the rule set has
- * no filter: a class sub-list longer than 64 rules, or the "every other
+ * receives the 32-bit words per bitmap row (1 to FW_FILTER_MAX_RULES / 32;
+ * 0 when the rule set has no filter: a class sub-list longer than
+ * FW_FILTER_MAX_RULES rules, or the "every other
  * protocol" class holding exact-protocol rules), *bytes the size of the
  * filter block each block of the filter kernel stages into shared memory.
  * Host only. FW_EINVAL for NULL arguments.
@@ -279,7 +288,7 @@ int fw_ruleset_filter(const fw_ruleset *rs, int32_t *words, int64_t *bytes);
  * fw_ruleset_filter), its filter block is built and copied to `block`.
  * The paper has no counterpart: this exposes the host-side construction so
  * that it can be checked without a GPU.
- *  Outputs: *words (0 = no filter, else 1 or 2 32-bit words per bitmap row),
+ *  Outputs: *words (0 = no filter, else the 32-bit words per bitmap row),
  *  *bytes (the block size, 0 without a filter), class_off / class_len
  *  (FW_MAX_CLASSES entries each, may be NULL): first stored record and record
  *  count (a multiple of 4, padding included) of every class sub-list.

@@ -277,7 +277,7 @@ struct fw_ruleset {
     // the class sub-list indexed by a packet's address and port buckets, plus an
     // exact-test record per stored record. Built when every sub-list holds at
     // most kFilterMaxRecords records and no class mixes exact protocols.
-    int32_t filter_words;              // 0 = no filter, else 1..16 (32-bit words per bitmap row)
+    int32_t filter_words;              // 0 = no filter, else 32-bit words per bitmap row
     int64_t filter_bytes;              // bytes of d_filter
     unsigned char *d_filter;           // the filter block (layout: FilterLayout)
     uint8_t *d_action;        // n_pad actions
@@ -324,7 +324,7 @@ struct FilterLayout {
     int64_t tables, classes, exact, recs, verdicts, class_of, total;
 };
 constexpr int kFilterTables = 3;  // source top 8 bits, destination top 8 bits, (sport, dport) top 4 bits each
-constexpr int kFilterMaxRecords = 512;  // longest class sub-list a filter covers (16-word rows)
+constexpr int kFilterMaxRecords = FW_FILTER_MAX_RULES;  // longest class sub-list a filter covers
 __host__ __device__ inline FilterLayout filter_layout(int n_classes, int words, int64_t records) {
     FilterLayout L;
     auto up16 = [](int64_t b) { return (b + 15) / 16 * 16; };

@@ -62,11 +62,9 @@ struct SvRequest {
 struct SvSlot {
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
-    BatchJobDev *d_jobs = nullptr;
-    int64_t *d_prefix = nullptr;   // first item of every job, then the item total
+    BatchJobDev *d_jobs = nullptr;  // the work list: jobs, then (16-byte aligned) the item prefix
     unsigned long long *d_next = nullptr;
     BatchJobDev *h_jobs = nullptr;  // pinned staging of the work list
-    int64_t *h_prefix = nullptr;
     bool busy = false;
     bool failed = false;  // the group's launch failed: it completes with FW_ECUDA
     std::vector<SvRequest *> group;
@@ -147,6 +145,9 @@ static cudaError_t launch_group(fw_server *sv, SvSlot &sl) {
     cudaError_t e = cudaSuccess;
     size_t off = sl.arena_off;
     int64_t n_items = 0;
+    // the item prefix follows the group's jobs in the same staging buffer
+    const size_t po = a16(sl.group.size() * sizeof(BatchJobDev));
+    int64_t *h_prefix = reinterpret_cast<int64_t *>(reinterpret_cast<uint8_t *>(sl.h_jobs) + po);
     for (size_t i = 0; i < sl.group.size() && e == cudaSuccess; ++i) {
         SvRequest *r = sl.group[i];
         fw_headers dh = r->dh;
@@ -172,19 +173,20 @@ static cudaError_t launch_group(fw_server *sv, SvSlot &sl) {
             dh = fw_headers{s, d, sp, dp, pr};
         }
         fill_batch_job(sl.h_jobs[i], sv->sets[r->set], dh, r->n, di, da, B, sv->cfg.segment_rules);
-        sl.h_prefix[i] = n_items;
+        h_prefix[i] = n_items;
         n_items += (r->n + B - 1) / B;
     }
-    sl.h_prefix[sl.group.size()] = n_items;
+    h_prefix[sl.group.size()] = n_items;
     const size_t nj = sl.group.size();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sl.d_jobs, sl.h_jobs, nj * sizeof(BatchJobDev), cudaMemcpyHostToDevice, sl.st);
+    // jobs and item prefix in one copy
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(sl.d_prefix, sl.h_prefix, (nj + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, sl.st);
+        e = cudaMemcpyAsync(sl.d_jobs, sl.h_jobs, po + (nj + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, sl.st);
+    const int64_t *d_prefix = reinterpret_cast<const int64_t *>(reinterpret_cast<const uint8_t *>(sl.d_jobs) + po);
     if (e == cudaSuccess) {
         const int wpb = sv->threads / 32;
         const int64_t blocks =
             std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count(sv->device) * 2, (n_items + wpb - 1) / wpb));
-        e = launch_batch(sl.d_jobs, sl.d_prefix, (int32_t)nj, n_items, sl.d_next, sv->qcap, sv->threads, blocks, sl.st);
+        e = launch_batch(sl.d_jobs, d_prefix, (int32_t)nj, n_items, sl.d_next, sv->qcap, sv->threads, blocks, sl.st);
     }
     if (copy) {
         for (size_t i = 0; i < nj && e == cudaSuccess; ++i) {
@@ -361,10 +363,8 @@ extern "C" void fw_server_destroy(fw_server *sv) {
         if (sl.ev) cudaEventDestroy(sl.ev);
         if (sl.st) cudaStreamDestroy(sl.st);
         cudaFree(sl.d_jobs);
-        cudaFree(sl.d_prefix);
         cudaFree(sl.d_next);
         cudaFreeHost(sl.h_jobs);
-        cudaFreeHost(sl.h_prefix);
     }
     cudaFree(sv->d_arena);
     for (auto &kv : sv->live) delete kv.second;
@@ -404,8 +404,6 @@ extern "C" int fw_server_create(const fw_ruleset *const *sets, int n_sets, const
     cudaGetDevice(&sv->device);
     sv->threads = c.block_threads;
     sv->qcap = c.packets_per_item;
-    // a request of n packets needs ceil(n / item_packets) items; a group holds
-    // at most max_group_packets packets plus one partial item per request
     cudaError_t e = prepare_batch_kernel(smem);
     if (e == cudaSuccess && c.mode == FW_HOST_COPY) {
         sv->arena_bytes = (size_t)c.arena_bytes;
@@ -416,11 +414,10 @@ extern "C" int fw_server_create(const fw_ruleset *const *sets, int n_sets, const
     for (SvSlot &sl : sv->slots) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = dev_malloc(&sl.d_jobs, c.max_group_requests * sizeof(BatchJobDev));
-        if (e == cudaSuccess) e = dev_malloc(&sl.d_prefix, (c.max_group_requests + 1) * sizeof(int64_t));
+        const size_t work_bytes = a16(c.max_group_requests * sizeof(BatchJobDev)) + (c.max_group_requests + 1) * sizeof(int64_t);
+        if (e == cudaSuccess) e = dev_malloc(&sl.d_jobs, work_bytes);
         if (e == cudaSuccess) e = dev_malloc(&sl.d_next, sizeof(unsigned long long));
-        if (e == cudaSuccess) e = pinned_malloc(&sl.h_jobs, c.max_group_requests * sizeof(BatchJobDev));
-        if (e == cudaSuccess) e = pinned_malloc(&sl.h_prefix, (c.max_group_requests + 1) * sizeof(int64_t));
+        if (e == cudaSuccess) e = pinned_malloc(&sl.h_jobs, work_bytes);
     }
     if (e != cudaSuccess) {
         fw_server_destroy(sv);

@@ -201,7 +201,7 @@ def test_default_deny_and_empty_rule_set(torch_cuda):
 
 
 def test_filter_refused_when_the_rule_set_has_none(torch_cuda):
-    long_list = W.gen_rules(4000, 12)
+    long_list = W.gen_rules(40_000, 12)
     long_list = long_list[~((long_list["src_prefix"] == 0) & (long_list["dst_prefix"] == 0))]
     many_protos = W.gen_rules(60, 13)
     many_protos["proto_any"] = 0

@@ -167,9 +167,9 @@ def test_exact_records_contain_every_packet_of_their_buckets():
 
 
 def test_no_filter_cases_and_arguments():
-    long_list = W.gen_rules(4000, 12)
+    long_list = W.gen_rules(40_000, 12)
     long_list = long_list[~((long_list["src_prefix"] == 0) & (long_list["dst_prefix"] == 0))]
-    assert fw.fw_filter_plan(long_list)["words"] == 0  # class sub-lists over 512 rules
+    assert fw.fw_filter_plan(long_list)["words"] == 0  # class sub-lists over FW_FILTER_MAX_RULES
     widths = {fw.fw_filter_plan(rule_set(k, n, s))["words"] for k, n, s in RULE_SETS}
     assert {1, 2} <= widths and max(widths) > 2, widths
     many = W.gen_rules(60, 13)
