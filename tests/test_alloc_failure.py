@@ -3,7 +3,7 @@
 The hook fails the armed allocation before the CUDA allocator is reached, so on a machine
 without a GPU the first allocation of a create call can still be made to fail: the call must
 return FW_ENOMEM with a NULL handle, and the hook must disarm after that one failure. The GPU
-test (test_zzz_2_alloc_failure_gpu.py) moves the failure across every allocation of every create call.
+test (test_alloc_failure_gpu.py) moves the failure across every allocation of every create call.
 """
 import ctypes
 
