@@ -398,6 +398,15 @@ int fw_plan_launch(fw_plan *plan, void *stream);
 int fw_plan_launch_graph(fw_plan *plan, void *stream);
 /* Number of work items in the plan (-1 for NULL). */
 int64_t fw_plan_items(const fw_plan *plan);
+/*
+ * The kernel a launch of the plan runs (-1 for NULL): 0 the general batched
+ * kernel (some job's rule set has no bucket filter: its items use the
+ * two-packet scan, queued in shared memory), 2 or 3 the filter-only kernel
+ * (every job has a bucket filter; four packets a lane, no shared memory),
+ * built for that many resident 512-thread blocks per SM (blocks_per_sm >= 3
+ * picks 3, else 2; the launch has blocks_per_sm blocks per SM, default 2).
+ */
+int fw_plan_kernel(const fw_plan *plan);
 /* Free the plan; no launch of it may still be in flight. */
 void fw_plan_destroy(fw_plan *plan);
 
@@ -432,7 +441,12 @@ typedef struct fw_server_config {
     int32_t packets_per_item;    /* queue entries per warp (multiple of 128, default 256); an item carries 8 fewer packets */
     int32_t segment_rules;       /* first rule segment of the compacting scan (default 64) */
     int32_t block_threads;       /* kernel block size (default 512) */
-    int32_t reserved[5];
+    int32_t items_per_warp;      /* a group launched while others are in flight has at most enough
+                                    blocks to give each warp this many work items on average
+                                    (default 1: every SM it can use, the lowest latency; larger
+                                    leaves SMs to the groups beside it); a group alone on the
+                                    device always gets one item a warp */
+    int32_t reserved[4];
 } fw_server_config;
 
 typedef struct fw_server_stats {
@@ -442,6 +456,9 @@ typedef struct fw_server_stats {
     int64_t max_inflight_groups;  /* most groups on the device at once */
     int64_t arena_high_water;     /* most arena bytes in use at once */
     int64_t pending;              /* queued now */
+    int64_t submit_ns;            /* host time spent checking and queueing requests (submit, replay) */
+    int64_t launch_ns;            /* scheduler time spent admitting groups and enqueueing their work */
+    int64_t complete_ns;          /* scheduler time spent polling groups and completing their requests */
 } fw_server_stats;
 
 /* One request of a replayed arrival schedule (fw_server_replay). */
@@ -454,6 +471,7 @@ typedef struct fw_request {
     uint8_t *out_action;
     double arrival_us;       /* in: arrival time after the replay starts */
     double latency_us;       /* out: completion time minus scheduled arrival */
+    double submit_lag_us;    /* out: queue entry time minus scheduled arrival (the submitter's own delay) */
 } fw_request;
 
 typedef struct fw_server fw_server;
@@ -464,10 +482,13 @@ int fw_server_create(const fw_ruleset *const *sets, int n_sets, const fw_server_
 void fw_server_destroy(fw_server *sv);
 /*
  * Queue a request of n (1..max_group_packets) packets for rule set `set`;
- * *ticket identifies it. Returns at once. FW_EBUSY when the queue is full,
- * FW_ERANGE when the request can never fit (too many packets, or more arena
- * bytes than the arena has), FW_EINVAL for bad arguments (in zero-copy mode
- * also for buffers the device cannot reach).
+ * *ticket identifies it. Returns at once. FW_EBUSY when the queue is full
+ * (max_pending requests queued) or when the ticket issued R submits earlier
+ * has not been released by fw_server_wait yet (R: max_pending + slots x
+ * max_group_requests, rounded up to a power of two; requests are kept in a
+ * ring of R entries), FW_ERANGE when the request can never fit (too many
+ * packets, or more arena bytes than the arena has), FW_EINVAL for bad
+ * arguments (in zero-copy mode also for buffers the device cannot reach).
  */
 int fw_server_submit(fw_server *sv, int set, const fw_headers *hdrs, int64_t n, int32_t *out_rule_idx,
                      uint8_t *out_action, uint64_t *ticket);
@@ -491,8 +512,9 @@ int fw_server_unregister_buffer(fw_server *sv, const void *p);
 int fw_server_get_stats(fw_server *sv, fw_server_stats *st);
 /*
  * Open-loop replay: submit reqs[i] at arrival_us[i] after the call starts
- * (retrying while the queue is full), then wait for all of them and fill
- * status and latency_us. Returns FW_OK when every request succeeded.
+ * (retrying while the queue is full; requests already due are prepared and
+ * queued together), then wait for all of them and fill status, latency_us
+ * and submit_lag_us. Returns FW_OK when every request succeeded.
  */
 int fw_server_replay(fw_server *sv, fw_request *reqs, int64_t n, int64_t timeout_us);
 

@@ -24,16 +24,109 @@
 
 namespace fwk {
 
-// One item of a job with a bucket filter: the job's filter block read through L1, one packet per
-// lane at a time. Kept out of line so that its registers do not add to the scan path's.
-__device__ __noinline__ void batch_filter_item(const BatchJobDev &J, const BatchItem &item, int lane, uint32_t one) {
+// Claim the next item of a launch for the calling warp: its index from the global counter, its
+// job by a search of the item prefix (the last j with prefix[j] <= index). False when none is left.
+__device__ __forceinline__ bool batch_claim(const BatchParams &p, int lane, int &job, int64_t &it) {
+    unsigned long long x = 0;
+    if (lane == 0) x = atomicAdd(p.next, 1ull);
+    x = __shfl_sync(0xFFFFFFFFu, x, 0);
+    if (x >= (unsigned long long)p.n_items) return false;
+    int j = 0;
+    if (lane == 0) {
+        int lo = 0, hi = p.n_jobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(p.prefix + mid) <= (int64_t)x) lo = mid;
+            else hi = mid - 1;
+        }
+        j = lo;
+    }
+    job = __shfl_sync(0xFFFFFFFFu, j, 0);
+    it = (int64_t)x;
+    return true;
+}
+
+// One item of a job with a bucket filter, its block read through L1: four consecutive packets
+// per lane (item starts are multiples of four packets, so aligned arrays allow vector loads and
+// stores), their first row words loaded together. Kept out of line in k_batch so that its
+// registers do not add to the scan path's.
+template <bool INLINE>
+__device__ __forceinline__ void batch_filter_quads(const BatchJobDev &J, const BatchItem &item, int lane,
+                                                   uint32_t one) {
     const FilterView fv = J.fv;
-    for (int k = lane; k < item.count; k += 32) {
-        const int64_t i = item.start + k;
-        const uint32_t vw = filter_packet_wide<-1>(J.filter, fv, J.h.src[i], J.h.dst[i], J.h.sport[i], J.h.dport[i],
-                                                   J.h.proto[i], one);
-        J.out_idx[i] = vw == 0xFFFFFFFFu ? -1 : (int32_t)(vw & 0x7FFFFFFFu);
-        J.out_act[i] = vw == 0xFFFFFFFFu ? (uint8_t)FW_DROP : (uint8_t)(vw >> 31);
+    const unsigned char *__restrict__ base = J.filter;
+    const int64_t st = item.start;
+    const bool vin = J.vec != 0;
+    const bool vout = vin && (reinterpret_cast<uintptr_t>(J.out_idx + st) % 16 == 0) &&
+                      (reinterpret_cast<uintptr_t>(J.out_act + st) % 4 == 0);
+    for (int q = 4 * lane; q < item.count; q += 128) {
+        const int64_t i = st + q;
+        const int m = min(4, item.count - q);
+        uint32_t s[4], d[4], sp[4], dp[4], pr[4], vw[4];
+        if (vin && m == 4) {
+            const uint4 a = __ldcs(reinterpret_cast<const uint4 *>(J.h.src + i));
+            const uint4 b = __ldcs(reinterpret_cast<const uint4 *>(J.h.dst + i));
+            const uint2 c = __ldcs(reinterpret_cast<const uint2 *>(J.h.sport + i));
+            const uint2 e = __ldcs(reinterpret_cast<const uint2 *>(J.h.dport + i));
+            const uint32_t f = __ldcs(reinterpret_cast<const unsigned int *>(J.h.proto + i));
+            s[0] = a.x; s[1] = a.y; s[2] = a.z; s[3] = a.w;
+            d[0] = b.x; d[1] = b.y; d[2] = b.z; d[3] = b.w;
+            sp[0] = c.x & 0xFFFFu; sp[1] = c.x >> 16; sp[2] = c.y & 0xFFFFu; sp[3] = c.y >> 16;
+            dp[0] = e.x & 0xFFFFu; dp[1] = e.x >> 16; dp[2] = e.y & 0xFFFFu; dp[3] = e.y >> 16;
+            pr[0] = f & 0xFFu; pr[1] = (f >> 8) & 0xFFu; pr[2] = (f >> 16) & 0xFFu; pr[3] = f >> 24;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int64_t ik = k < m ? i + k : i;  // past the item's end: a copy of its first packet
+                s[k] = J.h.src[ik];
+                d[k] = J.h.dst[ik];
+                sp[k] = J.h.sport[ik];
+                dp[k] = J.h.dport[ik];
+                pr[k] = J.h.proto[ik];
+            }
+        }
+        filter_packets_wide<4>(base, fv, s, d, sp, dp, pr, one, vw);
+        int32_t oi[4];
+        uint32_t oa = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            oi[k] = vw[k] == 0xFFFFFFFFu ? -1 : (int32_t)(vw[k] & 0x7FFFFFFFu);
+            oa |= (vw[k] == 0xFFFFFFFFu ? (uint32_t)FW_DROP : (vw[k] >> 31)) << (8 * k);
+        }
+        if (vout && m == 4) {
+            __stcs(reinterpret_cast<int4 *>(J.out_idx + i), make_int4(oi[0], oi[1], oi[2], oi[3]));
+            __stcs(reinterpret_cast<unsigned int *>(J.out_act + i), oa);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (k < m) {
+                    J.out_idx[i + k] = oi[k];
+                    J.out_act[i + k] = (uint8_t)(oa >> (8 * k));
+                }
+        }
+    }
+}
+
+__device__ __noinline__ void batch_filter_item(const BatchJobDev &J, const BatchItem &item, int lane, uint32_t one) {
+    batch_filter_quads<false>(J, item, lane, one);
+}
+
+// The persistent kernel of launches whose jobs all have a bucket filter: no scan queue in shared
+// memory, so more warps fit on an SM and the L1 cache keeps its whole capacity for the blocks.
+// MINB resident blocks per SM: 2 (64 registers a thread) or 3 (40, some of the four packets'
+// state spilled to L1).
+template <int MINB>
+__global__ void __launch_bounds__(kBatchFilterThreads, MINB) k_batch_filter(BatchParams p) {
+    const int lane = threadIdx.x & 31;
+    int job;
+    int64_t it;
+    while (batch_claim(p, lane, job, it)) {
+        const BatchJobDev &J = p.jobs[job];
+        BatchItem item;
+        item.job = job;
+        item.start = (it - __ldg(p.prefix + job)) * J.item_packets;
+        item.count = (int32_t)min((int64_t)J.item_packets, J.n - item.start);
+        batch_filter_quads<true>(J, item, lane, p.one);
     }
 }
 
@@ -42,23 +135,9 @@ __global__ void __launch_bounds__(1024) k_batch(BatchParams p) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     uint4 *Q = reinterpret_cast<uint4 *>(smem) + (size_t)warp * p.qcap;
     int *wc = reinterpret_cast<int *>(smem + (size_t)nw * p.qcap * sizeof(uint4)) + warp * 2 * kMaxClasses;
-    for (;;) {
-        unsigned long long it = 0;
-        if (lane == 0) it = atomicAdd(p.next, 1ull);
-        it = __shfl_sync(0xFFFFFFFFu, it, 0);
-        if (it >= (unsigned long long)p.n_items) break;
-        // the claimed item's job: the last j with prefix[j] <= it (lane 0 searches, all take it)
-        int job = 0;
-        if (lane == 0) {
-            int lo = 0, hi = p.n_jobs - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (__ldg(p.prefix + mid) <= (int64_t)it) lo = mid;
-                else hi = mid - 1;
-            }
-            job = lo;
-        }
-        job = __shfl_sync(0xFFFFFFFFu, job, 0);
+    int job;
+    int64_t it;
+    while (batch_claim(p, lane, job, it)) {
         const BatchJobDev &J = p.jobs[job];
         BatchItem item;
         item.job = job;
@@ -95,6 +174,10 @@ __global__ void __launch_bounds__(1024) k_batch(BatchParams p) {
 
 static bool al(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+int32_t job_vector_loads(const fw_headers &h) {
+    return al(h.src, 16) && al(h.dst, 16) && al(h.sport, 8) && al(h.dport, 8) && al(h.proto, 4);
+}
+
 void fill_batch_job(BatchJobDev &d, const fw_ruleset *rs, const fw_headers &h, int64_t n, int32_t *out_idx,
                     uint8_t *out_act, int32_t item_packets, int32_t seg0) {
     d.rec = rs->d_part;
@@ -110,7 +193,7 @@ void fill_batch_job(BatchJobDev &d, const fw_ruleset *rs, const fw_headers &h, i
         d.class_off[c] = rs->class_off[c];
         d.class_len[c] = rs->class_len[c];
     }
-    d.vec = al(h.src, 16) && al(h.dst, 16) && al(h.sport, 8) && al(h.dport, 8) && al(h.proto, 4);
+    d.vec = job_vector_loads(h);
     d.h = HdrPtrs{h.src, h.dst, h.sport, h.dport, h.proto};
     d.n = n;
     d.out_idx = out_idx;
@@ -126,11 +209,16 @@ size_t batch_smem_bytes(int threads, int32_t qcap) {
 }
 
 cudaError_t prepare_batch_kernel(size_t smem_bytes) {
-    return cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    // the filter-only kernel uses no shared memory: give the L1 cache the whole carve-out
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch_filter<2>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch_filter<3>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    return e;
 }
 
 cudaError_t launch_batch(const BatchJobDev *d_jobs, const int64_t *d_prefix, int32_t n_jobs, int64_t n_items,
-                         unsigned long long *d_next, int32_t qcap, int threads, int64_t blocks, cudaStream_t st) {
+                         unsigned long long *d_next, int32_t qcap, int threads, int64_t blocks, cudaStream_t st,
+                         int filter_minb) {
     cudaError_t e = cudaMemsetAsync(d_next, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess || n_items == 0 || n_jobs == 0) return e;
     BatchParams p;
@@ -141,7 +229,9 @@ cudaError_t launch_batch(const BatchJobDev *d_jobs, const int64_t *d_prefix, int
     p.next = d_next;
     p.qcap = qcap;
     p.one = 1u;
-    k_batch<<<(unsigned)blocks, threads, batch_smem_bytes(threads, qcap), st>>>(p);
+    if (filter_minb == 3) k_batch_filter<3><<<(unsigned)blocks, kBatchFilterThreads, 0, st>>>(p);
+    else if (filter_minb != 0) k_batch_filter<2><<<(unsigned)blocks, kBatchFilterThreads, 0, st>>>(p);
+    else k_batch<<<(unsigned)blocks, threads, batch_smem_bytes(threads, qcap), st>>>(p);
     return cudaGetLastError();
 }
 
@@ -159,6 +249,7 @@ struct fw_plan {
     int64_t *d_prefix = nullptr;  // n_jobs + 1 item offsets
     unsigned long long *d_next = nullptr;
     int32_t qcap = 256;
+    int filter_minb = 0;  // every job has a bucket filter: k_batch_filter<filter_minb> runs (else 0)
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -214,6 +305,10 @@ extern "C" int fw_plan_create(const fw_job *jobs, int64_t n_jobs, const fw_plan_
             return set_status(FW_EINVAL);
     }
     std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return jobs[a].rs->n_eff > jobs[b].rs->n_eff; });
+    // every job through a bucket filter: the filter-only kernel
+    bool filter_only = true;
+    for (int64_t j = 0; j < n_jobs; ++j)
+        if (jobs[j].n > 0 && jobs[j].rs->filter_words == 0) filter_only = false;
     std::vector<int64_t> prefix((size_t)n_jobs + 1, 0);
     for (int64_t k = 0; k < n_jobs; ++k) {
         const fw_job &J = jobs[order[k]];
@@ -233,9 +328,10 @@ extern "C" int fw_plan_create(const fw_job *jobs, int64_t n_jobs, const fw_plan_
     pl->n_items = prefix[(size_t)n_jobs];
     pl->n_jobs = n_jobs;
     pl->packets = packets;
-    const int per_sm = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : 2;
-    pl->blocks = std::max<int64_t>(
-        1, std::min<int64_t>((int64_t)sm_count(pl->device) * per_sm, (pl->n_items + threads / 32 - 1) / (threads / 32)));
+    const int per_sm = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : filter_only ? kBatchFilterMinBlocks : 2;
+    pl->filter_minb = filter_only ? (per_sm >= 3 ? 3 : 2) : 0;
+    const int wpb = (filter_only ? kBatchFilterThreads : threads) / 32;
+    pl->blocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count(pl->device) * per_sm, (pl->n_items + wpb - 1) / wpb));
     cudaError_t e = dev_malloc(&pl->d_jobs, std::max<size_t>(1, hj.size()) * sizeof(BatchJobDev));
     if (e == cudaSuccess) e = dev_malloc(&pl->d_prefix, prefix.size() * sizeof(int64_t));
     if (e == cudaSuccess) e = dev_malloc(&pl->d_next, sizeof(unsigned long long));
@@ -254,7 +350,7 @@ extern "C" int fw_plan_create(const fw_job *jobs, int64_t n_jobs, const fw_plan_
 
 static cudaError_t enqueue_plan(fw_plan *pl, cudaStream_t st) {
     return launch_batch(pl->d_jobs, pl->d_prefix, (int32_t)pl->n_jobs, pl->n_items, pl->d_next, pl->qcap, pl->threads,
-                        pl->blocks, st);
+                        pl->blocks, st, pl->filter_minb);
 }
 
 extern "C" int fw_plan_launch(fw_plan *pl, void *stream) {
@@ -289,3 +385,5 @@ extern "C" int fw_plan_launch_graph(fw_plan *pl, void *stream) {
 }
 
 extern "C" int64_t fw_plan_items(const fw_plan *pl) { return pl ? pl->n_items : -1; }
+
+extern "C" int fw_plan_kernel(const fw_plan *pl) { return pl ? pl->filter_minb : -1; }

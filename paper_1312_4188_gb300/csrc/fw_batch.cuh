@@ -56,16 +56,26 @@ struct BatchParams {
 // one pad for each of up to kMaxClasses classes.
 inline int32_t item_packets(int32_t qcap) { return qcap - kMaxClasses; }
 
+// 1 when a job's header arrays are aligned for the 16-byte vector loads of its scan.
+int32_t job_vector_loads(const fw_headers &h);
+
 // Fill a job entry from a rule set and device-accessible buffers (item size and first segment
 // of its work items included).
 void fill_batch_job(BatchJobDev &d, const fw_ruleset *rs, const fw_headers &h, int64_t n, int32_t *out_idx,
                     uint8_t *out_act, int32_t item_packets, int32_t seg0);
 
+// Block size and default resident blocks per SM of the filter-only batched kernel.
+constexpr int kBatchFilterThreads = 512;
+constexpr int kBatchFilterMinBlocks = 2;
+
 // Zero the item counter and launch the persistent kernel on `st` (nothing but
 // the counter reset when n_items is 0); d_prefix holds n_jobs + 1 item offsets. The kernel's shared-memory limit must
-// have been raised with prepare_batch_kernel for `qcap` and `threads`.
+// have been raised with prepare_batch_kernel for `qcap` and `threads`. filter_minb 2 or 3: every
+// job has a bucket filter and the filter-only kernel runs, built for that many resident blocks per
+// SM (kBatchFilterThreads threads a block; `threads` and `qcap` unused); 0: the general kernel.
 cudaError_t launch_batch(const BatchJobDev *d_jobs, const int64_t *d_prefix, int32_t n_jobs, int64_t n_items,
-                         unsigned long long *d_next, int32_t qcap, int threads, int64_t blocks, cudaStream_t st);
+                         unsigned long long *d_next, int32_t qcap, int threads, int64_t blocks, cudaStream_t st,
+                         int filter_minb);
 cudaError_t prepare_batch_kernel(size_t smem_bytes);
 size_t batch_smem_bytes(int threads, int32_t qcap);  // dynamic shared memory of k_batch
 

@@ -118,15 +118,14 @@ __device__ __forceinline__ uint32_t filter_first(const unsigned char *base, cons
     return 0xFFFFFFFFu;
 }
 
-// Any row width (v.words 32-bit words): the rows are ANDed one word at a time
-// from word 0, and the candidates of each word are tested before the next word
-// is read, so a packet reads its rows only up to its first match. The block is
-// read through the L1 cache (global memory).
-template <int KEY>
-__device__ __forceinline__ uint32_t filter_packet_wide(const unsigned char *__restrict__ base, const FilterView &v,
-                                                       uint32_t s, uint32_t d, uint32_t sp, uint32_t dp, uint32_t pr,
-                                                       uint32_t one) {
-    const uint32_t c = filter_class<KEY>(base, v, s, d, pr);
+// Candidates of a packet of class c from word 0 on, given word 0's AND (m0), for
+// any row width (v.words 32-bit words): each word's candidates are tested in
+// order before the next word is read, so a packet reads its rows only up to its
+// first match. Returns the verdict word of the first match, or ~0u. The block
+// is read through the L1 cache (global memory).
+__device__ __forceinline__ uint32_t filter_resolve(const unsigned char *__restrict__ base, const FilterView &v,
+                                                   uint32_t c, uint32_t s, uint32_t d, uint32_t sp, uint32_t dp,
+                                                   uint32_t m0, uint32_t one) {
     const int W = v.words;
     const uint32_t *T = reinterpret_cast<const uint32_t *>(base + v.tables) + (size_t)c * 768u * W;
     const uint32_t *r0 = T + (s >> 24) * W;
@@ -135,8 +134,9 @@ __device__ __forceinline__ uint32_t filter_packet_wide(const unsigned char *__re
     const uint32_t *ex = reinterpret_cast<const uint32_t *>(base + v.exact) + (size_t)c * W;
     const int first = (int)__ldg(reinterpret_cast<const uint32_t *>(base + v.classes) + 4 * c);
     const uint4 *V = reinterpret_cast<const uint4 *>(base + v.recs) + 2 * first;
+    uint32_t m = m0;
     for (int w = 0; w < W; ++w) {
-        uint32_t m = __ldg(r0 + w) & __ldg(r1 + w) & __ldg(r2 + w);
+        if (w > 0) m = __ldg(r0 + w) & __ldg(r1 + w) & __ldg(r2 + w);
         if (m == 0u) continue;
         const uint32_t e = __ldg(ex + w);
         while (m != 0u) {
@@ -148,6 +148,42 @@ __device__ __forceinline__ uint32_t filter_packet_wide(const unsigned char *__re
         }
     }
     return 0xFFFFFFFFu;
+}
+
+// Word 0 of the AND of a packet's three rows (class c), for any row width.
+__device__ __forceinline__ uint32_t filter_word0(const unsigned char *__restrict__ base, const FilterView &v, uint32_t c,
+                                                 uint32_t s, uint32_t d, uint32_t sp, uint32_t dp) {
+    const uint32_t W = (uint32_t)v.words;
+    const uint32_t *T = reinterpret_cast<const uint32_t *>(base + v.tables);
+    const uint32_t cb = c * 768u;
+    return __ldg(T + (cb + (s >> 24)) * W) & __ldg(T + (cb + 256u + (d >> 24)) * W) &
+           __ldg(T + (cb + 512u + (((sp >> 12) << 4) | (dp >> 12))) * W);
+}
+
+// One packet, any row width, block read through L1.
+template <int KEY>
+__device__ __forceinline__ uint32_t filter_packet_wide(const unsigned char *__restrict__ base, const FilterView &v,
+                                                       uint32_t s, uint32_t d, uint32_t sp, uint32_t dp, uint32_t pr,
+                                                       uint32_t one) {
+    const uint32_t c = filter_class<KEY>(base, v, s, d, pr);
+    return filter_resolve(base, v, c, s, d, sp, dp, filter_word0(base, v, c, s, d, sp, dp), one);
+}
+
+// P packets of one lane, any row width, block read through L1: the classes and the
+// first row words of all P packets are loaded before any candidate is tested, so
+// those loads are in flight together; then each packet's candidates are tested in
+// order. pr[] is overwritten with the classes; out[] gets the verdict words.
+template <int P>
+__device__ __forceinline__ void filter_packets_wide(const unsigned char *__restrict__ base, const FilterView &v,
+                                                    const uint32_t (&s)[P], const uint32_t (&d)[P],
+                                                    const uint32_t (&sp)[P], const uint32_t (&dp)[P], uint32_t (&pr)[P],
+                                                    uint32_t one, uint32_t (&out)[P]) {
+#pragma unroll
+    for (int k = 0; k < P; ++k) pr[k] = filter_class<-1>(base, v, s[k], d[k], pr[k]);
+#pragma unroll
+    for (int k = 0; k < P; ++k) out[k] = filter_word0(base, v, pr[k], s[k], d[k], sp[k], dp[k]);
+#pragma unroll
+    for (int k = 0; k < P; ++k) out[k] = filter_resolve(base, v, pr[k], s[k], d[k], sp[k], dp[k], out[k], one);
 }
 
 }  // namespace fwk

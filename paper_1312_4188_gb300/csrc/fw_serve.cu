@@ -16,15 +16,19 @@
 // are still running: several groups overlap on the device, and admission is
 // bounded by free slots and free memory rather than by whole batches.
 // Results are exactly fw_classify's for each request, alone or in a mix.
+//
+// Host cost per request is kept to a few tens of nanoseconds, below the
+// device time of a typical request: requests live in a ring indexed by ticket
+// (no allocation per request), the queue and every group are ranges of
+// consecutive tickets, and each rule set's part of a work-list entry is
+// built once, when the server starts.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
-#include <deque>
 #include <map>
 #include <mutex>
 #include <thread>
-#include <unordered_map>
 #include <vector>
 
 #include "fw_alloc.h"
@@ -36,6 +40,11 @@ static double now_us() {
     return std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+static int64_t now_ns() {
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
 static size_t a16(size_t x) { return (x + 15) / 16 * 16; }
 
 // Arena bytes of one copy-mode request: five header arrays and two verdict arrays.
@@ -44,20 +53,22 @@ static size_t request_bytes(int64_t n) {
     return a16(4 * m) * 2 + a16(2 * m) * 2 + a16(m) + a16(4 * m) + a16(m);
 }
 
-struct SvRequest {
-    uint64_t ticket = 0;
-    int set = 0;
-    fw_headers h{};         // caller's buffers
+// One request: an entry of the server's ring, at index ticket mod capacity (two cache lines).
+struct alignas(64) SvRequest {
+    uint64_t ticket = 0;    // 0: the entry is free (never used, or its ticket was released)
+    int32_t set = 0;
+    int32_t status = 1;     // 1 = not finished
     int64_t n = 0;
+    // the request's buffers: in zero-copy mode their device-accessible aliases, in copy mode the
+    // caller's host buffers
+    fw_headers h{};
     int32_t *out_idx = nullptr;
     uint8_t *out_act = nullptr;
-    fw_headers dh{};        // zero-copy: device-accessible aliases of the caller's buffers
-    int32_t *d_idx = nullptr;
-    uint8_t *d_act = nullptr;
-    size_t bytes = 0;       // copy mode arena bytes
     double t_submit = 0, t_done = 0;
-    int status = 1;         // 1 = not finished
 };
+static_assert(sizeof(SvRequest) == 128, "a ring entry is two cache lines");
+
+constexpr uint64_t kRingChunk = 1024;  // ring entries per allocation
 
 struct SvSlot {
     cudaStream_t st = nullptr;
@@ -67,7 +78,10 @@ struct SvSlot {
     BatchJobDev *h_jobs = nullptr;  // pinned staging of the work list
     bool busy = false;
     bool failed = false;  // the group's launch failed: it completes with FW_ECUDA
-    std::vector<SvRequest *> group;
+    uint64_t g_lo = 0, g_hi = 0;  // the group: tickets [g_lo, g_hi)
+    int beside = 0;               // groups in flight when this one was admitted
+    std::vector<uint32_t> order;  // the group's requests (offsets from g_lo) in job order
+    std::vector<uint32_t> count;  // per set rank: requests of the group (then their first job)
     size_t arena_off = 0, arena_len = 0;
 };
 
@@ -93,8 +107,18 @@ struct fw_server {
     std::map<size_t, size_t> free_blocks;  // offset -> length
     size_t arena_used = 0;
     std::vector<fwk::SvSlot> slots;
-    std::deque<fwk::SvRequest *> pending;
-    std::unordered_map<uint64_t, fwk::SvRequest *> live;
+    std::vector<fwk::BatchJobDev> tmpl;  // per rule set: its work-list entry without buffers
+    // rank of each rule set, costliest first (wider filter rows, then more reachable rules): a
+    // group's jobs are ordered by it, so that items of one rule set run together and share the
+    // L1-resident filter block
+    std::vector<int32_t> set_rank;
+    bool filter_only = false;            // every rule set has a bucket filter: k_batch_filter runs
+    // Requests by ticket: entry t lives at ring index t & ring_mask, in chunks of kRingChunk
+    // allocated when the server starts (addresses stay fixed). Tickets [admit_next, next_ticket) are
+    // queued; an entry is reused only after its ticket was released by fw_server_wait.
+    std::vector<fwk::SvRequest *> ring;
+    uint64_t ring_mask = 0;
+    uint64_t admit_next = 1;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::thread worker;
@@ -104,6 +128,20 @@ struct fw_server {
 };
 
 namespace fwk {
+
+// The ring entry of ticket t; its chunk must exist.
+static inline SvRequest &entry(fw_server *sv, uint64_t t) {
+    const uint64_t i = t & sv->ring_mask;
+    return sv->ring[i / kRingChunk][i % kRingChunk];
+}
+
+// The live request of a ticket, or nullptr (unknown or already released). Caller holds sv->mu.
+static SvRequest *live_find(fw_server *sv, uint64_t ticket) {
+    if (ticket == 0 || ticket >= sv->next_ticket) return nullptr;
+    const uint64_t i = ticket & sv->ring_mask;
+    SvRequest &e = sv->ring[i / kRingChunk][i % kRingChunk];
+    return e.ticket == ticket ? &e : nullptr;
+}
 
 static bool arena_alloc(fw_server *sv, size_t len, size_t *off) {
     for (auto it = sv->free_blocks.begin(); it != sv->free_blocks.end(); ++it) {
@@ -145,16 +183,25 @@ static cudaError_t launch_group(fw_server *sv, SvSlot &sl) {
     cudaError_t e = cudaSuccess;
     size_t off = sl.arena_off;
     int64_t n_items = 0;
+    const size_t nj = (size_t)(sl.g_hi - sl.g_lo);
+    // job order: by set rank (a counting sort, stable within a set)
+    const size_t ns = sv->set_rank.size();
+    sl.count.assign(ns + 1, 0);
+    for (size_t i = 0; i < nj; ++i) ++sl.count[(size_t)sv->set_rank[(size_t)entry(sv, sl.g_lo + i).set] + 1];
+    for (size_t k = 1; k <= ns; ++k) sl.count[k] += sl.count[k - 1];
+    sl.order.resize(nj);
+    for (size_t i = 0; i < nj; ++i)
+        sl.order[sl.count[(size_t)sv->set_rank[(size_t)entry(sv, sl.g_lo + i).set]]++] = (uint32_t)i;
     // the item prefix follows the group's jobs in the same staging buffer
-    const size_t po = a16(sl.group.size() * sizeof(BatchJobDev));
+    const size_t po = a16(nj * sizeof(BatchJobDev));
     int64_t *h_prefix = reinterpret_cast<int64_t *>(reinterpret_cast<uint8_t *>(sl.h_jobs) + po);
-    for (size_t i = 0; i < sl.group.size() && e == cudaSuccess; ++i) {
-        SvRequest *r = sl.group[i];
-        fw_headers dh = r->dh;
-        int32_t *di = r->d_idx;
-        uint8_t *da = r->d_act;
+    for (size_t i = 0; i < nj && e == cudaSuccess; ++i) {
+        const SvRequest &r = entry(sv, sl.g_lo + sl.order[i]);
+        fw_headers dh = r.h;
+        int32_t *di = r.out_idx;
+        uint8_t *da = r.out_act;
         if (copy) {
-            const size_t m = (size_t)r->n;
+            const size_t m = (size_t)r.n;
             uint8_t *base = sv->d_arena + off;
             size_t o = 0;
             uint32_t *s = reinterpret_cast<uint32_t *>(base + o); o += a16(4 * m);
@@ -165,35 +212,47 @@ static cudaError_t launch_group(fw_server *sv, SvSlot &sl) {
             di = reinterpret_cast<int32_t *>(base + o); o += a16(4 * m);
             da = base + o; o += a16(m);
             off += o;
-            e = cudaMemcpyAsync(s, r->h.src, 4 * m, cudaMemcpyHostToDevice, sl.st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(d, r->h.dst, 4 * m, cudaMemcpyHostToDevice, sl.st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(sp, r->h.sport, 2 * m, cudaMemcpyHostToDevice, sl.st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(dp, r->h.dport, 2 * m, cudaMemcpyHostToDevice, sl.st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(pr, r->h.proto, m, cudaMemcpyHostToDevice, sl.st);
+            e = cudaMemcpyAsync(s, r.h.src, 4 * m, cudaMemcpyHostToDevice, sl.st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(d, r.h.dst, 4 * m, cudaMemcpyHostToDevice, sl.st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(sp, r.h.sport, 2 * m, cudaMemcpyHostToDevice, sl.st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dp, r.h.dport, 2 * m, cudaMemcpyHostToDevice, sl.st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(pr, r.h.proto, m, cudaMemcpyHostToDevice, sl.st);
             dh = fw_headers{s, d, sp, dp, pr};
         }
-        fill_batch_job(sl.h_jobs[i], sv->sets[r->set], dh, r->n, di, da, B, sv->cfg.segment_rules);
+        // the rule set's part comes from its template; only the buffers are per request
+        BatchJobDev &J = sl.h_jobs[i];
+        J = sv->tmpl[(size_t)r.set];
+        J.vec = job_vector_loads(dh);
+        J.h = HdrPtrs{dh.src, dh.dst, dh.sport, dh.dport, dh.proto};
+        J.n = r.n;
+        J.out_idx = di;
+        J.out_act = da;
         h_prefix[i] = n_items;
-        n_items += (r->n + B - 1) / B;
+        n_items += (r.n + B - 1) / B;
     }
-    h_prefix[sl.group.size()] = n_items;
-    const size_t nj = sl.group.size();
+    h_prefix[nj] = n_items;
     // jobs and item prefix in one copy
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(sl.d_jobs, sl.h_jobs, po + (nj + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, sl.st);
     const int64_t *d_prefix = reinterpret_cast<const int64_t *>(reinterpret_cast<const uint8_t *>(sl.d_jobs) + po);
     if (e == cudaSuccess) {
-        const int wpb = sv->threads / 32;
-        const int64_t blocks =
-            std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count(sv->device) * 2, (n_items + wpb - 1) / wpb));
-        e = launch_batch(sl.d_jobs, d_prefix, (int32_t)nj, n_items, sl.d_next, sv->qcap, sv->threads, blocks, sl.st);
+        const int wpb = (sv->filter_only ? kBatchFilterThreads : sv->threads) / 32;
+        const int per_sm = sv->filter_only ? kBatchFilterMinBlocks : 2;
+        // alone on the device a group takes every SM it can use (one item a warp: the lowest
+        // latency); beside other groups a small one gets fewer blocks (each warp several items),
+        // leaving SMs to them
+        const int64_t per_block = (int64_t)wpb * (sl.beside > 0 ? sv->cfg.items_per_warp : 1);
+        const int64_t blocks = std::max<int64_t>(
+            1, std::min<int64_t>((int64_t)sm_count(sv->device) * per_sm, (n_items + per_block - 1) / per_block));
+        e = launch_batch(sl.d_jobs, d_prefix, (int32_t)nj, n_items, sl.d_next, sv->qcap, sv->threads, blocks, sl.st,
+                         sv->filter_only ? kBatchFilterMinBlocks : 0);
     }
     if (copy) {
         for (size_t i = 0; i < nj && e == cudaSuccess; ++i) {
-            SvRequest *r = sl.group[i];
+            const SvRequest &r = entry(sv, sl.g_lo + sl.order[i]);
             const BatchJobDev &J = sl.h_jobs[i];
-            e = cudaMemcpyAsync(r->out_idx, J.out_idx, 4 * (size_t)r->n, cudaMemcpyDeviceToHost, sl.st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(r->out_act, J.out_act, (size_t)r->n, cudaMemcpyDeviceToHost, sl.st);
+            e = cudaMemcpyAsync(r.out_idx, J.out_idx, 4 * (size_t)r.n, cudaMemcpyDeviceToHost, sl.st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(r.out_act, J.out_act, (size_t)r.n, cudaMemcpyDeviceToHost, sl.st);
         }
     }
     if (e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.st);
@@ -210,7 +269,11 @@ static void worker_loop(fw_server *sv) {
     std::vector<int> busy_idx, done_idx, launch_idx;
     std::vector<cudaError_t> qres(ns);
     std::unique_lock<std::mutex> lk(sv->mu);
+    int64_t launch_ns = 0;  // time of the last launches, added under the lock
     for (;;) {
+        const int64_t tc0 = now_ns();
+        sv->stats.launch_ns += launch_ns;
+        launch_ns = 0;
         busy_idx.clear();
         for (int i = 0; i < ns; ++i)
             if (sv->slots[i].busy) busy_idx.push_back(i);
@@ -229,61 +292,69 @@ static void worker_loop(fw_server *sv) {
             if (q != cudaSuccess) cudaGetLastError();
             const double t = now_us();
             const bool ok = q == cudaSuccess && !sl.failed;
-            for (SvRequest *r : sl.group) {
-                r->t_done = t;
-                r->status = ok ? FW_OK : FW_ECUDA;
-                if (ok) {
-                    sv->stats.completed += 1;
-                    sv->stats.packets += r->n;
-                } else {
-                    sv->stats.failed += 1;
-                }
+            int64_t pk = 0;
+            for (uint64_t k = sl.g_lo; k < sl.g_hi; ++k) {
+                SvRequest &r = entry(sv, k);
+                r.t_done = t;
+                r.status = ok ? FW_OK : FW_ECUDA;
+                pk += r.n;
+            }
+            const int64_t cnt = (int64_t)(sl.g_hi - sl.g_lo);
+            if (ok) {
+                sv->stats.completed += cnt;
+                sv->stats.packets += pk;
+            } else {
+                sv->stats.failed += cnt;
             }
             arena_free(sv, sl.arena_off, sl.arena_len);
             sl.arena_len = 0;
-            sl.group.clear();
+            sl.g_lo = sl.g_hi = 0;
             sl.busy = false;
             sl.failed = false;
             sv->cv_done.notify_all();
         }
+        const int64_t ta0 = now_ns();
+        sv->stats.complete_ns += ta0 - tc0;
         // 2. admission, locked: every free slot takes the queued requests that fit
         launch_idx.clear();
-        for (int i = 0; i < ns && !sv->pending.empty(); ++i) {
+        for (int i = 0; i < ns && sv->admit_next < sv->next_ticket; ++i) {
             SvSlot &sl = sv->slots[i];
             if (sl.busy) continue;
-            size_t take = 0, bytes = 0;
+            const uint64_t queued = sv->next_ticket - sv->admit_next;
+            uint64_t take = 0;
+            size_t bytes = 0;
             int64_t pk = 0;
-            while (take < sv->pending.size() && (int64_t)take < sv->cfg.max_group_requests) {
-                const SvRequest *r = sv->pending[take];
-                if (take > 0 && pk + r->n > sv->cfg.max_group_packets) break;
-                pk += r->n;
-                bytes += r->bytes;
+            while (take < queued && (int64_t)take < sv->cfg.max_group_requests) {
+                const SvRequest &r = entry(sv, sv->admit_next + take);
+                if (take > 0 && pk + r.n > sv->cfg.max_group_packets) break;
+                pk += r.n;
+                bytes += copy ? request_bytes(r.n) : 0;
                 ++take;
             }
             size_t off = 0;
             if (copy) {
                 while (take > 0 && !arena_alloc(sv, bytes, &off)) {
                     --take;  // not enough free memory: admit fewer
-                    bytes -= sv->pending[take]->bytes;
+                    bytes -= request_bytes(entry(sv, sv->admit_next + take).n);
                 }
                 if (take == 0) break;  // wait for memory to free up
             }
-            for (size_t k = 0; k < take; ++k) {
-                sl.group.push_back(sv->pending.front());
-                sv->pending.pop_front();
-            }
+            sl.g_lo = sv->admit_next;
+            sl.g_hi = sv->admit_next + take;
+            sl.beside = busy;
+            sv->admit_next += take;
             sl.arena_off = off;
             sl.arena_len = copy ? bytes : 0;
             sl.busy = true;
             ++busy;
             sv->stats.groups += 1;
-            sv->stats.max_group_requests = std::max<int64_t>(sv->stats.max_group_requests, (int64_t)sl.group.size());
+            sv->stats.max_group_requests = std::max<int64_t>(sv->stats.max_group_requests, (int64_t)take);
             launch_idx.push_back(i);
         }
         int inflight = 0;
         for (const SvSlot &sl : sv->slots) inflight += sl.busy ? 1 : 0;
         sv->stats.max_inflight_groups = std::max<int64_t>(sv->stats.max_inflight_groups, inflight);
-        sv->stats.pending = (int64_t)sv->pending.size();
+        sv->stats.pending = (int64_t)(sv->next_ticket - sv->admit_next);
         // 3. launches, unlocked
         if (!launch_idx.empty()) {
             lk.unlock();
@@ -295,11 +366,14 @@ static void worker_loop(fw_server *sv) {
                     cudaEventRecord(sl.ev, sl.st);  // the group completes, with an error status
                 }
             }
+            launch_ns = now_ns() - ta0;
             lk.lock();
             continue;
         }
-        if (sv->stop && sv->pending.empty() && busy == 0) break;
-        if (busy == 0 && sv->pending.empty()) {
+        sv->stats.launch_ns += now_ns() - ta0;
+        const bool queued = sv->admit_next < sv->next_ticket;
+        if (sv->stop && !queued && busy == 0) break;
+        if (busy == 0 && !queued) {
             sv->cv_work.wait(lk);
         } else {
             lk.unlock();
@@ -367,7 +441,7 @@ extern "C" void fw_server_destroy(fw_server *sv) {
         cudaFreeHost(sl.h_jobs);
     }
     cudaFree(sv->d_arena);
-    for (auto &kv : sv->live) delete kv.second;
+    for (SvRequest *c : sv->ring) delete[] c;
     delete sv;
 }
 
@@ -391,10 +465,14 @@ extern "C" int fw_server_create(const fw_ruleset *const *sets, int n_sets, const
     if (c.packets_per_item == 0) c.packets_per_item = 256;
     if (c.segment_rules == 0) c.segment_rules = 64;
     if (c.block_threads == 0) c.block_threads = 512;
+    if (c.items_per_warp == 0) c.items_per_warp = 1;
     if (c.slots < 1 || c.slots > 16 || c.max_group_requests < 1 || c.max_pending < 1 || c.max_group_packets < 1 ||
         c.arena_bytes < 4096 || c.packets_per_item % 128 != 0 || c.packets_per_item > 4096 ||
-        c.segment_rules % 4 != 0 || c.segment_rules < 4 || c.block_threads % 32 != 0 || c.block_threads > 1024)
+        c.segment_rules % 4 != 0 || c.segment_rules < 4 || c.block_threads % 32 != 0 || c.block_threads > 1024 ||
+        c.items_per_warp < 1)
         return set_status(FW_EINVAL);
+    for (int32_t r : c.reserved)
+        if (r != 0) return set_status(FW_EINVAL);
     const size_t smem = batch_smem_bytes(c.block_threads, c.packets_per_item);
     if (smem > 227 * 1024) return set_status(FW_EINVAL);
     fw_server *sv = new (std::nothrow) fw_server();
@@ -404,7 +482,35 @@ extern "C" int fw_server_create(const fw_ruleset *const *sets, int n_sets, const
     cudaGetDevice(&sv->device);
     sv->threads = c.block_threads;
     sv->qcap = c.packets_per_item;
-    cudaError_t e = prepare_batch_kernel(smem);
+    // ring capacity: every queued request plus every request of the groups in flight
+    uint64_t cap = kRingChunk;
+    while (cap < (uint64_t)c.max_pending + (uint64_t)c.slots * (uint64_t)c.max_group_requests) cap *= 2;
+    sv->ring.assign(cap / kRingChunk, nullptr);
+    sv->ring_mask = cap - 1;
+    bool ring_ok = true;
+    for (SvRequest *&c : sv->ring) {  // allocated (and touched) now, not while requests arrive
+        c = new (std::nothrow) SvRequest[kRingChunk];
+        if (c == nullptr) ring_ok = false;
+    }
+    sv->tmpl.resize((size_t)n_sets);
+    sv->filter_only = true;
+    for (int i = 0; i < n_sets; ++i)
+        if (sets[i]->filter_words == 0) sv->filter_only = false;
+    {
+        std::vector<int32_t> by_cost((size_t)n_sets);
+        for (int i = 0; i < n_sets; ++i) by_cost[(size_t)i] = i;
+        // a set without a filter scans its sub-lists: costlier than any filtered one
+        auto width = [&](int i) { return sets[i]->filter_words > 0 ? sets[i]->filter_words : INT32_MAX; };
+        std::stable_sort(by_cost.begin(), by_cost.end(), [&](int32_t a, int32_t b) {
+            return width(a) != width(b) ? width(a) > width(b) : sets[a]->n_eff > sets[b]->n_eff;
+        });
+        sv->set_rank.resize((size_t)n_sets);
+        for (int k = 0; k < n_sets; ++k) sv->set_rank[(size_t)by_cost[(size_t)k]] = k;
+    }
+    for (int i = 0; i < n_sets; ++i)
+        fill_batch_job(sv->tmpl[(size_t)i], sets[i], fw_headers{}, 0, nullptr, nullptr, item_packets(c.packets_per_item),
+                       c.segment_rules);
+    cudaError_t e = ring_ok ? prepare_batch_kernel(smem) : cudaErrorMemoryAllocation;
     if (e == cudaSuccess && c.mode == FW_HOST_COPY) {
         sv->arena_bytes = (size_t)c.arena_bytes;
         e = dev_malloc(&sv->d_arena, sv->arena_bytes);
@@ -432,15 +538,14 @@ extern "C" int fw_server_create(const fw_ruleset *const *sets, int n_sets, const
 namespace fwk {
 
 // A request checked and, in zero-copy mode, its buffers resolved to device-accessible aliases
-// (one pass over the registered ranges under one lock), without touching the queue.
+// (one pass over the registered ranges under one lock), written to *r without touching the queue.
+// hint[7]: per buffer, the registered range to try first (updated).
 static int prepare_request(fw_server *sv, int set, const fw_headers *h, int64_t n, int32_t *out_idx,
-                           uint8_t *out_act, SvRequest **out) {
+                           uint8_t *out_act, SvRequest *r, size_t *hint) {
     if (h == nullptr || n < 1 || n > INT32_MAX) return FW_EINVAL;
     if (set < 0 || set >= (int)sv->sets.size()) return FW_EINVAL;
     if (!h->src || !h->dst || !h->sport || !h->dport || !h->proto || !out_idx || !out_act) return FW_EINVAL;
     if (n > sv->cfg.max_group_packets) return FW_ERANGE;
-    SvRequest *r = new (std::nothrow) SvRequest();
-    if (r == nullptr) return FW_ENOMEM;
     r->set = set;
     r->h = *h;
     r->n = n;
@@ -454,56 +559,71 @@ static int prepare_request(fw_server *sv, int set, const fw_headers *h, int64_t 
         int found = 0;
         {
             std::lock_guard<std::mutex> lk(sv->reg_mu);
+            const size_t nr = sv->ranges.size();
             for (int k = 0; k < 7; ++k) {
                 const uintptr_t a = reinterpret_cast<uintptr_t>(p[k]);
-                for (const SvRange &rg : sv->ranges)
+                // start at the range that held this buffer last time (a request's buffers usually
+                // lie where the previous request's did)
+                const size_t h0 = hint[k] < nr ? hint[k] : 0;
+                for (size_t j = 0; j < nr; ++j) {
+                    const size_t i = h0 + j < nr ? h0 + j : h0 + j - nr;
+                    const SvRange &rg = sv->ranges[i];
                     if (a >= rg.lo && a + len[k] <= rg.hi) {
                         d[k] = reinterpret_cast<const void *>(a + rg.delta);
+                        hint[k] = i;
                         ++found;
                         break;
                     }
+                }
             }
         }
         if (found < 7)
             for (int k = 0; k < 7; ++k)
                 if (d[k] == nullptr) d[k] = device_alias(p[k]);  // not registered: looked up now
-        r->dh = fw_headers{static_cast<const uint32_t *>(d[0]), static_cast<const uint32_t *>(d[1]),
-                           static_cast<const uint16_t *>(d[2]), static_cast<const uint16_t *>(d[3]),
-                           static_cast<const uint8_t *>(d[4])};
-        r->d_idx = static_cast<int32_t *>(const_cast<void *>(d[5]));
-        r->d_act = static_cast<uint8_t *>(const_cast<void *>(d[6]));
         for (int k = 0; k < 7; ++k)
-            if (d[k] == nullptr) {
-                delete r;
-                return FW_EINVAL;
-            }
-    } else {
-        r->bytes = request_bytes(n);
-        if (r->bytes > sv->arena_bytes) {
-            delete r;
-            return FW_ERANGE;
-        }
+            if (d[k] == nullptr) return FW_EINVAL;
+        r->h = fw_headers{static_cast<const uint32_t *>(d[0]), static_cast<const uint32_t *>(d[1]),
+                          static_cast<const uint16_t *>(d[2]), static_cast<const uint16_t *>(d[3]),
+                          static_cast<const uint8_t *>(d[4])};
+        r->out_idx = static_cast<int32_t *>(const_cast<void *>(d[5]));
+        r->out_act = static_cast<uint8_t *>(const_cast<void *>(d[6]));
+    } else if (request_bytes(n) > sv->arena_bytes) {
+        return FW_ERANGE;
     }
-    *out = r;
     return FW_OK;
 }
 
-// Queue prepared requests, in order, under one lock; returns how many were queued (the rest do
-// not fit under max_pending and stay with the caller).
-static int64_t enqueue_requests(fw_server *sv, SvRequest *const *rs, int64_t count, uint64_t *tickets) {
+// Queue prepared requests, in order, under one lock. Returns how many were queued; when that is
+// fewer than `count`, *why is FW_EBUSY (max_pending requests queued, or the next ticket's ring
+// entry is still held by an unreleased ticket).
+static int64_t enqueue_requests(fw_server *sv, const SvRequest *rs, int64_t count, uint64_t *tickets,
+                                int64_t t_start_ns, int *why) {
     int64_t k = 0;
+    *why = FW_OK;
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         const double t = now_us();
-        for (; k < count && (int64_t)sv->pending.size() < sv->cfg.max_pending; ++k) {
-            SvRequest *r = rs[k];
-            r->ticket = sv->next_ticket++;
-            r->t_submit = t;
-            sv->pending.push_back(r);
-            sv->live[r->ticket] = r;
+        for (; k < count; ++k) {
+            if ((int64_t)(sv->next_ticket - sv->admit_next) >= sv->cfg.max_pending) {
+                *why = FW_EBUSY;
+                break;
+            }
+            const uint64_t tk = sv->next_ticket;
+            SvRequest &e = entry(sv, tk);
+            if (e.ticket != 0) {
+                *why = FW_EBUSY;
+                break;
+            }
+            e = rs[k];
+            e.ticket = tk;
+            e.status = 1;
+            e.t_submit = t;
+            e.t_done = 0;
+            sv->next_ticket = tk + 1;
             sv->stats.submitted += 1;
-            tickets[k] = r->ticket;
+            tickets[k] = tk;
         }
+        sv->stats.submit_ns += now_ns() - t_start_ns;
     }
     if (k > 0) sv->cv_work.notify_one();
     return k;
@@ -514,22 +634,21 @@ static int64_t enqueue_requests(fw_server *sv, SvRequest *const *rs, int64_t cou
 extern "C" int fw_server_submit(fw_server *sv, int set, const fw_headers *h, int64_t n, int32_t *out_idx,
                                 uint8_t *out_act, uint64_t *ticket) {
     if (sv == nullptr || ticket == nullptr) return set_status(FW_EINVAL);
-    SvRequest *r = nullptr;
-    const int s = prepare_request(sv, set, h, n, out_idx, out_act, &r);
+    SvRequest r;
+    size_t hint[7] = {};
+    const int64_t t0 = now_ns();
+    const int s = prepare_request(sv, set, h, n, out_idx, out_act, &r, hint);
     if (s != FW_OK) return set_status(s);
-    if (enqueue_requests(sv, &r, 1, ticket) == 0) {
-        delete r;
-        return set_status(FW_EBUSY);
-    }
+    int why = FW_OK;
+    if (enqueue_requests(sv, &r, 1, ticket, t0, &why) == 0) return set_status(why);
     return FW_OK;
 }
 
 extern "C" int fw_server_wait(fw_server *sv, uint64_t ticket, int64_t timeout_us, double *latency_us) {
     if (sv == nullptr) return set_status(FW_EINVAL);
     std::unique_lock<std::mutex> lk(sv->mu);
-    auto it = sv->live.find(ticket);
-    if (it == sv->live.end()) return set_status(FW_EINVAL);
-    SvRequest *r = it->second;
+    SvRequest *r = live_find(sv, ticket);
+    if (r == nullptr) return set_status(FW_EINVAL);
     const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(timeout_us < 0 ? 0 : timeout_us);
     while (r->status == 1) {
         if (timeout_us < 0) {
@@ -540,8 +659,7 @@ extern "C" int fw_server_wait(fw_server *sv, uint64_t ticket, int64_t timeout_us
     }
     if (latency_us) *latency_us = r->t_done - r->t_submit;
     const int s = r->status;
-    sv->live.erase(it);
-    delete r;
+    r->ticket = 0;  // released: the ring entry can take a new request
     return set_status(s);
 }
 
@@ -550,7 +668,7 @@ extern "C" int fw_server_drain(fw_server *sv, int64_t timeout_us) {
     std::unique_lock<std::mutex> lk(sv->mu);
     const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(timeout_us < 0 ? 0 : timeout_us);
     auto idle = [&] {
-        if (!sv->pending.empty()) return false;
+        if (sv->admit_next < sv->next_ticket) return false;
         for (const SvSlot &sl : sv->slots)
             if (sl.busy) return false;
         return true;
@@ -567,70 +685,68 @@ extern "C" int fw_server_get_stats(fw_server *sv, fw_server_stats *st) {
     if (sv == nullptr || st == nullptr) return set_status(FW_EINVAL);
     std::lock_guard<std::mutex> lk(sv->mu);
     *st = sv->stats;
-    st->pending = (int64_t)sv->pending.size();
+    st->pending = (int64_t)(sv->next_ticket - sv->admit_next);
     return FW_OK;
 }
 
 extern "C" int fw_server_replay(fw_server *sv, fw_request *reqs, int64_t n, int64_t timeout_us) {
     if (sv == nullptr || n < 0 || (n > 0 && reqs == nullptr)) return set_status(FW_EINVAL);
     std::vector<uint64_t> tickets((size_t)n, 0);
-    std::vector<SvRequest *> batch;
+    // requests already due are prepared together (up to kBatch) and queued under one lock
+    constexpr int64_t kBatch = 128;
+    std::vector<SvRequest> batch((size_t)kBatch);
+    std::vector<int64_t> batch_req((size_t)kBatch);
+    std::vector<uint64_t> batch_tickets((size_t)kBatch);
+    size_t hint[7] = {};
     const double t0 = now_us();
     // Open loop: every request is submitted at its arrival time; when the submitting thread is
-    // behind, all requests already due are prepared and queued together (one queue lock).
+    // behind, the requests already due go together.
     int64_t i = 0;
     while (i < n) {
         const double now = now_us();
         if (now < t0 + reqs[i].arrival_us) continue;
-        int64_t j = i;
-        batch.clear();
-        while (j < n && (j == i || now >= t0 + reqs[j].arrival_us) && j - i < 1024) {
+        int64_t j = i, nb = 0;
+        int64_t t_mark = now_ns();
+        while (j < n && (j == i || now >= t0 + reqs[j].arrival_us) && nb < kBatch) {
             fw_request &q = reqs[j];
-            SvRequest *r = nullptr;
-            const int s = prepare_request(sv, q.set, &q.hdrs, q.n, q.out_rule_idx, q.out_action, &r);
+            const int s = prepare_request(sv, q.set, &q.hdrs, q.n, q.out_rule_idx, q.out_action, &batch[(size_t)nb],
+                                          hint);
             if (s != FW_OK) {
-                q.status = s;
-                tickets[j] = 0;
-                r = nullptr;
+                q.status = s;  // refused: keeps its status and gets no ticket
+            } else {
+                batch_req[(size_t)nb++] = j;
             }
-            batch.push_back(r);
             ++j;
         }
-        // queue the prepared ones in order (a refused request keeps its status and no ticket)
-        int64_t k = 0;
-        while (k < (int64_t)batch.size()) {
-            if (batch[k] == nullptr) {
-                ++k;
-                continue;
-            }
-            int64_t e = k;
-            while (e < (int64_t)batch.size() && batch[e] != nullptr) ++e;
-            int64_t done = 0;
-            while (done < e - k) {
-                const int64_t got = enqueue_requests(sv, batch.data() + k + done, e - k - done, &tickets[i + k + done]);
-                done += got;
-                if (got == 0) std::this_thread::yield();  // the queue is full: wait for room
-            }
-            k = e;
+        int64_t done = 0;
+        while (done < nb) {
+            int why = FW_OK;
+            const int64_t got =
+                enqueue_requests(sv, batch.data() + done, nb - done, batch_tickets.data() + done, t_mark, &why);
+            for (int64_t k = done; k < done + got; ++k) tickets[(size_t)batch_req[(size_t)k]] = batch_tickets[(size_t)k];
+            done += got;
+            t_mark = now_ns();
+            if (got == 0) std::this_thread::yield();  // the queue is full: wait for room
         }
         i = j;
     }
     int worst = FW_OK;
     for (int64_t i2 = 0; i2 < n; ++i2) {
         fw_request &q = reqs[i2];
-        if (tickets[i2] == 0) {
+        if (tickets[(size_t)i2] == 0) {
             worst = q.status;
             continue;
         }
         std::unique_lock<std::mutex> lk(sv->mu);
-        SvRequest *r = sv->live[tickets[i2]];
-        lk.unlock();
+        const SvRequest *r = live_find(sv, tickets[(size_t)i2]);
         const double t_submit = r->t_submit;
+        lk.unlock();
         double lat = 0;
-        const int s = fw_server_wait(sv, tickets[i2], timeout_us, &lat);
+        const int s = fw_server_wait(sv, tickets[(size_t)i2], timeout_us, &lat);
         q.status = s;
         // open-loop latency: from the scheduled arrival, not from the submit call
         q.latency_us = (t_submit + lat) - (t0 + q.arrival_us);
+        q.submit_lag_us = t_submit - (t0 + q.arrival_us);
         if (s != FW_OK) worst = s;
     }
     return worst == FW_OK ? FW_OK : set_status(worst);

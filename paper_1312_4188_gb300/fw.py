@@ -105,19 +105,20 @@ class fw_server_config(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("slots", ctypes.c_int32), ("max_group_requests", ctypes.c_int32),
                 ("max_pending", ctypes.c_int32), ("max_group_packets", ctypes.c_int64),
                 ("arena_bytes", ctypes.c_int64), ("packets_per_item", ctypes.c_int32),
-                ("segment_rules", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("segment_rules", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+                ("items_per_warp", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class fw_server_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "completed", "failed", "packets", "groups",
                                                "max_group_requests", "max_inflight_groups", "arena_high_water",
-                                               "pending")]
+                                               "pending", "submit_ns", "launch_ns", "complete_ns")]
 
 
 class fw_request(ctypes.Structure):
     _fields_ = [("set", ctypes.c_int32), ("status", ctypes.c_int32), ("hdrs", fw_headers), ("n", ctypes.c_int64),
                 ("out_rule_idx", ctypes.c_void_p), ("out_action", ctypes.c_void_p), ("arrival_us", ctypes.c_double),
-                ("latency_us", ctypes.c_double)]
+                ("latency_us", ctypes.c_double), ("submit_lag_us", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -156,6 +157,7 @@ SIGNATURES = {
     "fw_plan_launch": (ctypes.c_int, [P, P]),
     "fw_plan_launch_graph": (ctypes.c_int, [P, P]),
     "fw_plan_items": (I64, [P]),
+    "fw_plan_kernel": (ctypes.c_int, [P]),
     "fw_plan_destroy": (None, [P]),
     "fw_server_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(fw_server_config),
                                         ctypes.POINTER(P)]),
@@ -464,6 +466,10 @@ class Plan:
     def items(self) -> int:
         return int(lib().fw_plan_items(self.handle))
 
+    def kernel(self) -> int:
+        """0: the general batched kernel; 2 or 3: the filter-only kernel (its resident blocks per SM)."""
+        return int(lib().fw_plan_kernel(self.handle))
+
     def launch(self, stream=None, graph: bool = True):
         fn = lib().fw_plan_launch_graph if graph else lib().fw_plan_launch
         _check(fn(self.handle, _stream_handle(stream)), "fw_plan_launch")
@@ -545,6 +551,8 @@ class Server:
         s = lib().fw_server_replay(self.handle, arr, len(specs), int(timeout_us))
         status = np.array([r.status for r in arr], dtype=np.int32)
         lat = np.array([r.latency_us for r in arr], dtype=np.float64)
+        # time each request waited for the submitting thread (part of its latency)
+        self.last_submit_lag_us = np.array([r.submit_lag_us for r in arr], dtype=np.float64)
         return int(s), status, lat
 
     def destroy(self):

@@ -25,11 +25,21 @@ def no_catch_all(rules):
     return rules[~((rules["src_prefix"] == 0) & (rules["dst_prefix"] == 0))]
 
 
+def many_protocols(rules):
+    # exact protocols beyond TCP, UDP and ICMP share the "other" class: no bucket filter
+    rules = rules.copy()
+    rules["proto_any"] = 0
+    rules["proto"] = np.arange(len(rules)) % 12
+    return rules
+
+
 def make_jobs(torch, specs, misalign=()):
     jobs, host = [], []
     for i, (nr, npk, drop) in enumerate(specs):
         rules = W.gen_rules(nr, 500 + i)
-        if drop:
+        if drop == "protos":
+            rules = many_protocols(rules)
+        elif drop:
             rules = no_catch_all(rules)
         hdr = W.gen_packets(rules, npk, 600 + i)
         rs = fw.fw_ruleset_create(rules)
@@ -45,8 +55,12 @@ def make_jobs(torch, specs, misalign=()):
     return jobs, host
 
 
-SPECS = [(0, 10, False), (1, 1, False), (33, 5, True), (300, 1000, True), (5000, 50_000, True), (2000, 0, False),
-         (64, 4099, False), (700, 30_000, False), (12_000, 20_000, True), (3, 129, True)]
+# every rule set here has a bucket filter ...
+FILTER_SPECS = [(0, 10, False), (1, 1, False), (33, 5, True), (300, 1000, True), (5000, 50_000, True),
+                (2000, 0, False), (64, 4099, False), (700, 30_000, False), (12_000, 20_000, True), (3, 129, True),
+                (40, 2, False), (200, 3, True)]
+# ... and two here have none (their items take the general kernel's scan path)
+SPECS = FILTER_SPECS[:10] + [(300, 5000, "protos"), (60, 1001, "protos")]
 
 
 @pytest.mark.parametrize("cfg,threads", [(None, 0), ([(256, 128, 8), (4096, 256, 16), (0, 384, 32)], 0),
@@ -55,10 +69,38 @@ SPECS = [(0, 10, False), (1, 1, False), (33, 5, True), (300, 1000, True), (5000,
 @pytest.mark.parametrize("graph", [False, True], ids=["direct", "graph"])
 def test_plan_matches_scan_and_oracle(torch_cuda, cfg, threads, graph):
     torch = torch_cuda
-    jobs, host = make_jobs(torch, SPECS, misalign=(3, 7))
+    jobs, host = make_jobs(torch, SPECS, misalign=(3, 7, 11))
+    assert [j[0].filter()["words"] == 0 for j in jobs].count(True) == 2
     plan = fw.fw_plan_create(jobs, fw.make_plan_config(cfg, block_threads=threads) if cfg else None)
+    assert plan.kernel() == 0  # the general kernel: two jobs have no filter
     plan.launch(graph=graph)
     plan.launch(graph=graph)  # a relaunch rewrites the same outputs
+    torch.cuda.synchronize()
+    for (rs, dh, oi, oa), (rules, hdr) in zip(jobs, host):
+        n = len(hdr["src"])
+        if n == 0:
+            continue
+        si, sa = fw.fw_classify(rs, dh, n)
+        torch.cuda.synchronize()
+        assert torch.equal(oi, si) and torch.equal(oa, sa)
+        want = oracle.classify(rules, hdr, threads=THREADS)
+        assert np.array_equal(oi.cpu().numpy(), want[0]) and np.array_equal(oa.cpu().numpy(), want[1])
+    plan.destroy()
+    for j in jobs:
+        j[0].destroy()
+
+
+@pytest.mark.parametrize("per_sm", [0, 3], ids=["two_blocks", "three_blocks"])
+@pytest.mark.parametrize("graph", [False, True], ids=["direct", "graph"])
+def test_filter_only_plan(torch_cuda, per_sm, graph):
+    """Every job has a bucket filter: the filter-only kernel (four packets a lane; ragged and
+    misaligned jobs take its scalar loads and stores) must equal fw_classify and the oracle."""
+    torch = torch_cuda
+    jobs, host = make_jobs(torch, FILTER_SPECS, misalign=(2, 7, 10))
+    assert all(j[0].filter()["words"] > 0 for j in jobs)
+    plan = fw.fw_plan_create(jobs, fw.make_plan_config(None, blocks_per_sm=per_sm))
+    assert plan.kernel() == (3 if per_sm == 3 else 2)
+    plan.launch(graph=graph)
     torch.cuda.synchronize()
     for (rs, dh, oi, oa), (rules, hdr) in zip(jobs, host):
         n = len(hdr["src"])

@@ -149,3 +149,48 @@ def test_bad_arguments(env):
     with pytest.raises(fw.FwError):
         sv.submit(s, pageable, torch.empty(n, dtype=torch.int32), torch.empty(n, dtype=torch.uint8))
     sv.destroy()
+
+
+def test_ticket_ring_reuse_and_limit(env):
+    """Requests live in a ring of R entries (here R = 1,024): an unreleased ticket holds its entry, so
+    the submit R tickets later is refused with FW_EBUSY until it is released, and the ring wraps
+    around several times with every result still exact."""
+    torch, rules, sets, reqs, want = env
+    sv = fw.Server(sets, mode=fw.FW_HOST_ZEROCOPY, slots=1, max_group_requests=64, max_pending=512)
+    s, hdr = 3, W.gen_packets(rules[3], 64 * 4096, 77, zipf_s=1.1)
+    dh = fw.headers_to_device(hdr)
+    ref_i, ref_a = fw.fw_classify(sets[s], dh)
+    for t in dh.values():
+        sv.register(t)
+    out_i = torch.full((64 * 4096,), -3, dtype=torch.int32, device="cuda")
+    out_a = torch.zeros(64 * 4096, dtype=torch.uint8, device="cuda")
+    sv.register(out_i)
+    sv.register(out_a)
+
+    def sub(k):
+        sl = slice(64 * k, 64 * (k + 1))
+        return sv.submit(s, {f: t[sl] for f, t in dh.items()}, out_i[sl], out_a[sl], n=64)
+
+    tickets = []
+    for k in range(1024):  # 1,024 requests completed and not released: every ring entry is held
+        tickets.append(sub(k))
+        if len(tickets) % 256 == 0:
+            assert sv.drain(10_000_000) == fw.FW_OK
+    assert sv.drain(10_000_000) == fw.FW_OK
+    with pytest.raises(fw.FwError) as ei:
+        sub(1024)
+    assert ei.value.status == fw.FW_EBUSY
+    assert sv.wait(tickets[0])[0] == fw.FW_OK  # releasing the oldest ticket frees its entry
+    tickets = tickets[1:] + [sub(1024)]
+    assert all(sv.wait(t)[0] == fw.FW_OK for t in tickets)
+    assert sv.wait(tickets[0])[0] == fw.FW_EINVAL  # already released
+    # wrap around: windows of 256 submits, each window waited for
+    for base in range(1025, 4096, 256):
+        ts = [sub(k) for k in range(base, min(base + 256, 4096))]
+        assert all(sv.wait(t)[0] == fw.FW_OK for t in ts)
+    assert torch.equal(out_i, ref_i) and torch.equal(out_a, ref_a)
+    o = oracle.classify(rules[s], {f: v[:4096] for f, v in hdr.items()})
+    assert np.array_equal(out_i[:4096].cpu().numpy(), o[0]) and np.array_equal(out_a[:4096].cpu().numpy(), o[1])
+    st = sv.stats()
+    assert st["completed"] == 4096 and st["failed"] == 0 and st["submit_ns"] > 0 and st["launch_ns"] > 0
+    sv.destroy()
