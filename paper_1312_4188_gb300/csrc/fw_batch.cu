@@ -24,6 +24,11 @@
 
 namespace fwk {
 
+// Packets a lane of the batched filter path takes at a time. Two: on four rule sets of 1K..100K
+// rules (rows of 1..5 words) one launch over 37.7M packets ran at 82 Gpackets/s, against 77 with
+// one packet and 76 with four (whose state no longer fits the 64 registers of two blocks an SM).
+constexpr int kBatchFilterPackets = 2;
+
 // Claim the next item of a launch for the calling warp: its index from the global counter, its
 // job by a search of the item prefix (the last j with prefix[j] <= index). False when none is left.
 __device__ __forceinline__ bool batch_claim(const BatchParams &p, int lane, int &job, int64_t &it) {
@@ -46,37 +51,57 @@ __device__ __forceinline__ bool batch_claim(const BatchParams &p, int lane, int 
     return true;
 }
 
-// One item of a job with a bucket filter, its block read through L1: four consecutive packets
-// per lane (item starts are multiples of four packets, so aligned arrays allow vector loads and
-// stores), their first row words loaded together. Kept out of line in k_batch so that its
-// registers do not add to the scan path's.
-template <bool INLINE>
-__device__ __forceinline__ void batch_filter_quads(const BatchJobDev &J, const BatchItem &item, int lane,
-                                                   uint32_t one) {
+// One item of a job with a bucket filter, its block read through L1: P consecutive packets per
+// lane (item starts are multiples of four packets, so aligned arrays allow vector loads and
+// stores); the classes and first row words of a lane's packets are loaded together, then each
+// packet is resolved in turn (filter_packets_wide).
+template <int P>
+__device__ __forceinline__ void batch_filter_run(const BatchJobDev &J, const BatchItem &item, int lane,
+                                                 uint32_t one) {
+    static_assert(P == 1 || P == 2 || P == 4, "one, two or four packets a lane");
     const FilterView fv = J.fv;
     const unsigned char *__restrict__ base = J.filter;
     const int64_t st = item.start;
     const bool vin = J.vec != 0;
-    const bool vout = vin && (reinterpret_cast<uintptr_t>(J.out_idx + st) % 16 == 0) &&
-                      (reinterpret_cast<uintptr_t>(J.out_act + st) % 4 == 0);
-    for (int q = 4 * lane; q < item.count; q += 128) {
+    const bool vout = vin && (reinterpret_cast<uintptr_t>(J.out_idx + st) % (4 * P) == 0) &&
+                      (reinterpret_cast<uintptr_t>(J.out_act + st) % P == 0);
+    for (int q = P * lane; q < item.count; q += 32 * P) {
         const int64_t i = st + q;
-        const int m = min(4, item.count - q);
-        uint32_t s[4], d[4], sp[4], dp[4], pr[4], vw[4];
-        if (vin && m == 4) {
-            const uint4 a = __ldcs(reinterpret_cast<const uint4 *>(J.h.src + i));
-            const uint4 b = __ldcs(reinterpret_cast<const uint4 *>(J.h.dst + i));
-            const uint2 c = __ldcs(reinterpret_cast<const uint2 *>(J.h.sport + i));
-            const uint2 e = __ldcs(reinterpret_cast<const uint2 *>(J.h.dport + i));
-            const uint32_t f = __ldcs(reinterpret_cast<const unsigned int *>(J.h.proto + i));
-            s[0] = a.x; s[1] = a.y; s[2] = a.z; s[3] = a.w;
-            d[0] = b.x; d[1] = b.y; d[2] = b.z; d[3] = b.w;
-            sp[0] = c.x & 0xFFFFu; sp[1] = c.x >> 16; sp[2] = c.y & 0xFFFFu; sp[3] = c.y >> 16;
-            dp[0] = e.x & 0xFFFFu; dp[1] = e.x >> 16; dp[2] = e.y & 0xFFFFu; dp[3] = e.y >> 16;
-            pr[0] = f & 0xFFu; pr[1] = (f >> 8) & 0xFFu; pr[2] = (f >> 16) & 0xFFu; pr[3] = f >> 24;
+        const int m = min(P, item.count - q);
+        uint32_t s[P], d[P], sp[P], dp[P], pr[P], vw[P];
+        if (vin && m == P && P > 1) {
+            if (P == 4) {
+                const uint4 a = __ldcs(reinterpret_cast<const uint4 *>(J.h.src + i));
+                const uint4 b = __ldcs(reinterpret_cast<const uint4 *>(J.h.dst + i));
+                const uint2 c = __ldcs(reinterpret_cast<const uint2 *>(J.h.sport + i));
+                const uint2 e = __ldcs(reinterpret_cast<const uint2 *>(J.h.dport + i));
+                const uint32_t f = __ldcs(reinterpret_cast<const unsigned int *>(J.h.proto + i));
+                const uint32_t sa[4] = {a.x, a.y, a.z, a.w}, da[4] = {b.x, b.y, b.z, b.w};
+                const uint32_t spa[4] = {c.x & 0xFFFFu, c.x >> 16, c.y & 0xFFFFu, c.y >> 16};
+                const uint32_t dpa[4] = {e.x & 0xFFFFu, e.x >> 16, e.y & 0xFFFFu, e.y >> 16};
+#pragma unroll
+                for (int k = 0; k < P; ++k) {
+                    s[k] = sa[k];
+                    d[k] = da[k];
+                    sp[k] = spa[k];
+                    dp[k] = dpa[k];
+                    pr[k] = (f >> (8 * k)) & 0xFFu;
+                }
+            } else {
+                const uint2 a = __ldcs(reinterpret_cast<const uint2 *>(J.h.src + i));
+                const uint2 b = __ldcs(reinterpret_cast<const uint2 *>(J.h.dst + i));
+                const uint32_t c = __ldcs(reinterpret_cast<const unsigned int *>(J.h.sport + i));
+                const uint32_t e = __ldcs(reinterpret_cast<const unsigned int *>(J.h.dport + i));
+                const uint32_t f = __ldcs(reinterpret_cast<const unsigned short *>(J.h.proto + i));
+                s[0] = a.x; s[P - 1] = a.y;
+                d[0] = b.x; d[P - 1] = b.y;
+                sp[0] = c & 0xFFFFu; sp[P - 1] = c >> 16;
+                dp[0] = e & 0xFFFFu; dp[P - 1] = e >> 16;
+                pr[0] = f & 0xFFu; pr[P - 1] = f >> 8;
+            }
         } else {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < P; ++k) {
                 const int64_t ik = k < m ? i + k : i;  // past the item's end: a copy of its first packet
                 s[k] = J.h.src[ik];
                 d[k] = J.h.dst[ik];
@@ -85,20 +110,25 @@ __device__ __forceinline__ void batch_filter_quads(const BatchJobDev &J, const B
                 pr[k] = J.h.proto[ik];
             }
         }
-        filter_packets_wide<4>(base, fv, s, d, sp, dp, pr, one, vw);
-        int32_t oi[4];
+        filter_packets_wide<P>(base, fv, s, d, sp, dp, pr, one, vw);
+        int32_t oi[P];
         uint32_t oa = 0;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < P; ++k) {
             oi[k] = vw[k] == 0xFFFFFFFFu ? -1 : (int32_t)(vw[k] & 0x7FFFFFFFu);
             oa |= (vw[k] == 0xFFFFFFFFu ? (uint32_t)FW_DROP : (vw[k] >> 31)) << (8 * k);
         }
-        if (vout && m == 4) {
-            __stcs(reinterpret_cast<int4 *>(J.out_idx + i), make_int4(oi[0], oi[1], oi[2], oi[3]));
-            __stcs(reinterpret_cast<unsigned int *>(J.out_act + i), oa);
+        if (vout && m == P && P > 1) {
+            if (P == 4) {
+                __stcs(reinterpret_cast<int4 *>(J.out_idx + i), make_int4(oi[0], oi[1 % P], oi[2 % P], oi[3 % P]));
+                __stcs(reinterpret_cast<unsigned int *>(J.out_act + i), oa);
+            } else {
+                __stcs(reinterpret_cast<int2 *>(J.out_idx + i), make_int2(oi[0], oi[P - 1]));
+                __stcs(reinterpret_cast<unsigned short *>(J.out_act + i), (unsigned short)oa);
+            }
         } else {
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
+            for (int k = 0; k < P; ++k)
                 if (k < m) {
                     J.out_idx[i + k] = oi[k];
                     J.out_act[i + k] = (uint8_t)(oa >> (8 * k));
@@ -108,7 +138,7 @@ __device__ __forceinline__ void batch_filter_quads(const BatchJobDev &J, const B
 }
 
 __device__ __noinline__ void batch_filter_item(const BatchJobDev &J, const BatchItem &item, int lane, uint32_t one) {
-    batch_filter_quads<false>(J, item, lane, one);
+    batch_filter_run<kBatchFilterPackets>(J, item, lane, one);
 }
 
 // The persistent kernel of launches whose jobs all have a bucket filter: no scan queue in shared
@@ -126,7 +156,7 @@ __global__ void __launch_bounds__(kBatchFilterThreads, MINB) k_batch_filter(Batc
         item.job = job;
         item.start = (it - __ldg(p.prefix + job)) * J.item_packets;
         item.count = (int32_t)min((int64_t)J.item_packets, J.n - item.start);
-        batch_filter_quads<true>(J, item, lane, p.one);
+        batch_filter_run<kBatchFilterPackets>(J, item, lane, p.one);
     }
 }
 

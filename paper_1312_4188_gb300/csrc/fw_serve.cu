@@ -80,6 +80,7 @@ struct SvSlot {
     bool failed = false;  // the group's launch failed: it completes with FW_ECUDA
     uint64_t g_lo = 0, g_hi = 0;  // the group: tickets [g_lo, g_hi)
     int beside = 0;               // groups in flight when this one was admitted
+    int64_t packets = 0;          // the group's packets
     std::vector<uint32_t> order;  // the group's requests (offsets from g_lo) in job order
     std::vector<uint32_t> count;  // per set rank: requests of the group (then their first job)
     size_t arena_off = 0, arena_len = 0;
@@ -179,7 +180,15 @@ static void arena_free(fw_server *sv, size_t off, size_t len) {
 // the persistent kernel, (copy mode) verdict copies out, the completion event.
 static cudaError_t launch_group(fw_server *sv, SvSlot &sl) {
     const bool copy = sv->cfg.mode != FW_HOST_ZEROCOPY;
-    const int B = item_packets(sv->cfg.packets_per_item);
+    int B = item_packets(sv->cfg.packets_per_item);
+    if (sv->filter_only) {
+        // filter items need no scan queue: a small group gets smaller items (down to 64 packets,
+        // one step of a warp), about one for every warp of the launch, so its packets spread over
+        // more warps and its latency falls; a large one keeps the configured size
+        const int64_t warps = (int64_t)sm_count(sv->device) * kBatchFilterMinBlocks * (kBatchFilterThreads / 32);
+        const int64_t want = (sl.packets + warps - 1) / warps;
+        B = (int)std::min<int64_t>(B, std::max<int64_t>(64, (want + 63) / 64 * 64));
+    }
     cudaError_t e = cudaSuccess;
     size_t off = sl.arena_off;
     int64_t n_items = 0;
@@ -227,6 +236,7 @@ static cudaError_t launch_group(fw_server *sv, SvSlot &sl) {
         J.n = r.n;
         J.out_idx = di;
         J.out_act = da;
+        J.item_packets = B;
         h_prefix[i] = n_items;
         n_items += (r.n + B - 1) / B;
     }
@@ -335,13 +345,16 @@ static void worker_loop(fw_server *sv) {
             if (copy) {
                 while (take > 0 && !arena_alloc(sv, bytes, &off)) {
                     --take;  // not enough free memory: admit fewer
-                    bytes -= request_bytes(entry(sv, sv->admit_next + take).n);
+                    const int64_t n = entry(sv, sv->admit_next + take).n;
+                    bytes -= request_bytes(n);
+                    pk -= n;
                 }
                 if (take == 0) break;  // wait for memory to free up
             }
             sl.g_lo = sv->admit_next;
             sl.g_hi = sv->admit_next + take;
             sl.beside = busy;
+            sl.packets = pk;
             sv->admit_next += take;
             sl.arena_off = off;
             sl.arena_len = copy ? bytes : 0;
