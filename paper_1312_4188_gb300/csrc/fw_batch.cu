@@ -250,7 +250,14 @@ cudaError_t launch_batch(const BatchJobDev *d_jobs, const int64_t *d_prefix, int
                          unsigned long long *d_next, int32_t qcap, int threads, int64_t blocks, cudaStream_t st,
                          int filter_minb) {
     cudaError_t e = cudaMemsetAsync(d_next, 0, sizeof(unsigned long long), st);
-    if (e != cudaSuccess || n_items == 0 || n_jobs == 0) return e;
+    if (e != cudaSuccess) return e;
+    return launch_batch_kernel(d_jobs, d_prefix, n_jobs, n_items, d_next, qcap, threads, blocks, st, filter_minb);
+}
+
+cudaError_t launch_batch_kernel(const BatchJobDev *d_jobs, const int64_t *d_prefix, int32_t n_jobs, int64_t n_items,
+                                unsigned long long *d_next, int32_t qcap, int threads, int64_t blocks, cudaStream_t st,
+                                int filter_minb) {
+    if (n_items == 0 || n_jobs == 0) return cudaSuccess;
     BatchParams p;
     p.jobs = d_jobs;
     p.prefix = d_prefix;

@@ -76,6 +76,10 @@ constexpr int kBatchFilterMinBlocks = 2;
 cudaError_t launch_batch(const BatchJobDev *d_jobs, const int64_t *d_prefix, int32_t n_jobs, int64_t n_items,
                          unsigned long long *d_next, int32_t qcap, int threads, int64_t blocks, cudaStream_t st,
                          int filter_minb);
+// The same launch without the counter reset: *d_next must already be zero on `st`.
+cudaError_t launch_batch_kernel(const BatchJobDev *d_jobs, const int64_t *d_prefix, int32_t n_jobs, int64_t n_items,
+                                unsigned long long *d_next, int32_t qcap, int threads, int64_t blocks, cudaStream_t st,
+                                int filter_minb);
 cudaError_t prepare_batch_kernel(size_t smem_bytes);
 size_t batch_smem_bytes(int threads, int32_t qcap);  // dynamic shared memory of k_batch
 

@@ -73,13 +73,15 @@ constexpr uint64_t kRingChunk = 1024;  // ring entries per allocation
 struct SvSlot {
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
-    BatchJobDev *d_jobs = nullptr;  // the work list: jobs, then (16-byte aligned) the item prefix
-    unsigned long long *d_next = nullptr;
-    BatchJobDev *h_jobs = nullptr;  // pinned staging of the work list
+    // the work list: the item counter (16 bytes), the jobs, then (16-byte aligned) the item
+    // prefix; staged in pinned memory and copied in one piece, which also zeroes the counter
+    unsigned char *d_work = nullptr;
+    unsigned char *h_work = nullptr;
     bool busy = false;
     bool failed = false;  // the group's launch failed: it completes with FW_ECUDA
     uint64_t g_lo = 0, g_hi = 0;  // the group: tickets [g_lo, g_hi)
     int beside = 0;               // groups in flight when this one was admitted
+    bool flip = false;            // the group takes the rule sets in reverse rank order
     int64_t packets = 0;          // the group's packets
     std::vector<uint32_t> order;  // the group's requests (offsets from g_lo) in job order
     std::vector<uint32_t> count;  // per set rank: requests of the group (then their first job)
@@ -193,17 +195,25 @@ static cudaError_t launch_group(fw_server *sv, SvSlot &sl) {
     size_t off = sl.arena_off;
     int64_t n_items = 0;
     const size_t nj = (size_t)(sl.g_hi - sl.g_lo);
-    // job order: by set rank (a counting sort, stable within a set)
+    // job order: by set rank (a counting sort, stable within a set), every other group in reverse
+    // rank order, so that the end of one group and the start of the next, which overlap on the
+    // device, work on the same rule set
     const size_t ns = sv->set_rank.size();
+    auto rank = [&](size_t i) {
+        const size_t r = (size_t)sv->set_rank[(size_t)entry(sv, sl.g_lo + i).set];
+        return sl.flip ? ns - 1 - r : r;
+    };
     sl.count.assign(ns + 1, 0);
-    for (size_t i = 0; i < nj; ++i) ++sl.count[(size_t)sv->set_rank[(size_t)entry(sv, sl.g_lo + i).set] + 1];
+    for (size_t i = 0; i < nj; ++i) ++sl.count[rank(i) + 1];
     for (size_t k = 1; k <= ns; ++k) sl.count[k] += sl.count[k - 1];
     sl.order.resize(nj);
-    for (size_t i = 0; i < nj; ++i)
-        sl.order[sl.count[(size_t)sv->set_rank[(size_t)entry(sv, sl.g_lo + i).set]]++] = (uint32_t)i;
+    for (size_t i = 0; i < nj; ++i) sl.order[sl.count[rank(i)]++] = (uint32_t)i;
+    unsigned long long *h_next = reinterpret_cast<unsigned long long *>(sl.h_work);
+    *h_next = 0;
+    BatchJobDev *h_jobs = reinterpret_cast<BatchJobDev *>(sl.h_work + 16);
     // the item prefix follows the group's jobs in the same staging buffer
-    const size_t po = a16(nj * sizeof(BatchJobDev));
-    int64_t *h_prefix = reinterpret_cast<int64_t *>(reinterpret_cast<uint8_t *>(sl.h_jobs) + po);
+    const size_t po = 16 + a16(nj * sizeof(BatchJobDev));
+    int64_t *h_prefix = reinterpret_cast<int64_t *>(sl.h_work + po);
     for (size_t i = 0; i < nj && e == cudaSuccess; ++i) {
         const SvRequest &r = entry(sv, sl.g_lo + sl.order[i]);
         fw_headers dh = r.h;
@@ -229,7 +239,7 @@ static cudaError_t launch_group(fw_server *sv, SvSlot &sl) {
             dh = fw_headers{s, d, sp, dp, pr};
         }
         // the rule set's part comes from its template; only the buffers are per request
-        BatchJobDev &J = sl.h_jobs[i];
+        BatchJobDev &J = h_jobs[i];
         J = sv->tmpl[(size_t)r.set];
         J.vec = job_vector_loads(dh);
         J.h = HdrPtrs{dh.src, dh.dst, dh.sport, dh.dport, dh.proto};
@@ -241,10 +251,12 @@ static cudaError_t launch_group(fw_server *sv, SvSlot &sl) {
         n_items += (r.n + B - 1) / B;
     }
     h_prefix[nj] = n_items;
-    // jobs and item prefix in one copy
+    // counter, jobs and item prefix in one copy
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(sl.d_jobs, sl.h_jobs, po + (nj + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, sl.st);
-    const int64_t *d_prefix = reinterpret_cast<const int64_t *>(reinterpret_cast<const uint8_t *>(sl.d_jobs) + po);
+        e = cudaMemcpyAsync(sl.d_work, sl.h_work, po + (nj + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, sl.st);
+    unsigned long long *d_next = reinterpret_cast<unsigned long long *>(sl.d_work);
+    const BatchJobDev *d_jobs = reinterpret_cast<const BatchJobDev *>(sl.d_work + 16);
+    const int64_t *d_prefix = reinterpret_cast<const int64_t *>(sl.d_work + po);
     if (e == cudaSuccess) {
         const int wpb = (sv->filter_only ? kBatchFilterThreads : sv->threads) / 32;
         const int per_sm = sv->filter_only ? kBatchFilterMinBlocks : 2;
@@ -254,13 +266,13 @@ static cudaError_t launch_group(fw_server *sv, SvSlot &sl) {
         const int64_t per_block = (int64_t)wpb * (sl.beside > 0 ? sv->cfg.items_per_warp : 1);
         const int64_t blocks = std::max<int64_t>(
             1, std::min<int64_t>((int64_t)sm_count(sv->device) * per_sm, (n_items + per_block - 1) / per_block));
-        e = launch_batch(sl.d_jobs, d_prefix, (int32_t)nj, n_items, sl.d_next, sv->qcap, sv->threads, blocks, sl.st,
+        e = launch_batch_kernel(d_jobs, d_prefix, (int32_t)nj, n_items, d_next, sv->qcap, sv->threads, blocks, sl.st,
                          sv->filter_only ? kBatchFilterMinBlocks : 0);
     }
     if (copy) {
         for (size_t i = 0; i < nj && e == cudaSuccess; ++i) {
             const SvRequest &r = entry(sv, sl.g_lo + sl.order[i]);
-            const BatchJobDev &J = sl.h_jobs[i];
+            const BatchJobDev &J = h_jobs[i];
             e = cudaMemcpyAsync(r.out_idx, J.out_idx, 4 * (size_t)r.n, cudaMemcpyDeviceToHost, sl.st);
             if (e == cudaSuccess) e = cudaMemcpyAsync(r.out_act, J.out_act, (size_t)r.n, cudaMemcpyDeviceToHost, sl.st);
         }
@@ -354,6 +366,7 @@ static void worker_loop(fw_server *sv) {
             sl.g_lo = sv->admit_next;
             sl.g_hi = sv->admit_next + take;
             sl.beside = busy;
+            sl.flip = (sv->stats.groups & 1) != 0;
             sl.packets = pk;
             sv->admit_next += take;
             sl.arena_off = off;
@@ -449,9 +462,8 @@ extern "C" void fw_server_destroy(fw_server *sv) {
         if (sl.st) cudaStreamSynchronize(sl.st);
         if (sl.ev) cudaEventDestroy(sl.ev);
         if (sl.st) cudaStreamDestroy(sl.st);
-        cudaFree(sl.d_jobs);
-        cudaFree(sl.d_next);
-        cudaFreeHost(sl.h_jobs);
+        cudaFree(sl.d_work);
+        cudaFreeHost(sl.h_work);
     }
     cudaFree(sv->d_arena);
     for (SvRequest *c : sv->ring) delete[] c;
@@ -533,10 +545,10 @@ extern "C" int fw_server_create(const fw_ruleset *const *sets, int n_sets, const
     for (SvSlot &sl : sv->slots) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
-        const size_t work_bytes = a16(c.max_group_requests * sizeof(BatchJobDev)) + (c.max_group_requests + 1) * sizeof(int64_t);
-        if (e == cudaSuccess) e = dev_malloc(&sl.d_jobs, work_bytes);
-        if (e == cudaSuccess) e = dev_malloc(&sl.d_next, sizeof(unsigned long long));
-        if (e == cudaSuccess) e = pinned_malloc(&sl.h_jobs, work_bytes);
+        const size_t work_bytes =
+            16 + a16(c.max_group_requests * sizeof(BatchJobDev)) + (c.max_group_requests + 1) * sizeof(int64_t);
+        if (e == cudaSuccess) e = dev_malloc(&sl.d_work, work_bytes);
+        if (e == cudaSuccess) e = pinned_malloc(&sl.h_work, work_bytes);
     }
     if (e != cudaSuccess) {
         fw_server_destroy(sv);
@@ -551,8 +563,8 @@ extern "C" int fw_server_create(const fw_ruleset *const *sets, int n_sets, const
 namespace fwk {
 
 // A request checked and, in zero-copy mode, its buffers resolved to device-accessible aliases
-// (one pass over the registered ranges under one lock), written to *r without touching the queue.
-// hint[7]: per buffer, the registered range to try first (updated).
+// (one pass over the registered ranges), written to *r without touching the queue. hint[7]: per
+// buffer, the registered range to try first (updated). The caller holds sv->reg_mu.
 static int prepare_request(fw_server *sv, int set, const fw_headers *h, int64_t n, int32_t *out_idx,
                            uint8_t *out_act, SvRequest *r, size_t *hint) {
     if (h == nullptr || n < 1 || n > INT32_MAX) return FW_EINVAL;
@@ -570,23 +582,20 @@ static int prepare_request(fw_server *sv, int set, const fw_headers *h, int64_t 
         const size_t len[7] = {4 * m, 4 * m, 2 * m, 2 * m, m, 4 * m, m};
         const void *d[7] = {};
         int found = 0;
-        {
-            std::lock_guard<std::mutex> lk(sv->reg_mu);
-            const size_t nr = sv->ranges.size();
-            for (int k = 0; k < 7; ++k) {
-                const uintptr_t a = reinterpret_cast<uintptr_t>(p[k]);
-                // start at the range that held this buffer last time (a request's buffers usually
-                // lie where the previous request's did)
-                const size_t h0 = hint[k] < nr ? hint[k] : 0;
-                for (size_t j = 0; j < nr; ++j) {
-                    const size_t i = h0 + j < nr ? h0 + j : h0 + j - nr;
-                    const SvRange &rg = sv->ranges[i];
-                    if (a >= rg.lo && a + len[k] <= rg.hi) {
-                        d[k] = reinterpret_cast<const void *>(a + rg.delta);
-                        hint[k] = i;
-                        ++found;
-                        break;
-                    }
+        const size_t nr = sv->ranges.size();
+        for (int k = 0; k < 7; ++k) {
+            const uintptr_t a = reinterpret_cast<uintptr_t>(p[k]);
+            // start at the range that held this buffer last time (a request's buffers usually lie
+            // where the previous request's did)
+            const size_t h0 = hint[k] < nr ? hint[k] : 0;
+            for (size_t j = 0; j < nr; ++j) {
+                const size_t i = h0 + j < nr ? h0 + j : h0 + j - nr;
+                const SvRange &rg = sv->ranges[i];
+                if (a >= rg.lo && a + len[k] <= rg.hi) {
+                    d[k] = reinterpret_cast<const void *>(a + rg.delta);
+                    hint[k] = i;
+                    ++found;
+                    break;
                 }
             }
         }
@@ -650,7 +659,11 @@ extern "C" int fw_server_submit(fw_server *sv, int set, const fw_headers *h, int
     SvRequest r;
     size_t hint[7] = {};
     const int64_t t0 = now_ns();
-    const int s = prepare_request(sv, set, h, n, out_idx, out_act, &r, hint);
+    int s;
+    {
+        std::lock_guard<std::mutex> lk(sv->reg_mu);
+        s = prepare_request(sv, set, h, n, out_idx, out_act, &r, hint);
+    }
     if (s != FW_OK) return set_status(s);
     int why = FW_OK;
     if (enqueue_requests(sv, &r, 1, ticket, t0, &why) == 0) return set_status(why);
@@ -720,6 +733,7 @@ extern "C" int fw_server_replay(fw_server *sv, fw_request *reqs, int64_t n, int6
         if (now < t0 + reqs[i].arrival_us) continue;
         int64_t j = i, nb = 0;
         int64_t t_mark = now_ns();
+        std::unique_lock<std::mutex> rl(sv->reg_mu);  // one hold of the registrations for the batch
         while (j < n && (j == i || now >= t0 + reqs[j].arrival_us) && nb < kBatch) {
             fw_request &q = reqs[j];
             const int s = prepare_request(sv, q.set, &q.hdrs, q.n, q.out_rule_idx, q.out_action, &batch[(size_t)nb],
@@ -731,6 +745,7 @@ extern "C" int fw_server_replay(fw_server *sv, fw_request *reqs, int64_t n, int6
             }
             ++j;
         }
+        rl.unlock();
         int64_t done = 0;
         while (done < nb) {
             int why = FW_OK;
