@@ -643,10 +643,10 @@ def side_serving(ctx):
     rec = {"config": {"workload": "serving_4_sets", "sets_rules": sizes, "requests": n_req,
                       "request_packets": [64, 65536], "packets": total, "arrivals": "Poisson",
                       "buffers": "device-resident request headers and verdicts", "slots": 8,
-                      "max_group_requests": 1024, "max_group_packets": 1 << 22}}
+                      "max_group_requests": 4096, "max_group_packets": 1 << 23, "busy_groups": 2}}
     loads = {}
-    sv = fw.Server(sets, mode=fw.FW_HOST_ZEROCOPY, slots=8, max_group_requests=1024, max_group_packets=1 << 22,
-                   arena_bytes=1 << 30)
+    sv = fw.Server(sets, mode=fw.FW_HOST_ZEROCOPY, slots=8, max_group_requests=4096, max_group_packets=1 << 23,
+                   busy_groups=2, arena_bytes=1 << 30)
     for pool in dpools:
         for t in pool.values():
             sv.register(t)

@@ -446,7 +446,10 @@ typedef struct fw_server_config {
                                     (default 1: every SM it can use, the lowest latency; larger
                                     leaves SMs to the groups beside it); a group alone on the
                                     device always gets one item a warp */
-    int32_t reserved[4];
+    int32_t busy_groups;         /* with this many groups in flight (default 2), queued requests
+                                    wait to form a full group (max_group_packets queued) or for a
+                                    group to complete: under load groups grow, fewer launches */
+    int32_t reserved[3];
 } fw_server_config;
 
 typedef struct fw_server_stats {
@@ -514,7 +517,9 @@ int fw_server_get_stats(fw_server *sv, fw_server_stats *st);
  * Open-loop replay: submit reqs[i] at arrival_us[i] after the call starts
  * (retrying while the queue is full; requests already due are prepared and
  * queued together), then wait for all of them and fill status, latency_us
- * and submit_lag_us. Returns FW_OK when every request succeeded.
+ * and submit_lag_us. While it submits, the scheduler thread is kept polling
+ * instead of sleeping between requests, as under steady traffic; the clock
+ * starts once it is awake. Returns FW_OK when every request succeeded.
  */
 int fw_server_replay(fw_server *sv, fw_request *reqs, int64_t n, int64_t timeout_us);
 

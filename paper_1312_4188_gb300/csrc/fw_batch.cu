@@ -16,6 +16,7 @@
 // start first. Per size class of rule set (by reachable rules) the plan
 // carries its own item size and first rule segment, chosen by the autotuner.
 #include <algorithm>
+#include <map>
 #include <cstring>
 #include <vector>
 
@@ -56,11 +57,11 @@ __device__ __forceinline__ bool batch_claim(const BatchParams &p, int lane, int 
 // stores); the classes and first row words of a lane's packets are loaded together, then each
 // packet is resolved in turn (filter_packets_wide).
 template <int P>
-__device__ __forceinline__ void batch_filter_run(const BatchJobDev &J, const BatchItem &item, int lane,
-                                                 uint32_t one) {
-    static_assert(P == 1 || P == 2 || P == 4, "one, two or four packets a lane");
-    const FilterView fv = J.fv;
-    const unsigned char *__restrict__ base = J.filter;
+__device__ __forceinline__ void batch_filter_run(const BatchFilterJob &J, const BatchFilterSet &S,
+                                                 const BatchItem &item, int lane, uint32_t one) {
+    static_assert(P == 1 || P == 2, "one or two packets a lane");
+    const FilterView fv = S.fv;
+    const unsigned char *__restrict__ base = S.filter;
     const int64_t st = item.start;
     const bool vin = J.vec != 0;
     const bool vout = vin && (reinterpret_cast<uintptr_t>(J.out_idx + st) % (4 * P) == 0) &&
@@ -69,36 +70,17 @@ __device__ __forceinline__ void batch_filter_run(const BatchJobDev &J, const Bat
         const int64_t i = st + q;
         const int m = min(P, item.count - q);
         uint32_t s[P], d[P], sp[P], dp[P], pr[P], vw[P];
-        if (vin && m == P && P > 1) {
-            if (P == 4) {
-                const uint4 a = __ldcs(reinterpret_cast<const uint4 *>(J.h.src + i));
-                const uint4 b = __ldcs(reinterpret_cast<const uint4 *>(J.h.dst + i));
-                const uint2 c = __ldcs(reinterpret_cast<const uint2 *>(J.h.sport + i));
-                const uint2 e = __ldcs(reinterpret_cast<const uint2 *>(J.h.dport + i));
-                const uint32_t f = __ldcs(reinterpret_cast<const unsigned int *>(J.h.proto + i));
-                const uint32_t sa[4] = {a.x, a.y, a.z, a.w}, da[4] = {b.x, b.y, b.z, b.w};
-                const uint32_t spa[4] = {c.x & 0xFFFFu, c.x >> 16, c.y & 0xFFFFu, c.y >> 16};
-                const uint32_t dpa[4] = {e.x & 0xFFFFu, e.x >> 16, e.y & 0xFFFFu, e.y >> 16};
-#pragma unroll
-                for (int k = 0; k < P; ++k) {
-                    s[k] = sa[k];
-                    d[k] = da[k];
-                    sp[k] = spa[k];
-                    dp[k] = dpa[k];
-                    pr[k] = (f >> (8 * k)) & 0xFFu;
-                }
-            } else {
-                const uint2 a = __ldcs(reinterpret_cast<const uint2 *>(J.h.src + i));
-                const uint2 b = __ldcs(reinterpret_cast<const uint2 *>(J.h.dst + i));
-                const uint32_t c = __ldcs(reinterpret_cast<const unsigned int *>(J.h.sport + i));
-                const uint32_t e = __ldcs(reinterpret_cast<const unsigned int *>(J.h.dport + i));
-                const uint32_t f = __ldcs(reinterpret_cast<const unsigned short *>(J.h.proto + i));
-                s[0] = a.x; s[P - 1] = a.y;
-                d[0] = b.x; d[P - 1] = b.y;
-                sp[0] = c & 0xFFFFu; sp[P - 1] = c >> 16;
-                dp[0] = e & 0xFFFFu; dp[P - 1] = e >> 16;
-                pr[0] = f & 0xFFu; pr[P - 1] = f >> 8;
-            }
+        if (P == 2 && vin && m == P) {
+            const uint2 a = __ldcs(reinterpret_cast<const uint2 *>(J.h.src + i));
+            const uint2 b = __ldcs(reinterpret_cast<const uint2 *>(J.h.dst + i));
+            const uint32_t c = __ldcs(reinterpret_cast<const unsigned int *>(J.h.sport + i));
+            const uint32_t e = __ldcs(reinterpret_cast<const unsigned int *>(J.h.dport + i));
+            const uint32_t f = __ldcs(reinterpret_cast<const unsigned short *>(J.h.proto + i));
+            s[0] = a.x; s[P - 1] = a.y;
+            d[0] = b.x; d[P - 1] = b.y;
+            sp[0] = c & 0xFFFFu; sp[P - 1] = c >> 16;
+            dp[0] = e & 0xFFFFu; dp[P - 1] = e >> 16;
+            pr[0] = f & 0xFFu; pr[P - 1] = f >> 8;
         } else {
 #pragma unroll
             for (int k = 0; k < P; ++k) {
@@ -118,14 +100,9 @@ __device__ __forceinline__ void batch_filter_run(const BatchJobDev &J, const Bat
             oi[k] = vw[k] == 0xFFFFFFFFu ? -1 : (int32_t)(vw[k] & 0x7FFFFFFFu);
             oa |= (vw[k] == 0xFFFFFFFFu ? (uint32_t)FW_DROP : (vw[k] >> 31)) << (8 * k);
         }
-        if (vout && m == P && P > 1) {
-            if (P == 4) {
-                __stcs(reinterpret_cast<int4 *>(J.out_idx + i), make_int4(oi[0], oi[1 % P], oi[2 % P], oi[3 % P]));
-                __stcs(reinterpret_cast<unsigned int *>(J.out_act + i), oa);
-            } else {
-                __stcs(reinterpret_cast<int2 *>(J.out_idx + i), make_int2(oi[0], oi[P - 1]));
-                __stcs(reinterpret_cast<unsigned short *>(J.out_act + i), (unsigned short)oa);
-            }
+        if (P == 2 && vout && m == P) {
+            __stcs(reinterpret_cast<int2 *>(J.out_idx + i), make_int2(oi[0], oi[P - 1]));
+            __stcs(reinterpret_cast<unsigned short *>(J.out_act + i), (unsigned short)oa);
         } else {
 #pragma unroll
             for (int k = 0; k < P; ++k)
@@ -137,26 +114,37 @@ __device__ __forceinline__ void batch_filter_run(const BatchJobDev &J, const Bat
     }
 }
 
+// A filter job's item inside the general kernel (whose jobs carry their rule set's fields). Kept
+// out of line so that its registers do not add to the scan path's.
 __device__ __noinline__ void batch_filter_item(const BatchJobDev &J, const BatchItem &item, int lane, uint32_t one) {
-    batch_filter_run<kBatchFilterPackets>(J, item, lane, one);
+    BatchFilterJob fj;
+    fj.h = J.h;
+    fj.out_idx = J.out_idx;
+    fj.out_act = J.out_act;
+    fj.n = J.n;
+    fj.vec = J.vec;
+    BatchFilterSet fs;
+    fs.filter = J.filter;
+    fs.fv = J.fv;
+    batch_filter_run<kBatchFilterPackets>(fj, fs, item, lane, one);
 }
 
-// The persistent kernel of launches whose jobs all have a bucket filter: no scan queue in shared
-// memory, so more warps fit on an SM and the L1 cache keeps its whole capacity for the blocks.
-// MINB resident blocks per SM: 2 (64 registers a thread) or 3 (40, some of the four packets'
-// state spilled to L1).
+// The persistent kernel of launches whose jobs all have a bucket filter: compact jobs and a table of
+// their rule sets, no scan queue in shared memory, so more warps fit on an SM and the L1 cache
+// keeps its whole capacity for the filter blocks. MINB resident blocks per SM: 2 (64 registers a
+// thread) or 3 (40).
 template <int MINB>
 __global__ void __launch_bounds__(kBatchFilterThreads, MINB) k_batch_filter(BatchParams p) {
     const int lane = threadIdx.x & 31;
     int job;
     int64_t it;
     while (batch_claim(p, lane, job, it)) {
-        const BatchJobDev &J = p.jobs[job];
+        const BatchFilterJob &J = p.fjobs[job];
         BatchItem item;
         item.job = job;
         item.start = (it - __ldg(p.prefix + job)) * J.item_packets;
         item.count = (int32_t)min((int64_t)J.item_packets, J.n - item.start);
-        batch_filter_run<kBatchFilterPackets>(J, item, lane, p.one);
+        batch_filter_run<kBatchFilterPackets>(J, p.fsets[J.set], item, lane, p.one);
     }
 }
 
@@ -247,18 +235,10 @@ cudaError_t prepare_batch_kernel(size_t smem_bytes) {
 }
 
 cudaError_t launch_batch(const BatchJobDev *d_jobs, const int64_t *d_prefix, int32_t n_jobs, int64_t n_items,
-                         unsigned long long *d_next, int32_t qcap, int threads, int64_t blocks, cudaStream_t st,
-                         int filter_minb) {
+                         unsigned long long *d_next, int32_t qcap, int threads, int64_t blocks, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(d_next, 0, sizeof(unsigned long long), st);
-    if (e != cudaSuccess) return e;
-    return launch_batch_kernel(d_jobs, d_prefix, n_jobs, n_items, d_next, qcap, threads, blocks, st, filter_minb);
-}
-
-cudaError_t launch_batch_kernel(const BatchJobDev *d_jobs, const int64_t *d_prefix, int32_t n_jobs, int64_t n_items,
-                                unsigned long long *d_next, int32_t qcap, int threads, int64_t blocks, cudaStream_t st,
-                                int filter_minb) {
-    if (n_items == 0 || n_jobs == 0) return cudaSuccess;
-    BatchParams p;
+    if (e != cudaSuccess || n_items == 0 || n_jobs == 0) return e;
+    BatchParams p{};
     p.jobs = d_jobs;
     p.prefix = d_prefix;
     p.n_jobs = n_jobs;
@@ -266,10 +246,32 @@ cudaError_t launch_batch_kernel(const BatchJobDev *d_jobs, const int64_t *d_pref
     p.next = d_next;
     p.qcap = qcap;
     p.one = 1u;
-    if (filter_minb == 3) k_batch_filter<3><<<(unsigned)blocks, kBatchFilterThreads, 0, st>>>(p);
-    else if (filter_minb != 0) k_batch_filter<2><<<(unsigned)blocks, kBatchFilterThreads, 0, st>>>(p);
-    else k_batch<<<(unsigned)blocks, threads, batch_smem_bytes(threads, qcap), st>>>(p);
+    k_batch<<<(unsigned)blocks, threads, batch_smem_bytes(threads, qcap), st>>>(p);
     return cudaGetLastError();
+}
+
+cudaError_t launch_batch_filter(const BatchFilterJob *d_jobs, const BatchFilterSet *d_sets, const int64_t *d_prefix,
+                                int32_t n_jobs, int64_t n_items, unsigned long long *d_next, int64_t blocks,
+                                cudaStream_t st, int filter_minb) {
+    if (n_items == 0 || n_jobs == 0) return cudaSuccess;
+    BatchParams p{};
+    p.fjobs = d_jobs;
+    p.fsets = d_sets;
+    p.prefix = d_prefix;
+    p.n_jobs = n_jobs;
+    p.n_items = n_items;
+    p.next = d_next;
+    p.one = 1u;
+    if (filter_minb == 3) k_batch_filter<3><<<(unsigned)blocks, kBatchFilterThreads, 0, st>>>(p);
+    else k_batch_filter<2><<<(unsigned)blocks, kBatchFilterThreads, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+BatchFilterSet batch_filter_set(const fw_ruleset *rs) {
+    BatchFilterSet s;
+    s.filter = rs->filter_words > 0 ? rs->d_filter : nullptr;
+    s.fv = filter_view(rs);
+    return s;
 }
 
 }  // namespace fwk
@@ -282,7 +284,9 @@ struct fw_plan {
     int64_t n_items = 0;
     int64_t n_jobs = 0;
     int64_t packets = 0;
-    fwk::BatchJobDev *d_jobs = nullptr;
+    fwk::BatchJobDev *d_jobs = nullptr;       // the general kernel's jobs, or
+    fwk::BatchFilterJob *d_fjobs = nullptr;   // the filter-only kernel's jobs
+    fwk::BatchFilterSet *d_fsets = nullptr;   // and their rule sets
     int64_t *d_prefix = nullptr;  // n_jobs + 1 item offsets
     unsigned long long *d_next = nullptr;
     int32_t qcap = 256;
@@ -300,6 +304,8 @@ extern "C" void fw_plan_destroy(fw_plan *pl) {
     if (pl->graph) cudaGraphDestroy(pl->graph);
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
     cudaFree(pl->d_jobs);
+    cudaFree(pl->d_fjobs);
+    cudaFree(pl->d_fsets);
     cudaFree(pl->d_prefix);
     cudaFree(pl->d_next);
     delete pl;
@@ -347,12 +353,30 @@ extern "C" int fw_plan_create(const fw_job *jobs, int64_t n_jobs, const fw_plan_
     for (int64_t j = 0; j < n_jobs; ++j)
         if (jobs[j].n > 0 && jobs[j].rs->filter_words == 0) filter_only = false;
     std::vector<int64_t> prefix((size_t)n_jobs + 1, 0);
+    // filter-only: compact jobs and a table of their distinct rule sets
+    std::vector<BatchFilterJob> hf;
+    std::vector<BatchFilterSet> hs;
+    std::map<const fw_ruleset *, int32_t> set_index;
+    if (filter_only) hf.resize((size_t)n_jobs);
     for (int64_t k = 0; k < n_jobs; ++k) {
         const fw_job &J = jobs[order[k]];
         int c = 0;
         while (c < n_classes - 1 && J.rs->n_eff > cfg.class_max_rules[c]) ++c;
         const int32_t B = item_packets(per_item[c]);
         fill_batch_job(hj[k], J.rs, J.hdrs, J.n, J.out_rule_idx, J.out_action, B, seg0[c]);
+        if (filter_only) {
+            auto ins = set_index.emplace(J.rs, (int32_t)hs.size());
+            if (ins.second) hs.push_back(batch_filter_set(J.rs));
+            BatchFilterJob &f = hf[(size_t)k];
+            f = BatchFilterJob{};
+            f.h = hj[k].h;
+            f.out_idx = hj[k].out_idx;
+            f.out_act = hj[k].out_act;
+            f.n = J.n;
+            f.set = ins.first->second;
+            f.item_packets = B;
+            f.vec = hj[k].vec;
+        }
         prefix[k + 1] = prefix[k] + (J.n + B - 1) / B;
         packets += J.n;
     }
@@ -369,11 +393,21 @@ extern "C" int fw_plan_create(const fw_job *jobs, int64_t n_jobs, const fw_plan_
     pl->filter_minb = filter_only ? (per_sm >= 3 ? 3 : 2) : 0;
     const int wpb = (filter_only ? kBatchFilterThreads : threads) / 32;
     pl->blocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count(pl->device) * per_sm, (pl->n_items + wpb - 1) / wpb));
-    cudaError_t e = dev_malloc(&pl->d_jobs, std::max<size_t>(1, hj.size()) * sizeof(BatchJobDev));
+    cudaError_t e = cudaSuccess;
+    if (filter_only) {
+        e = dev_malloc(&pl->d_fjobs, std::max<size_t>(1, hf.size()) * sizeof(BatchFilterJob));
+        if (e == cudaSuccess) e = dev_malloc(&pl->d_fsets, std::max<size_t>(1, hs.size()) * sizeof(BatchFilterSet));
+        if (e == cudaSuccess && !hf.empty())
+            e = cudaMemcpy(pl->d_fjobs, hf.data(), hf.size() * sizeof(BatchFilterJob), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !hs.empty())
+            e = cudaMemcpy(pl->d_fsets, hs.data(), hs.size() * sizeof(BatchFilterSet), cudaMemcpyHostToDevice);
+    } else {
+        e = dev_malloc(&pl->d_jobs, std::max<size_t>(1, hj.size()) * sizeof(BatchJobDev));
+        if (e == cudaSuccess && !hj.empty())
+            e = cudaMemcpy(pl->d_jobs, hj.data(), hj.size() * sizeof(BatchJobDev), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = dev_malloc(&pl->d_prefix, prefix.size() * sizeof(int64_t));
     if (e == cudaSuccess) e = dev_malloc(&pl->d_next, sizeof(unsigned long long));
-    if (e == cudaSuccess && !hj.empty())
-        e = cudaMemcpy(pl->d_jobs, hj.data(), hj.size() * sizeof(BatchJobDev), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(pl->d_prefix, prefix.data(), prefix.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = prepare_batch_kernel(smem);
     if (e != cudaSuccess) {
@@ -386,8 +420,13 @@ extern "C" int fw_plan_create(const fw_job *jobs, int64_t n_jobs, const fw_plan_
 }
 
 static cudaError_t enqueue_plan(fw_plan *pl, cudaStream_t st) {
-    return launch_batch(pl->d_jobs, pl->d_prefix, (int32_t)pl->n_jobs, pl->n_items, pl->d_next, pl->qcap, pl->threads,
-                        pl->blocks, st, pl->filter_minb);
+    if (pl->filter_minb == 0)
+        return launch_batch(pl->d_jobs, pl->d_prefix, (int32_t)pl->n_jobs, pl->n_items, pl->d_next, pl->qcap,
+                            pl->threads, pl->blocks, st);
+    cudaError_t e = cudaMemsetAsync(pl->d_next, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    return launch_batch_filter(pl->d_fjobs, pl->d_fsets, pl->d_prefix, (int32_t)pl->n_jobs, pl->n_items, pl->d_next,
+                               pl->blocks, st, pl->filter_minb);
 }
 
 extern "C" int fw_plan_launch(fw_plan *pl, void *stream) {

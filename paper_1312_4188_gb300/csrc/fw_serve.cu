@@ -23,6 +23,7 @@
 // consecutive tickets, and each rule set's part of a work-list entry is
 // built once, when the server starts.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -116,12 +117,20 @@ struct fw_server {
     // L1-resident filter block
     std::vector<int32_t> set_rank;
     bool filter_only = false;            // every rule set has a bucket filter: k_batch_filter runs
+    fwk::BatchFilterSet *d_fsets = nullptr;  // filter-only: the rule sets' filter blocks, by set index
     // Requests by ticket: entry t lives at ring index t & ring_mask, in chunks of kRingChunk
     // allocated when the server starts (addresses stay fixed). Tickets [admit_next, next_ticket) are
     // queued; an entry is reused only after its ticket was released by fw_server_wait.
     std::vector<fwk::SvRequest *> ring;
     uint64_t ring_mask = 0;
     uint64_t admit_next = 1;
+    // a replay keeps the scheduler awake while it submits: the idle scheduler then polls the
+    // submit counter (a cache line of its own, read without the lock) instead of sleeping
+    alignas(64) std::atomic<uint64_t> enq_count{0};
+    std::atomic<bool> hold_awake{false};
+    std::atomic<bool> is_awake{false};
+    char awake_pad[48];
+    int64_t queued_packets = 0;  // packets of the queued requests
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::thread worker;
@@ -210,9 +219,12 @@ static cudaError_t launch_group(fw_server *sv, SvSlot &sl) {
     for (size_t i = 0; i < nj; ++i) sl.order[sl.count[rank(i)]++] = (uint32_t)i;
     unsigned long long *h_next = reinterpret_cast<unsigned long long *>(sl.h_work);
     *h_next = 0;
+    // filter-only: compact jobs indexing the server's set table; else full jobs from the templates
+    const bool fo = sv->filter_only;
     BatchJobDev *h_jobs = reinterpret_cast<BatchJobDev *>(sl.h_work + 16);
+    BatchFilterJob *h_fjobs = reinterpret_cast<BatchFilterJob *>(sl.h_work + 16);
     // the item prefix follows the group's jobs in the same staging buffer
-    const size_t po = 16 + a16(nj * sizeof(BatchJobDev));
+    const size_t po = 16 + a16(nj * (fo ? sizeof(BatchFilterJob) : sizeof(BatchJobDev)));
     int64_t *h_prefix = reinterpret_cast<int64_t *>(sl.h_work + po);
     for (size_t i = 0; i < nj && e == cudaSuccess; ++i) {
         const SvRequest &r = entry(sv, sl.g_lo + sl.order[i]);
@@ -238,15 +250,27 @@ static cudaError_t launch_group(fw_server *sv, SvSlot &sl) {
             if (e == cudaSuccess) e = cudaMemcpyAsync(pr, r.h.proto, m, cudaMemcpyHostToDevice, sl.st);
             dh = fw_headers{s, d, sp, dp, pr};
         }
-        // the rule set's part comes from its template; only the buffers are per request
-        BatchJobDev &J = h_jobs[i];
-        J = sv->tmpl[(size_t)r.set];
-        J.vec = job_vector_loads(dh);
-        J.h = HdrPtrs{dh.src, dh.dst, dh.sport, dh.dport, dh.proto};
-        J.n = r.n;
-        J.out_idx = di;
-        J.out_act = da;
-        J.item_packets = B;
+        if (fo) {
+            BatchFilterJob &J = h_fjobs[i];
+            J.h = HdrPtrs{dh.src, dh.dst, dh.sport, dh.dport, dh.proto};
+            J.out_idx = di;
+            J.out_act = da;
+            J.n = r.n;
+            J.set = r.set;
+            J.item_packets = B;
+            J.vec = job_vector_loads(dh);
+            J.pad = 0;
+        } else {
+            // the rule set's part comes from its template; only the buffers are per request
+            BatchJobDev &J = h_jobs[i];
+            J = sv->tmpl[(size_t)r.set];
+            J.vec = job_vector_loads(dh);
+            J.h = HdrPtrs{dh.src, dh.dst, dh.sport, dh.dport, dh.proto};
+            J.n = r.n;
+            J.out_idx = di;
+            J.out_act = da;
+            J.item_packets = B;
+        }
         h_prefix[i] = n_items;
         n_items += (r.n + B - 1) / B;
     }
@@ -255,26 +279,30 @@ static cudaError_t launch_group(fw_server *sv, SvSlot &sl) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(sl.d_work, sl.h_work, po + (nj + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, sl.st);
     unsigned long long *d_next = reinterpret_cast<unsigned long long *>(sl.d_work);
-    const BatchJobDev *d_jobs = reinterpret_cast<const BatchJobDev *>(sl.d_work + 16);
     const int64_t *d_prefix = reinterpret_cast<const int64_t *>(sl.d_work + po);
     if (e == cudaSuccess) {
-        const int wpb = (sv->filter_only ? kBatchFilterThreads : sv->threads) / 32;
-        const int per_sm = sv->filter_only ? kBatchFilterMinBlocks : 2;
+        const int wpb = (fo ? kBatchFilterThreads : sv->threads) / 32;
+        const int per_sm = fo ? kBatchFilterMinBlocks : 2;
         // alone on the device a group takes every SM it can use (one item a warp: the lowest
         // latency); beside other groups a small one gets fewer blocks (each warp several items),
         // leaving SMs to them
         const int64_t per_block = (int64_t)wpb * (sl.beside > 0 ? sv->cfg.items_per_warp : 1);
         const int64_t blocks = std::max<int64_t>(
             1, std::min<int64_t>((int64_t)sm_count(sv->device) * per_sm, (n_items + per_block - 1) / per_block));
-        e = launch_batch_kernel(d_jobs, d_prefix, (int32_t)nj, n_items, d_next, sv->qcap, sv->threads, blocks, sl.st,
-                         sv->filter_only ? kBatchFilterMinBlocks : 0);
+        if (fo)
+            e = launch_batch_filter(reinterpret_cast<const BatchFilterJob *>(sl.d_work + 16), sv->d_fsets, d_prefix,
+                                    (int32_t)nj, n_items, d_next, blocks, sl.st, kBatchFilterMinBlocks);
+        else
+            e = launch_batch(reinterpret_cast<const BatchJobDev *>(sl.d_work + 16), d_prefix, (int32_t)nj, n_items,
+                             d_next, sv->qcap, sv->threads, blocks, sl.st);
     }
     if (copy) {
         for (size_t i = 0; i < nj && e == cudaSuccess; ++i) {
             const SvRequest &r = entry(sv, sl.g_lo + sl.order[i]);
-            const BatchJobDev &J = h_jobs[i];
-            e = cudaMemcpyAsync(r.out_idx, J.out_idx, 4 * (size_t)r.n, cudaMemcpyDeviceToHost, sl.st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(r.out_act, J.out_act, (size_t)r.n, cudaMemcpyDeviceToHost, sl.st);
+            const int32_t *oi = fo ? h_fjobs[i].out_idx : h_jobs[i].out_idx;
+            const uint8_t *oa = fo ? h_fjobs[i].out_act : h_jobs[i].out_act;
+            e = cudaMemcpyAsync(r.out_idx, oi, 4 * (size_t)r.n, cudaMemcpyDeviceToHost, sl.st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(r.out_act, oa, (size_t)r.n, cudaMemcpyDeviceToHost, sl.st);
         }
     }
     if (e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.st);
@@ -342,6 +370,8 @@ static void worker_loop(fw_server *sv) {
         for (int i = 0; i < ns && sv->admit_next < sv->next_ticket; ++i) {
             SvSlot &sl = sv->slots[i];
             if (sl.busy) continue;
+            // enough groups in flight: let the queue grow into a full group (fewer, larger launches)
+            if (busy >= sv->cfg.busy_groups && sv->queued_packets < sv->cfg.max_group_packets) break;
             const uint64_t queued = sv->next_ticket - sv->admit_next;
             uint64_t take = 0;
             size_t bytes = 0;
@@ -363,6 +393,7 @@ static void worker_loop(fw_server *sv) {
                 }
                 if (take == 0) break;  // wait for memory to free up
             }
+            sv->queued_packets -= pk;
             sl.g_lo = sv->admit_next;
             sl.g_hi = sv->admit_next + take;
             sl.beside = busy;
@@ -400,8 +431,19 @@ static void worker_loop(fw_server *sv) {
         const bool queued = sv->admit_next < sv->next_ticket;
         if (sv->stop && !queued && busy == 0) break;
         if (busy == 0 && !queued) {
-            sv->cv_work.wait(lk);
+            if (sv->hold_awake.load(std::memory_order_acquire)) {
+                sv->is_awake.store(true, std::memory_order_release);
+                const uint64_t seen = sv->enq_count.load(std::memory_order_acquire);
+                lk.unlock();
+                while (sv->hold_awake.load(std::memory_order_acquire) &&
+                       sv->enq_count.load(std::memory_order_acquire) == seen)
+                    std::this_thread::yield();
+                lk.lock();
+            } else {
+                sv->cv_work.wait(lk);
+            }
         } else {
+            if (sv->hold_awake.load(std::memory_order_relaxed)) sv->is_awake.store(true, std::memory_order_relaxed);
             lk.unlock();
             std::this_thread::yield();
             lk.lock();
@@ -455,6 +497,7 @@ extern "C" void fw_server_destroy(fw_server *sv) {
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         sv->stop = true;
+        sv->hold_awake.store(false, std::memory_order_release);
     }
     sv->cv_work.notify_all();
     if (sv->worker.joinable()) sv->worker.join();
@@ -466,6 +509,7 @@ extern "C" void fw_server_destroy(fw_server *sv) {
         cudaFreeHost(sl.h_work);
     }
     cudaFree(sv->d_arena);
+    cudaFree(sv->d_fsets);
     for (SvRequest *c : sv->ring) delete[] c;
     delete sv;
 }
@@ -491,10 +535,11 @@ extern "C" int fw_server_create(const fw_ruleset *const *sets, int n_sets, const
     if (c.segment_rules == 0) c.segment_rules = 64;
     if (c.block_threads == 0) c.block_threads = 512;
     if (c.items_per_warp == 0) c.items_per_warp = 1;
+    if (c.busy_groups == 0) c.busy_groups = 2;
     if (c.slots < 1 || c.slots > 16 || c.max_group_requests < 1 || c.max_pending < 1 || c.max_group_packets < 1 ||
         c.arena_bytes < 4096 || c.packets_per_item % 128 != 0 || c.packets_per_item > 4096 ||
         c.segment_rules % 4 != 0 || c.segment_rules < 4 || c.block_threads % 32 != 0 || c.block_threads > 1024 ||
-        c.items_per_warp < 1)
+        c.items_per_warp < 1 || c.busy_groups < 1)
         return set_status(FW_EINVAL);
     for (int32_t r : c.reserved)
         if (r != 0) return set_status(FW_EINVAL);
@@ -545,10 +590,16 @@ extern "C" int fw_server_create(const fw_ruleset *const *sets, int n_sets, const
     for (SvSlot &sl : sv->slots) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
-        const size_t work_bytes =
-            16 + a16(c.max_group_requests * sizeof(BatchJobDev)) + (c.max_group_requests + 1) * sizeof(int64_t);
+        const size_t work_bytes = 16 + a16(c.max_group_requests * std::max(sizeof(BatchJobDev), sizeof(BatchFilterJob))) +
+                                  (c.max_group_requests + 1) * sizeof(int64_t);
         if (e == cudaSuccess) e = dev_malloc(&sl.d_work, work_bytes);
         if (e == cudaSuccess) e = pinned_malloc(&sl.h_work, work_bytes);
+    }
+    if (e == cudaSuccess && sv->filter_only) {
+        std::vector<BatchFilterSet> fs((size_t)n_sets);
+        for (int i = 0; i < n_sets; ++i) fs[(size_t)i] = batch_filter_set(sets[i]);
+        e = dev_malloc(&sv->d_fsets, fs.size() * sizeof(BatchFilterSet));
+        if (e == cudaSuccess) e = cudaMemcpy(sv->d_fsets, fs.data(), fs.size() * sizeof(BatchFilterSet), cudaMemcpyHostToDevice);
     }
     if (e != cudaSuccess) {
         fw_server_destroy(sv);
@@ -641,11 +692,13 @@ static int64_t enqueue_requests(fw_server *sv, const SvRequest *rs, int64_t coun
             e.status = 1;
             e.t_submit = t;
             e.t_done = 0;
+            sv->queued_packets += e.n;
             sv->next_ticket = tk + 1;
             sv->stats.submitted += 1;
             tickets[k] = tk;
         }
         sv->stats.submit_ns += now_ns() - t_start_ns;
+        if (k > 0) sv->enq_count.fetch_add((uint64_t)k, std::memory_order_release);
     }
     if (k > 0) sv->cv_work.notify_one();
     return k;
@@ -724,6 +777,16 @@ extern "C" int fw_server_replay(fw_server *sv, fw_request *reqs, int64_t n, int6
     std::vector<int64_t> batch_req((size_t)kBatch);
     std::vector<uint64_t> batch_tickets((size_t)kBatch);
     size_t hint[7] = {};
+    // wake the scheduler and keep it polling while the requests are submitted, as under steady
+    // traffic (waking a sleeping thread takes tens of microseconds); the clock starts once it is up
+    sv->is_awake.store(false, std::memory_order_release);
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->hold_awake.store(true, std::memory_order_release);
+    }
+    sv->cv_work.notify_one();
+    for (const double w0 = now_us(); !sv->is_awake.load(std::memory_order_acquire) && now_us() - w0 < 20000.0;)
+        std::this_thread::yield();
     const double t0 = now_us();
     // Open loop: every request is submitted at its arrival time; when the submitting thread is
     // behind, the requests already due go together.
@@ -758,6 +821,7 @@ extern "C" int fw_server_replay(fw_server *sv, fw_request *reqs, int64_t n, int6
         }
         i = j;
     }
+    sv->hold_awake.store(false, std::memory_order_release);
     int worst = FW_OK;
     for (int64_t i2 = 0; i2 < n; ++i2) {
         fw_request &q = reqs[i2];

@@ -106,7 +106,8 @@ class fw_server_config(ctypes.Structure):
                 ("max_pending", ctypes.c_int32), ("max_group_packets", ctypes.c_int64),
                 ("arena_bytes", ctypes.c_int64), ("packets_per_item", ctypes.c_int32),
                 ("segment_rules", ctypes.c_int32), ("block_threads", ctypes.c_int32),
-                ("items_per_warp", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("items_per_warp", ctypes.c_int32), ("busy_groups", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class fw_server_stats(ctypes.Structure):

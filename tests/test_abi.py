@@ -241,12 +241,12 @@ def test_server_rejects_bad_arguments(L):
     for kw in ({"mode": 3}, {"slots": 17}, {"slots": -1}, {"max_group_requests": -1}, {"max_pending": -1},
                {"max_group_packets": -1}, {"arena_bytes": 1000}, {"packets_per_item": 100},
                {"packets_per_item": 8192}, {"segment_rules": 6}, {"block_threads": 33}, {"block_threads": 2048},
-               {"block_threads": 1024, "packets_per_item": 4096}, {"items_per_warp": -1}):
+               {"block_threads": 1024, "packets_per_item": 4096}, {"items_per_warp": -1}, {"busy_groups": -1}):
         cfg = _cfg(fw.fw_server_config, **kw)
         assert L.fw_server_create(sets, 2, ctypes.byref(cfg), ctypes.byref(out)) == fw.FW_EINVAL, kw
         assert out.value is None
     cfg = fw.fw_server_config()
-    cfg.reserved[3] = 1  # reserved fields must be zero
+    cfg.reserved[1] = 1  # reserved fields must be zero
     assert L.fw_server_create(sets, 2, ctypes.byref(cfg), ctypes.byref(out)) == fw.FW_EINVAL
     ticket = ctypes.c_uint64()
     h = fw.fw_headers()
