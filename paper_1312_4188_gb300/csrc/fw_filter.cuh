@@ -105,14 +105,24 @@ __device__ __forceinline__ uint32_t filter_first(const unsigned char *base, cons
                                                  uint32_t one) {
     using M = FilterMask<W>;
     if (m == 0) return 0xFFFFFFFFu;
-    // class info: first stored record, exact mask (low, high word)
-    const uint4 ci = reinterpret_cast<const uint4 *>(base + v.classes)[cls];
-    const M ex = W == 1 ? (M)ci.y : (M)(((uint64_t)ci.z << 32) | ci.y);
-    const uint4 *V = reinterpret_cast<const uint4 *>(base + v.recs) + 2 * ci.x;
+    // class info: first stored record, exact mask (low, high word); one-word rows read only the
+    // first eight bytes (half the shared-memory wavefronts of the 16-byte entry)
+    uint32_t first;
+    M ex;
+    if constexpr (W == 1) {
+        const uint2 ci = reinterpret_cast<const uint2 *>(base + v.classes)[2 * cls];
+        first = ci.x;
+        ex = (M)ci.y;
+    } else {
+        const uint4 ci = reinterpret_cast<const uint4 *>(base + v.classes)[cls];
+        first = ci.x;
+        ex = (M)(((uint64_t)ci.z << 32) | ci.y);
+    }
+    const uint4 *V = reinterpret_cast<const uint4 *>(base + v.recs) + 2 * first;
     while (m != 0) {
         const int k = W == 1 ? __ffs((unsigned)m) - 1 : __ffsll((unsigned long long)m) - 1;
         if (((ex >> k) & 1u) || filter_mismatch(s, d, sp, dp, V[2 * k], V[2 * k + 1], one) == 0u)
-            return reinterpret_cast<const uint32_t *>(base + v.verdicts)[ci.x + k];
+            return reinterpret_cast<const uint32_t *>(base + v.verdicts)[first + k];
         m &= m - 1;
     }
     return 0xFFFFFFFFu;
