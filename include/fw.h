@@ -523,6 +523,130 @@ int fw_server_get_stats(fw_server *sv, fw_server_stats *st);
  */
 int fw_server_replay(fw_server *sv, fw_request *reqs, int64_t n, int64_t timeout_us);
 
+/* ------------------------------------------------------- device request queue */
+/*
+ * Continuous batching with the scheduling on the device. The host writes each
+ * request (a packet batch for one of the queue's rule sets) into a ring of
+ * descriptors in pinned host memory and publishes it by its ticket; nothing
+ * else happens on the host per request. One persistent kernel runs while
+ * requests keep coming: its first warp reads new descriptors from the ring,
+ * splits each request into work items of chunk_packets packets and releases
+ * them into a device item ring; every other warp claims item tickets from a
+ * global counter, classifies its item through the request's bucket filter
+ * (the routine of fw_classify's default packet split, Sec. IV.A) and, when it
+ * finishes a request's last item, stores the ticket into the request's
+ * completion word in pinned host memory, which fw_dqueue_wait polls. Requests
+ * that arrive while others run are taken up as soon as the reading warp sees
+ * them, and items of different requests and rule sets run side by side, so
+ * there are no groups and no launch per request. The paper's prototype
+ * collects packets, classifies them in one launch and hands the verdicts
+ * back (Sec. IV, Fig. 1) and names asynchronous launches as the next step
+ * (Sec. V); here the launch outlives the requests.
+ *
+ * Every device-side wait is bounded by %globaltimer: the reading warp gives up
+ * after idle_us without a new request (the kernel then exits, and the next
+ * submit launches it again, or, when the submit and the exit cross, the
+ * first wait that finds the request pending for 50 us; fw_dqueue_stats counts
+ * launches and exits), a kernel stops
+ * taking requests after life_ms (the host relaunches it), and a worker that
+ * waited over 4 x life_ms for its item sets an error flag and exits. While the
+ * kernel runs it holds blocks_per_sm x 512 threads on every SM; work on other
+ * streams waits for SMs it frees, at the latest idle_us after the last request.
+ *
+ * Results are exactly fw_classify's for each request. Every rule set must
+ * have a bucket filter (fw_ruleset_filter: words > 0). Request buffers must
+ * lie in ranges registered with fw_dqueue_register_buffer (device memory or
+ * pinned host memory) and stay valid until the request is waited for.
+ *
+ * fw_dqueue_config (zero = default):
+ *  ring:                requests in flight at once, a power of two 64..65536
+ *                       (default 4096); a ticket's ring entry is reused only
+ *                       after it was waited for.
+ *  chunk_packets:       packets per work item while at most 8 requests wait
+ *                       in the ring, a multiple of 64 up to 65536 (default
+ *                       64); the device takes 4x with up to 128 waiting and
+ *                       16x beyond (fewer, larger items under load).
+ *  blocks_per_sm:       1 or 2 (default 2) resident 512-thread blocks.
+ *  idle_us:             the kernel's idle limit (default 1000).
+ *  max_request_packets: largest request (default 65536); the item ring holds
+ *                       ring x ceil(max_request_packets / chunk_packets) items
+ *                       of 8 bytes, at most 2^26.
+ *  life_ms:             the kernel's time limit (default 2000).
+ *  poll_ns:             the longest sleep of a waiting worker between polls
+ *                       (from 32 ns, doubling; default 2048).
+ */
+typedef struct fw_dqueue_config {
+    int32_t ring;
+    int32_t chunk_packets;
+    int32_t blocks_per_sm;
+    int32_t idle_us;
+    int64_t max_request_packets;
+    int32_t life_ms;
+    int32_t poll_ns;
+    int32_t reserved[4];           /* must be zero */
+} fw_dqueue_config;
+
+typedef struct fw_dqueue_stats {
+    int64_t submitted, completed, packets;
+    int64_t launches;              /* persistent-kernel launches */
+    int64_t idle_exits;            /* launches that ended because no request came for idle_us */
+    int64_t life_exits;            /* launches that ended at life_ms */
+    int64_t fed_requests;          /* requests the device took from the ring */
+    int64_t fed_items;             /* work items it released */
+    int64_t device_status;         /* error flags: 1 = a worker's wait ran out */
+    int64_t submit_ns;             /* host time spent in submit */
+    int64_t feed_ns, feeds;        /* device time the reading warp spent taking requests, and how
+                                      many times it took some */
+    int64_t feed_read_ns;          /* the part of feed_ns spent reading ring entries */
+    int64_t work_ns, items_done;   /* device time workers spent on items (summed over warps), and
+                                      the items (these two and device_status are read while no
+                                      launch runs; they keep their last values otherwise) */
+} fw_dqueue_stats;
+
+typedef struct fw_dqueue fw_dqueue;
+
+/*
+ * Create a queue over n_sets rule sets (kept alive by the caller until
+ * destroy; all on the current device). FW_EINVAL for bad arguments, a bad
+ * config or a rule set without a bucket filter; FW_ERANGE when the item ring
+ * would exceed 2^26 items; FW_ENOMEM, FW_ECUDA. The kernel starts at the first
+ * submit.
+ */
+int fw_dqueue_create(const fw_ruleset *const *sets, int n_sets, const fw_dqueue_config *cfg, fw_dqueue **out);
+/* Stop the kernel (it finishes what it has taken), free everything. No request may be pending. */
+void fw_dqueue_destroy(fw_dqueue *q);
+/*
+ * Declare [p, p + bytes) (device memory or pinned host memory of the queue's
+ * device) as holding request buffers. FW_EINVAL if the range is not device
+ * accessible as one piece.
+ */
+int fw_dqueue_register_buffer(fw_dqueue *q, const void *p, size_t bytes);
+/*
+ * Queue a request of n (1..max_request_packets) packets for rule set `set`;
+ * returns at once with *ticket. FW_EBUSY when the ticket's ring entry still
+ * holds a request not waited for; FW_ERANGE for n above max_request_packets;
+ * FW_EINVAL for bad arguments or buffers outside the registered ranges.
+ * One thread at a time may submit.
+ */
+int fw_dqueue_submit(fw_dqueue *q, int set, const fw_headers *hdrs, int64_t n, int32_t *out_rule_idx,
+                     uint8_t *out_action, uint64_t *ticket);
+/*
+ * Wait for a request (timeout_us < 0: no limit). FW_OK: done, the ticket is
+ * released and *latency_us (may be NULL) holds completion minus submit time;
+ * FW_ETIMEOUT: not done yet (the ticket stays valid); FW_EINVAL for a ticket
+ * that is not pending; FW_ECUDA when the kernel failed.
+ */
+int fw_dqueue_wait(fw_dqueue *q, uint64_t ticket, int64_t timeout_us, double *latency_us);
+int fw_dqueue_get_stats(fw_dqueue *q, fw_dqueue_stats *st);
+/*
+ * Open-loop replay, as fw_server_replay: reqs[i] is submitted at arrival_us[i]
+ * after the call starts (retrying while its ring entry is busy), a second
+ * host thread records each completion as it happens, and status, latency_us
+ * (completion minus scheduled arrival) and submit_lag_us are filled in.
+ * Returns FW_OK when every request succeeded.
+ */
+int fw_dqueue_replay(fw_dqueue *q, fw_request *reqs, int64_t n, int64_t timeout_us);
+
 /* ------------------------------------------------------------ learned index */
 /*
  * Decomposition classifier with a learned locator (same result as

@@ -25,10 +25,6 @@
 
 namespace fwk {
 
-// Packets a lane of the batched filter path takes at a time. Two: on four rule sets of 1K..100K
-// rules (rows of 1..5 words) one launch over 37.7M packets ran at 82 Gpackets/s, against 77 with
-// one packet and 76 with four (whose state no longer fits the 64 registers of two blocks an SM).
-constexpr int kBatchFilterPackets = 2;
 
 // Claim the next item of a launch for the calling warp: its index from the global counter, its
 // job by a search of the item prefix (the last j with prefix[j] <= index). False when none is left.
@@ -50,68 +46,6 @@ __device__ __forceinline__ bool batch_claim(const BatchParams &p, int lane, int 
     job = __shfl_sync(0xFFFFFFFFu, j, 0);
     it = (int64_t)x;
     return true;
-}
-
-// One item of a job with a bucket filter, its block read through L1: P consecutive packets per
-// lane (item starts are multiples of four packets, so aligned arrays allow vector loads and
-// stores); the classes and first row words of a lane's packets are loaded together, then each
-// packet is resolved in turn (filter_packets_wide).
-template <int P>
-__device__ __forceinline__ void batch_filter_run(const BatchFilterJob &J, const BatchFilterSet &S,
-                                                 const BatchItem &item, int lane, uint32_t one) {
-    static_assert(P == 1 || P == 2, "one or two packets a lane");
-    const FilterView fv = S.fv;
-    const unsigned char *__restrict__ base = S.filter;
-    const int64_t st = item.start;
-    const bool vin = J.vec != 0;
-    const bool vout = vin && (reinterpret_cast<uintptr_t>(J.out_idx + st) % (4 * P) == 0) &&
-                      (reinterpret_cast<uintptr_t>(J.out_act + st) % P == 0);
-    for (int q = P * lane; q < item.count; q += 32 * P) {
-        const int64_t i = st + q;
-        const int m = min(P, item.count - q);
-        uint32_t s[P], d[P], sp[P], dp[P], pr[P], vw[P];
-        if (P == 2 && vin && m == P) {
-            const uint2 a = __ldcs(reinterpret_cast<const uint2 *>(J.h.src + i));
-            const uint2 b = __ldcs(reinterpret_cast<const uint2 *>(J.h.dst + i));
-            const uint32_t c = __ldcs(reinterpret_cast<const unsigned int *>(J.h.sport + i));
-            const uint32_t e = __ldcs(reinterpret_cast<const unsigned int *>(J.h.dport + i));
-            const uint32_t f = __ldcs(reinterpret_cast<const unsigned short *>(J.h.proto + i));
-            s[0] = a.x; s[P - 1] = a.y;
-            d[0] = b.x; d[P - 1] = b.y;
-            sp[0] = c & 0xFFFFu; sp[P - 1] = c >> 16;
-            dp[0] = e & 0xFFFFu; dp[P - 1] = e >> 16;
-            pr[0] = f & 0xFFu; pr[P - 1] = f >> 8;
-        } else {
-#pragma unroll
-            for (int k = 0; k < P; ++k) {
-                const int64_t ik = k < m ? i + k : i;  // past the item's end: a copy of its first packet
-                s[k] = J.h.src[ik];
-                d[k] = J.h.dst[ik];
-                sp[k] = J.h.sport[ik];
-                dp[k] = J.h.dport[ik];
-                pr[k] = J.h.proto[ik];
-            }
-        }
-        filter_packets_wide<P>(base, fv, s, d, sp, dp, pr, one, vw);
-        int32_t oi[P];
-        uint32_t oa = 0;
-#pragma unroll
-        for (int k = 0; k < P; ++k) {
-            oi[k] = vw[k] == 0xFFFFFFFFu ? -1 : (int32_t)(vw[k] & 0x7FFFFFFFu);
-            oa |= (vw[k] == 0xFFFFFFFFu ? (uint32_t)FW_DROP : (vw[k] >> 31)) << (8 * k);
-        }
-        if (P == 2 && vout && m == P) {
-            __stcs(reinterpret_cast<int2 *>(J.out_idx + i), make_int2(oi[0], oi[P - 1]));
-            __stcs(reinterpret_cast<unsigned short *>(J.out_act + i), (unsigned short)oa);
-        } else {
-#pragma unroll
-            for (int k = 0; k < P; ++k)
-                if (k < m) {
-                    J.out_idx[i + k] = oi[k];
-                    J.out_act[i + k] = (uint8_t)(oa >> (8 * k));
-                }
-        }
-    }
 }
 
 // A filter job's item inside the general kernel (whose jobs carry their rule set's fields). Kept

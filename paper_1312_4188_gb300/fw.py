@@ -122,6 +122,19 @@ class fw_request(ctypes.Structure):
                 ("latency_us", ctypes.c_double), ("submit_lag_us", ctypes.c_double)]
 
 
+class fw_dqueue_config(ctypes.Structure):
+    _fields_ = [("ring", ctypes.c_int32), ("chunk_packets", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("idle_us", ctypes.c_int32), ("max_request_packets", ctypes.c_int64), ("life_ms", ctypes.c_int32),
+                ("poll_ns", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+
+
+class fw_dqueue_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "completed", "packets", "launches", "idle_exits",
+                                               "life_exits", "fed_requests", "fed_items", "device_status",
+                                               "submit_ns", "feed_ns", "feeds", "feed_read_ns", "work_ns",
+                                               "items_done")]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -171,6 +184,15 @@ SIGNATURES = {
     "fw_server_unregister_buffer": (ctypes.c_int, [P, P]),
     "fw_server_get_stats": (ctypes.c_int, [P, ctypes.POINTER(fw_server_stats)]),
     "fw_server_replay": (ctypes.c_int, [P, ctypes.POINTER(fw_request), I64, I64]),
+    "fw_dqueue_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(fw_dqueue_config),
+                                        ctypes.POINTER(P)]),
+    "fw_dqueue_destroy": (None, [P]),
+    "fw_dqueue_register_buffer": (ctypes.c_int, [P, P, ctypes.c_size_t]),
+    "fw_dqueue_submit": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(fw_headers), I64, P, P,
+                                        ctypes.POINTER(ctypes.c_uint64)]),
+    "fw_dqueue_wait": (ctypes.c_int, [P, ctypes.c_uint64, I64, ctypes.POINTER(ctypes.c_double)]),
+    "fw_dqueue_get_stats": (ctypes.c_int, [P, ctypes.POINTER(fw_dqueue_stats)]),
+    "fw_dqueue_replay": (ctypes.c_int, [P, ctypes.POINTER(fw_request), I64, I64]),
     "fw_int32_peak_launch": (ctypes.c_int, [ctypes.c_int, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P,
                                             ctypes.POINTER(I64)]),
     "fw_last_status": (ctypes.c_int, []),
@@ -559,6 +581,73 @@ class Server:
     def destroy(self):
         if self.handle is not None and self.handle.value:
             lib().fw_server_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class DeviceQueue:
+    """Owning wrapper of an ``fw_dqueue*`` (continuous batching scheduled on the device by one
+    persistent kernel). Request buffers must lie in registered tensors."""
+
+    def __init__(self, rulesets, **cfg):
+        self._sets = list(rulesets)
+        arr = (ctypes.c_void_p * len(self._sets))(*[r.handle.value for r in self._sets])
+        c = fw_dqueue_config()
+        for k, v in cfg.items():
+            setattr(c, k, int(v))
+        out = ctypes.c_void_p()
+        _check(lib().fw_dqueue_create(arr, len(self._sets), ctypes.byref(c), ctypes.byref(out)), "fw_dqueue_create")
+        self.handle = out
+
+    def register(self, tensor):
+        """Declare a tensor's storage as holding request buffers (see fw_dqueue_register_buffer)."""
+        _check(lib().fw_dqueue_register_buffer(self.handle, ctypes.c_void_p(tensor.data_ptr()),
+                                               tensor.numel() * tensor.element_size()), "fw_dqueue_register_buffer")
+
+    def submit(self, set_index: int, hdrs: dict, out_idx, out_act, n: int | None = None) -> int:
+        """Queue a request; returns its ticket. Raises FwError (e.g. FW_EBUSY when its ring entry is held)."""
+        if n is None:
+            n = int(hdrs["src"].shape[0])
+        hs = headers_struct(hdrs)
+        t = ctypes.c_uint64()
+        s = lib().fw_dqueue_submit(self.handle, int(set_index), ctypes.byref(hs), int(n),
+                                   ctypes.c_void_p(out_idx.data_ptr()), ctypes.c_void_p(out_act.data_ptr()),
+                                   ctypes.byref(t))
+        _check(s, "fw_dqueue_submit")
+        return int(t.value)
+
+    def wait(self, ticket: int, timeout_us: int = -1):
+        """(status, latency_us) of a request; FW_OK releases the ticket."""
+        lat = ctypes.c_double()
+        s = lib().fw_dqueue_wait(self.handle, ctypes.c_uint64(ticket), int(timeout_us), ctypes.byref(lat))
+        return int(s), float(lat.value)
+
+    def stats(self) -> dict:
+        st = fw_dqueue_stats()
+        _check(lib().fw_dqueue_get_stats(self.handle, ctypes.byref(st)), "fw_dqueue_get_stats")
+        return {k: int(getattr(st, k)) for k, _ in fw_dqueue_stats._fields_}
+
+    def replay(self, specs, timeout_us: int = 60_000_000):
+        """``specs``: list of (set, hdrs dict, out_idx, out_act, arrival_us). Returns (status, status array,
+        latency array); ``last_submit_lag_us`` keeps each request's wait for the submitting thread."""
+        arr = (fw_request * len(specs))()
+        for i, (st, h, oi, oa, t) in enumerate(specs):
+            arr[i] = fw_request(int(st), 0, headers_struct(h), int(h["src"].shape[0]), ctypes.c_void_p(oi.data_ptr()),
+                                ctypes.c_void_p(oa.data_ptr()), float(t), 0.0)
+        s = lib().fw_dqueue_replay(self.handle, arr, len(specs), int(timeout_us))
+        status = np.array([r.status for r in arr], dtype=np.int32)
+        lat = np.array([r.latency_us for r in arr], dtype=np.float64)
+        self.last_submit_lag_us = np.array([r.submit_lag_us for r in arr], dtype=np.float64)
+        return int(s), status, lat
+
+    def destroy(self):
+        if self.handle is not None and self.handle.value:
+            lib().fw_dqueue_destroy(self.handle)
         self.handle = None
 
     def __del__(self):

@@ -152,7 +152,7 @@ def test_int32_peak_rejects_bad_arguments(L):
 
 
 STRUCTS = ("fw_headers", "fw_config", "fw_lindex_config", "fw_lindex_stats", "fw_job", "fw_plan_config",
-           "fw_server_config", "fw_server_stats", "fw_request")
+           "fw_server_config", "fw_server_stats", "fw_request", "fw_dqueue_config", "fw_dqueue_stats")
 
 
 def test_binding_structs_match_header(tmp_path):
@@ -258,6 +258,34 @@ def test_server_rejects_bad_arguments(L):
     assert L.fw_server_unregister_buffer(None, None) == fw.FW_EINVAL
     assert L.fw_server_replay(None, None, 0, 0) == fw.FW_EINVAL
     L.fw_server_destroy(None)
+
+
+def test_dqueue_rejects_bad_arguments(L):
+    out = ctypes.c_void_p()
+    sets = (ctypes.c_void_p * 2)(1, 1)  # never dereferenced: configuration checks come first
+    nulls = (ctypes.c_void_p * 2)(None, None)
+    assert L.fw_dqueue_create(sets, 2, None, None) == fw.FW_EINVAL
+    assert L.fw_dqueue_create(sets, 0, None, ctypes.byref(out)) == fw.FW_EINVAL
+    assert L.fw_dqueue_create(None, 2, None, ctypes.byref(out)) == fw.FW_EINVAL
+    assert L.fw_dqueue_create(nulls, 2, None, ctypes.byref(out)) == fw.FW_EINVAL
+    for kw in ({"ring": 63}, {"ring": 100}, {"ring": 1 << 17}, {"ring": -64}, {"chunk_packets": 32},
+               {"chunk_packets": 100}, {"chunk_packets": -64}, {"blocks_per_sm": 3}, {"blocks_per_sm": -1},
+               {"idle_us": -1}, {"life_ms": -1}, {"poll_ns": -1}, {"max_request_packets": -1},
+               {"max_request_packets": 1 << 31}):
+        cfg = _cfg(fw.fw_dqueue_config, **kw)
+        assert L.fw_dqueue_create(sets, 2, ctypes.byref(cfg), ctypes.byref(out)) == fw.FW_EINVAL, kw
+        assert out.value is None
+    cfg = fw.fw_dqueue_config()
+    cfg.reserved[2] = 1  # reserved fields must be zero
+    assert L.fw_dqueue_create(sets, 2, ctypes.byref(cfg), ctypes.byref(out)) == fw.FW_EINVAL
+    ticket = ctypes.c_uint64()
+    h = fw.fw_headers()
+    assert L.fw_dqueue_submit(None, 0, ctypes.byref(h), 10, None, None, ctypes.byref(ticket)) == fw.FW_EINVAL
+    assert L.fw_dqueue_wait(None, 1, 0, None) == fw.FW_EINVAL
+    assert L.fw_dqueue_get_stats(None, None) == fw.FW_EINVAL
+    assert L.fw_dqueue_register_buffer(None, None, 0) == fw.FW_EINVAL
+    assert L.fw_dqueue_replay(None, None, 0, 0) == fw.FW_EINVAL
+    L.fw_dqueue_destroy(None)
 
 
 def test_host_pipeline_rejects_bad_arguments(L):
