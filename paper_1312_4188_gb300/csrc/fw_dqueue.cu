@@ -216,6 +216,7 @@ __device__ __noinline__ void dq_feeder(const DqParams &p, int warp, int lane) {
     uint64_t fed_req = 0, fed_items = 0, feed_ns = 0, feeds = 0, feed_read_ns = 0;
     const uint64_t t_start = warp_ns();
     uint64_t t_work = t_start, t_pass = t_start, backlog = 0;
+    uint32_t nap = 32;
     int why = 0;  // 1 idle, 2 life, 3 stop
     if (tid == 0) st_release_sys(&ctl->state, epoch << 2 | kPhaseRunning);
     for (;;) {
@@ -237,13 +238,16 @@ __device__ __noinline__ void dq_feeder(const DqParams &p, int warp, int lane) {
                 const uint64_t now = warp_ns();
                 const bool life = now - t_start > life_ns;
                 if (tail > head && !life) {
+                    nap = 32;
                     k = (int)min(tail - head, (uint64_t)kFeedBatch);
                     backlog = tail - head;
                     t_pass = now;
                     break;
                 }
                 if (!life && now - t_work <= idle_ns) {
-                    __nanosleep(32);
+                    // back off from 32 to 512 ns while idle: every poll reads the host's tail line
+                    __nanosleep(nap);
+                    nap = min(2u * nap, 512u);
                     continue;
                 }
                 // leaving: announce it, then look once more (a request that arrived meanwhile
@@ -544,7 +548,12 @@ struct fw_dqueue {
     uint64_t launched = 0;           // epochs launched
     bool launch_failed = false;
     fwk::DqDev last_dev{};           // the device state as last read between launches
-    std::atomic<int64_t> submitted{0}, completed{0}, packets{0}, submit_ns{0};
+    // counters of the submitting side and of the completing side on cache lines of their own
+    alignas(64) std::atomic<int64_t> submitted{0};
+    std::atomic<int64_t> submit_ns{0};
+    alignas(64) std::atomic<int64_t> completed{0};
+    std::atomic<int64_t> packets{0};
+    char counters_pad[48];
 };
 
 using namespace fwk;
