@@ -537,6 +537,7 @@ struct fw_dqueue {
     std::vector<const fw_ruleset *> sets;
     std::mutex reg_mu;
     std::vector<fwk::DqRange> ranges;
+    size_t hint[7] = {};  // fw_dqueue_submit's range hints (under reg_mu)
     std::mutex mu;  // the submitting side: next_ticket and the ring entries it writes
     uint64_t next_ticket = 1;
     // per ring entry: the ticket submitted and not yet released (0 = free); released by waiters
@@ -622,11 +623,24 @@ int dq_kick(fw_dqueue *q, bool check_event) {
     return s2;
 }
 
-// Device-accessible alias of [p, p + bytes) when it lies in one registered range, else 0.
-uint64_t dq_alias(fw_dqueue *q, const void *p, size_t bytes) {
+// Device-accessible alias of [p, p + bytes) when it lies in one registered range, else 0. The
+// range that matched last for this argument (*hint) is tried first: a caller's requests usually
+// come from the same few buffers.
+uint64_t dq_alias(fw_dqueue *q, const void *p, size_t bytes, size_t *hint) {
     const uintptr_t a = reinterpret_cast<uintptr_t>(p);
-    for (const DqRange &r : q->ranges)
-        if (a >= r.lo && a + bytes <= r.hi && a + bytes >= a) return (uint64_t)(a + r.delta);
+    if (a + bytes < a) return 0;
+    const size_t nr = q->ranges.size();
+    if (*hint < nr) {
+        const DqRange &r = q->ranges[*hint];
+        if (a >= r.lo && a + bytes <= r.hi) return (uint64_t)(a + r.delta);
+    }
+    for (size_t i = 0; i < nr; ++i) {
+        const DqRange &r = q->ranges[i];
+        if (a >= r.lo && a + bytes <= r.hi) {
+            *hint = i;
+            return (uint64_t)(a + r.delta);
+        }
+    }
     return 0;
 }
 
@@ -792,16 +806,16 @@ namespace {
 // Check one request and fill its ring entry (all but seq) with device-accessible addresses.
 // Caller holds reg_mu.
 int dq_prepare(fw_dqueue *q, int set, const fw_headers *hdrs, int64_t n, int32_t *out_idx, uint8_t *out_act,
-               DqHostReq *e) {
+               DqHostReq *e, size_t (&hint)[7]) {
     if (set < 0 || set >= (int)q->sets.size() || hdrs == nullptr || n < 1 || out_idx == nullptr ||
         out_act == nullptr)
         return FW_EINVAL;
     if (n > q->cfg.max_request_packets) return FW_ERANGE;
     const size_t m = (size_t)n;
-    const uint64_t a[7] = {dq_alias(q, hdrs->src, 4 * m),   dq_alias(q, hdrs->dst, 4 * m),
-                           dq_alias(q, hdrs->sport, 2 * m), dq_alias(q, hdrs->dport, 2 * m),
-                           dq_alias(q, hdrs->proto, m),     dq_alias(q, out_idx, 4 * m),
-                           dq_alias(q, out_act, m)};
+    const uint64_t a[7] = {dq_alias(q, hdrs->src, 4 * m, &hint[0]),   dq_alias(q, hdrs->dst, 4 * m, &hint[1]),
+                           dq_alias(q, hdrs->sport, 2 * m, &hint[2]), dq_alias(q, hdrs->dport, 2 * m, &hint[3]),
+                           dq_alias(q, hdrs->proto, m, &hint[4]),     dq_alias(q, out_idx, 4 * m, &hint[5]),
+                           dq_alias(q, out_act, m, &hint[6])};
     for (int k = 0; k < 7; ++k)
         if (a[k] == 0) return FW_EINVAL;
     const fw_headers dh{reinterpret_cast<const uint32_t *>(a[0]), reinterpret_cast<const uint32_t *>(a[1]),
@@ -855,7 +869,7 @@ extern "C" int fw_dqueue_submit(fw_dqueue *q, int set, const fw_headers *hdrs, i
     int s;
     {
         std::lock_guard<std::mutex> lk(q->reg_mu);
-        s = dq_prepare(q, set, hdrs, n, out_rule_idx, out_action, &e);
+        s = dq_prepare(q, set, hdrs, n, out_rule_idx, out_action, &e, q->hint);
     }
     if (s != FW_OK) return set_status(s);
     if (dq_publish(q, &e, 1, ticket) != 1) return set_status(FW_EBUSY);
@@ -970,6 +984,7 @@ extern "C" int fw_dqueue_replay(fw_dqueue *q, fw_request *reqs, int64_t n, int64
     // Open loop: every request is submitted at its arrival time; when the submitting thread is
     // behind, the requests already due are prepared together and published in one pass.
     constexpr int64_t kBatch = 64;
+    size_t hint[7] = {};
     DqHostReq batch[kBatch];
     int64_t batch_req[kBatch];
     uint64_t batch_tickets[kBatch];
@@ -983,7 +998,7 @@ extern "C" int fw_dqueue_replay(fw_dqueue *q, fw_request *reqs, int64_t n, int64
             std::lock_guard<std::mutex> lk(q->reg_mu);
             while (j < n && nb < kBatch && (j == i || now >= t0 + reqs[j].arrival_us)) {
                 fw_request &r = reqs[j];
-                r.status = dq_prepare(q, r.set, &r.hdrs, r.n, r.out_rule_idx, r.out_action, &batch[nb]);
+                r.status = dq_prepare(q, r.set, &r.hdrs, r.n, r.out_rule_idx, r.out_action, &batch[nb], hint);
                 if (r.status == FW_OK) batch_req[nb++] = j;
                 ++j;
             }
