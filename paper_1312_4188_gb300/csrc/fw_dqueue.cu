@@ -546,8 +546,9 @@ struct fw_dqueue {
     std::vector<double> t_submit;    // per ring entry
     std::vector<int64_t> n_of;       // per ring entry: packets
     std::mutex launch_mu;
-    uint64_t launched = 0;           // epochs launched
-    bool launch_failed = false;
+    // epochs launched; written under launch_mu, read without it by the submit and poll paths
+    std::atomic<uint64_t> launched{0};
+    std::atomic<bool> launch_failed{false};
     fwk::DqDev last_dev{};           // the device state as last read between launches
     // counters of the submitting side and of the completing side on cache lines of their own
     alignas(64) std::atomic<int64_t> submitted{0};
@@ -576,7 +577,7 @@ int dq_launch(fw_dqueue *q) {
     p.ring_mask = q->ring_mask;
     p.items_mask = q->items_mask;
     p.items_log2 = q->items_log2;
-    p.epoch = q->launched + 1;
+    p.epoch = q->launched.load() + 1;
     p.idle_ns = (uint64_t)q->cfg.idle_us * 1000ull;
     p.life_ns = (uint64_t)q->cfg.life_ms * 1000000ull;
     p.worker_limit_ns = 4ull * p.life_ns + p.idle_ns;
@@ -590,31 +591,40 @@ int dq_launch(fw_dqueue *q) {
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaEventRecord(q->ev_last, q->st);
     if (e != cudaSuccess) {
-        q->launch_failed = true;
+        q->launch_failed.store(true);
         return cuda_status(e);
     }
-    q->launched = p.epoch;
+    q->launched.store(p.epoch);
     return FW_OK;
 }
 
-// Launch the kernel again when the latest launch announced that it leaves, or (check_event) has
-// finished while requests may be pending.
-int dq_kick(fw_dqueue *q, bool check_event) {
+// Whether a launch is due: the latest launch announced that it leaves, or (check_event) it has
+// finished while requests may be pending. -1 when the queue's launches failed.
+int dq_need_launch(fw_dqueue *q, bool check_event) {
+    if (q->launch_failed.load()) return -1;
     const uint64_t s = __atomic_load_n(&q->ctl->state, __ATOMIC_ACQUIRE);
-    std::lock_guard<std::mutex> lk(q->launch_mu);
-    if (q->launch_failed) return FW_ECUDA;
-    bool need = q->launched == 0 || ((s >> 2) == q->launched && (s & 3u) >= kPhaseExiting);
-    if (!need && check_event) {
-        const cudaError_t e = cudaEventQuery(q->ev_last);
-        if (e == cudaSuccess) {
-            need = true;
-        } else if (e != cudaErrorNotReady) {
-            cudaGetLastError();
-            q->launch_failed = true;
-            return FW_ECUDA;
-        }
+    const uint64_t launched = q->launched.load();
+    if (launched == 0 || ((s >> 2) == launched && (s & 3u) >= kPhaseExiting)) return 1;
+    if (!check_event) return 0;
+    const cudaError_t e = cudaEventQuery(q->ev_last);
+    if (e == cudaSuccess) return 1;
+    if (e != cudaErrorNotReady) {
+        cudaGetLastError();
+        q->launch_failed.store(true);
+        return -1;
     }
-    if (!need) return FW_OK;
+    return 0;
+}
+
+// Launch the kernel again when it is due. The check runs without the lock (it is on every
+// submit); a launch takes the lock and checks again.
+int dq_kick(fw_dqueue *q, bool check_event) {
+    int need = dq_need_launch(q, check_event);
+    if (need == 0) return FW_OK;
+    if (need < 0) return FW_ECUDA;
+    std::lock_guard<std::mutex> lk(q->launch_mu);
+    need = dq_need_launch(q, check_event);
+    if (need <= 0) return need == 0 ? FW_OK : FW_ECUDA;
     int prev = q->device;
     cudaGetDevice(&prev);
     if (prev != q->device) cudaSetDevice(q->device);
@@ -911,7 +921,7 @@ extern "C" int fw_dqueue_get_stats(fw_dqueue *q, fw_dqueue_stats *st) {
     st->packets = q->packets.load();
     {
         std::lock_guard<std::mutex> lk(q->launch_mu);
-        st->launches = (int64_t)q->launched;
+        st->launches = (int64_t)q->launched.load();
     }
     st->idle_exits = (int64_t)__atomic_load_n(&q->ctl->idle_exits, __ATOMIC_ACQUIRE);
     st->life_exits = (int64_t)__atomic_load_n(&q->ctl->life_exits, __ATOMIC_ACQUIRE);
