@@ -302,7 +302,10 @@ int fw_ruleset_filter(const fw_ruleset *rs, int32_t *words, int64_t *bytes);
  *  ({saddr & smask, smask, daddr & dmask, dmask} and {-sport_lo,
  *  sport_hi - sport_lo, -dport_lo, dport_hi - dport_lo}, mod 2^32); R verdict
  *  words (original rule index | action << 31); the 256-byte protocol ->
- *  protocol class table.
+ *  protocol class table; for W >= 32, row summaries, [class][table][256]
+ *  rows of ceil(W / 32) uint32 words (bit w set when word w of the row is not
+ *  zero: a packet reads only the words set in the AND of its three
+ *  summaries).
  * FW_EINVAL as fw_partition_plan, or for NULL bytes/words, capacity < 0, or a
  * NULL block with capacity > 0; FW_ERANGE when 0 < capacity < the block size.
  * With capacity 0 only the sizes are returned.

@@ -65,12 +65,13 @@ struct FilterParams {
 };
 
 // Verdict word of one packet (~0u when no rule matches). W = 1, 2: one-integer
-// rows from `base` (shared memory); W = 0: rows of any width from global memory.
+// rows from `base` (shared memory); W = 0: rows of any width from global memory;
+// W = -1: the same, rows with summaries.
 template <int W, int KEY>
 __device__ __forceinline__ uint32_t filter_verdict(const unsigned char *base, const FilterParams &p, uint32_t s,
                                                    uint32_t d, uint32_t sp, uint32_t dp, uint32_t pr) {
-    if constexpr (W == 0) {
-        return filter_packet_wide<KEY>(base, p.v, s, d, sp, dp, pr, p.one);
+    if constexpr (W <= 0) {
+        return filter_packet_wide<KEY, (W < 0)>(base, p.v, s, d, sp, dp, pr, p.one);
     } else {
         uint32_t cls;
         const FilterMask<W> m = filter_candidates<W, KEY>(base, p.v, s, d, sp, dp, pr, cls);
@@ -230,10 +231,11 @@ __global__ void __launch_bounds__(512, 3) k_packet_split_filter(FilterParams p) 
     }
 }
 
-// Rows wider than two words: the filter block is read from global memory (L1).
-template <int KEY, bool VEC>
-__global__ void __launch_bounds__(512, 3) k_packet_split_filter_wide(FilterParams p) {
-    filter_loop<0, KEY, VEC>(p, p.blk);
+// Rows wider than two words: the filter block is read from global memory (L1); SUMM: the rows
+// carry summaries.
+template <int KEY, bool VEC, bool SUMM>
+__global__ void __launch_bounds__(512, SUMM ? 2 : 3) k_packet_split_filter_wide(FilterParams p) {
+    filter_loop<SUMM ? -1 : 0, KEY, VEC>(p, p.blk);
 }
 
 // ------------------------------------------------------------ host side
@@ -298,6 +300,18 @@ int filter_block(const fw_rule *rules, const std::vector<std::vector<int64_t>> &
             if (whole) exact[j >> 5] |= 1u << (j & 31);
         }
         cinfo[c] = make_uint4((uint32_t)class_off[c], exact[0], W > 1 ? exact[1] : 0u, 0u);
+        // summaries of wide rows: bit w of a row's summary set when its word w is not zero
+        const int S = filter_summary_words(W);
+        if (S > 0) {
+            uint32_t *summ = reinterpret_cast<uint32_t *>(blk.data() + L.summary);
+            for (int t = 0; t < kFilterTables; ++t)
+                for (uint32_t b = 0; b < 256; ++b) {
+                    const uint32_t *rw = row(c, t, b);
+                    uint32_t *sw = summ + (((size_t)c * kFilterTables + t) * 256 + b) * S;
+                    for (int w = 0; w < W; ++w)
+                        if (rw[w] != 0u) sw[w >> 5] |= 1u << (w & 31);
+                }
+        }
     }
     std::memcpy(blk.data() + L.class_of, class_of.data(), 256);
     return W;
@@ -346,7 +360,9 @@ int launch_filter(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *ou
     // packets per thread 234.
     threads = threads > 0 ? threads : 512;
     if (threads % 32 != 0 || threads > 512 || blocks_per_sm > 64) return FW_EINVAL;
-    int per_sm = blocks_per_sm > 0 ? blocks_per_sm : (pairs ? 4 : 3);
+    // (the wide kernel with row summaries holds two 512-thread blocks per SM)
+    const bool summ = !staged && rs->filter_words >= kFilterSummaryMin;
+    int per_sm = blocks_per_sm > 0 ? blocks_per_sm : (pairs ? 4 : summ ? 2 : 3);
     if (blocks_per_sm <= 0)
         while (per_sm > 1 && (size_t)per_sm * (smem + 1024) > 228 * 1024) --per_sm;
     if (staged && (size_t)per_sm * (smem + 1024) > 228 * 1024) return FW_EINVAL;
@@ -376,7 +392,12 @@ int launch_filter(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *ou
         }                                                                                                   \
     } while (0)
 #define FW_LAUNCH_G(KK, V)                                                                                  \
-    k_packet_split_filter_wide<KK, V><<<(unsigned)blocks, threads, 0, st>>>(p)
+    do {                                                                                                    \
+        if (rs->filter_words >= kFilterSummaryMin)                                                         \
+            k_packet_split_filter_wide<KK, V, true><<<(unsigned)blocks, threads, 0, st>>>(p);              \
+        else                                                                                                \
+            k_packet_split_filter_wide<KK, V, false><<<(unsigned)blocks, threads, 0, st>>>(p);             \
+    } while (0)
 #define FW_LAUNCH_FK(WW, V)                                                                                 \
     do {                                                                                                    \
         if (!staged) {                                                                                      \

@@ -13,7 +13,9 @@
 //    whole buckets, so that its bits alone decide it);
 //  - per record an exact-test record (two uint4) and a verdict word
 //    (original rule index | action << 31);
-//  - the protocol -> protocol class table.
+//  - the protocol -> protocol class table;
+//  - for rows wider than two words, a summary of each row (bit w set when
+//    word w is not zero).
 // A rule that contains the packet has its bit set in all three of the
 // packet's rows (each of its field sets holds the packet's value, so it meets
 // that value's bucket): the AND of the rows is a superset of the matching
@@ -128,11 +130,36 @@ __device__ __forceinline__ uint32_t filter_first(const unsigned char *base, cons
     return 0xFFFFFFFFu;
 }
 
+// First candidate of word w's AND m (record bits 32 w .. 32 w + 31 of class c's sub-list) that
+// passes its exact test: its verdict word, or ~0u.
+__device__ __forceinline__ uint32_t filter_word_first(const unsigned char *__restrict__ base, const FilterView &v,
+                                                      const uint32_t *ex, const uint4 *V, int first, int w,
+                                                      uint32_t m, uint32_t s, uint32_t d, uint32_t sp, uint32_t dp,
+                                                      uint32_t one) {
+    if (m == 0u) return 0xFFFFFFFFu;
+    const uint32_t e = __ldg(ex + w);
+    while (m != 0u) {
+        const int k = 32 * w + __ffs(m) - 1;
+        if (((e >> (k & 31)) & 1u) || filter_mismatch(s, d, sp, dp, __ldg(V + 2 * k), __ldg(V + 2 * k + 1), one) == 0u)
+            return __ldg(reinterpret_cast<const uint32_t *>(base + v.verdicts) + first + k);
+        m &= m - 1u;
+    }
+    return 0xFFFFFFFFu;
+}
+
 // Candidates of a packet of class c from word 0 on, given word 0's AND (m0), for
 // any row width (v.words 32-bit words): each word's candidates are tested in
 // order before the next word is read, so a packet reads its rows only up to its
-// first match. Returns the verdict word of the first match, or ~0u. The block
-// is read through the L1 cache (global memory).
+// first match. Rows of kFilterSummaryMin words or more carry summaries (bit w:
+// word w of the row is not zero); past word 0 a packet ANDs its three rows'
+// summaries and reads only the words set in it, which include every word where
+// the AND of the rows is not zero (a packet no rule matches often stops after
+// the summaries).
+// Returns the verdict word of the first match, or ~0u. The block is read
+// through the L1 cache (global memory).
+// SUMM: the rule set's rows carry summaries (v.words >= kFilterSummaryMin); without, every word
+// up to the first match is read.
+template <bool SUMM>
 __device__ __forceinline__ uint32_t filter_resolve(const unsigned char *__restrict__ base, const FilterView &v,
                                                    uint32_t c, uint32_t s, uint32_t d, uint32_t sp, uint32_t dp,
                                                    uint32_t m0, uint32_t one) {
@@ -144,20 +171,44 @@ __device__ __forceinline__ uint32_t filter_resolve(const unsigned char *__restri
     const uint32_t *ex = reinterpret_cast<const uint32_t *>(base + v.exact) + (size_t)c * W;
     const int first = (int)__ldg(reinterpret_cast<const uint32_t *>(base + v.classes) + 4 * c);
     const uint4 *V = reinterpret_cast<const uint4 *>(base + v.recs) + 2 * first;
-    uint32_t m = m0;
-    for (int w = 0; w < W; ++w) {
-        if (w > 0) m = __ldg(r0 + w) & __ldg(r1 + w) & __ldg(r2 + w);
-        if (m == 0u) continue;
-        const uint32_t e = __ldg(ex + w);
-        while (m != 0u) {
-            const int k = 32 * w + __ffs(m) - 1;
-            if (((e >> (k & 31)) & 1u) ||
-                filter_mismatch(s, d, sp, dp, __ldg(V + 2 * k), __ldg(V + 2 * k + 1), one) == 0u)
-                return __ldg(reinterpret_cast<const uint32_t *>(base + v.verdicts) + first + k);
-            m &= m - 1u;
+    if constexpr (!SUMM) {
+        uint32_t m = m0;
+        for (int w = 0; w < W; ++w) {
+            if (w > 0) m = __ldg(r0 + w) & __ldg(r1 + w) & __ldg(r2 + w);
+            if (m == 0u) continue;
+            const uint32_t e = __ldg(ex + w);
+            while (m != 0u) {
+                const int k = 32 * w + __ffs(m) - 1;
+                if (((e >> (k & 31)) & 1u) ||
+                    filter_mismatch(s, d, sp, dp, __ldg(V + 2 * k), __ldg(V + 2 * k + 1), one) == 0u)
+                    return __ldg(reinterpret_cast<const uint32_t *>(base + v.verdicts) + first + k);
+                m &= m - 1u;
+            }
         }
+        return 0xFFFFFFFFu;
+    } else {
+        uint32_t vw = filter_word_first(base, v, ex, V, first, 0, m0, s, d, sp, dp, one);
+        if (vw != 0xFFFFFFFFu) return vw;
+        const int S = filter_summary_words(W);
+        // the summaries follow the protocol class table (filter_layout)
+        const uint32_t *Q = reinterpret_cast<const uint32_t *>(base + ((v.class_of + 256 + 15) & ~15)) +
+                            (size_t)c * 768u * S;
+        const uint32_t *q0 = Q + (s >> 24) * S;
+        const uint32_t *q1 = Q + (256u + (d >> 24)) * S;
+        const uint32_t *q2 = Q + (512u + (((sp >> 12) << 4) | (dp >> 12))) * S;
+        for (int g = 0; g < S; ++g) {
+            uint32_t sm = __ldg(q0 + g) & __ldg(q1 + g) & __ldg(q2 + g);
+            if (g == 0) sm &= ~1u;  // word 0 is done
+            while (sm != 0u) {
+                const int w = 32 * g + __ffs(sm) - 1;
+                sm &= sm - 1u;
+                vw = filter_word_first(base, v, ex, V, first, w, __ldg(r0 + w) & __ldg(r1 + w) & __ldg(r2 + w), s, d,
+                                       sp, dp, one);
+                if (vw != 0xFFFFFFFFu) return vw;
+            }
+        }
+        return 0xFFFFFFFFu;
     }
-    return 0xFFFFFFFFu;
 }
 
 // Word 0 of the AND of a packet's three rows (class c), for any row width.
@@ -170,16 +221,19 @@ __device__ __forceinline__ uint32_t filter_word0(const unsigned char *__restrict
            __ldg(T + (cb + 512u + (((sp >> 12) << 4) | (dp >> 12))) * W);
 }
 
-// One packet, any row width, block read through L1.
-template <int KEY>
+// One packet, any row width, block read through L1 (SUMM: the rows carry summaries).
+template <int KEY, bool SUMM>
 __device__ __forceinline__ uint32_t filter_packet_wide(const unsigned char *__restrict__ base, const FilterView &v,
                                                        uint32_t s, uint32_t d, uint32_t sp, uint32_t dp, uint32_t pr,
                                                        uint32_t one) {
     const uint32_t c = filter_class<KEY>(base, v, s, d, pr);
-    return filter_resolve(base, v, c, s, d, sp, dp, filter_word0(base, v, c, s, d, sp, dp), one);
+    const uint32_t m0 = filter_word0(base, v, c, s, d, sp, dp);
+    return SUMM ? filter_resolve<true>(base, v, c, s, d, sp, dp, m0, one)
+                : filter_resolve<false>(base, v, c, s, d, sp, dp, m0, one);
 }
 
-// P packets of one lane, any row width, block read through L1: the classes and the
+// P packets of one lane, any row width, block read through L1 (every word up to the first match;
+// the row summaries are left to the packet-split kernel, whose registers allow them): the classes and the
 // first row words of all P packets are loaded before any candidate is tested, so
 // those loads are in flight together; then each packet's candidates are tested in
 // order. pr[] is overwritten with the classes; out[] gets the verdict words.
@@ -193,7 +247,7 @@ __device__ __forceinline__ void filter_packets_wide(const unsigned char *__restr
 #pragma unroll
     for (int k = 0; k < P; ++k) out[k] = filter_word0(base, v, pr[k], s[k], d[k], sp[k], dp[k]);
 #pragma unroll
-    for (int k = 0; k < P; ++k) out[k] = filter_resolve(base, v, pr[k], s[k], d[k], sp[k], dp[k], out[k], one);
+    for (int k = 0; k < P; ++k) out[k] = filter_resolve<false>(base, v, pr[k], s[k], d[k], sp[k], dp[k], out[k], one);
 }
 
 }  // namespace fwk

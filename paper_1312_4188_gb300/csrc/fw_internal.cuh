@@ -321,8 +321,16 @@ int sm_count(int dev);                  // SMs of device `dev` (cached)
 // for n_classes classes, `words` 32-bit words per bitmap row and `records`
 // stored sub-list records (every part starts on a 16-byte boundary).
 struct FilterLayout {
-    int64_t tables, classes, exact, recs, verdicts, class_of, total;
+    int64_t tables, classes, exact, recs, verdicts, class_of, summary, total;
 };
+// Summary words per bitmap row: rows of at least kFilterSummaryMin words carry, after the rest of
+// the block, a summary of ceil(W / 32) words per row whose bit w is set when word w of the row is
+// not zero. (On 95-word rows reading the summaries first took a classification from 3.36 to 2.31
+// ms; on 9-word rows, most of whose words are not zero, it cost a quarter more time.)
+constexpr int kFilterSummaryMin = 32;
+__host__ __device__ inline int filter_summary_words(int words) {
+    return words >= kFilterSummaryMin ? (words + 31) / 32 : 0;
+}
 constexpr int kFilterTables = 3;  // source top 8 bits, destination top 8 bits, (sport, dport) top 4 bits each
 constexpr int kFilterMaxRecords = FW_FILTER_MAX_RULES;  // longest class sub-list a filter covers
 __host__ __device__ inline FilterLayout filter_layout(int n_classes, int words, int64_t records) {
@@ -334,7 +342,8 @@ __host__ __device__ inline FilterLayout filter_layout(int n_classes, int words, 
     L.recs = up16(L.exact + (int64_t)n_classes * words * 4);               // [record] 2 x uint4
     L.verdicts = L.recs + records * 32;                                    // [record] uint32
     L.class_of = up16(L.verdicts + records * 4);                           // [256] uint8
-    L.total = up16(L.class_of + 256);
+    L.summary = up16(L.class_of + 256);  // W >= kFilterSummaryMin: [class][table][256][ceil(W / 32)] uint32
+    L.total = L.summary + (int64_t)kFilterTables * n_classes * 256 * filter_summary_words(words) * 4;
     return L;
 }
 // Builds rs->d_filter from the partition (lists[c] = original rule indices of

@@ -1,12 +1,13 @@
 """The bucket-filter packet split against the CPU oracle, element by element.
 
 Every call goes through the C ABI. The rule sets are built so that the filter
-applies (every class sub-list at most 64 rules) and so that they reach the
-cases its exactness rests on: address prefixes of every length 0..32 (lengths
-1..7 cover several address buckets, 8 and below are decided by the bucket
-alone), port ranges that cross or line up with the 4,096-port bucket edges,
-exact ports on those edges, rules that need no exact test (whole buckets on
-every field), one- and two-word bitmaps, the partition's address key, and
+applies and so that they reach the cases its exactness rests on: address
+prefixes of every length 0..32 (lengths 1..7 cover several address buckets, 8
+and below are decided by the bucket alone), port ranges that cross or line up
+with the 4,096-port bucket edges, exact ports on those edges, rules that need
+no exact test (whole buckets on every field), one- and two-word bitmaps, wider
+ones, ones of 32 words or more (read through row summaries), the partition's
+address key, and
 packets that no rule of their class matches (default deny). Edge packets sit
 just inside and just outside every rule's prefix and port range.
 """
@@ -126,7 +127,8 @@ def assert_same(got, want, what=""):
                            f"want ({wi[bad[0]]},{wa[bad[0]]})")
 
 
-CASES = [(12, 1), (30, 2), (45, 3), (70, 4), (100, 5), (160, 6), (400, 7), (900, 8)]
+# one- and two-word rows, wider rows, and rows of 32 words or more (with row summaries)
+CASES = [(12, 1), (30, 2), (45, 3), (70, 4), (100, 5), (160, 6), (400, 7), (900, 8), (2000, 9), (6000, 11)]
 
 
 @pytest.mark.parametrize("n_rules,seed", CASES)
@@ -138,7 +140,7 @@ def test_edges_against_oracle(torch_cuda, n_rules, seed, cfg):
     rs = fw.fw_ruleset_create(rules)
     if rs.filter()["words"] == 0:
         rs.destroy()
-        pytest.skip("this rule set has no filter (a class sub-list over 64 rules)")
+        pytest.skip("this rule set has no filter")
     hdr = mixed_packets(rules, 6000, 40 + seed)
     want = oracle.classify(rules, hdr, threads=THREADS)
     assert_same(classify(torch_cuda, rs, hdr, fw.make_config("packet_split", **cfg)), want, f"{n_rules} rules")
@@ -146,13 +148,14 @@ def test_edges_against_oracle(torch_cuda, n_rules, seed, cfg):
 
 
 def test_all_bitmap_widths_are_exercised(torch_cuda):
-    """One- and two-word rows (staged in shared memory) and wider rows (read from global memory)."""
+    """One- and two-word rows (staged in shared memory), wider rows (read from global memory) and
+    rows of 32 words or more (read through their summaries)."""
     widths = set()
     for n_rules, seed in CASES:
         rs = fw.fw_ruleset_create(edge_rules(n_rules, 900 + seed))
         widths.add(rs.filter()["words"])
         rs.destroy()
-    assert {1, 2} <= widths and max(widths) > 2, widths
+    assert {1, 2} <= widths and any(2 < w < 32 for w in widths) and max(widths) >= 32, widths
 
 
 @pytest.mark.parametrize("n_pkts", [1, 3, 4, 5, 63, 1023, 4097, 100_003])

@@ -166,6 +166,45 @@ def test_exact_records_contain_every_packet_of_their_buckets():
             assert np.all(o_idx == 0), f"exact record {j} (rule {rule}) misses packets of its buckets"
 
 
+def no_catch_all(n, seed):
+    r = W.gen_rules(n, seed)
+    return r[~((r["src_prefix"] == 0) & (r["dst_prefix"] == 0))]
+
+
+def test_wide_row_summaries_mark_nonzero_words():
+    """Rows of 32 words or more carry summaries after the protocol class table: bit w of a row's
+    summary is set exactly when word w of the row is not zero (so the AND of a packet's three
+    summaries holds every word where the AND of its rows is not zero); narrower blocks end there."""
+    seen_wide = False
+    cases = [rule_set(k, n, s) for k, n, s in RULE_SETS] + [no_catch_all(3000, 12), no_catch_all(4000, 12),
+                                                             no_catch_all(6000, 5)]
+    for rules in cases:
+        plan = fw.fw_filter_plan(rules)
+        w = plan["words"]
+        if w == 0:
+            continue
+        nc = fw.fw_partition_plan(reachable(rules))["classes"]
+        rows = decode(plan, nc)[0]  # [table][class][bucket][word]
+        recs_n = int(plan["class_off"][-1] + plan["class_len"][-1])
+        tab_bytes = nc * 3 * 256 * w * 4
+        ex_off = up16(tab_bytes) + nc * 16
+        pc_off = up16(up16(ex_off + nc * w * 4) + recs_n * 32 + recs_n * 4)
+        summ_off = up16(pc_off + 256)
+        blk = plan["block"]
+        if w < 32:
+            assert blk.size == summ_off
+            continue
+        seen_wide = True
+        sw = (w + 31) // 32
+        assert blk.size == summ_off + nc * 3 * 256 * sw * 4
+        summ = blk[summ_off:].view(np.uint32).reshape(nc, 3, 256, sw).transpose(1, 0, 2, 3)
+        for word in range(w):
+            marked = ((summ[..., word // 32] >> np.uint32(word % 32)) & np.uint32(1)).astype(bool)
+            assert np.array_equal(marked, rows[..., word] != 0), (w, word)
+        assert not np.any(summ[..., -1] >> np.uint32(w - 32 * (sw - 1))) if w % 32 else True
+    assert seen_wide
+
+
 def test_no_filter_cases_and_arguments():
     long_list = W.gen_rules(40_000, 12)
     long_list = long_list[~((long_list["src_prefix"] == 0) & (long_list["dst_prefix"] == 0))]
