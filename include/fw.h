@@ -530,23 +530,25 @@ int fw_server_replay(fw_server *sv, fw_request *reqs, int64_t n, int64_t timeout
 /*
  * Continuous batching with the scheduling on the device. The host writes each
  * request (a packet batch for one of the queue's rule sets) into a ring of
- * descriptors in pinned host memory and publishes it by its ticket; nothing
- * else happens on the host per request. One persistent kernel runs while
- * requests keep coming: its first warp reads new descriptors from the ring,
- * splits each request into work items of chunk_packets packets and releases
- * them into a device item ring; every other warp claims item tickets from a
+ * descriptors in pinned host memory and publishes it by storing the next
+ * ticket into a tail word after the ring; nothing else happens on the host per
+ * request. One persistent kernel runs while requests keep coming: four warps
+ * of its first block read new descriptors from the ring (up to 128 a pass),
+ * split each request into work items (chunk_packets packets, larger when many
+ * requests wait) and write them into a device item ring; every other warp
+ * claims item tickets from a
  * global counter, classifies its item through the request's bucket filter
  * (the routine of fw_classify's default packet split, Sec. IV.A) and, when it
  * finishes a request's last item, stores the ticket into the request's
  * completion word in pinned host memory, which fw_dqueue_wait polls. Requests
- * that arrive while others run are taken up as soon as the reading warp sees
+ * that arrive while others run are taken up as soon as the reading warps see
  * them, and items of different requests and rule sets run side by side, so
  * there are no groups and no launch per request. The paper's prototype
  * collects packets, classifies them in one launch and hands the verdicts
  * back (Sec. IV, Fig. 1) and names asynchronous launches as the next step
  * (Sec. V); here the launch outlives the requests.
  *
- * Every device-side wait is bounded by %globaltimer: the reading warp gives up
+ * Every device-side wait is bounded by %globaltimer: the reading warps give up
  * after idle_us without a new request (the kernel then exits, and the next
  * submit launches it again, or, when the submit and the exit cross, the
  * first wait that finds the request pending for 50 us; fw_dqueue_stats counts

@@ -6,32 +6,36 @@
 // asynchronous launches as the way to cut the per-batch delay (Sec. V). Here a
 // launch serves any number of requests:
 //
-//  host  -- descriptor ring (pinned host memory, one entry per ticket, the
-//           ticket stored last with release semantics) -->
-//  feeder warp (warp 0 of the first block of the launch to start) -- watches the next
-//           ring entry (acquire, system scope), then reads up to 32 new ones,
-//           copies each into a device request table, splits it into items of
-//           chunk_packets packets and, after one fence, writes the items into
-//           a device item ring (one 64-bit word each: the lap of its item
-//           ticket, the request's slot and the chunk) -->
-//  worker warps -- claim item tickets from a global counter, wait (bounded)
-//           for the item word of their ticket's lap, classify its packets through the request's
-//           bucket filter (batch_filter_run, the routine of the batched
-//           kernel), and count the request's items down; the warp that
+//  host  -- a ring of request entries in pinned host memory (one entry per
+//           ticket) and, after the ring, a tail word: the host writes new
+//           entries, then stores the next ticket into the tail (release) -->
+//  feeder (warps 0..3 of the first block of the launch to start) -- warp 0
+//           polls the tail; once it is past the feeder's head, the four warps
+//           copy up to 128 new entries into a device request table (one entry
+//           a thread), split each request into items (64 packets while the
+//           ring holds few requests, 256 or 1,024 when more wait), and, after
+//           one fence, write the items into a device item ring (one 64-bit
+//           word each: the lap of its item ticket, the request's slot, the
+//           chunk) -->
+//  worker warps -- claim item tickets from a global counter, poll the item
+//           word of their ticket's lap (relaxed loads, backing off), classify
+//           its packets through the request's bucket filter (batch_filter_run,
+//           the routine of the batched kernel, headers read from L2), and
+//           count the request's items down with a release add; the warp that
 //           finishes the last one stores the ticket into the request's
 //           completion word in pinned host memory (release, system scope).
 //
 // Every wait is bounded by %globaltimer. The feeder gives up after idle_ns
-// without a new entry and, once the launch is life_ns old, stops taking
-// entries; before it leaves for lack of work it announces "exiting" to the
-// host, then looks at the ring once more and carries on if an entry arrived
+// without a new request and, once the launch is life_ns old, stops taking
+// requests; before it leaves for lack of work it announces "exiting" to the
+// host, then looks at the tail once more and carries on if a request arrived
 // meanwhile, so that a request submitted around that moment is in most cases
 // either taken by this launch or seen by the host at its submit, which then
-// launches the kernel again. (The host does not fence between its entry and
-// its look, which would cost a round trip over the host link per request; the
-// rare request that both miss waits for the backstop:) the host also relaunches
-// whenever a request has been pending for 50 us and the last launch has
-// finished. Workers leave when the feeder has quit and their claimed ticket
+// launches the kernel again. (The host does not fence between its tail store
+// and its look, which would cost a round trip over the host link per request;
+// the rare request that both miss waits for the backstop:) the host also
+// relaunches whenever a request has been pending for 50 us and the last launch
+// has finished. Workers leave when the feeder has quit and their claimed ticket
 // was not released; item and request state lives in device memory across
 // launches, and a small kernel before each launch resets the claim counter to
 // the released item count.
