@@ -179,9 +179,9 @@ typedef struct fw_headers {
  *                     block_threads (<= 512, default 512), blocks_per_sm
  *                     (default 3, or 4 with two packets per thread; fewer
  *                     when the staged filter's shared memory does not fit) and
- *                     lane_packets (packets a thread takes per step: 4 by
- *                     default, 2 with filter = 1 and one- or two-word rows)
- *                     shape its launch.
+ *                     lane_packets (packets a thread takes per step with one-
+ *                     or two-word rows: 2 or 4; 0 = default, 2 for batches
+ *                     under 2^20 packets, else 4) shape its launch.
  */
 typedef struct fw_config {
     int32_t mode;

@@ -352,12 +352,15 @@ int launch_filter(const fw_ruleset *rs, const HdrPtrs &h, int64_t n, int32_t *ou
     p.status = rs->d_status;
     const bool staged = filter_staged(rs);
     if (lane_packets != 0 && lane_packets != 2 && lane_packets != 4) return FW_EINVAL;
-    const bool pairs = staged && lane_packets == 2;  // two packets per thread, four blocks per SM
+    // two packets per thread, four blocks per SM: on request, and by default for batches under 2^20
+    // packets, which four packets per thread spread over too few blocks (1,000 rules x 100,000
+    // packets, L2 flushed: 8.19 against 8.93-9.95 us per launch); larger batches take four (the
+    // 10K x 16M step: 241 against 234 Gpackets/s)
+    const bool pairs = staged && (lane_packets == 2 || (lane_packets == 0 && n < (int64_t(1) << 20)));
     const size_t smem = staged ? (size_t)rs->filter_bytes : 0;
     // Default shape: three 512-thread blocks per SM (1,536 threads, 40 registers each), fewer
     // when their shared memory does not fit; two packets per thread: four blocks. On the 10K x 16M
-    // step, 256 x 6, 384 x 4 and 512 x 3 measure the same (241 Gpackets/s back to back), two
-    // packets per thread 234.
+    // step, 256 x 6, 384 x 4 and 512 x 3 measure the same (241 Gpackets/s back to back).
     threads = threads > 0 ? threads : 512;
     if (threads % 32 != 0 || threads > 512 || blocks_per_sm > 64) return FW_EINVAL;
     // (the wide kernel with row summaries holds two 512-thread blocks per SM)
