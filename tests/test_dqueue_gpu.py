@@ -144,6 +144,34 @@ def test_poisson_replay(env, load_gpps):
     q.destroy()
 
 
+def test_replay_with_refused_requests(env):
+    """Requests the queue refuses (a buffer outside the registered ranges, a request over the size
+    limit) get their own status; every other request of the replay completes correctly."""
+    torch, rules, sets, pools, dpools, reqs, offs, total, ref_i, ref_a = env
+    q, out_i, out_a = _queue(env, max_request_packets=32768)
+    loose = torch.empty(70_000, dtype=torch.int32, device="cuda")  # not registered
+    specs, bad = [], {}
+    for k in range(60):
+        s, h, oi, oa = _args(env, k, out_i, out_a)
+        if h["src"].shape[0] > 32768:  # checked before the buffers
+            bad[k] = fw.FW_ERANGE
+        elif k % 15 == 3:
+            oi = loose[:oi.shape[0]]
+            bad[k] = fw.FW_EINVAL
+        specs.append((s, h, oi, oa, 2.0 * k))
+    rc, status, lat = q.replay(specs, timeout_us=LIMIT)
+    assert rc != fw.FW_OK and fw.FW_EINVAL in bad.values()
+    for k in range(60):
+        assert status[k] == bad.get(k, fw.FW_OK), (k, status[k])
+    torch.cuda.synchronize()
+    for k in range(60):
+        if k in bad:
+            continue
+        o, n = int(offs[k]), reqs[k][2]
+        assert torch.equal(out_i[o:o + n], ref_i[o:o + n]) and torch.equal(out_a[o:o + n], ref_a[o:o + n]), k
+    q.destroy()
+
+
 def test_idle_exit_and_relaunch(env):
     """The kernel's wait for new requests runs out (idle limit): it exits, and the next submit relaunches it."""
     torch, rules, sets, pools, dpools, reqs, offs, total, ref_i, ref_a = env
