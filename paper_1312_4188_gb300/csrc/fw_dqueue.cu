@@ -39,6 +39,8 @@
 // was not released; item and request state lives in device memory across
 // launches, and a small kernel before each launch resets the claim counter to
 // the released item count.
+#include <cuda.h>  // driver types only: the one driver call used is resolved at run time
+
 #include <atomic>
 #include <chrono>
 #include <cstring>
@@ -790,6 +792,37 @@ extern "C" void fw_dqueue_destroy(fw_dqueue *q) {
     cudaGetLastError();
 }
 
+namespace {
+
+// The address range of the allocation holding device address a, as the driver records it
+// (cuPointerGetAttribute: RANGE_START_ADDR, RANGE_SIZE), in [*lo, *hi). False when the driver
+// gives no range for it.
+bool alloc_range(uintptr_t a, uintptr_t *lo, uintptr_t *hi) {
+    using GetAttr = CUresult (*)(void *, CUpointer_attribute, CUdeviceptr);
+    static const GetAttr get = []() -> GetAttr {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult r = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &f, 12000, cudaEnableDefault, &r) !=
+                cudaSuccess ||
+            r != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return reinterpret_cast<GetAttr>(f);
+    }();
+    if (get == nullptr) return false;
+    CUdeviceptr start = 0;
+    size_t size = 0;
+    if (get(&start, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, (CUdeviceptr)a) != CUDA_SUCCESS ||
+        get(&size, CU_POINTER_ATTRIBUTE_RANGE_SIZE, (CUdeviceptr)a) != CUDA_SUCCESS || size == 0)
+        return false;
+    *lo = (uintptr_t)start;
+    *hi = (uintptr_t)start + size;
+    return true;
+}
+
+}  // namespace
+
 extern "C" int fw_dqueue_register_buffer(fw_dqueue *q, const void *p, size_t bytes) {
     if (q == nullptr || p == nullptr || bytes == 0) return set_status(FW_EINVAL);
     const void *ends[2] = {p, static_cast<const uint8_t *>(p) + bytes - 1};
@@ -809,8 +842,13 @@ extern "C" int fw_dqueue_register_buffer(fw_dqueue *q, const void *p, size_t byt
         delta[k] = reinterpret_cast<intptr_t>(d) - reinterpret_cast<intptr_t>(ends[k]);
     }
     if (delta[0] != delta[1]) return set_status(FW_EINVAL);
-    std::lock_guard<std::mutex> lk(q->reg_mu);
     const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    // both ends in one allocation: two allocations with the same mapping (device memory, or
+    // pinned host memory under unified addressing) can have unmapped addresses between them
+    uintptr_t lo = 0, hi = 0;
+    const uintptr_t d0 = (uintptr_t)((intptr_t)a + delta[0]);
+    if (alloc_range(d0, &lo, &hi) && (d0 < lo || bytes > hi - d0)) return set_status(FW_EINVAL);
+    std::lock_guard<std::mutex> lk(q->reg_mu);
     q->ranges.push_back(DqRange{a, a + bytes, delta[0]});
     return set_status(FW_OK);
 }

@@ -213,6 +213,36 @@ def test_time_limit_relaunch(env):
     q.destroy()
 
 
+def test_register_refuses_a_range_across_allocations(env):
+    """Device memory has one mapping everywhere, so a range whose two ends lie in two allocations
+    passes a check of its ends although the addresses between them need not be mapped: the
+    driver's record of the allocation decides. A range inside one allocation is taken."""
+    import ctypes
+    import os
+    torch = env[0]
+    if "expandable" in os.environ.get("PYTORCH_CUDA_ALLOC_CONF", ""):
+        pytest.skip("the allocator maps its segments into reserved address ranges")
+    q = fw.DeviceQueue(env[2])
+    torch.cuda.empty_cache()
+    size = 96 << 20
+    a, b = (torch.empty(size, dtype=torch.uint8, device="cuda") for _ in range(2))
+    dev = torch.cuda.current_device()
+    segs = [(s["address"], s["total_size"]) for s in torch.cuda.memory_snapshot() if s["device"] == dev]
+
+    def seg_of(t):
+        return next((lo, n) for lo, n in segs if lo <= t.data_ptr() < lo + n)
+
+    (lo1, n1), (lo2, n2) = sorted([seg_of(a), seg_of(b)])
+    assert lo1 + n1 <= lo2  # two allocations
+    reg = fw.lib().fw_dqueue_register_buffer
+    assert reg(q.handle, ctypes.c_void_p(lo1), lo2 - lo1 + 1) == fw.FW_EINVAL
+    assert reg(q.handle, ctypes.c_void_p(lo1 + n1 - 16), 32) == fw.FW_EINVAL
+    assert reg(q.handle, ctypes.c_void_p(lo1), n1) == fw.FW_OK
+    assert reg(q.handle, ctypes.c_void_p(a.data_ptr()), size) == fw.FW_OK
+    q.destroy()
+    del a, b
+
+
 def test_argument_errors(env):
     torch, rules, sets, pools, dpools, reqs, offs, total, ref_i, ref_a = env
     q, out_i, out_a = _queue(env, ring=64, max_request_packets=4096)
